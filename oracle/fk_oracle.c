@@ -1,0 +1,415 @@
+/*
+ * FP64 CPU oracle for the forward-kinematics (FK) kernel and the Fastron
+ * proxy collision checker (Das and Yip, "Forward Kinematics Kernel for
+ * Improved Proxy Collision Checking", arXiv 1910.06451).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * statement of what the CUDA library computes.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * Everything is FP64.  Inputs are the canonical FP32 values widened to FP64.
+ * Compiled with -ffp-contract=off so that x86 and Arm builds round alike.
+ *
+ * Layouts (all row-major, caller-owned):
+ *   dh      D rows of (a, alpha, d, theta0, type), type 0 revolute, 1 prismatic
+ *   base    4x4 world-from-frame-0 transform
+ *   q       n rows of D joint values
+ *   cp      n x M x 3 control-point positions
+ *   boxes   nb rows of (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z)
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- FK ---- */
+
+/* C = A * B for row-major 4x4 matrices. */
+static void mat4_mul(const double *A, const double *B, double *C)
+{
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k)
+                s += A[4 * r + k] * B[4 * k + c];
+            C[4 * r + c] = s;
+        }
+}
+
+/* The standard DH link transform of Eq. 1 for one joint with joint value q.
+ * A revolute joint adds q to theta, a prismatic joint adds q to d. */
+static void dh_link(const double *row, double q, double *A)
+{
+    double a = row[0], alpha = row[1], d = row[2], theta = row[3];
+    if ((int)row[4] == 0)
+        theta += q;
+    else
+        d += q;
+    double ct = cos(theta), st = sin(theta), ca = cos(alpha), sa = sin(alpha);
+    double M[16] = {
+        ct, -ca * st,  sa * st, a * ct,
+        st,  ca * ct, -sa * ct, a * st,
+        0.0,      sa,       ca,      d,
+        0.0,     0.0,      0.0,    1.0,
+    };
+    memcpy(A, M, sizeof M);
+}
+
+/* Frame poses of one configuration (Sec. II-A): T[0] = wA0 (the base) and
+ * T[i] = wA0 0A1 ... (i-1)Ai for i = 1..D.  T holds (D+1) 4x4 matrices. */
+void orc_frames(int D, const double *dh, const double *base, const double *q, double *T)
+{
+    memcpy(T, base, 16 * sizeof(double));
+    for (int i = 1; i <= D; ++i) {
+        double A[16];
+        dh_link(dh + 5 * (i - 1), q[i - 1], A);
+        mat4_mul(T + 16 * (i - 1), A, T + 16 * i);
+    }
+}
+
+/* Control-point positions, Eq. 2: FK_m(x) = pos(wA_{j_m} T_m) with T_m the
+ * translation by cp_off[m].  Returns 0, or -1 if a joint index is invalid. */
+int orc_fk_points(int D, const double *dh, const double *base, int M, const int32_t *cp_joint,
+                  const double *cp_off, int64_t n, const double *q, double *cp)
+{
+    for (int m = 0; m < M; ++m)
+        if (cp_joint[m] < 0 || cp_joint[m] > D)
+            return -1;
+    double *T = (double *)malloc(sizeof(double) * 16 * (size_t)(D + 1));
+    if (!T)
+        return -2;
+    for (int64_t k = 0; k < n; ++k) {
+        orc_frames(D, dh, base, q + k * D, T);
+        for (int m = 0; m < M; ++m) {
+            const double *W = T + 16 * cp_joint[m];
+            const double *t = cp_off + 3 * m;
+            for (int c = 0; c < 3; ++c)
+                cp[(k * M + m) * 3 + c] = W[4 * c + 0] * t[0] + W[4 * c + 1] * t[1] + W[4 * c + 2] * t[2] + W[4 * c + 3];
+        }
+    }
+    free(T);
+    return 0;
+}
+
+/* ------------------------------------------------------------ kernels --- */
+
+/* Second-order rational quadratic kernel, Eq. 3, between two dim-vectors:
+ * (1 + gamma/2 * |x - x'|^2)^-2, evaluated as 1 / (t * t). */
+double orc_k_rq(int dim, const double *x, const double *xp, double gamma)
+{
+    double d2 = 0.0;
+    for (int c = 0; c < dim; ++c) {
+        double dc = x[c] - xp[c];
+        d2 += dc * dc;
+    }
+    double t = 1.0 + 0.5 * gamma * d2;
+    return 1.0 / (t * t);
+}
+
+/* FK kernel, Eq. 4: the mean over the M corresponding control points of the
+ * RQ kernel, summed in ascending m.  cpa, cpb: M x 3 each. */
+double orc_k_fk(int M, const double *cpa, const double *cpb, double gamma)
+{
+    double s = 0.0;
+    for (int m = 0; m < M; ++m)
+        s += orc_k_rq(3, cpa + 3 * m, cpb + 3 * m, gamma);
+    return s / M;
+}
+
+/* Kernel matrix K[i][j] = K_FK(a_i, b_j) (Sec. II-B), na x nb. */
+void orc_gram(int M, double gamma, int64_t na, const double *cpa, int64_t nb, const double *cpb, double *K)
+{
+    for (int64_t i = 0; i < na; ++i)
+        for (int64_t j = 0; j < nb; ++j)
+            K[i * nb + j] = orc_k_fk(M, cpa + i * M * 3, cpb + j * M * 3, gamma);
+}
+
+/* ------------------------------------------------------------- score ---- */
+
+typedef struct {
+    int M;
+    double gamma;
+    int64_t ns;
+    const double *cps, *alpha;
+    const double *cpq;
+    double *f;
+    int64_t lo, hi;
+} score_job;
+
+static void *score_range(void *arg)
+{
+    score_job *j = (score_job *)arg;
+    for (int64_t k = j->lo; k < j->hi; ++k) {
+        double f = 0.0;
+        for (int64_t s = 0; s < j->ns; ++s)
+            f += j->alpha[s] * orc_k_fk(j->M, j->cps + s * j->M * 3, j->cpq + k * j->M * 3, j->gamma);
+        j->f[k] = f;
+    }
+    return NULL;
+}
+
+/* Fastron model value (Sec. III-B): f(x) = sum_s alpha_s K_FK(S_s, x), the
+ * support points taken in ascending order.  Queries are split into nthreads
+ * contiguous blocks; each query is summed by one thread, so the result does
+ * not depend on nthreads. */
+int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *alpha, int64_t nq,
+              const double *cpq, double *f, int nthreads)
+{
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 256)
+        nthreads = 256;
+    pthread_t th[256];
+    score_job jobs[256];
+    int64_t per = (nq + nthreads - 1) / nthreads;
+    int started = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        score_job j = {M, gamma, ns, cps, alpha, cpq, f, t * per, (t + 1) * per};
+        if (j.hi > nq)
+            j.hi = nq;
+        if (j.lo >= j.hi)
+            break;
+        jobs[t] = j;
+        if (t == 0)
+            continue;
+        if (pthread_create(&th[t], NULL, score_range, &jobs[t]) != 0) {
+            for (int u = 1; u <= started; ++u)
+                pthread_join(th[u], NULL);
+            return -1;
+        }
+        started = t;
+    }
+    if (nq > 0)
+        score_range(&jobs[0]);
+    for (int t = 1; t <= started; ++t)
+        pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* ----------------------------------------------------------- Fastron ---- */
+
+/* Column i of the kernel matrix over the training set (computeKernelMatrixColumn). */
+static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col)
+{
+    for (int64_t j = 0; j < N; ++j)
+        col[j] = orc_k_fk(M, cpX + j * M * 3, cpX + i * M * 3, gamma);
+}
+
+/*
+ * Fastron model update, Algorithm 1 (Sec. III-B), taken step by step:
+ *
+ *   for iter = 1..iter_max:
+ *     if min_j y_j F_j <= 0:                               (misclassified point)
+ *       i = argmin_j y_j F_j
+ *       if count(alpha != 0) < s_max or alpha_i != 0:      (add / adjust, Eqs. 6-8)
+ *         delta = b_i y_i - F_i,  b_i = beta^(0.5 (y_i + 1))
+ *         alpha_i += delta;  F += delta K e_i;  continue
+ *     if max_{alpha_j != 0} y_j (F_j - alpha_j) > 0:       (redundant support point)
+ *       i = that argmax;  F -= alpha_i K e_i;  alpha_i = 0;  continue
+ *     break
+ *
+ * Readings where the paper is silent: argmin/argmax ties go to the lowest
+ * index; "continue" after an add means a removal is tried only when no add
+ * was made in that pass; each pass is one iteration.
+ *
+ * alpha and F are in/out (zeros for a cold start, a previous model's values
+ * for a warm start, loadPreviousModel).  stats = {iterations, adds, removals,
+ * converged (1 if the loop ended by break), support size}.  If trace_kind is
+ * not NULL, pass k records kind (1 add, 2 removal), index and delta (the
+ * change of alpha_i) in trace_kind/trace_idx/trace_delta[k].
+ */
+int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                      int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                      int8_t *trace_kind, int64_t *trace_idx, double *trace_delta)
+{
+    double *col = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    if (!col)
+        return -2;
+    int64_t nnz = 0, adds = 0, removes = 0, iters = 0;
+    int converged = 0;
+    for (int64_t j = 0; j < N; ++j)
+        nnz += alpha[j] != 0.0;
+
+    for (int64_t iter = 1; iter <= iter_max; ++iter) {
+        /* check for misclassifications */
+        int64_t i = -1;
+        double mmin = INFINITY;
+        for (int64_t j = 0; j < N; ++j) {
+            double m = y[j] * F[j];
+            if (m < mmin) {
+                mmin = m;
+                i = j;
+            }
+        }
+        if (i >= 0 && mmin <= 0.0) {
+            kernel_column(M, gamma, N, cpX, i, col);
+            if (nnz < s_max || alpha[i] != 0.0) {
+                double b = y[i] > 0 ? beta : 1.0;
+                double delta = b * y[i] - F[i];
+                int was_zero = alpha[i] == 0.0;
+                alpha[i] += delta;
+                for (int64_t j = 0; j < N; ++j)
+                    F[j] += delta * col[j];
+                nnz += (alpha[i] != 0.0) - !was_zero;
+                ++adds;
+                ++iters;
+                if (trace_kind) {
+                    trace_kind[iter - 1] = 1;
+                    trace_idx[iter - 1] = i;
+                    trace_delta[iter - 1] = delta;
+                }
+                continue;
+            }
+        }
+        /* remove redundant support points */
+        int64_t r = -1;
+        double mmax = -INFINITY;
+        for (int64_t j = 0; j < N; ++j) {
+            if (alpha[j] == 0.0)
+                continue;
+            double m = y[j] * (F[j] - alpha[j]);
+            if (m > mmax) {
+                mmax = m;
+                r = j;
+            }
+        }
+        if (r >= 0 && mmax > 0.0) {
+            kernel_column(M, gamma, N, cpX, r, col);
+            double a = alpha[r];
+            for (int64_t j = 0; j < N; ++j)
+                F[j] -= a * col[j];
+            alpha[r] = 0.0;
+            --nnz;
+            ++removes;
+            ++iters;
+            if (trace_kind) {
+                trace_kind[iter - 1] = 2;
+                trace_idx[iter - 1] = r;
+                trace_delta[iter - 1] = -a;
+            }
+            continue;
+        }
+        converged = 1;
+        break;
+    }
+    free(col);
+    stats[0] = iters;
+    stats[1] = adds;
+    stats[2] = removes;
+    stats[3] = converged;
+    stats[4] = nnz;
+    return 0;
+}
+
+/* --------------------------------------------------- geometric checker -- */
+
+/* Squared distance from point p to the box [lo, hi]. */
+static double point_box_dist2(const double *p, const double *lo, const double *hi)
+{
+    double s = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double e = 0.0;
+        if (p[c] < lo[c])
+            e = lo[c] - p[c];
+        else if (p[c] > hi[c])
+            e = p[c] - hi[c];
+        s += e * e;
+    }
+    return s;
+}
+
+/* Squared distance from the segment p0 -> p1 to the box [lo, hi].
+ * g(t) = dist2(p0 + t (p1 - p0), box) is convex and quadratic between the
+ * parameters where a coordinate crosses a slab face.  On each piece the
+ * quadratic's minimiser is found in closed form, clamped to the piece, and g
+ * is evaluated there; the smallest value over the pieces is the distance. */
+double orc_seg_box_dist2(const double *p0, const double *p1, const double *lo, const double *hi)
+{
+    double dp[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+    double ts[8];
+    int nt = 0;
+    ts[nt++] = 0.0;
+    ts[nt++] = 1.0;
+    for (int c = 0; c < 3; ++c) {
+        if (dp[c] == 0.0)
+            continue;
+        double bnd[2] = {lo[c], hi[c]};
+        for (int b = 0; b < 2; ++b) {
+            double t = (bnd[b] - p0[c]) / dp[c];
+            if (t > 0.0 && t < 1.0)
+                ts[nt++] = t;
+        }
+    }
+    for (int a = 1; a < nt; ++a)            /* insertion sort */
+        for (int b = a; b > 0 && ts[b - 1] > ts[b]; --b) {
+            double tmp = ts[b];
+            ts[b] = ts[b - 1];
+            ts[b - 1] = tmp;
+        }
+    double best = INFINITY;
+    for (int k = 0; k + 1 < nt; ++k) {
+        double ta = ts[k], tb = ts[k + 1];
+        double tm = 0.5 * (ta + tb);
+        double sab = 0.0, sbb = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double x = p0[c] + tm * dp[c];
+            double bound;
+            if (x < lo[c])
+                bound = lo[c];
+            else if (x > hi[c])
+                bound = hi[c];
+            else
+                continue;
+            double A = p0[c] - bound, B = dp[c];
+            sab += A * B;
+            sbb += B * B;
+        }
+        double t = ta;
+        if (sbb > 0.0) {
+            t = -sab / sbb;
+            if (t < ta)
+                t = ta;
+            if (t > tb)
+                t = tb;
+        }
+        double p[3] = {p0[0] + t * dp[0], p0[1] + t * dp[1], p0[2] + t * dp[2]};
+        double g = point_box_dist2(p, lo, hi);
+        if (g < best)
+            best = g;
+    }
+    double ge0 = point_box_dist2(p0, lo, hi), ge1 = point_box_dist2(p1, lo, hi);
+    if (ge0 < best)
+        best = ge0;
+    if (ge1 < best)
+        best = ge1;
+    return best;
+}
+
+/* Ground-truth labels: link i (i = 1..D) is the segment between the origins of
+ * frames i-1 and i, swept by a sphere of the given radius.  A configuration
+ * collides (+1) if any link comes within radius of any box (touching counts),
+ * else it is free (-1).  Labels follow Sec. II-B: +1 = C_obs, -1 = C_free. */
+int orc_check(int D, const double *dh, const double *base, int64_t nb, const double *boxes, double radius,
+              int64_t n, const double *q, int8_t *y)
+{
+    double *T = (double *)malloc(sizeof(double) * 16 * (size_t)(D + 1));
+    if (!T)
+        return -2;
+    double r2 = radius * radius;
+    for (int64_t k = 0; k < n; ++k) {
+        orc_frames(D, dh, base, q + k * D, T);
+        int hit = 0;
+        for (int i = 1; i <= D && !hit; ++i) {
+            double o0[3] = {T[16 * (i - 1) + 3], T[16 * (i - 1) + 7], T[16 * (i - 1) + 11]};
+            double o1[3] = {T[16 * i + 3], T[16 * i + 7], T[16 * i + 11]};
+            for (int64_t b = 0; b < nb && !hit; ++b)
+                if (orc_seg_box_dist2(o0, o1, boxes + 6 * b, boxes + 6 * b + 3) <= r2)
+                    hit = 1;
+        }
+        y[k] = hit ? 1 : -1;
+    }
+    free(T);
+    return 0;
+}

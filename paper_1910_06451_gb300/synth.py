@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs: robot arms, box obstacles and joint configurations.
+
+This module is the only code shared by the CUDA path and the FP64 oracle.  It
+draws numbers and nothing else: it holds no forward kinematics, no kernel, no
+Fastron arithmetic and no collision test.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used as a counter-based
+generator: draw ``k`` of stream ``seed`` is the SplitMix64 finaliser applied to
+``seed + (k + 1) * 0x9E3779B97F4A7C15``.  Uniform doubles take the top 53 bits.
+Every value is drawn in FP64 and rounded to FP32 once; the FP32 value (widened
+back to FP64 where FP64 is needed) is the canonical input both sides consume.
+
+The shapes follow the workloads of the paper's evaluation (Sec. IV): serial
+revolute arms described by standard Denavit-Hartenberg parameters (Eq. 1) with
+control points at the joint-frame origins (Sec. III-A), random axis-aligned box
+obstacles, and configurations drawn uniformly inside the joint limits.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 outputs for the given draw indices of stream ``seed``."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _MASK) + (c + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+class Stream:
+    """Sequential reader over one SplitMix64 stream."""
+
+    def __init__(self, seed: int):
+        self.seed = int(seed) & _MASK
+        self.pos = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        out = splitmix64(self.seed, np.arange(self.pos, self.pos + n, dtype=np.uint64))
+        self.pos += n
+        return out
+
+    def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        u = (self.u64(n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        return lo + (hi - lo) * u
+
+
+def _f32(x) -> np.ndarray:
+    """Round once to FP32 and widen back: the canonical value of a draw."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+REVOLUTE = 0
+PRISMATIC = 1
+
+
+@dataclasses.dataclass
+class Arm:
+    """A serial chain in standard DH form plus its control points.
+
+    ``dh`` rows are ``(a, alpha, d, theta0, type)`` (Eq. 1; ``theta0`` is the
+    joint-angle offset, ``type`` 0 = revolute, 1 = prismatic).  ``base`` is the
+    world-from-frame-0 transform.  Control point ``m`` sits at offset
+    ``cp_off[m]`` in frame ``cp_joint[m]`` (Eq. 2, ``T_m`` a pure translation).
+    """
+
+    dh: np.ndarray
+    base: np.ndarray
+    cp_joint: np.ndarray
+    cp_off: np.ndarray
+    qlim: float
+
+    @property
+    def D(self) -> int:
+        return int(self.dh.shape[0])
+
+    @property
+    def M(self) -> int:
+        return int(self.cp_joint.shape[0])
+
+
+@dataclasses.dataclass
+class Scene:
+    arm: Arm
+    boxes: np.ndarray   # (nb, 6): lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
+    radius: float       # radius of the sphere swept along each link
+
+
+def frame_origin_cps(D: int) -> tuple[np.ndarray, np.ndarray]:
+    """Control points at the origins of frames 0..D (offset zero)."""
+    return np.arange(D + 1, dtype=np.int32), np.zeros((D + 1, 3))
+
+
+def random_arm(seed: int, D: int, a_range, d_range, qlim: float) -> Arm:
+    """Random revolute arm: twist +-pi/2 with a random sign, theta0 = 0, base = I."""
+    st = Stream(seed)
+    a = _f32(st.uniform(D, *a_range))
+    d = _f32(st.uniform(D, *d_range)) if d_range is not None else np.zeros(D)
+    sign = np.where(st.uniform(D) < 0.5, -1.0, 1.0)
+    alpha = _f32(sign * (math.pi / 2))
+    dh = np.zeros((D, 5))
+    dh[:, 0], dh[:, 1], dh[:, 2] = a, alpha, d
+    cj, co = frame_origin_cps(D)
+    return Arm(dh=dh, base=np.eye(4), cp_joint=cj, cp_off=co, qlim=float(_f32(qlim)))
+
+
+def arm_3dof(seed: int) -> Arm:
+    """3-DOF spatial arm: a ~ U[0.2, 0.5] m, d = 0, limits +-pi, 4 control points."""
+    return random_arm(seed, 3, (0.2, 0.5), None, math.pi)
+
+
+def arm_7dof(seed: int) -> Arm:
+    """7-DOF arm: a ~ U[0.1, 0.4] m, d ~ U[0, 0.1] m, limits +-170 deg, 8 control points."""
+    return random_arm(seed, 7, (0.1, 0.4), (0.0, 0.1), math.radians(170.0))
+
+
+def random_boxes(seed: int, nb: int, centre=(-0.8, 0.8), half=(0.05, 0.15),
+                 keep_clear: float = 0.1) -> np.ndarray:
+    """Axis-aligned boxes; a draw whose box comes within ``keep_clear`` of the
+    base origin is rejected and redrawn (otherwise every configuration collides)."""
+    st = Stream(seed ^ 0x5DEECE66D)
+    out = []
+    while len(out) < nb:
+        c = st.uniform(3, *centre)
+        h = st.uniform(3, *half)
+        lo, hi = _f32(c - h), _f32(c + h)
+        gap = np.maximum(np.maximum(lo, -hi), 0.0)      # per-axis gap from the origin
+        if math.sqrt(float(np.sum(gap * gap))) <= keep_clear:
+            continue
+        out.append(np.concatenate([lo, hi]))
+    return np.array(out)
+
+
+def uniform_configs(seed: int, n: int, D: int, qlim: float) -> np.ndarray:
+    """n configurations uniform in [-qlim, qlim]^D, canonical FP32, shape (n, D)."""
+    st = Stream(seed)
+    return st.uniform(n * D, -qlim, qlim).astype(np.float32).reshape(n, D)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    scene: Scene
+    gamma: float
+    beta: float
+    n_train: int
+    n_query: int
+    iter_max: int
+    s_max: int
+    seed: int
+
+    def train_configs(self) -> np.ndarray:
+        return uniform_configs(self.seed + 1, self.n_train, self.scene.arm.D, self.scene.arm.qlim)
+
+    def query_configs(self, n: int | None = None) -> np.ndarray:
+        return uniform_configs(self.seed + 2, self.n_query if n is None else n,
+                               self.scene.arm.D, self.scene.arm.qlim)
+
+
+def workload(name: str, trial: int = 0, **over) -> Workload:
+    """Named workloads.  Scene seed s, training seed s+1, query seed s+2.
+
+    ``arm3-n1000``: 3-DOF arm, 4 control points, 6 boxes, N = 1000 training
+    configurations, 10,000 queries, gamma = 10, up to 5000 iterations.
+    ``arm7-n5000``: 7-DOF arm, 8 control points, 10 boxes, N = 5000, 4M queries.
+    """
+    if name == "arm3-n1000":
+        s = 1000 * 0 + trial
+        sc = Scene(arm_3dof(s), random_boxes(s, 6), 0.03)
+        w = Workload(name, sc, 10.0, 1.0, 1000, 10_000, 5000, 1000, s)
+    elif name == "arm7-n5000":
+        s = 1000 * 1 + trial
+        sc = Scene(arm_7dof(s), random_boxes(s, 10), 0.03)
+        w = Workload(name, sc, 10.0, 1.0, 5000, 4_000_000, 5000, 5000, s)
+    else:
+        raise KeyError(name)
+    return dataclasses.replace(w, **over)

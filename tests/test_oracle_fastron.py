@@ -1,0 +1,143 @@
+"""Pins of the oracle's Fastron update, Algorithm 1 (Sec. III-B): closed-form
+tiny cases, the update rule's invariants (Eqs. 6-8), the loss decrease and step
+bound of Claim 2, and the S_max cap."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1910_06451_gb300 import synth
+
+
+def _small_problem(n=150, seed=0, name="arm3-n1000"):
+    w = synth.workload(name, trial=seed)
+    X = w.train_configs()[:n].astype(np.float64)
+    y = O.check(w.scene, X)
+    cp = O.fk_points(w.scene.arm, X)
+    return w, X, y, cp
+
+
+def test_single_point():
+    cp = np.zeros((1, 2, 3))
+    for y, beta, want in ((1, 1.5, 1.5), (-1, 1.5, -1.0), (1, 1.0, 1.0)):
+        r = O.fastron_train(cp, np.array([y]), 10.0, beta=beta, iter_max=100, trace=True)
+        assert r.converged and r.adds == 1 and r.removes == 0 and r.iters == 1
+        assert r.alpha[0] == want and r.F[0] == want
+        assert list(r.support) == [0]
+
+
+def _two_points(sep):
+    cp = np.zeros((2, 1, 3))
+    cp[1, 0, 0] = sep
+    return cp
+
+
+def test_two_points_opposite_labels_closed_form():
+    g = 10.0
+    cp = _two_points(0.3)
+    k = O.k_fk(cp[0], cp[1], g)
+    assert k < 0.6
+    r = O.fastron_train(cp, np.array([1, -1]), g, iter_max=100, trace=True)
+    # pass 1: all margins 0, tie -> index 0, delta = 1; pass 2: index 1 with
+    # margin -k, delta = -1 - k; then every margin is positive, nothing to remove
+    kind, idx, delta = r.trace
+    assert list(kind) == [1, 1] and list(idx) == [0, 1]
+    assert delta[0] == 1.0 and delta[1] == pytest.approx(-1 - k, rel=1e-15)
+    np.testing.assert_allclose(r.alpha, [1.0, -1.0 - k], rtol=1e-15)
+    np.testing.assert_allclose(r.F, [1 - k - k * k, -1.0], rtol=1e-14)
+    assert r.converged and list(r.support) == [0, 1]
+
+
+def test_two_points_same_label_keeps_one():
+    cp = _two_points(0.2)
+    r = O.fastron_train(cp, np.array([1, 1]), 10.0, iter_max=100, trace=True)
+    assert list(r.trace[0]) == [1] and list(r.trace[1]) == [0]
+    assert list(r.support) == [0] and r.converged
+
+
+def test_redundant_point_is_removed():
+    # four points on a line: after points 0, 3 and 1 are added, point 0 keeps a
+    # positive margin without its own weight, y_0 (F_0 - alpha_0) > 0, so the
+    # removal step sets alpha_0 = 0 and every margin stays positive.
+    g = 10.0
+    cp = np.zeros((4, 1, 3))
+    cp[:, 0, 0] = [0.4, 0.73, 0.71, 0.93]
+    y = np.array([-1, -1, -1, 1])
+    r = O.fastron_train(cp, y, g, iter_max=100, trace=True)
+    kind, idx, delta = r.trace
+    assert list(kind) == [1, 1, 1, 2] and list(idx) == [0, 3, 1, 0]
+    K = O.gram(cp, cp, g)
+    a3 = np.zeros(4)
+    for k in range(3):
+        a3[idx[k]] += delta[k]
+    F3 = K @ a3
+    assert y[0] * (F3[0] - a3[0]) > 0
+    assert delta[3] == -a3[0]
+    assert r.converged and list(r.support) == [1, 3]
+    assert np.all(y * r.F > 0)
+    np.testing.assert_allclose(r.F, K @ r.alpha, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("beta", [1.0, 1.5])
+def test_update_invariants_and_loss_decrease(beta):
+    w, X, y, cp = _small_problem(120, seed=1)
+    K = O.gram(cp, cp, w.gamma)
+    b = np.where(y > 0, beta, 1.0)
+    full = O.fastron_train(cp, y, w.gamma, beta=beta, iter_max=5000, trace=True)
+    kind, idx, delta = full.trace
+    assert full.converged and full.iters == len(kind)
+    prev_alpha = np.zeros(len(y))
+    for k in range(len(kind)):
+        r = O.fastron_train(cp, y, w.gamma, beta=beta, iter_max=k + 1)
+        i = idx[k]
+        # the incrementally maintained F is K alpha
+        np.testing.assert_allclose(r.F, K @ r.alpha, rtol=1e-10, atol=1e-10)
+        if kind[k] == 1:
+            # after an add step the point sits exactly at its target margin: F_i = b_i y_i
+            assert r.F[i] == pytest.approx(b[i] * y[i], abs=1e-12)
+            # loss L = 1/2 a'Ka - y'Ba falls by exactly 1/2 (b_i - m_i)^2 (Claim 2)
+            m_i = y[i] * (K @ prev_alpha)[i]
+            L0 = 0.5 * prev_alpha @ K @ prev_alpha - (y * b) @ prev_alpha
+            L1 = 0.5 * r.alpha @ K @ r.alpha - (y * b) @ r.alpha
+            assert L1 - L0 == pytest.approx(-0.5 * (b[i] - m_i) ** 2, rel=1e-8, abs=1e-10)
+            assert m_i <= 0
+        else:
+            assert r.alpha[i] == 0.0 and prev_alpha[i] != 0.0
+        prev_alpha = r.alpha
+    assert np.all(y * full.F > 0)
+    # no support point is redundant at the end
+    sup = full.alpha != 0
+    assert not np.any(y[sup] * (full.F[sup] - full.alpha[sup]) > 0)
+
+
+def test_add_step_bound_of_claim_2():
+    # number of descent steps <= y'BK^-1By + 2 L(alpha0), alpha0 = 0
+    w, X, y, cp = _small_problem(150, seed=2)
+    K = O.gram(cp, cp, w.gamma)
+    By = y.astype(float)
+    bound = By @ np.linalg.solve(K, By)
+    r = O.fastron_train(cp, y, w.gamma, iter_max=100000)
+    assert r.converged
+    assert r.adds <= bound
+
+
+def test_smax_caps_support_size_and_iter_max_stops():
+    w, X, y, cp = _small_problem(200, seed=3)
+    r = O.fastron_train(cp, y, w.gamma, iter_max=5000, s_max=5, trace=True)
+    assert r.n_support <= 5
+    r2 = O.fastron_train(cp, y, w.gamma, iter_max=3)
+    assert r2.iters == 3 and not r2.converged
+
+
+def test_warm_start_is_a_fixed_point():
+    w, X, y, cp = _small_problem(200, seed=4)
+    r = O.fastron_train(cp, y, w.gamma)
+    r2 = O.fastron_train(cp, y, w.gamma, alpha0=r.alpha, F0=r.F)
+    assert r2.converged and r2.iters == 0
+    assert np.array_equal(r2.alpha, r.alpha)
+
+
+def test_workloads_train_to_positive_margins():
+    w, X, y, cp = _small_problem(1000, seed=0)
+    r = O.fastron_train(cp, y, w.gamma, iter_max=w.iter_max)
+    assert r.converged and np.all(y * r.F > 0)
+    assert 0 < r.n_support < 1000
