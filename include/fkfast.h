@@ -1,0 +1,189 @@
+/*
+ * fkfast: forward-kinematics (FK) kernel proxy collision checking on one
+ * GB300 GPU.  C ABI of libfkfast.so.
+ *
+ * Method: Das and Yip, "Forward Kinematics Kernel for Improved Proxy
+ * Collision Checking", arXiv 1910.06451.  Sections and equations below refer
+ * to that paper.
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *     pointers marked "host" are ordinary host memory owned by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it in call order; a call returns
+ *     once its work is enqueued, except where an output is host memory, in
+ *     which case the call synchronises `stream` before returning.
+ *   - Arrays are dense and row-major unless stated otherwise.
+ *   - Return value 0 (FK_OK) on success, a negative FK_ERR_* code otherwise;
+ *     fk_last_error() then describes the failure (thread-local string).  No
+ *     call falls back to the CPU.
+ *   - Handles (fk_chain_t, fastron_model_t) own their device workspaces.  A
+ *     handle may be used from one stream at a time; calls on one handle from
+ *     different streams must be ordered by the caller.
+ *   - Labels are int8: +1 = in collision (C_obs), -1 = free (C_free)
+ *     (Sec. II-B).  A score f = 0 is labelled +1.
+ */
+#ifndef FKFAST_H
+#define FKFAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FK_OK 0
+#define FK_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, unsupported shape) */
+#define FK_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define FK_ERR_CAPACITY (-3)  /* a size exceeds the handle's or the library's limit */
+#define FK_ERR_TIMEOUT (-4)   /* a bounded wait inside a kernel gave up */
+#define FK_ERR_STATE (-5)     /* handle not ready for this call (e.g. untrained model) */
+
+#define FK_REVOLUTE 0
+#define FK_PRISMATIC 1
+
+#define FK_F32 0  /* FP32 arithmetic */
+#define FK_F64 1  /* FP64 arithmetic */
+
+#define FK_MAX_DOF 16
+#define FK_MAX_CP 32
+
+/* One standard Denavit-Hartenberg link (Eq. 1).  For a revolute joint the
+ * joint value adds to theta0; for a prismatic joint it adds to d. */
+typedef struct {
+    double a, alpha, d, theta0;
+    int32_t type; /* FK_REVOLUTE or FK_PRISMATIC */
+    int32_t reserved;
+} fk_dh;
+
+/* One control point (Eq. 2): position of frame `joint` (0 = base frame,
+ * i = frame of joint i) offset by the static translation t (in that frame). */
+typedef struct {
+    int32_t joint;
+    int32_t reserved;
+    double t[3];
+} fk_cp;
+
+typedef struct fk_chain fk_chain_t;
+typedef struct fastron_model fastron_model_t;
+
+/* Text of the last error on this thread ("" if none). */
+const char *fk_last_error(void);
+
+/* ---- kinematic chain ---------------------------------------------------
+ * Builds a chain from D links (host array, 1 <= D <= FK_MAX_DOF), the
+ * world-from-frame-0 transform base4x4 (host, 16 doubles, row-major; NULL =
+ * identity) and M control points (host array, 1 <= M <= FK_MAX_CP, joint in
+ * [0, D]).  The paper places control points at joint-frame origins (T_m = I,
+ * Sec. III-A); any offsets are accepted.  *out receives the handle. */
+int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, const fk_cp *cps, int M, fk_chain_t **out);
+void fk_chain_destroy(fk_chain_t *chain);
+
+/* ---- forward kinematics (Sec. II-A, Eqs. 1-2) --------------------------
+ * q: device, n x D joint values.  cp: device, control-point positions in
+ * structure-of-arrays layout [M][3][n] (coordinate c of point m of
+ * configuration k at cp[(m*3 + c)*n + k]).  n = 0 is a no-op. */
+int fk_forward(const fk_chain_t *chain, const float *q, int64_t n, float *cp, void *stream);
+int fk_forward_f64(const fk_chain_t *chain, const double *q, int64_t n, double *cp, void *stream);
+
+/* ---- kernel matrix (Sec. II-B with the FK kernel of Eq. 4) -------------
+ * K[i][j] = K_FK(Xa_i, Xb_j) = (1/M) sum_m (1 + gamma/2 |FK_m(Xa_i) - FK_m(Xb_j)|^2)^-2.
+ * precision FK_F64: Xa, Xb are device double arrays (na x D, nb x D) and K a
+ * device double array na x nb.  FK_F32: float inputs and a float K.  gamma > 0.
+ * Control points are computed into the chain's workspace first. */
+int fk_gram(const fk_chain_t *chain, const void *Xa, int64_t na, const void *Xb, int64_t nb, double gamma,
+            int precision, void *K, void *stream);
+
+/* ---- Fastron model (Sec. III-B) ---------------------------------------- */
+typedef struct {
+    double gamma;      /* FK kernel width, > 0 (Eq. 3) */
+    double beta;       /* conditional bias, >= 1 (Eq. 5): b_i = beta for y_i = +1, 1 otherwise */
+    int64_t iter_max;  /* iteration limit of Algorithm 1, >= 0 */
+    int64_t s_max;     /* support-set size limit S_max of Algorithm 1, >= 1 */
+    int32_t warm_start;/* 1: start from this model's alpha and F of the previous call on the
+                          same training set (loadPreviousModel); 0: alpha = F = 0 */
+    int32_t trace;     /* 1: record every pass (kind, index, change of alpha) for
+                          fastron_model_trace; 0: do not */
+} fastron_params;
+
+typedef struct {
+    int64_t iterations; /* passes of Algorithm 1 that changed alpha */
+    int64_t adds;       /* add/adjust steps (Eqs. 6-8) */
+    int64_t removes;    /* redundant-support removals */
+    int64_t n_support;  /* |S| after removeNonsupportPoints */
+    int32_t converged;  /* 1 if every training margin y_i F_i > 0 and no removal applied */
+    int32_t reserved;
+} fastron_stats;
+
+/* Creates an empty (untrained) model bound to `chain`; the chain must outlive it. */
+int fastron_model_create(const fk_chain_t *chain, fastron_model_t **out);
+void fastron_model_destroy(fastron_model_t *model);
+
+/* Algorithm 1.  X: device double, N x D training configurations; y: device
+ * int8 labels (+1/-1), N >= 1.  The FP64 kernel matrix of X is built on the
+ * device, then the greedy coordinate descent runs in one persistent kernel:
+ * argmin of the margins y_i F_i (lowest index wins ties; a margin <= 0 is a
+ * misclassification), add/adjust alpha_i by b_i y_i - F_i and F by that times
+ * column i, subject to S_max; otherwise remove the support point with the
+ * largest y_i (F_i - alpha_i) > 0 (lowest index wins ties); stop when neither
+ * applies or after iter_max passes.  alpha and F are FP64.  The support set
+ * (ascending training indices with alpha != 0) and its weights become the
+ * model.  stats: host, may be NULL; filling it synchronises `stream`.
+ * Requires N <= 8192 (the FP64 kernel matrix is N^2 doubles), else FK_ERR_CAPACITY. */
+int fastron_train(fastron_model_t *model, const double *X, const int8_t *y, int64_t N, const fastron_params *p,
+                  fastron_stats *stats, void *stream);
+
+/* Copies the per-pass record of the last fastron_train call made with
+ * p->trace = 1: kind (host int8: 1 add/adjust, 2 removal), idx (host int64,
+ * training index) and delta (host double, change of alpha_i) for up to cap
+ * passes; *n receives the number of passes.  Any output may be NULL except n.
+ * Synchronous. */
+int fastron_model_trace(const fastron_model_t *model, int8_t *kind, int64_t *idx, double *delta, int64_t cap,
+                        int64_t *n);
+
+/* Replaces the model by the given support set: q host double ns x D
+ * configurations, alpha host double ns weights, kernel width gamma.  Used to
+ * score a model trained elsewhere.  Synchronous. */
+int fastron_model_set(fastron_model_t *model, const double *q, const double *alpha, int64_t ns, double gamma);
+
+/* Copies the support set out: idx (host int64, training indices; NULL
+ * allowed) and alpha (host double) for up to cap entries; *ns receives |S|.
+ * Synchronous. */
+int fastron_model_get(const fastron_model_t *model, int64_t *idx, double *alpha, int64_t cap, int64_t *ns);
+
+/* ---- proxy collision check (Sec. III-B) --------------------------------
+ * f(q) = sum_{s in S} alpha_s K_FK(S_s, q); label = +1 if f >= 0 else -1.
+ * q: device float, n x D.  label: device int8 [n].  f: device float [n] or NULL.
+ * precision FK_F32: FK of each query and the kernel sums run in FP32; a bound
+ * B(q) = sum_s |alpha_s| K_FK(S_s, q) is accumulated beside f.
+ * rescore != 0: every query with |f| <= rescore_eps * B(q) is evaluated
+ * again in FP64 (FK and kernel), and its f and label are replaced, so that
+ * labels equal an FP64 evaluation.  rescore_eps <= 0 selects the library
+ * default.  n_rescored (host, may be NULL) receives the number of queries
+ * re-evaluated; filling it synchronises `stream`. */
+int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, int rescore, double rescore_eps,
+             float *f, int8_t *label, int64_t *n_rescored, void *stream);
+
+/* ---- ground-truth labels (geometric checker) ---------------------------
+ * Link i (1..D) is the segment between the origins of frames i-1 and i,
+ * swept by a sphere of radius `radius`; a configuration collides (+1) if any
+ * link comes within `radius` of any axis-aligned box, else -1.  Stands in for
+ * the geometric checker used to label training data (Sec. III-B active
+ * learning, Sec. IV).  boxes: host double nb x 6 (lo xyz, hi xyz), nb <= 64.
+ * q: device float n x D.  y: device int8 [n].  Computed in FP64. */
+int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double radius, const float *q, int64_t n,
+             int8_t *y, void *stream);
+
+/* ---- pipe throughput probes --------------------------------------------
+ * Measures sustained per-SM throughput of one instruction class with a
+ * register-only loop on all SMs: kind 0 FP32 FMA, 1 packed FP32x2 FMA,
+ * 2 FP32 reciprocal (MUFU), 3 packed FP16x2 FMA, 4 FP64 FMA, 5 FP16x2 ex2
+ * (MUFU).  *ops_per_clk_sm (host) receives lane-operations per SM clock,
+ * from clock64() deltas; *seconds the kernel's wall time.  Synchronous. */
+int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKFAST_H */

@@ -1,0 +1,159 @@
+// Device-side building blocks shared by the fkfast kernels: chain parameters
+// passed by value to every kernel, and forward kinematics in FP32 and FP64
+// (Das and Yip, arXiv 1910.06451, Sec. II-A, Eqs. 1-2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fkfast.h"
+
+namespace fk {
+
+// Error bits a kernel may raise in the workspace error word.
+enum : int { kErrTimeout = 1, kErrCapacity = 2, kErrIndex = 4 };
+
+// Kinematic chain in the form the FP32 kernels use.  Control points fixed to
+// frame 0 (the base) have the same position for every configuration, so
+// their RQ summand is exactly 1; they are counted in n_const and the FP32
+// score kernels evaluate only the Mv configuration-dependent points.
+struct ChainF {
+  int D, M, Mv, n_const;
+  int type[FK_MAX_DOF];
+  float a[FK_MAX_DOF], ca[FK_MAX_DOF], sa[FK_MAX_DOF], d[FK_MAX_DOF], th0[FK_MAX_DOF];
+  float R0[9], p0[3];           // base rotation (row-major) and translation
+  int vj[FK_MAX_CP];            // frame of each configuration-dependent point
+  float vt[FK_MAX_CP][3];       // its offset in that frame
+  int vidx[FK_MAX_CP];          // its index among all M points
+  int cj[FK_MAX_CP];            // frame of every point (fk_forward output order)
+  float ct[FK_MAX_CP][3];
+};
+
+// The same chain for the FP64 kernels.  cos/sin of the link twists are taken
+// on the host once.  The FP64 code evaluates Eq. 1 and the product of Eq. 2
+// with separately rounded products and sums in a fixed order (no fused
+// multiply-add), so that its rounding is that of the plain 4x4 product.
+struct ChainD {
+  int D, M;
+  int type[FK_MAX_DOF];
+  double a[FK_MAX_DOF], ca[FK_MAX_DOF], sa[FK_MAX_DOF], d[FK_MAX_DOF], th0[FK_MAX_DOF];
+  double T0[12];                // rows 0..2 of the base transform
+  int cj[FK_MAX_CP];
+  double ct[FK_MAX_CP][3];
+};
+
+// ------------------------------------------------------------------ FP32 --
+// Pose of the current frame: rotation columns x, y, z and origin p.
+struct PoseF {
+  float x[3], y[3], z[3], p[3];
+};
+
+__device__ __forceinline__ void pose_base(const ChainF &c, PoseF &P) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    P.x[r] = c.R0[3 * r + 0];
+    P.y[r] = c.R0[3 * r + 1];
+    P.z[r] = c.R0[3 * r + 2];
+    P.p[r] = c.p0[r];
+  }
+}
+
+// Advance the pose by link i: R <- R Rz(theta) Rx(alpha), p <- p + R (a c, a s, d).
+__device__ __forceinline__ void pose_step(const ChainF &c, int i, float qi, PoseF &P) {
+  float theta = c.th0[i], dd = c.d[i];
+  if (c.type[i] == FK_REVOLUTE)
+    theta += qi;
+  else
+    dd += qi;
+  float s, co;
+  sincosf(theta, &s, &co);
+  const float ca = c.ca[i], sa = c.sa[i], a = c.a[i];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float xn = co * P.x[r] + s * P.y[r];
+    float yn = co * P.y[r] - s * P.x[r];
+    P.p[r] += a * xn + dd * P.z[r];
+    float zn = ca * P.z[r] - sa * yn;
+    P.y[r] = ca * yn + sa * P.z[r];
+    P.z[r] = zn;
+    P.x[r] = xn;
+  }
+}
+
+__device__ __forceinline__ void pose_point(const PoseF &P, const float t[3], float out[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) out[r] = P.p[r] + P.x[r] * t[0] + P.y[r] * t[1] + P.z[r] * t[2];
+}
+
+// Configuration-dependent control points of one configuration (FP32).
+template <int MV>
+__device__ __forceinline__ void fk_points_f32(const ChainF &c, const float *q, float (&cp)[MV][3]) {
+  PoseF P;
+  pose_base(c, P);
+#pragma unroll
+  for (int m = 0; m < MV; ++m)
+    if (c.vj[m] == 0) pose_point(P, c.vt[m], cp[m]);
+  for (int i = 0; i < c.D; ++i) {
+    pose_step(c, i, q[i], P);
+#pragma unroll
+    for (int m = 0; m < MV; ++m)
+      if (c.vj[m] == i + 1) pose_point(P, c.vt[m], cp[m]);
+  }
+}
+
+// ------------------------------------------------------------------ FP64 --
+// Rows 0..2 of the frame transform; row 3 is (0, 0, 0, 1).
+struct PoseD {
+  double T[12];
+};
+
+__device__ __forceinline__ void pose_base(const ChainD &c, PoseD &P) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) P.T[k] = c.T0[k];
+}
+
+// T <- T * A_i with A_i of Eq. 1.  Each entry is the sum over k of
+// T[r][k] A[k][c] taken in ascending k with every product rounded; terms with
+// an exact zero factor in A are left out (adding an exact zero is exact).
+__device__ __forceinline__ void pose_step(const ChainD &c, int i, double qi, PoseD &P) {
+  double theta = c.th0[i], dd = c.d[i];
+  if (c.type[i] == FK_REVOLUTE)
+    theta = __dadd_rn(theta, qi);
+  else
+    dd = __dadd_rn(dd, qi);
+  double st, ct;
+  sincos(theta, &st, &ct);
+  const double ca = c.ca[i], sa = c.sa[i], a = c.a[i];
+  const double A01 = __dmul_rn(-ca, st), A11 = __dmul_rn(ca, ct);
+  const double A02 = __dmul_rn(sa, st), A12 = __dmul_rn(-sa, ct);
+  const double A03 = __dmul_rn(a, ct), A13 = __dmul_rn(a, st);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double t0 = P.T[4 * r + 0], t1 = P.T[4 * r + 1], t2 = P.T[4 * r + 2], t3 = P.T[4 * r + 3];
+    P.T[4 * r + 0] = __dadd_rn(__dmul_rn(t0, ct), __dmul_rn(t1, st));
+    P.T[4 * r + 1] = __dadd_rn(__dadd_rn(__dmul_rn(t0, A01), __dmul_rn(t1, A11)), __dmul_rn(t2, sa));
+    P.T[4 * r + 2] = __dadd_rn(__dadd_rn(__dmul_rn(t0, A02), __dmul_rn(t1, A12)), __dmul_rn(t2, ca));
+    P.T[4 * r + 3] =
+        __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(t0, A03), __dmul_rn(t1, A13)), __dmul_rn(t2, dd)), t3);
+  }
+}
+
+// pos(T * Trans(t)) with the products and sums in ascending order.
+__device__ __forceinline__ void pose_point(const PoseD &P, const double t[3], double out[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    out[r] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(P.T[4 * r + 0], t[0]), __dmul_rn(P.T[4 * r + 1], t[1])),
+                                 __dmul_rn(P.T[4 * r + 2], t[2])),
+                       P.T[4 * r + 3]);
+}
+
+// RQ summand of Eq. 3 in FP64: 1 / (t * t) with t = 1 + (gamma/2) |x - x'|^2,
+// with the squared distance summed over x, y, z in order.
+__device__ __forceinline__ double k_rq_f64(double hg, const double *x, const double *xp) {
+  const double d0 = __dsub_rn(x[0], xp[0]), d1 = __dsub_rn(x[1], xp[1]), d2 = __dsub_rn(x[2], xp[2]);
+  const double s = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+  const double t = __dadd_rn(1.0, __dmul_rn(hg, s));
+  return __ddiv_rn(1.0, __dmul_rn(t, t));
+}
+
+}  // namespace fk

@@ -1,0 +1,165 @@
+// Forward kinematics (Sec. II-A, Eqs. 1-2) and the FK-kernel matrix
+// (Sec. II-B with Eq. 4) on the GPU.
+#include "fk_internal.h"
+
+namespace fk {
+
+// ------------------------------------------------------------ forward ---
+// One thread per configuration; the pose is carried link by link in
+// registers and each control point is written when its frame is reached.
+
+__global__ void fk_forward_f32_kernel(const ChainF c, const float *__restrict__ q, int64_t n, float *__restrict__ cp) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  PoseF P;
+  pose_base(c, P);
+  auto emit = [&](int frame) {
+    for (int m = 0; m < c.M; ++m)
+      if (c.cj[m] == frame) {
+        float o[3];
+        pose_point(P, c.ct[m], o);
+        for (int r = 0; r < 3; ++r) cp[(m * 3 + r) * n + k] = o[r];
+      }
+  };
+  emit(0);
+  for (int i = 0; i < c.D; ++i) {
+    pose_step(c, i, q[k * c.D + i], P);
+    emit(i + 1);
+  }
+}
+
+template <typename QT>
+__global__ void fk_forward_f64_kernel(const ChainD c, const QT *__restrict__ q, int64_t n, double *__restrict__ cp) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  PoseD P;
+  pose_base(c, P);
+  auto emit = [&](int frame) {
+    for (int m = 0; m < c.M; ++m)
+      if (c.cj[m] == frame) {
+        double o[3];
+        pose_point(P, c.ct[m], o);
+        for (int r = 0; r < 3; ++r) cp[(m * 3 + r) * n + k] = o[r];
+      }
+  };
+  emit(0);
+  for (int i = 0; i < c.D; ++i) {
+    pose_step(c, i, (double)q[k * c.D + i], P);
+    emit(i + 1);
+  }
+}
+
+static inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_fk_forward_f32(const ChainF &c, const float *q, int64_t n, float *cp, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fk_forward_f32_kernel<<<grid_for(n, 128), 128, 0, s>>>(c, q, n, cp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fk_forward_f64(const ChainD &c, const double *q, int64_t n, double *cp, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fk_forward_f64_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(c, q, n, cp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t n, double *cp, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fk_forward_f64_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(c, q, n, cp);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- Gram ---
+// K[i][j] = (1/M) sum_m K_RQ(FK_m(a_i), FK_m(b_j)).  One CTA computes a
+// 32 x 32 tile with 256 threads (4 rows each).  Control points of the tile's
+// 32 + 32 configurations are staged in shared memory as [M*3][32].  With
+// sym != 0 only tiles with bi <= bj run; an off-diagonal tile is written
+// twice, directly and transposed through shared memory, because the RQ
+// summand is exactly symmetric in its arguments.
+
+constexpr int kGT = 32;
+
+__device__ __forceinline__ double gram_entry(int M, double hg, const double *A, const double *B, int ia, int jb) {
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double x[3] = {A[(m * 3 + 0) * kGT + ia], A[(m * 3 + 1) * kGT + ia], A[(m * 3 + 2) * kGT + ia]};
+    const double y[3] = {B[(m * 3 + 0) * kGT + jb], B[(m * 3 + 1) * kGT + jb], B[(m * 3 + 2) * kGT + jb]};
+    s = __dadd_rn(s, k_rq_f64(hg, x, y));
+  }
+  return __ddiv_rn(s, (double)M);
+}
+
+__device__ __forceinline__ float gram_entry(int M, float hg, const float *A, const float *B, int ia, int jb) {
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) {
+    const float d0 = A[(m * 3 + 0) * kGT + ia] - B[(m * 3 + 0) * kGT + jb];
+    const float d1 = A[(m * 3 + 1) * kGT + ia] - B[(m * 3 + 1) * kGT + jb];
+    const float d2 = A[(m * 3 + 2) * kGT + ia] - B[(m * 3 + 2) * kGT + jb];
+    const float t = fmaf(hg, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.f);
+    const float r = 1.f / t;
+    s = fmaf(r, r, s);
+  }
+  return s / (float)M;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(int M, T hg, const T *__restrict__ cpa, int64_t na,
+                                                   const T *__restrict__ cpb, int64_t nb, int sym,
+                                                   T *__restrict__ K) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (sym && bi > bj) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *A = reinterpret_cast<T *>(smem_raw);
+  T *B = A + M * 3 * kGT;
+  T *O = B + M * 3 * kGT;  // [kGT][kGT + 1] output tile for the transposed write
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)bi * kGT, j0 = (int64_t)bj * kGT;
+  for (int e = threadIdx.x; e < M * 3 * kGT; e += blockDim.x) {
+    const int row = e / kGT, col = e % kGT;
+    A[e] = (i0 + col < na) ? cpa[row * na + i0 + col] : T(0);
+    B[e] = (j0 + col < nb) ? cpb[row * nb + j0 + col] : T(0);
+  }
+  __syncthreads();
+  const bool mirror = sym && bi != bj;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int il = ty + 8 * r;
+    const T v = gram_entry(M, hg, A, B, il, tx);
+    if (i0 + il < na && j0 + tx < nb) K[(i0 + il) * nb + j0 + tx] = v;
+    if (mirror) O[il * (kGT + 1) + tx] = v;
+  }
+  if (!mirror) return;
+  __syncthreads();
+  // transposed tile: K[j0 + jl][i0 + il] = O[il][jl]
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int jl = ty + 8 * r;
+    if (j0 + jl < na && i0 + tx < nb) K[(j0 + jl) * nb + i0 + tx] = O[tx * (kGT + 1) + jl];
+  }
+}
+
+template <typename T>
+static cudaError_t launch_gram(int M, T gamma, const T *cpa, int64_t na, const T *cpb, int64_t nb, int sym, T *K,
+                               cudaStream_t s) {
+  if (na <= 0 || nb <= 0) return cudaSuccess;
+  const size_t smem = sizeof(T) * (2 * (size_t)M * 3 * kGT + kGT * (kGT + 1));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(grid_for(nb, kGT), grid_for(na, kGT));
+  gram_kernel<T><<<grid, 256, smem, s>>>(M, T(0.5) * gamma, cpa, na, cpb, nb, sym, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_f64(int M, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
+                            int sym, double *K, cudaStream_t s) {
+  return launch_gram<double>(M, gamma, cpa, na, cpb, nb, sym, K, s);
+}
+
+cudaError_t launch_gram_f32(int M, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
+                            int sym, float *K, cudaStream_t s) {
+  return launch_gram<float>(M, gamma, cpa, na, cpb, nb, sym, K, s);
+}
+
+}  // namespace fk

@@ -1,0 +1,345 @@
+// Proxy collision check: the Fastron model value f(q) = sum_s alpha_s
+// K_FK(S_s, q) with the FK kernel of Eq. 4 and its sign (Sec. III-B).
+//
+// Three kernels:
+//   pack     support set -> per support point s one record of Mv + 1 float4:
+//            for each configuration-dependent control point m,
+//            (-gamma s_m, 1 + gamma/2 |s_m|^2), then (w_s, |w_s|, 0, 0) with
+//            w_s = alpha_s / M; plus the FP64 control points for re-scoring.
+//            All from FP64 kinematics, rounded to FP32 once.
+//   score    FP32.  One thread scores two queries: FK in registers, then the
+//            support records stream through shared memory by tile (1-D TMA
+//            bulk copies, double-buffered, mbarrier completion) and every
+//            thread reads each record as a broadcast.  Per (s, m):
+//              t = (c_sm + gamma/2 |p_m|^2) + s'_m . p_m  = 1 + gamma/2 |p_m - s_m|^2
+//            and two summands share one reciprocal:
+//              1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2.
+//            Beside f the kernel accumulates B(q) = sum_s |w_s| sum_m t^-2,
+//            which bounds |f| and scales the FP32 error; queries with
+//            |f| <= eps B(q) are appended to a band list.
+//   rescore  FP64, one warp per band query: FK and Eq. 3/4 in FP64 with the
+//            operation order of the plain definition, lanes splitting the
+//            support set, a fixed-order warp sum; f and the label are replaced.
+#include "fk_internal.h"
+
+namespace fk {
+
+// -------------------------------------------------------------- helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (with a short sleep between).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (mbar_test_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ---------------------------------------------------------------- pack ---
+__global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= a.ns) return;
+  const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
+  const double *x = a.X + src * cd.D;
+  double cp[FK_MAX_CP][3];
+  PoseD P;
+  pose_base(cd, P);
+  for (int m = 0; m < cd.M; ++m)
+    if (cd.cj[m] == 0) pose_point(P, cd.ct[m], cp[m]);
+  for (int i = 0; i < cd.D; ++i) {
+    a.q_out[s * cd.D + i] = x[i];
+    pose_step(cd, i, x[i], P);
+    for (int m = 0; m < cd.M; ++m)
+      if (cd.cj[m] == i + 1) pose_point(P, cd.ct[m], cp[m]);
+  }
+  for (int m = 0; m < cd.M; ++m)
+    for (int r = 0; r < 3; ++r) a.cp64[(m * 3 + r) * a.ns + s] = cp[m][r];
+  const double al = a.alpha[s];
+  a.alpha_out[s] = al;
+  float4 *rec = a.rec + s * (cf.Mv + 1);
+  for (int v = 0; v < cf.Mv; ++v) {
+    const double *p = cp[cf.vidx[v]];
+    const double n2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    rec[v] = make_float4((float)(-a.gamma * p[0]), (float)(-a.gamma * p[1]), (float)(-a.gamma * p[2]),
+                         (float)(1.0 + 0.5 * a.gamma * n2));
+  }
+  const double w = al / cd.M;
+  rec[cf.Mv] = make_float4((float)w, (float)fabs(w), 0.f, 0.f);
+}
+
+cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s) {
+  if (a.ns <= 0) return cudaSuccess;
+  pack_kernel<<<(unsigned)((a.ns + 127) / 128), 128, 0, s>>>(cf, cd, a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- score ---
+constexpr int kScoreThreads = 256;
+constexpr int kQ = 2;                          // queries per thread
+constexpr int kQueriesPerCta = kScoreThreads * kQ;
+constexpr int kTile = 128;                     // support points per shared-memory tile
+constexpr uint32_t kWaitLimit = 1u << 22;      // polls before a wait gives up
+
+template <int MV>
+__global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
+  extern __shared__ __align__(128) float4 tiles[];  // [2][kTile][MV + 1]
+  __shared__ __align__(8) uint64_t bar[2];
+  constexpr int REC = MV + 1;
+
+  const int tid = threadIdx.x;
+  const int64_t ns = a.ns;
+  const int ntiles = (int)((ns + kTile - 1) / kTile);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int64_t s0 = (int64_t)t * kTile;
+    const int64_t cnt = ns - s0 < kTile ? ns - s0 : kTile;
+    const uint32_t bytes = (uint32_t)(cnt * REC * sizeof(float4));
+    uint64_t *b = &bar[t & 1];
+    mbar_arrive_expect_tx(b, bytes);
+    tma_bulk_load(tiles + (size_t)(t & 1) * kTile * REC, a.rec + s0 * REC, bytes, b);
+  };
+  if (tid == 0) {
+    if (ntiles > 0) issue(0);
+    if (ntiles > 1) issue(1);
+  }
+
+  // forward kinematics of this thread's queries (FP32, in registers)
+  const int64_t qbase = (int64_t)blockIdx.x * kQueriesPerCta + tid;
+  float p[kQ][MV][3], u[kQ][MV];
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) {
+    const int64_t qi = qbase + k * kScoreThreads;
+    float qv[FK_MAX_DOF];
+    for (int i = 0; i < c.D; ++i) qv[i] = qi < a.n ? a.q[qi * c.D + i] : 0.f;
+    fk_points_f32<MV>(c, qv, p[k]);
+#pragma unroll
+    for (int m = 0; m < MV; ++m)
+      u[k][m] = a.hg * fmaf(p[k][m][0], p[k][m][0], fmaf(p[k][m][1], p[k][m][1], p[k][m][2] * p[k][m][2]));
+  }
+
+  float f[kQ], B[kQ];
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) f[k] = B[k] = 0.f;
+  int t_fail = -1;
+  for (int t = 0; t < ntiles; ++t) {
+    const bool got = mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, kWaitLimit);
+    if (!__syncthreads_and(got)) {
+      t_fail = t;
+      break;
+    }
+    const float4 *tile = tiles + (size_t)(t & 1) * kTile * REC;
+    const int cnt = (int)(ns - (int64_t)t * kTile < kTile ? ns - (int64_t)t * kTile : kTile);
+#pragma unroll 1
+    for (int s = 0; s < cnt; ++s) {
+      const float4 *r = tile + s * REC;
+      float acc[kQ];
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) acc[k] = (float)c.n_const;
+#pragma unroll
+      for (int m = 0; m + 1 < MV; m += 2) {
+        const float4 s1 = r[m], s2 = r[m + 1];
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) {
+          const float t1 = fmaf(s1.x, p[k][m][0], fmaf(s1.y, p[k][m][1], fmaf(s1.z, p[k][m][2], s1.w + u[k][m])));
+          const float t2 =
+              fmaf(s2.x, p[k][m + 1][0], fmaf(s2.y, p[k][m + 1][1], fmaf(s2.z, p[k][m + 1][2], s2.w + u[k][m + 1])));
+          const float pr = t1 * t2;
+          const float num = fmaf(t1, t1, t2 * t2);
+          acc[k] = fmaf(num, rcp_approx(pr * pr), acc[k]);
+        }
+      }
+      if (MV & 1) {
+        const float4 s1 = r[MV - 1];
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) {
+          const float t1 = fmaf(s1.x, p[k][MV - 1][0],
+                                fmaf(s1.y, p[k][MV - 1][1], fmaf(s1.z, p[k][MV - 1][2], s1.w + u[k][MV - 1])));
+          const float rr = rcp_approx(t1);
+          acc[k] = fmaf(rr, rr, acc[k]);
+        }
+      }
+      const float4 w = r[MV];
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) {
+        f[k] = fmaf(w.x, acc[k], f[k]);
+        B[k] = fmaf(w.y, acc[k], B[k]);
+      }
+    }
+    __syncthreads();  // every thread is done with this buffer
+    if (tid == 0 && t + 2 < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + 2);
+    }
+  }
+  if (t_fail >= 0) {
+    // give the copies still in flight (tiles t_fail and t_fail + 1) a
+    // bounded chance to land before the CTA exits, then report
+    if (tid == 0) {
+      for (int t = t_fail; t < ntiles && t < t_fail + 2; ++t)
+        mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, kWaitLimit);
+      atomicOr(a.err, kErrTimeout);
+    }
+    return;
+  }
+
+  const unsigned lane = tid & 31;
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) {
+    const int64_t qi = qbase + k * kScoreThreads;
+    const bool valid = qi < a.n;
+    if (valid) {
+      if (a.f) a.f[qi] = f[k];
+      a.label[qi] = f[k] >= 0.f ? 1 : -1;
+    }
+    if (a.band_idx) {
+      const bool flag = valid && fabsf(f[k]) <= a.eps * B[k];
+      const unsigned bal = __ballot_sync(0xffffffffu, flag);
+      if (bal) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.band_cnt, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (flag) a.band_idx[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)qi;
+      }
+    }
+  }
+}
+
+}  // namespace fk
+
+namespace fk {
+
+template <int MV>
+static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)kTile * (MV + 1) * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(score_f32_kernel<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  score_f32_kernel<MV><<<grid, kScoreThreads, smem, s>>>(c, a);
+  return cudaGetLastError();
+}
+
+// Shapes with a compiled score kernel: the number of configuration-dependent
+// control points.
+bool score_supported(int mv) {
+  switch (mv) {
+    case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 11: case 12:
+      return true;
+    default:
+      return false;
+  }
+}
+
+cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (c.Mv) {
+    case 1: return launch_score_mv<1>(c, a, s);
+    case 2: return launch_score_mv<2>(c, a, s);
+    case 3: return launch_score_mv<3>(c, a, s);
+    case 4: return launch_score_mv<4>(c, a, s);
+    case 5: return launch_score_mv<5>(c, a, s);
+    case 6: return launch_score_mv<6>(c, a, s);
+    case 7: return launch_score_mv<7>(c, a, s);
+    case 8: return launch_score_mv<8>(c, a, s);
+    case 11: return launch_score_mv<11>(c, a, s);
+    case 12: return launch_score_mv<12>(c, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------- rescore ---
+constexpr int kRescoreWarps = 8;
+
+__global__ void __launch_bounds__(kRescoreWarps * 32) rescore_f64_kernel(const ChainD c, const RescoreArgs a) {
+  __shared__ double qcp[kRescoreWarps][FK_MAX_CP][3];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t gw = blockIdx.x * (int64_t)kRescoreWarps + wl;
+  const int64_t nw = (int64_t)gridDim.x * kRescoreWarps;
+  const int64_t cnt = *a.band_cnt;
+  const double hg = 0.5 * a.gamma;
+  for (int64_t e = gw; e < cnt; e += nw) {
+    const int64_t k = a.band_idx[e];
+    if (lane == 0) {
+      PoseD P;
+      pose_base(c, P);
+      for (int m = 0; m < c.M; ++m)
+        if (c.cj[m] == 0) pose_point(P, c.ct[m], qcp[wl][m]);
+      for (int i = 0; i < c.D; ++i) {
+        pose_step(c, i, (double)a.q[k * c.D + i], P);
+        for (int m = 0; m < c.M; ++m)
+          if (c.cj[m] == i + 1) pose_point(P, c.ct[m], qcp[wl][m]);
+      }
+    }
+    __syncwarp();
+    double f = 0.0;
+    for (int64_t s = lane; s < a.ns; s += 32) {
+      double ks = 0.0;
+      for (int m = 0; m < c.M; ++m) {
+        const double sp[3] = {a.cp64[(m * 3 + 0) * a.ns + s], a.cp64[(m * 3 + 1) * a.ns + s],
+                              a.cp64[(m * 3 + 2) * a.ns + s]};
+        ks = __dadd_rn(ks, k_rq_f64(hg, sp, qcp[wl][m]));
+      }
+      f = __dadd_rn(f, __dmul_rn(a.alpha[s], __ddiv_rn(ks, (double)c.M)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f = __dadd_rn(f, __shfl_xor_sync(0xffffffffu, f, o));
+    if (lane == 0) {
+      if (a.f) a.f[k] = (float)f;
+      a.label[k] = f >= 0.0 ? 1 : -1;
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_rescore_f64(const ChainD &c, const RescoreArgs &a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  rescore_f64_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 304), kRescoreWarps * 32, 0, s>>>(c, a);
+  return cudaGetLastError();
+}
+
+}  // namespace fk

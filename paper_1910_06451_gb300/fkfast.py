@@ -1,0 +1,276 @@
+"""ctypes binding of libfkfast.so (include/fkfast.h).
+
+Argument marshalling only: every function here checks tensor placement,
+dtype and shape, converts to raw pointers and calls the C function of the
+same name, which runs the work in the library's CUDA kernels.  There is no
+CPU path: if the library is not built or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FK_OK = 0
+FK_ERR_ARG = -1
+FK_ERR_CUDA = -2
+FK_ERR_CAPACITY = -3
+FK_ERR_TIMEOUT = -4
+FK_ERR_STATE = -5
+FK_F32 = 0
+FK_F64 = 1
+FK_MAX_DOF = 16
+FK_MAX_CP = 32
+
+EXPORTS = (
+    "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
+    "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
+    "fastron_model_set", "fastron_model_get", "fk_score", "fk_label", "fk_probe_pipe",
+)
+
+
+class FkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fkfast error {code}: {msg}")
+        self.code = code
+
+
+class FkDh(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("alpha", ctypes.c_double), ("d", ctypes.c_double),
+                ("theta0", ctypes.c_double), ("type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class FkCp(ctypes.Structure):
+    _fields_ = [("joint", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t", ctypes.c_double * 3)]
+
+
+class FastronParams(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("beta", ctypes.c_double), ("iter_max", ctypes.c_int64),
+                ("s_max", ctypes.c_int64), ("warm_start", ctypes.c_int32), ("trace", ctypes.c_int32)]
+
+
+class FastronStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("adds", ctypes.c_int64), ("removes", ctypes.c_int64),
+                ("n_support", ctypes.c_int64), ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libfkfast.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise FkError(FK_ERR_STATE, f"{path} is not built; run python -m paper_1910_06451_gb300.build")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "fk_last_error": ([], ctypes.c_char_p),
+            "fk_chain_create": ([P, I, P, P, I, PP], I),
+            "fk_chain_destroy": ([P], None),
+            "fk_forward": ([P, P, I64, P, P], I),
+            "fk_forward_f64": ([P, P, I64, P, P], I),
+            "fk_gram": ([P, P, I64, P, I64, D, I, P, P], I),
+            "fastron_model_create": ([P, PP], I),
+            "fastron_model_destroy": ([P], None),
+            "fastron_train": ([P, P, P, I64, P, P, P], I),
+            "fastron_model_trace": ([P, P, P, P, I64, P], I),
+            "fastron_model_set": ([P, P, P, I64, D], I),
+            "fastron_model_get": ([P, P, P, I64, P], I),
+            "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
+            "fk_label": ([P, P, I64, D, P, I64, P, P], I),
+            "fk_probe_pipe": ([I, P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != FK_OK:
+        raise FkError(rc, load().fk_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- chain ---
+
+def fk_chain_create(dh, base, cp_joint, cp_off):
+    """dh: (D, 5) rows (a, alpha, d, theta0, type); base: (4, 4) or None;
+    cp_joint: (M,) frames; cp_off: (M, 3) offsets.  Returns a chain handle."""
+    dh = np.asarray(dh, dtype=np.float64)
+    D = dh.shape[0]
+    links = (FkDh * D)(*[FkDh(r[0], r[1], r[2], r[3], int(r[4]), 0) for r in dh])
+    cj = np.asarray(cp_joint)
+    co = np.asarray(cp_off, dtype=np.float64).reshape(-1, 3)
+    M = cj.shape[0]
+    cps = (FkCp * M)(*[FkCp(int(cj[m]), 0, (ctypes.c_double * 3)(*co[m])) for m in range(M)])
+    bp = None
+    if base is not None:
+        bk, bp = _host(np.asarray(base, dtype=np.float64).reshape(16), np.float64)
+    out = ctypes.c_void_p()
+    _check(load().fk_chain_create(ctypes.cast(links, ctypes.c_void_p), D, bp, ctypes.cast(cps, ctypes.c_void_p), M,
+                                  ctypes.byref(out)))
+    return out
+
+
+def chain_from_arm(arm):
+    return fk_chain_create(arm.dh, arm.base, arm.cp_joint, arm.cp_off)
+
+
+def fk_chain_destroy(chain):
+    load().fk_chain_destroy(chain)
+
+
+# ------------------------------------------------------------ kinematics --
+
+def fk_forward(chain, q, cp, stream=None):
+    """q: float32 (n, D) -> cp: float32 (M, 3, n)."""
+    import torch
+    n = q.shape[0]
+    _check(load().fk_forward(chain, _dev(q, torch.float32, "q"), n, _dev(cp, torch.float32, "cp"), _stream(stream)))
+
+
+def fk_forward_f64(chain, q, cp, stream=None):
+    """q: float64 (n, D) -> cp: float64 (M, 3, n)."""
+    import torch
+    n = q.shape[0]
+    _check(load().fk_forward_f64(chain, _dev(q, torch.float64, "q"), n, _dev(cp, torch.float64, "cp"),
+                                 _stream(stream)))
+
+
+def fk_gram(chain, Xa, Xb, gamma, K, stream=None):
+    """K[i][j] = K_FK(Xa_i, Xb_j); float64 inputs -> FP64, float32 -> FP32."""
+    import torch
+    dt = Xa.dtype
+    prec = FK_F64 if dt == torch.float64 else FK_F32
+    pa = _dev(Xa, dt, "Xa")
+    pb = pa if Xb is Xa else _dev(Xb, dt, "Xb")
+    _check(load().fk_gram(chain, pa, Xa.shape[0], pb, Xb.shape[0], float(gamma), prec,
+                          _dev(K, dt, "K", (Xa.shape[0], Xb.shape[0])), _stream(stream)))
+
+
+# ---------------------------------------------------------------- model ---
+
+def fastron_model_create(chain):
+    out = ctypes.c_void_p()
+    _check(load().fastron_model_create(chain, ctypes.byref(out)))
+    return out
+
+
+def fastron_model_destroy(model):
+    load().fastron_model_destroy(model)
+
+
+def fastron_train(model, X, y, gamma, beta=1.0, iter_max=5000, s_max=None, warm_start=False, trace=False,
+                  stream=None) -> dict:
+    """Algorithm 1 on device training data X (float64, (N, D)) and y (int8, (N,))."""
+    import torch
+    N = X.shape[0]
+    p = FastronParams(float(gamma), float(beta), int(iter_max), int(N if s_max is None else s_max),
+                      int(bool(warm_start)), int(bool(trace)))
+    st = FastronStats()
+    _check(load().fastron_train(model, _dev(X, torch.float64, "X"), _dev(y, torch.int8, "y", (N,)), N,
+                                ctypes.byref(p), ctypes.byref(st), _stream(stream)))
+    return {"iterations": st.iterations, "adds": st.adds, "removes": st.removes, "n_support": st.n_support,
+            "converged": bool(st.converged)}
+
+
+def fastron_model_trace(model, cap: int):
+    kind = np.zeros(cap, dtype=np.int8)
+    idx = np.zeros(cap, dtype=np.int64)
+    delta = np.zeros(cap, dtype=np.float64)
+    n = ctypes.c_int64()
+    _check(load().fastron_model_trace(model, kind.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),
+                                      delta.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)))
+    k = min(n.value, cap)
+    return kind[:k], idx[:k], delta[:k]
+
+
+def fastron_model_set(model, q, alpha, gamma):
+    qa, qp = _host(q, np.float64)
+    aa, ap = _host(alpha, np.float64)
+    _check(load().fastron_model_set(model, qp, ap, aa.shape[0], float(gamma)))
+
+
+def fastron_model_get(model):
+    ns = ctypes.c_int64()
+    _check(load().fastron_model_get(model, None, None, 0, ctypes.byref(ns)))
+    idx = np.zeros(ns.value, dtype=np.int64)
+    alpha = np.zeros(ns.value, dtype=np.float64)
+    _check(load().fastron_model_get(model, idx.ctypes.data_as(ctypes.c_void_p), alpha.ctypes.data_as(ctypes.c_void_p),
+                                    ns.value, ctypes.byref(ns)))
+    return idx, alpha
+
+
+# ---------------------------------------------------------------- score ---
+
+def fk_score(model, q, label, f=None, rescore=True, eps=0.0, count=False, stream=None):
+    """Labels (and optionally f) of float32 queries q (n, D).  With count=True
+    the call synchronises and returns the number of FP64 re-evaluations."""
+    import torch
+    n = q.shape[0]
+    nr = ctypes.c_int64()
+    _check(load().fk_score(model, _dev(q, torch.float32, "q"), n, FK_F32, int(bool(rescore)), float(eps),
+                           None if f is None else _dev(f, torch.float32, "f", (n,)),
+                           _dev(label, torch.int8, "label", (n,)), ctypes.byref(nr) if count else None,
+                           _stream(stream)))
+    return nr.value if count else None
+
+
+def fk_label(chain, boxes, radius, q, y, stream=None):
+    """Geometric labels (FP64) of float32 configurations q into int8 y."""
+    import torch
+    bx, bp = _host(np.asarray(boxes, dtype=np.float64).reshape(-1, 6), np.float64)
+    n = q.shape[0]
+    _check(load().fk_label(chain, bp, bx.shape[0], float(radius), _dev(q, torch.float32, "q"), n,
+                           _dev(y, torch.int8, "y", (n,)), _stream(stream)))
+
+
+def fk_probe_pipe(kind: int):
+    ops = ctypes.c_double()
+    sec = ctypes.c_double()
+    _check(load().fk_probe_pipe(int(kind), ctypes.byref(ops), ctypes.byref(sec)))
+    return ops.value, sec.value
