@@ -1,0 +1,317 @@
+"""Benchmark: proxy collision checks per second on the 7-DOF workload
+(7-DOF arm, 8 control points, 10 boxes, N = 5000 training configurations,
+4,194,304 uniform query configurations, FK kernel with gamma = 40).
+
+One step is one pass of the whole path over one batch:
+  ground-truth labels of the N training configurations (GPU checker),
+  FP64 control points and FP64 kernel matrix, Fastron Algorithm 1,
+  support packing, then FK + FP32 score + FP64 re-score of the band for
+  every query of the batch, whose labels are the output.
+value = queries per second of steps (each query is one proxy collision check).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1910_06451_gb300 import synth  # noqa: E402
+
+WORKLOAD = "arm7-n5000"
+N_QUERY = 1 << 22
+METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
+UNIT = "checks/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._th = threading.Thread(target=run, daemon=True)
+        self._th.start()
+
+    def stop(self) -> dict:
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and "Active" in s[4 + i]
+                          and "Not" not in s[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def oracle_cpu_baseline(w, sample_queries: int, threads: int) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample: labels + training on
+    the full training set, scoring of `sample_queries` queries; the per-query
+    time is scaled to the full batch."""
+    from oracle import oracle as O
+    arm = w.scene.arm
+    X = w.train_configs().astype(np.float64)
+    t0 = time.perf_counter()
+    y = O.check(w.scene, X)
+    r = O.fastron_train(O.fk_points(arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+    t1 = time.perf_counter()
+    Q = w.query_configs(sample_queries).astype(np.float64)
+    S = X[r.support]
+    f = O.score(arm, S, r.alpha[r.support], Q, w.gamma, nthreads=threads)
+    O.labels_from_f(f)
+    t2 = time.perf_counter()
+    per_q = (t2 - t1) / sample_queries
+    step = (t1 - t0) + per_q * N_QUERY
+    return {"value": N_QUERY / step, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"labels+Algorithm 1 on all {w.n_train} training configs ({t1 - t0:.2f} s), "
+                      f"FP64 scoring of {sample_queries} of {N_QUERY} queries ({t2 - t1:.2f} s) scaled to the batch",
+            "train_s": t1 - t0, "score_us_per_query": per_q * 1e6, "n_support": int(r.n_support)}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    w = synth.workload(WORKLOAD)
+    threads = os.cpu_count() or 1
+    sample = 16384
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = oracle_cpu_baseline(w, sample, threads)
+        if i >= args.warmup:
+            vals.append(cb)
+    value = statistics.mean(v["value"] for v in vals)
+    ms = N_QUERY / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_train": w.n_train, "n_query": N_QUERY, "gamma": w.gamma,
+                       "l2": "host CPU run"},
+            "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fkfast")
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--queries", type=int, default=N_QUERY, help="query batch size (profiling runs use a smaller one)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1910_06451_gb300 import build, fkfast as fk
+    build.build()
+    fk.load()
+
+    # every rank runs an independent scene (trial = rank): the path shards by
+    # scene and by query batch with no exchange
+    w = synth.workload(WORKLOAD, trial=rank)
+    arm = w.scene.arm
+    X = torch.from_numpy(w.train_configs().astype(np.float64)).to(dev)
+    Xq32 = torch.from_numpy(w.train_configs()).to(dev)
+    nq = args.queries
+    Q = torch.from_numpy(w.query_configs(nq)).to(dev)
+    ytr = torch.empty(w.n_train, dtype=torch.int8, device=dev)
+    lab = torch.empty(nq, dtype=torch.int8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    chain = fk.chain_from_arm(arm)
+    model = fk.fastron_model_create(chain)
+    stream = torch.cuda.current_stream()
+
+    def step(q_dev, x_dev, xq32_dev, lab_dev):
+        fk.fk_label(chain, w.scene.boxes, w.scene.radius, xq32_dev, ytr)
+        st = fk.fastron_train(model, x_dev, ytr, w.gamma, w.beta, w.iter_max, w.s_max)
+        fk.fk_score(model, q_dev, lab_dev, rescore=True)
+        return st
+
+    # phase timing (untimed run): update vs query pass, band size
+    st = step(Q, X, Xq32, lab)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    fk.fk_label(chain, w.scene.boxes, w.scene.radius, Xq32, ytr)
+    st = fk.fastron_train(model, X, ytr, w.gamma, w.beta, w.iter_max, w.s_max)
+    e[1].record()
+    nres = fk.fk_score(model, Q, lab, rescore=True, count=True)
+    e[2].record()
+    fk.fk_score(model, Q, lab, rescore=False)
+    e[3].record()
+    torch.cuda.synchronize()
+    update_ms = e[0].elapsed_time(e[1])
+    query_ms = e[1].elapsed_time(e[2])
+    score_only_ms = e[2].elapsed_time(e[3])
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(Q, X, Xq32, lab)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(Q, X, Xq32, lab)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * nq / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel: the FP32 score, one launch per step.
+    # Algorithmic work = |S| * Mv RQ evaluations per query.
+    Mv = int(np.sum(arm.cp_joint != 0))
+    evals = st["n_support"] * Mv * nq
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    score_times = []
+    for _ in range(5):
+        flush.zero_()
+        ev[0].record()
+        fk.fk_score(model, Q, lab, rescore=False)
+        ev[1].record()
+        ev[1].synchronize()
+        score_times.append(ev[0].elapsed_time(ev[1]))
+    score_ms = statistics.median(score_times)
+    achieved = evals / (score_ms * 1e-3) / 1e12
+    # peak: 152 SMs x 128 FP32 lanes x max SM clock / 5 FMA-pipe ops per evaluation
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(clocks.get("sm_max_mhz") or _peaks().get("sm_max_mhz") or 2070.0)
+    peak = props.multi_processor_count * 128 * sm_max * 1e6 / 5 / 1e12
+
+    # end to end through the public API with host buffers
+    Qh = Q.cpu().pin_memory()
+    Xh = X.cpu().pin_memory()
+    X32h = Xq32.cpu().pin_memory()
+    labh = torch.empty(nq, dtype=torch.int8).pin_memory()
+    qd = torch.empty_like(Q)
+    xd = torch.empty_like(X)
+    x32d = torch.empty_like(Xq32)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        qd.copy_(Qh, non_blocking=True)
+        xd.copy_(Xh, non_blocking=True)
+        x32d.copy_(X32h, non_blocking=True)
+        step(qd, xd, x32d, lab)
+        labh.copy_(lab, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    h2d = Qh.numel() * 4 + Xh.numel() * 8 + X32h.numel() * 4
+    d2h = labh.numel()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(w, args.cpu_sample, os.cpu_count() or 1)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 score, f64 band re-score and training", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dof": arm.D, "control_points": arm.M, "boxes": len(w.scene.boxes),
+                       "n_train": w.n_train, "n_query": nq, "gamma": w.gamma,
+                       "support": st["n_support"], "iterations": st["iterations"],
+                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+fp64-rescore"},
+            "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
+                          "rescored_queries": nres},
+            "query_only_checks_per_s": nq / (query_ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": ws * nq / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 7 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    fk.fastron_model_destroy(model)
+    fk.fk_chain_destroy(chain)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,6 +174,13 @@ int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, i
 int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double radius, const float *q, int64_t n,
              int8_t *y, void *stream);
 
+/* Sets how many times a kernel polls a shared-memory tile barrier before it
+ * gives up, raises FK_ERR_TIMEOUT and exits cleanly (default 4194304 polls,
+ * about a quarter of a second).  0 makes every such wait give up at once,
+ * which exercises the timeout path without a hang.  Process-wide; not
+ * synchronised with calls in flight on other threads. */
+void fk_set_wait_limit(uint32_t polls);
+
 /* ---- pipe throughput probes --------------------------------------------
  * Measures sustained per-SM throughput of one instruction class with a
  * register-only loop on all SMs: kind 0 FP32 FMA, 1 packed FP32x2 FMA,

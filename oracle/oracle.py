@@ -25,10 +25,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _elf_matches_host(path: str) -> bool:
+    import platform
+    want = {"x86_64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(platform.machine())
+    with open(path, "rb") as fh:
+        head = fh.read(20)
+    return len(head) == 20 and head[:4] == b"\x7fELF" and (want is None or int.from_bytes(head[18:20], "little") == want)
+
+
 def build(force: bool = False) -> str:
     """Compile fk_oracle.c with gcc into oracle/_build/liboracle.so."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
+    if (not force and os.path.exists(_LIB_PATH) and _elf_matches_host(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"

@@ -38,8 +38,22 @@ def _deps():
                                + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
+def elf_matches_host(path: str) -> bool:
+    """True if the ELF file at path was built for this machine's architecture."""
+    import platform
+    want = {"x86_64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(platform.machine())
+    try:
+        with open(path, "rb") as fh:
+            head = fh.read(20)
+    except OSError:
+        return False
+    if len(head) < 20 or head[:4] != b"\x7fELF":
+        return False
+    return want is None or int.from_bytes(head[18:20], "little") == want
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not elf_matches_host(LIB):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())

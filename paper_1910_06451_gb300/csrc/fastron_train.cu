@@ -1,53 +1,81 @@
-// Fastron model update, Algorithm 1 (Sec. III-B), as one persistent CTA.
+// Fastron model update, Algorithm 1 (Sec. III-B), as one persistent
+// thread-block cluster.
 //
-// The training margins F (FP64) live in registers: thread t owns the points
-// j = t + 1024 k.  The weights alpha (FP64) live in shared memory and are only
-// ever read or written by their owner thread.  Each pass:
-//   1. every thread holds the block-wide argmin of y_j F_j and the block-wide
-//      argmax over alpha_j != 0 of y_j (F_j - alpha_j); each candidate carries
-//      its label and its alpha through the reduction, so no thread reads
-//      another thread's alpha (F_i = y_i * margin is exact for y_i = +-1);
-//   2. the add/adjust step (Eqs. 6-8) or the removal step is applied: every
-//      thread updates its F_j with row i of the stored kernel matrix (the
-//      matrix is symmetric, so row i is column i);
-//   3. the new candidates are reduced: warp shuffles, one __syncthreads, and
-//      every warp reduces the 32 warp results itself (the per-warp slots are
-//      double-buffered by pass parity, so one barrier per pass suffices).
-// Ties go to the lowest index, as in a left-to-right scan.  F and alpha are
-// updated with separately rounded products and sums, in the order of Eqs. 6-8.
-// The loop has no inter-CTA waits.
+// Ownership: the cluster has C CTAs of 256 threads; global thread
+// g = rank * 256 + tid owns the training points j = g + 256 C k.  Its
+// margins F_j (FP64) live in registers, its weights alpha_j (FP64) in its
+// CTA's shared memory (read and written only by the owner).  Each pass:
+//   1. every thread holds the same two candidates, the argmin of y_j F_j and
+//      the argmax over alpha_j != 0 of y_j (F_j - alpha_j), each with its
+//      label and alpha, and takes the same decision: add/adjust (Eqs. 6-8),
+//      removal, or stop;
+//   2. every thread updates its F_j with row i of the stored kernel matrix
+//      (symmetric, so row i is column i); the owner of i updates alpha_i;
+//   3. candidates are reduced: per thread, warp shuffles, one __syncthreads
+//      for the CTA, then warp 0 stores the CTA's pair into a slot of every
+//      CTA of the cluster (distributed shared memory) and, one cluster
+//      barrier later, every warp reduces the C slots itself.  Slots are
+//      double-buffered by pass parity, so one cluster barrier per pass
+//      suffices.
+// Comparisons run on int64 keys that order like the doubles (sign-magnitude
+// folded to two's complement, zeros made +0), so the argmin/argmax work stays
+// off the FP64 pipe, which on this part runs at 1/64 of the FP32 rate; ties
+// go to the lowest index, as in a left-to-right scan.  F and alpha are
+// updated with separately rounded FP64 products and sums, in the order of
+// Eqs. 6-8.  The cluster barrier is a hardware barrier (no polling); the loop
+// is bounded by iter_max.
+#include <cooperative_groups.h>
+
 #include <climits>
 
 #include "fk_internal.h"
 
+namespace cg = cooperative_groups;
+
 namespace fk {
 
-constexpr int kTrainThreads = 1024;
+constexpr int kTrainThreads = 256;
 constexpr int kTrainWarps = kTrainThreads / 32;
+constexpr int kMaxCluster = 16;
+constexpr long long kMag = 0x7fffffffffffffffLL;
 
 struct Cand {
-  double v;      // margin y F (argmin) or removal margin y (F - alpha) (argmax)
-  double alpha;  // alpha of the candidate
-  int i;         // index; INT_MAX if none
-  int y;         // label of the candidate
+  long long key;  // ordered key of the margin (argmin) or removal margin (argmax)
+  double alpha;   // alpha of the candidate
+  int iy;         // index | (label < 0) << 31; INT_MAX if none
 };
 
+// Order-preserving int64 image of the double with bit pattern b: for
+// non-negative values the pattern, for negative values the pattern with all
+// but the sign bit flipped.  -0.0 maps to the key of +0.0, so the two compare
+// equal, as doubles do.
+__device__ __forceinline__ long long bits_key(long long b) {
+  if ((b & kMag) == 0) return 0;
+  return b ^ ((b >> 63) & kMag);
+}
+__device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k >= 0 ? k : (k ^ kMag)); }
+__device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) & kMag) != 0; }
+
+__device__ __forceinline__ int cidx(const Cand &c) { return c.iy & 0x7fffffff; }
 __device__ __forceinline__ bool better_min(const Cand &a, const Cand &b) {
-  return a.v < b.v || (a.v == b.v && a.i < b.i);
+  return a.key < b.key || (a.key == b.key && cidx(a) < cidx(b));
 }
 __device__ __forceinline__ bool better_max(const Cand &a, const Cand &b) {
-  return a.v > b.v || (a.v == b.v && a.i < b.i);
+  return a.key > b.key || (a.key == b.key && cidx(a) < cidx(b));
 }
 
 __device__ __forceinline__ Cand shfl_cand(const Cand &c, int lane_mask) {
   Cand o;
-  o.v = __shfl_xor_sync(0xffffffffu, c.v, lane_mask);
+  o.key = __shfl_xor_sync(0xffffffffu, c.key, lane_mask);
   o.alpha = __shfl_xor_sync(0xffffffffu, c.alpha, lane_mask);
-  o.i = __shfl_xor_sync(0xffffffffu, c.i, lane_mask);
-  o.y = __shfl_xor_sync(0xffffffffu, c.y, lane_mask);
+  o.iy = __shfl_xor_sync(0xffffffffu, c.iy, lane_mask);
   return o;
 }
 
+// Full 32-lane butterfly: afterwards every lane holds the best candidate of
+// the whole warp.  (Every decision below must be identical in every thread of
+// the cluster, because every thread then meets the same barriers; a narrower
+// butterfly would leave the upper lanes with a different answer.)
 __device__ __forceinline__ void warp_reduce(Cand &mn, Cand &mx) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -57,101 +85,144 @@ __device__ __forceinline__ void warp_reduce(Cand &mn, Cand &mx) {
   }
 }
 
-__device__ __forceinline__ int block_sum(int v, int *tot, int lane, int warp) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) tot[warp] = v;
-  __syncthreads();
-  int t = tot[lane];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  __syncthreads();
-  return t;
-}
+__device__ __forceinline__ Cand no_min() { return {LLONG_MAX, 0.0, INT_MAX}; }
+__device__ __forceinline__ Cand no_max() { return {LLONG_MIN, 0.0, INT_MAX}; }
+
+struct TrainShared {
+  Cand slot_min[2][kMaxCluster], slot_max[2][kMaxCluster];
+  Cand wmin[kTrainWarps], wmax[kTrainWarps];
+  int slot_cnt[kMaxCluster], wcnt[kTrainWarps];
+};
 
 template <int KMAX>
 __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const TrainArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ Cand slot_min[2][kTrainWarps], slot_max[2][kTrainWarps];
-  __shared__ int tot[kTrainWarps];
-  double *alpha = reinterpret_cast<double *>(smem_raw);  // [N], owner-private entries
+  __shared__ TrainShared sh;
+  double *alpha = reinterpret_cast<double *>(smem_raw);  // [KMAX][kTrainThreads], owner-private
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int stride = kTrainThreads * C;
+  const int g = rank * kTrainThreads + tid;
   const int N = (int)a.N;
+
   double F[KMAX];
-  int yv[KMAX];
+  int yneg[KMAX];
   int nnz_local = 0;
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
-    const int j = tid + kTrainThreads * k;
+    const int j = g + stride * k;
     F[k] = 0.0;
-    yv[k] = 1;
+    yneg[k] = 0;
+    double aj = 0.0;
     if (j < N) {
       F[k] = a.F[j];
-      yv[k] = a.y[j] > 0 ? 1 : -1;
-      alpha[j] = a.alpha[j];
-      nnz_local += a.alpha[j] != 0.0;
+      yneg[k] = a.y[j] > 0 ? 0 : 1;
+      aj = a.alpha[j];
+      nnz_local += nonzero(aj);
     }
+    alpha[k * kTrainThreads + tid] = aj;
   }
-  // |{alpha != 0}|, identical in every thread and updated uniformly below.
-  int64_t nnz = block_sum(nnz_local, tot, lane, warp);
+  cluster.sync();  // every CTA of the cluster is running before any remote store
+
+  // |{alpha != 0}| over the cluster: identical in every thread afterwards and
+  // updated uniformly by the decisions below.
+  long long nnz;
+  {
+    int w = nnz_local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) sh.wcnt[warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+      int t = lane < kTrainWarps ? sh.wcnt[lane] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane < C) *cluster.map_shared_rank(&sh.slot_cnt[rank], lane) = t;
+    }
+    cluster.sync();
+    int t = lane < C ? sh.slot_cnt[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    nnz = t;
+  }
 
   int parity = 0;
-  auto reduce_candidates = [&](Cand &mn, Cand &mx) {
-    mn = {INFINITY, 0.0, INT_MAX, 1};
-    mx = {-INFINITY, 0.0, INT_MAX, 1};
+  Cand mn, mx;
+  auto local_candidates = [&]() {
+    mn = no_min();
+    mx = no_max();
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-      const int j = tid + kTrainThreads * k;
+      const int j = g + stride * k;
       if (j < N) {
-        const double aj = alpha[j];
-        const double m = yv[k] > 0 ? F[k] : -F[k];
-        if (m < mn.v) mn = {m, aj, j, yv[k]};  // j ascends within a thread
-        if (aj != 0.0) {
-          const double d = __dsub_rn(F[k], aj);
-          const double r = yv[k] > 0 ? d : -d;
-          if (r > mx.v) mx = {r, aj, j, yv[k]};
+        const long long sign = (long long)yneg[k] << 63;
+        const int iy = j | (yneg[k] << 31);
+        const double aj = alpha[k * kTrainThreads + tid];
+        const long long km = bits_key(__double_as_longlong(F[k]) ^ sign);  // key of y_j F_j
+        if (km < mn.key) mn = {km, aj, iy};  // j ascends within a thread
+        if (nonzero(aj)) {
+          const long long kr = bits_key(__double_as_longlong(__dsub_rn(F[k], aj)) ^ sign);
+          if (kr > mx.key) mx = {kr, aj, iy};
         }
       }
     }
+  };
+  auto reduce_cluster = [&]() {
     warp_reduce(mn, mx);
     if (lane == 0) {
-      slot_min[parity][warp] = mn;
-      slot_max[parity][warp] = mx;
+      sh.wmin[warp] = mn;
+      sh.wmax[warp] = mx;
     }
     __syncthreads();
-    mn = slot_min[parity][lane];
-    mx = slot_max[parity][lane];
+    if (warp == 0) {
+      mn = lane < kTrainWarps ? sh.wmin[lane] : no_min();
+      mx = lane < kTrainWarps ? sh.wmax[lane] : no_max();
+      warp_reduce(mn, mx);
+      if (lane < C) {
+        *cluster.map_shared_rank(&sh.slot_min[parity][rank], lane) = mn;
+        *cluster.map_shared_rank(&sh.slot_max[parity][rank], lane) = mx;
+      }
+    }
+    cluster.sync();
+    mn = lane < C ? sh.slot_min[parity][lane] : no_min();
+    mx = lane < C ? sh.slot_max[parity][lane] : no_max();
     warp_reduce(mn, mx);
     parity ^= 1;
   };
 
-  Cand mn, mx;
-  reduce_candidates(mn, mx);
-  int64_t iters = 0, adds = 0, removes = 0;
+  local_candidates();
+  reduce_cluster();
+  long long iters = 0, adds = 0, removes = 0;
   int converged = 0;
-  for (int64_t iter = 1; iter <= a.iter_max; ++iter) {
-    int i = -1, kind = 0;
-    double coef = 0.0, delta = 0.0;
-    if (mn.i != INT_MAX && mn.v <= 0.0 && (nnz < a.s_max || mn.alpha != 0.0)) {
-      // add / adjust support point i (Eqs. 6-8)
-      i = mn.i;
+  for (long long iter = 1; iter <= a.iter_max; ++iter) {
+    int kind, i;
+    double coef, delta;
+    if (cidx(mn) != INT_MAX && mn.key <= 0 && (nnz < a.s_max || nonzero(mn.alpha))) {
+      // add / adjust support point i: delta = b_i y_i - F_i (Eq. 6)
       kind = 1;
-      const double Fi = mn.y > 0 ? mn.v : -mn.v;
-      const double by = mn.y > 0 ? a.beta : -1.0;  // b_i y_i, b_i = beta^(0.5 (y_i + 1))
+      i = cidx(mn);
+      const bool yn = mn.iy < 0;
+      const double m = key_value(mn.key);  // y_i F_i
+      const double Fi = yn ? -m : m;
+      const double by = yn ? -1.0 : a.beta;  // b_i y_i with b_i = beta^(0.5 (y_i + 1))
       delta = __dsub_rn(by, Fi);
       coef = delta;
-      const double anew = __dadd_rn(mn.alpha, delta);
-      nnz += (anew != 0.0) - (mn.alpha != 0.0);
-      if ((i & (kTrainThreads - 1)) == tid) alpha[i] = anew;
+      const double anew = __dadd_rn(mn.alpha, delta);  // Eq. 7
+      nnz += (long long)nonzero(anew) - (long long)nonzero(mn.alpha);
+      const int gi = i % stride;
+      if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = anew;
       ++adds;
-    } else if (mx.i != INT_MAX && mx.v > 0.0) {
-      // remove redundant support point i
-      i = mx.i;
+    } else if (cidx(mx) != INT_MAX && mx.key > 0) {
+      // remove the redundant support point i
       kind = 2;
-      coef = -mx.alpha;
+      i = cidx(mx);
+      coef = mx.alpha;
       delta = -mx.alpha;
-      if ((i & (kTrainThreads - 1)) == tid) alpha[i] = 0.0;
+      const int gi = i % stride;
+      if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = 0.0;
       --nnz;
       ++removes;
     } else {
@@ -159,80 +230,126 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       break;
     }
     ++iters;
-    if (tid == 0 && a.trace_kind) {
+    if (rank == 0 && tid == 0 && a.trace_kind) {
       a.trace_kind[iter - 1] = (int8_t)kind;
       a.trace_idx[iter - 1] = i;
       a.trace_delta[iter - 1] = delta;
     }
-    const double *row = a.G + (int64_t)i * N;
+    const double *row = a.G + (long long)i * N;
+    double gk[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-      const int j = tid + kTrainThreads * k;
-      if (j < N) {
-        const double g = row[j];
-        // F += delta K e_i (add) or F -= alpha_i K e_i (removal)
-        F[k] = kind == 1 ? __dadd_rn(F[k], __dmul_rn(coef, g)) : __dsub_rn(F[k], __dmul_rn(mx.alpha, g));
-      }
+      const int j = g + stride * k;
+      gk[k] = j < N ? row[j] : 0.0;
     }
-    reduce_candidates(mn, mx);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal)
+      const double p = __dmul_rn(coef, gk[k]);
+      F[k] = kind == 1 ? __dadd_rn(F[k], p) : __dsub_rn(F[k], p);
+    }
+    local_candidates();
+    reduce_cluster();
   }
 
-  // write back alpha and F (warm starts reuse them)
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
-    const int j = tid + kTrainThreads * k;
+    const int j = g + stride * k;
     if (j < N) {
       a.F[j] = F[k];
-      a.alpha[j] = alpha[j];
+      a.alpha[j] = alpha[k * kTrainThreads + tid];
     }
   }
-  // removeNonsupportPoints: ascending indices with alpha != 0
+  if (rank == 0 && tid == 0) {
+    a.stats[0] = iters;
+    a.stats[1] = adds;
+    a.stats[2] = removes;
+    a.stats[3] = converged;
+  }
+  cluster.sync();  // no CTA leaves while a remote store into it could be pending
+}
+
+// removeNonsupportPoints: ascending indices with alpha != 0, one CTA.
+constexpr int kCompactThreads = 1024;
+
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(const double *__restrict__ alpha, int N,
+                                                                 int32_t *__restrict__ sup_idx,
+                                                                 double *__restrict__ sup_alpha,
+                                                                 int64_t *__restrict__ stats) {
+  __shared__ int tot[kCompactThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int base = 0;
-  for (int c0 = 0; c0 < N; c0 += kTrainThreads) {
+  for (int c0 = 0; c0 < N; c0 += kCompactThreads) {
     const int j = c0 + tid;
-    const bool keep = j < N && alpha[j] != 0.0;
+    const double aj = j < N ? alpha[j] : 0.0;
+    const bool keep = nonzero(aj);
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) tot[warp] = __popc(bal);
     __syncthreads();
     int before = 0, total = 0;
-    for (int w = 0; w < kTrainWarps; ++w) {
+    for (int w = 0; w < kCompactThreads / 32; ++w) {
       const int t = tot[w];
       before += w < warp ? t : 0;
       total += t;
     }
     if (keep) {
       const int pos = base + before + __popc(bal & ((1u << lane) - 1u));
-      a.sup_idx[pos] = j;
-      a.sup_alpha[pos] = alpha[j];
+      sup_idx[pos] = j;
+      sup_alpha[pos] = aj;
     }
     base += total;
     __syncthreads();
   }
-  if (tid == 0) {
-    a.stats[0] = iters;
-    a.stats[1] = adds;
-    a.stats[2] = removes;
-    a.stats[3] = converged;
-    a.stats[4] = base;
-  }
+  if (tid == 0) stats[4] = base;
 }
 
 template <int KMAX>
-static cudaError_t launch_k(const TrainArgs &a, cudaStream_t s) {
-  const size_t smem = sizeof(double) * (size_t)a.N;
-  cudaError_t e =
-      cudaFuncSetAttribute(fastron_train_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t launch_k(const TrainArgs &a, int C, cudaStream_t s) {
+  auto kern = fastron_train_kernel<KMAX>;
+  const size_t smem = sizeof(double) * KMAX * kTrainThreads;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  fastron_train_kernel<KMAX><<<1, kTrainThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kTrainThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorLaunchOutOfResources;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+static cudaError_t launch_c(const TrainArgs &a, int C, cudaStream_t s) {
+  const int64_t per = (int64_t)kTrainThreads * C;
+  const int64_t kneed = (a.N + per - 1) / per;
+  if (kneed <= 1) return launch_k<1>(a, C, s);
+  if (kneed <= 2) return launch_k<2>(a, C, s);
+  if (kneed <= 4) return launch_k<4>(a, C, s);
+  if (kneed <= 8) return launch_k<8>(a, C, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s) {
-  if (a.N <= 1 * kTrainThreads) return launch_k<1>(a, s);
-  if (a.N <= 2 * kTrainThreads) return launch_k<2>(a, s);
-  if (a.N <= 4 * kTrainThreads) return launch_k<4>(a, s);
-  if (a.N <= 8 * kTrainThreads) return launch_k<8>(a, s);
-  return cudaErrorInvalidValue;
+  // as many CTAs as the points need (at least 2 per thread below 16 CTAs)
+  int C = 1;
+  while (C < kMaxCluster && (int64_t)kTrainThreads * C * 2 < a.N) C *= 2;
+  cudaError_t e = launch_c(a, C, s);
+  if (e != cudaSuccess && C > 8) {
+    cudaGetLastError();  // the non-portable size may be unavailable: fall back to 8
+    e = launch_c(a, 8, s);
+  }
+  if (e != cudaSuccess) return e;
+  compact_kernel<<<1, kCompactThreads, 0, s>>>(a.alpha, (int)a.N, a.sup_idx, a.sup_alpha, a.stats);
+  return cudaGetLastError();
 }
 
 }  // namespace fk

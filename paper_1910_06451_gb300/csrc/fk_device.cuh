@@ -34,7 +34,8 @@ struct ChainF {
 // with separately rounded products and sums in a fixed order (no fused
 // multiply-add), so that its rounding is that of the plain 4x4 product.
 struct ChainD {
-  int D, M;
+  int D, M, Mv, n_const;
+  int vidx[FK_MAX_CP];          // indices of the configuration-dependent points
   int type[FK_MAX_DOF];
   double a[FK_MAX_DOF], ca[FK_MAX_DOF], sa[FK_MAX_DOF], d[FK_MAX_DOF], th0[FK_MAX_DOF];
   double T0[12];                // rows 0..2 of the base transform
@@ -147,13 +148,26 @@ __device__ __forceinline__ void pose_point(const PoseD &P, const double t[3], do
                        P.T[4 * r + 3]);
 }
 
-// RQ summand of Eq. 3 in FP64: 1 / (t * t) with t = 1 + (gamma/2) |x - x'|^2,
-// with the squared distance summed over x, y, z in order.
+// FP64 reciprocal of x in [1, 2^100]: an FP32 MUFU estimate (relative error
+// about 2^-23) refined by two Newton-Raphson steps y <- y + y (1 - x y),
+// each of which squares the relative error; the result is within an ulp or
+// so of 1/x.  It replaces the IEEE division, which is a long instruction
+// sequence on a part whose FP64 rate is 1/64 of its FP32 rate.
+__device__ __forceinline__ double rcp_f64(double x) {
+  float xf = __double2float_rn(x), yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+  double y = (double)yf;
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// RQ summand of Eq. 3 in FP64: (1 + (gamma/2) |x - x'|^2)^-2.
 __device__ __forceinline__ double k_rq_f64(double hg, const double *x, const double *xp) {
-  const double d0 = __dsub_rn(x[0], xp[0]), d1 = __dsub_rn(x[1], xp[1]), d2 = __dsub_rn(x[2], xp[2]);
-  const double s = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-  const double t = __dadd_rn(1.0, __dmul_rn(hg, s));
-  return __ddiv_rn(1.0, __dmul_rn(t, t));
+  const double d0 = x[0] - xp[0], d1 = x[1] - xp[1], d2 = x[2] - xp[2];
+  const double t = fma(hg, fma(d0, d0, fma(d1, d1, d2 * d2)), 1.0);
+  return rcp_f64(t * t);
 }
 
 }  // namespace fk

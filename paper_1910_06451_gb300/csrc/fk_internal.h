@@ -18,9 +18,11 @@ cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t
 
 // Kernel matrix from SoA control points (all M points).  sym != 0 requires
 // cpa == cpb and na == nb and fills only the upper tiles, mirroring them.
-cudaError_t launch_gram_f64(int M, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
-                            int sym, double *K, cudaStream_t s);
-cudaError_t launch_gram_f32(int M, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
+// Summands of control points fixed to the base frame are exactly 1 and are
+// added without evaluation.
+cudaError_t launch_gram_f64(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
+                            int64_t nb, int sym, double *K, cudaStream_t s);
+cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
                             int sym, float *K, cudaStream_t s);
 
 // Fastron Algorithm 1 on a stored FP64 kernel matrix G [N][N].
@@ -41,6 +43,13 @@ struct TrainArgs {
 };
 cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s);
 
+// float4 entries of one support-pair record of the FP32 score: for each of
+// the Mv configuration-dependent control points (x_a, x_b, y_a, y_b), then
+// the z coordinates two points at a time (z_a, z_b, z_a', z_b'), then the
+// weights (w_a, w_b, |w_a|, |w_b|) with w = alpha / M; coordinates are scaled
+// by sqrt(gamma / 2).
+__host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 1; }
+
 // Packs a support set for scoring: gathers X[idx[s]] (FP64 configurations,
 // idx may be null for identity), computes their FP64 control points and
 // writes the FP32 score records and the FP64 SoA control points.
@@ -50,7 +59,7 @@ struct PackArgs {
   const double *alpha;
   int64_t ns;
   double gamma;
-  float4 *rec;        // [ns][Mv + 1]
+  float4 *rec;        // [(ns + 1) / 2][rec_len(Mv)]
   double *cp64;       // SoA [M][3][ns]
   double *alpha_out;  // [ns] (copy of alpha, compacted)
   double *q_out;      // [ns][D] support configurations
@@ -63,13 +72,14 @@ struct ScoreArgs {
   int64_t n;
   const float4 *rec;
   int64_t ns;
-  float hg;           // gamma / 2
+  float gs;           // sqrt(gamma / 2): scale of the control points
   float eps;          // band: |f| <= eps * B(q)
   float *f;           // [n] or null
   int8_t *label;      // [n]
   int32_t *band_idx;  // [n] or null (no rescore)
   int32_t *band_cnt;  // [1]
   int32_t *err;       // [1]
+  uint32_t wait_limit;  // polls of a tile wait before it gives up
 };
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
 

@@ -79,19 +79,28 @@ cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t
 
 constexpr int kGT = 32;
 
-__device__ __forceinline__ double gram_entry(int M, double hg, const double *A, const double *B, int ia, int jb) {
-  double s = 0.0;
-  for (int m = 0; m < M; ++m) {
+struct GramCps {
+  int M, Mv, n_const;
+  int vidx[FK_MAX_CP];
+};
+
+__device__ __forceinline__ double gram_entry(const GramCps &g, double hg, const double *A, const double *B, int ia,
+                                             int jb) {
+  double s = (double)g.n_const;
+  for (int v = 0; v < g.Mv; ++v) {
+    const int m = g.vidx[v];
     const double x[3] = {A[(m * 3 + 0) * kGT + ia], A[(m * 3 + 1) * kGT + ia], A[(m * 3 + 2) * kGT + ia]};
     const double y[3] = {B[(m * 3 + 0) * kGT + jb], B[(m * 3 + 1) * kGT + jb], B[(m * 3 + 2) * kGT + jb]};
-    s = __dadd_rn(s, k_rq_f64(hg, x, y));
+    s += k_rq_f64(hg, x, y);
   }
-  return __ddiv_rn(s, (double)M);
+  return s / (double)g.M;
 }
 
-__device__ __forceinline__ float gram_entry(int M, float hg, const float *A, const float *B, int ia, int jb) {
-  float s = 0.f;
-  for (int m = 0; m < M; ++m) {
+__device__ __forceinline__ float gram_entry(const GramCps &g, float hg, const float *A, const float *B, int ia,
+                                            int jb) {
+  float s = (float)g.n_const;
+  for (int v = 0; v < g.Mv; ++v) {
+    const int m = g.vidx[v];
     const float d0 = A[(m * 3 + 0) * kGT + ia] - B[(m * 3 + 0) * kGT + jb];
     const float d1 = A[(m * 3 + 1) * kGT + ia] - B[(m * 3 + 1) * kGT + jb];
     const float d2 = A[(m * 3 + 2) * kGT + ia] - B[(m * 3 + 2) * kGT + jb];
@@ -99,17 +108,18 @@ __device__ __forceinline__ float gram_entry(int M, float hg, const float *A, con
     const float r = 1.f / t;
     s = fmaf(r, r, s);
   }
-  return s / (float)M;
+  return s / (float)g.M;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_kernel(int M, T hg, const T *__restrict__ cpa, int64_t na,
+__global__ void __launch_bounds__(256) gram_kernel(const GramCps g, T hg, const T *__restrict__ cpa, int64_t na,
                                                    const T *__restrict__ cpb, int64_t nb, int sym,
                                                    T *__restrict__ K) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *A = reinterpret_cast<T *>(smem_raw);
+  const int M = g.M;
   T *B = A + M * 3 * kGT;
   T *O = B + M * 3 * kGT;  // [kGT][kGT + 1] output tile for the transposed write
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -124,7 +134,7 @@ __global__ void __launch_bounds__(256) gram_kernel(int M, T hg, const T *__restr
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int il = ty + 8 * r;
-    const T v = gram_entry(M, hg, A, B, il, tx);
+    const T v = gram_entry(g, hg, A, B, il, tx);
     if (i0 + il < na && j0 + tx < nb) K[(i0 + il) * nb + j0 + tx] = v;
     if (mirror) O[il * (kGT + 1) + tx] = v;
   }
@@ -139,27 +149,30 @@ __global__ void __launch_bounds__(256) gram_kernel(int M, T hg, const T *__restr
 }
 
 template <typename T>
-static cudaError_t launch_gram(int M, T gamma, const T *cpa, int64_t na, const T *cpb, int64_t nb, int sym, T *K,
-                               cudaStream_t s) {
+static cudaError_t launch_gram(const ChainD &c, T gamma, const T *cpa, int64_t na, const T *cpb, int64_t nb, int sym,
+                               T *K, cudaStream_t s) {
   if (na <= 0 || nb <= 0) return cudaSuccess;
+  GramCps g{c.M, c.Mv, c.n_const, {}};
+  for (int v = 0; v < c.Mv; ++v) g.vidx[v] = c.vidx[v];
+  const int M = c.M;
   const size_t smem = sizeof(T) * (2 * (size_t)M * 3 * kGT + kGT * (kGT + 1));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(grid_for(nb, kGT), grid_for(na, kGT));
-  gram_kernel<T><<<grid, 256, smem, s>>>(M, T(0.5) * gamma, cpa, na, cpb, nb, sym, K);
+  gram_kernel<T><<<grid, 256, smem, s>>>(g, T(0.5) * gamma, cpa, na, cpb, nb, sym, K);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_f64(int M, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
-                            int sym, double *K, cudaStream_t s) {
-  return launch_gram<double>(M, gamma, cpa, na, cpb, nb, sym, K, s);
+cudaError_t launch_gram_f64(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
+                            int64_t nb, int sym, double *K, cudaStream_t s) {
+  return launch_gram<double>(c, gamma, cpa, na, cpb, nb, sym, K, s);
 }
 
-cudaError_t launch_gram_f32(int M, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
+cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
                             int sym, float *K, cudaStream_t s) {
-  return launch_gram<float>(M, gamma, cpa, na, cpb, nb, sym, K, s);
+  return launch_gram<float>(c, gamma, cpa, na, cpb, nb, sym, K, s);
 }
 
 }  // namespace fk

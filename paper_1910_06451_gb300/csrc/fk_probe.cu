@@ -31,7 +31,7 @@ __global__ void probe_kernel(int iters, long long *rec, float *sink) {
           if (KIND == 0)
             asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(x[c]) : "f"(b), "f"(cc));
           else
-            asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+            asm volatile("rcp.approx.ftz.f32 %0, %0;\n\tadd.f32 %0, %0, %1;" : "+f"(x[c]) : "f"(cc));
         }
     }
 #pragma unroll

@@ -105,8 +105,8 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
   ChainD &d = c->cd;
   f.D = d.D = D;
   f.M = d.M = M;
-  f.Mv = mv;
-  f.n_const = nconst;
+  f.Mv = d.Mv = mv;
+  f.n_const = d.n_const = nconst;
   for (int i = 0; i < D; ++i) {
     const double ca = cos(dh[i].alpha), sa = sin(dh[i].alpha);
     d.type[i] = f.type[i] = dh[i].type;
@@ -135,7 +135,7 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
     }
     if (cps[m].joint != 0) {
       f.vj[v] = cps[m].joint;
-      f.vidx[v] = m;
+      f.vidx[v] = d.vidx[v] = m;
       for (int r = 0; r < 3; ++r) f.vt[v][r] = (float)cps[m].t[r];
       ++v;
     }
@@ -189,19 +189,23 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
     double *A = c->ws_a.as<double>(), *B = sym ? A : c->ws_b.as<double>();
     CK(launch_fk_forward_f64(c->cd, (const double *)Xa, na, A, s));
     if (!sym) CK(launch_fk_forward_f64(c->cd, (const double *)Xb, nb, B, s));
-    CK(launch_gram_f64(c->M, gamma, A, na, B, nb, sym, (double *)K, s));
+    CK(launch_gram_f64(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
   } else {
     float *A = c->ws_a.as<float>(), *B = sym ? A : c->ws_b.as<float>();
     CK(launch_fk_forward_f32(c->cf, (const float *)Xa, na, A, s));
     if (!sym) CK(launch_fk_forward_f32(c->cf, (const float *)Xb, nb, B, s));
-    CK(launch_gram_f32(c->M, (float)gamma, A, na, B, nb, sym, (float *)K, s));
+    CK(launch_gram_f32(c->cd, (float)gamma, A, na, B, nb, sym, (float *)K, s));
   }
   return FK_OK;
 }
 
 // -------------------------------------------------------------- model ---
 static constexpr int64_t kMaxTrainN = 8192;
-static constexpr double kDefaultEps = 2e-6;
+static constexpr double kDefaultEps = 6e-6;
+static constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // about a quarter second of polling
+static uint32_t g_wait_limit = kDefaultWaitLimit;
+
+extern "C" void fk_set_wait_limit(uint32_t polls) { g_wait_limit = polls; }
 
 struct fastron_model {
   const fk_chain *chain = nullptr;
@@ -244,7 +248,7 @@ extern "C" void fastron_model_destroy(fastron_model_t *m) {
 static int pack(fastron_model *m, const double *X, const int32_t *idx, const double *alpha, int64_t ns, double gamma,
                 cudaStream_t s) {
   const fk_chain *c = m->chain;
-  CK(m->rec.ensure(sizeof(float4) * (size_t)(ns > 0 ? ns : 1) * (c->cf.Mv + 1)));
+  CK(m->rec.ensure(sizeof(float4) * (size_t)((ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1) * rec_len(c->cf.Mv)));
   CK(m->cp64.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->M * 3));
   CK(m->alpha_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
@@ -291,7 +295,7 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   }
   m->N = N;
   CK(launch_fk_forward_f64(c->cd, X, N, m->cpX.as<double>(), s));
-  CK(launch_gram_f64(c->M, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
+  CK(launch_gram_f64(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
   TrainArgs ta{m->G.as<double>(), y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
                m->stats.as<int64_t>(), m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(),
                trace ? m->trace_kind.as<int8_t>() : nullptr, trace ? m->trace_idx.as<int32_t>() : nullptr,
@@ -392,8 +396,8 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
   const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
-  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)(0.5 * m->gamma), (float)eps, f, label,
-               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err};
+  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
+               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit};
   CK(launch_score_f32(c->cf, sa, s));
   if (rescore) {
     RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,

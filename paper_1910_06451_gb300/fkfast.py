@@ -29,7 +29,7 @@ FK_MAX_CP = 32
 EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
-    "fastron_model_set", "fastron_model_get", "fk_score", "fk_label", "fk_probe_pipe",
+    "fastron_model_set", "fastron_model_get", "fk_score", "fk_label", "fk_set_wait_limit", "fk_probe_pipe",
 )
 
 
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = False):
             "fastron_model_get": ([P, P, P, I64, P], I),
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
+            "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -267,6 +268,10 @@ def fk_label(chain, boxes, radius, q, y, stream=None):
     n = q.shape[0]
     _check(load().fk_label(chain, bp, bx.shape[0], float(radius), _dev(q, torch.float32, "q"), n,
                            _dev(y, torch.int8, "y", (n,)), _stream(stream)))
+
+
+def fk_set_wait_limit(polls: int):
+    load().fk_set_wait_limit(int(polls))
 
 
 def fk_probe_pipe(kind: int):

@@ -1,0 +1,275 @@
+"""Parity of the CUDA library against the FP64 oracle, element by element,
+through the C ABI.  Tolerances:
+
+  control points (FP32)   |dp| <= 1e-5 * max(|p|, reach)
+  control points (FP64)   |dp| <= 1e-13
+  kernel matrix (FP64)    |dK| <= 1e-14;  (FP32) |dK| <= 2e-6
+  score (FP32, tier 1)    |df| <= 1e-4 * sum|alpha|   and   |df| <= eps/2 * B(q),
+                          B(q) = sum_s |alpha_s| K_FK(S_s, q), eps the re-score band
+  labels after re-score   identical
+  training                support set, pass sequence identical; alpha within 1e-12 relative
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1910_06451_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+EPS_BAND = 6e-6  # the library's default re-score band
+
+
+def _reach(arm):
+    return float(np.sum(np.hypot(arm.dh[:, 0], arm.dh[:, 2])))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def arm3(fk):
+    w = synth.workload("arm3-n1000")
+    ch = fk.chain_from_arm(w.scene.arm)
+    yield w, ch
+    fk.fk_chain_destroy(ch)
+
+
+@pytest.fixture(scope="module")
+def arm7(fk):
+    w = synth.workload("arm7-n5000")
+    ch = fk.chain_from_arm(w.scene.arm)
+    yield w, ch
+    fk.fk_chain_destroy(ch)
+
+
+def _cp_soa_to_aos(cp):
+    return cp.permute(2, 0, 1).cpu().numpy()  # (M, 3, n) -> (n, M, 3)
+
+
+@pytest.mark.parametrize("n", [1, 31, 257, 10001])
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_fk_forward(fk, arm3, arm7, dev, n, which):
+    w, ch = arm3 if which == "arm3" else arm7
+    arm = w.scene.arm
+    q = w.query_configs(n)
+    want = O.fk_points(arm, q.astype(np.float64))
+    cp32 = torch.empty((arm.M, 3, n), dtype=torch.float32, device=dev)
+    fk.fk_forward(ch, torch.from_numpy(q).to(dev), cp32)
+    cp64 = torch.empty((arm.M, 3, n), dtype=torch.float64, device=dev)
+    fk.fk_forward_f64(ch, torch.from_numpy(q.astype(np.float64)).to(dev), cp64)
+    got32, got64 = _cp_soa_to_aos(cp32), _cp_soa_to_aos(cp64)
+    scale = np.maximum(np.linalg.norm(want, axis=2, keepdims=True), _reach(arm))
+    assert np.all(np.abs(got32 - want) <= 1e-5 * scale)
+    assert np.max(np.abs(got64 - want)) <= 1e-13
+
+
+@pytest.mark.parametrize("na,nb", [(77, 77), (1000, 1000), (50, 33), (1, 5)])
+def test_gram(fk, arm3, dev, na, nb):
+    w, ch = arm3
+    arm = w.scene.arm
+    Xa = w.train_configs()[:na].astype(np.float64)
+    Xb = Xa if na == nb else w.query_configs(nb).astype(np.float64)
+    want = O.gram(O.fk_points(arm, Xa), O.fk_points(arm, Xb), w.gamma)
+    ta = torch.from_numpy(Xa).to(dev)
+    tb = ta if na == nb else torch.from_numpy(Xb).to(dev)
+    K = torch.empty((na, nb), dtype=torch.float64, device=dev)
+    fk.fk_gram(ch, ta, tb, w.gamma, K)
+    got = K.cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-14
+    if na == nb:
+        assert np.array_equal(got, got.T)
+        assert np.all(np.diag(got) == 1.0)
+    K32 = torch.empty((na, nb), dtype=torch.float32, device=dev)
+    t32a = ta.float()
+    fk.fk_gram(ch, t32a, t32a if na == nb else tb.float(), w.gamma, K32)
+    assert np.max(np.abs(K32.cpu().numpy() - want)) <= 2e-6
+
+
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_labels(fk, arm3, arm7, dev, which):
+    w, ch = arm3 if which == "arm3" else arm7
+    q = w.query_configs(20000)
+    want = O.check(w.scene, q.astype(np.float64))
+    y = torch.empty(20000, dtype=torch.int8, device=dev)
+    fk.fk_label(ch, w.scene.boxes, w.scene.radius, torch.from_numpy(q).to(dev), y)
+    got = y.cpu().numpy()
+    assert np.array_equal(got, want)
+    assert 0 < np.sum(want == 1) < len(want)
+
+
+def _train_both(fk, w, ch, dev, n=None, beta=None):
+    X = w.train_configs()[:n].astype(np.float64)
+    y = O.check(w.scene, X)
+    beta = w.beta if beta is None else beta
+    r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, beta, w.iter_max, w.s_max, trace=True)
+    m = fk.fastron_model_create(ch)
+    st = fk.fastron_train(m, torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev), w.gamma, beta,
+                          w.iter_max, w.s_max, trace=True)
+    return X, y, r, m, st
+
+
+@pytest.mark.parametrize("which,n,beta", [("arm3", 1000, 1.0), ("arm3", 1000, 1.5), ("arm3", 333, 1.0),
+                                          ("arm7", 5000, 1.0)])
+def test_fastron_train_matches_oracle(fk, arm3, arm7, dev, which, n, beta):
+    w, ch = arm3 if which == "arm3" else arm7
+    X, y, r, m, st = _train_both(fk, w, ch, dev, n, beta)
+    try:
+        assert st["iterations"] == r.iters and st["adds"] == r.adds and st["removes"] == r.removes
+        assert st["converged"] == r.converged and st["n_support"] == r.n_support
+        kind, idx, delta = fk.fastron_model_trace(m, r.iters + 1)
+        assert np.array_equal(kind, r.trace[0]) and np.array_equal(idx, r.trace[1])
+        np.testing.assert_allclose(delta, r.trace[2], rtol=1e-12, atol=1e-12)
+        gidx, galpha = fk.fastron_model_get(m)
+        assert np.array_equal(gidx, r.support)
+        np.testing.assert_allclose(galpha, r.alpha[r.support], rtol=1e-12)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
+def test_fastron_train_limits_and_warm_start(fk, arm3, dev):
+    w, ch = arm3
+    X = w.train_configs()[:400].astype(np.float64)
+    y = O.check(w.scene, X)
+    cp = O.fk_points(w.scene.arm, X)
+    tX, ty = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    m = fk.fastron_model_create(ch)
+    try:
+        for it, smax in ((7, 400), (5000, 6)):
+            r = O.fastron_train(cp, y, w.gamma, 1.0, it, smax)
+            st = fk.fastron_train(m, tX, ty, w.gamma, 1.0, it, smax)
+            assert (st["iterations"], st["n_support"], st["converged"]) == (r.iters, r.n_support, r.converged)
+            assert np.array_equal(fk.fastron_model_get(m)[0], r.support)
+        # warm start continues from the last alpha and F (loadPreviousModel)
+        r1 = O.fastron_train(cp, y, w.gamma, 1.0, 9)
+        r2 = O.fastron_train(cp, y, w.gamma, 1.0, 5000, alpha0=r1.alpha, F0=r1.F)
+        fk.fastron_train(m, tX, ty, w.gamma, 1.0, 9)
+        st = fk.fastron_train(m, tX, ty, w.gamma, 1.0, 5000, warm_start=True)
+        assert st["iterations"] == r2.iters and np.array_equal(fk.fastron_model_get(m)[0], r2.support)
+        st = fk.fastron_train(m, tX, ty, w.gamma, 1.0, 5000, warm_start=True)
+        assert st["iterations"] == 0 and st["converged"]
+        with pytest.raises(fk.FkError):
+            fk.fastron_train(m, tX[:10], ty[:10], w.gamma, 1.0, 10, warm_start=True)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
+def _score_case(fk, w, ch, dev, S, alpha, Q):
+    arm = w.scene.arm
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, alpha, w.gamma)
+        n = Q.shape[0]
+        tq = torch.from_numpy(Q).to(dev)
+        f_raw = torch.empty(n, dtype=torch.float32, device=dev)
+        lab_raw = torch.empty(n, dtype=torch.int8, device=dev)
+        fk.fk_score(m, tq, lab_raw, f_raw, rescore=False)
+        f = torch.empty(n, dtype=torch.float32, device=dev)
+        lab = torch.empty(n, dtype=torch.int8, device=dev)
+        nres = fk.fk_score(m, tq, lab, f, rescore=True, count=True)
+        torch.cuda.synchronize()
+    finally:
+        fk.fastron_model_destroy(m)
+    Qd = Q.astype(np.float64)
+    cps, cpq = O.fk_points(arm, S), O.fk_points(arm, Qd)
+    want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
+    B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=8)
+    return f_raw.cpu().numpy(), lab_raw.cpu().numpy(), f.cpu().numpy(), lab.cpu().numpy(), nres, want, B
+
+
+def _check_score(f_raw, lab_raw, f, lab, nres, want, B, alpha):
+    sa = np.sum(np.abs(alpha))
+    err = np.abs(f_raw.astype(np.float64) - want)
+    assert np.all(err <= 1e-4 * sa + 1e-30)
+    assert np.all(err <= 0.5 * EPS_BAND * B + 1e-30), np.max(err / np.maximum(B, 1e-300))
+    assert np.array_equal(lab_raw == 1, f_raw >= 0)
+    assert np.array_equal(lab, O.labels_from_f(want))
+    band = np.abs(f_raw) <= np.float32(EPS_BAND) * B.astype(np.float32) * (1 + 1e-6)
+    assert nres >= np.sum(np.abs(f_raw.astype(np.float64)) < 0.99 * EPS_BAND * B)
+    assert nres <= np.sum(band) + 8
+    # re-scored queries carry the FP64 value (rounded to FP32)
+    sel = np.abs(f_raw.astype(np.float64)) < 0.99 * EPS_BAND * B
+    np.testing.assert_allclose(f[sel], want[sel].astype(np.float32), rtol=1e-6, atol=1e-30)
+
+
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_score_trained_model(fk, arm3, arm7, dev, which):
+    w, ch = arm3 if which == "arm3" else arm7
+    X = w.train_configs().astype(np.float64)
+    y = O.check(w.scene, X)
+    r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+    S, alpha = X[r.support], r.alpha[r.support]
+    Q = w.query_configs(10000 if which == "arm3" else 20000)
+    out = _score_case(fk, w, ch, dev, S, alpha, Q)
+    _check_score(*out, alpha)
+
+
+@pytest.mark.parametrize("ns,n", [(0, 100), (1, 1), (1, 513), (127, 700), (128, 512), (129, 1025), (300, 3)])
+def test_score_edge_sizes(fk, arm7, dev, ns, n):
+    w, ch = arm7
+    rng = np.random.default_rng(ns * 7 + n)
+    S = w.train_configs()[:ns].astype(np.float64)
+    alpha = rng.normal(size=ns) * 3
+    Q = w.query_configs(n)
+    out = _score_case(fk, w, ch, dev, S, alpha, Q)
+    if ns == 0:
+        assert np.all(out[2] == 0) and np.all(out[3] == 1)
+    else:
+        _check_score(*out, alpha)
+
+
+def test_score_query_equal_to_support_point(fk, arm7, dev):
+    # K(x, x) = 1: a single support point scored at itself gives alpha
+    w, ch = arm7
+    S = w.train_configs()[:1].astype(np.float64)
+    f_raw, lab_raw, f, lab, nres, want, B = _score_case(fk, w, ch, dev, S, np.array([-0.75]), S.astype(np.float32))
+    assert want[0] == -0.75
+    assert abs(f_raw[0] + 0.75) <= 1e-6 and lab[0] == -1
+
+
+def test_score_timeout_path_reports_and_recovers(fk, arm7, dev):
+    # a tile wait that gives up at once returns FK_ERR_TIMEOUT; the context
+    # stays usable and the next call with the normal limit succeeds
+    w, ch = arm7
+    S = w.train_configs()[:300].astype(np.float64)
+    alpha = np.random.default_rng(0).normal(size=300)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, alpha, w.gamma)
+        q = torch.from_numpy(w.query_configs(4096)).to(dev)
+        lab = torch.empty(4096, dtype=torch.int8, device=dev)
+        fk.fk_set_wait_limit(0)
+        try:
+            with pytest.raises(fk.FkError) as e:
+                fk.fk_score(m, q, lab, rescore=True, count=True)
+            assert e.value.code == fk.FK_ERR_TIMEOUT
+        finally:
+            fk.fk_set_wait_limit(1 << 22)
+        fk.fk_score(m, q, lab, rescore=True, count=True)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
+def test_argument_errors(fk, arm3, dev):
+    w, ch = arm3
+    m = fk.fastron_model_create(ch)
+    try:
+        q = torch.zeros((4, 3), dtype=torch.float32, device=dev)
+        lab = torch.empty(4, dtype=torch.int8, device=dev)
+        with pytest.raises(fk.FkError) as e:
+            fk.fk_score(m, q, lab)
+        assert e.value.code == fk.FK_ERR_STATE
+        X = torch.zeros((9000, 3), dtype=torch.float64, device=dev)
+        y = torch.ones(9000, dtype=torch.int8, device=dev)
+        with pytest.raises(fk.FkError) as e:
+            fk.fastron_train(m, X, y, 10.0)
+        assert e.value.code == fk.FK_ERR_CAPACITY
+        with pytest.raises(fk.FkError):
+            fk.fastron_train(m, X[:10], y[:10], -1.0)
+        with pytest.raises(ValueError):
+            fk.fk_score(m, q.double(), lab)
+    finally:
+        fk.fastron_model_destroy(m)
