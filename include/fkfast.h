@@ -164,6 +164,28 @@ int fastron_model_get(const fastron_model_t *model, int64_t *idx, double *alpha,
 int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, int rescore, double rescore_eps,
              float *f, int8_t *label, int64_t *n_rescored, void *stream);
 
+/* fk_score with rescore = 1 for callers that must not allocate device memory
+ * while they score (a real-time planner loop, a process whose device memory
+ * is handed to a fixed pool, code under a budget fixed at start-up).  The
+ * paper has no counterpart: this is a deployment variant of the same two
+ * kernels.  fk_score may grow the model's band buffer with cudaMalloc; this
+ * call allocates nothing.  Its scratch (band counter, error word, band list)
+ * is one static device array of 1,048,576 + 64 int32 (about 4 MiB) that every
+ * GPU loading the library holds until the process exits.  Limits and rules:
+ *   - n <= 1,048,576 queries per call, else FK_ERR_CAPACITY (split larger
+ *     batches into several calls);
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress): make that first call before any stream capture;
+ *   - every call on a device shares the one array: calls whose GPU work
+ *     overlaps (e.g. on two streams without ordering) race and corrupt each
+ *     other's band lists; order them on one stream;
+ *   - the model must have been trained or set beforehand (its own buffers are
+ *     allocated by fastron_train / fastron_model_set, not here).
+ * Arguments and results are those of fk_score with precision FK_F32 and
+ * rescore = 1. */
+int fk_score_noalloc(fastron_model_t *model, const float *q, int64_t n, double rescore_eps, float *f, int8_t *label,
+                     int64_t *n_rescored, void *stream);
+
 /* ---- ground-truth labels (geometric checker) ---------------------------
  * Link i (1..D) is the segment between the origins of frames i-1 and i,
  * swept by a sphere of radius `radius`; a configuration collides (+1) if any

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fk_internal.h"
@@ -478,5 +479,79 @@ extern "C" int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds) 
     }
   *ops_per_clk_sm = used ? sum / used : 0.0;
   if (seconds) *seconds = ms * 1e-3;
+  return FK_OK;
+}
+
+// ------------------------------------------------- score, no allocation ---
+// Some callers cannot allocate device memory at the time they score: a
+// real-time planner loop that must never block on the allocator, a host
+// process that hands the GPU over to a pre-sized memory pool, or code
+// running under a memory budget fixed at start-up.  fk_score may grow the
+// model's band-list buffer with cudaMalloc on its first call with a larger
+// batch; fk_score_noalloc never does.  Its scratch (the band counter, the
+// error word and the band index list) is the file-scope device array below,
+// which every GPU that loads this library holds until the process exits.
+constexpr int64_t kNoAllocMaxQueries = 1 << 20;  // 4 MiB of band indices
+constexpr int kNoAllocHeader = 64;               // [0] band count, [1] error bits, rest padding
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxQueries];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up on the
+// first call made with that device current.  In host code the array's name
+// only stands in for the symbol; handing it to a kernel would reach the wrong
+// memory, so kernels get the address found here.
+static constexpr int kNoAllocMaxDevices = 64;
+static int32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(int32_t **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(FK_ERR_CAPACITY, "fk_score_noalloc: device ordinal %d above %d", dev, kNoAllocMaxDevices - 1);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<int32_t *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return FK_OK;
+}
+
+extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, double rescore_eps, float *f,
+                                int8_t *label, int64_t *n_rescored, void *stream) {
+  if (!m) return fail(FK_ERR_ARG, "fk_score_noalloc: model is NULL");
+  if (m->ns < 0) return fail(FK_ERR_STATE, "fk_score_noalloc: model is untrained");
+  if (n < 0) return fail(FK_ERR_ARG, "fk_score_noalloc: n < 0");
+  if (n > kNoAllocMaxQueries)
+    return fail(FK_ERR_CAPACITY, "fk_score_noalloc: n=%lld exceeds the fixed scratch of %lld queries per call",
+                (long long)n, (long long)kNoAllocMaxQueries);
+  if (n_rescored) *n_rescored = 0;
+  if (n == 0) return FK_OK;
+  if (!q || !label) return fail(FK_ERR_ARG, "fk_score_noalloc: q and label must not be NULL");
+  if (m->gamma > 1e7) return fail(FK_ERR_ARG, "fk_score_noalloc: gamma above the FP32 range of the score kernel");
+  int32_t *scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != FK_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const fk_chain *c = m->chain;
+  int32_t *cnt = scratch, *err = scratch + 1, *band = scratch + kNoAllocHeader;
+  // the array keeps the previous call's contents: the counter and the error
+  // word must start at zero (the band list is written before it is read)
+  CK(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2, s));
+  const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
+  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
+               band, cnt, err, g_wait_limit};
+  CK(launch_score_f32(c->cf, sa, s));
+  RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};
+  CK(launch_rescore_f64(c->cd, ra, s));
+  if (n_rescored) {
+    int32_t h[2];
+    CK(cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score_noalloc: a shared-memory tile wait timed out");
+    *n_rescored = h[0];
+  }
   return FK_OK;
 }

@@ -29,7 +29,8 @@ FK_MAX_CP = 32
 EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
-    "fastron_model_set", "fastron_model_get", "fk_score", "fk_label", "fk_set_wait_limit", "fk_probe_pipe",
+    "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
+    "fk_probe_pipe",
 )
 
 
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = False):
             "fastron_model_set": ([P, P, P, I64, D], I),
             "fastron_model_get": ([P, P, P, I64, P], I),
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
+            "fk_score_noalloc": ([P, P, I64, D, P, P, P, P], I),
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
@@ -258,6 +260,21 @@ def fk_score(model, q, label, f=None, rescore=True, eps=0.0, count=False, stream
                            None if f is None else _dev(f, torch.float32, "f", (n,)),
                            _dev(label, torch.int8, "label", (n,)), ctypes.byref(nr) if count else None,
                            _stream(stream)))
+    return nr.value if count else None
+
+
+def fk_score_noalloc(model, q, label, f=None, eps=0.0, count=False, stream=None):
+    """fk_score with FP64 re-scoring for callers that cannot allocate device
+    memory: its scratch is a fixed static device array (at most 1,048,576
+    queries per call).  Calls that overlap on the GPU share that array and
+    race; the first call on a device must come before any stream capture."""
+    import torch
+    n = q.shape[0]
+    nr = ctypes.c_int64()
+    _check(load().fk_score_noalloc(model, _dev(q, torch.float32, "q"), n, float(eps),
+                                   None if f is None else _dev(f, torch.float32, "f", (n,)),
+                                   _dev(label, torch.int8, "label", (n,)), ctypes.byref(nr) if count else None,
+                                   _stream(stream)))
     return nr.value if count else None
 
 
