@@ -207,7 +207,9 @@ void fk_set_wait_limit(uint32_t polls);
  * Measures sustained per-SM throughput of one instruction class with a
  * register-only loop on all SMs: kind 0 FP32 FMA, 1 packed FP32x2 FMA,
  * 2 FP32 reciprocal (MUFU), 3 packed FP16x2 FMA, 4 FP64 FMA, 5 FP16x2 ex2
- * (MUFU).  *ops_per_clk_sm (host) receives lane-operations per SM clock,
+ * (MUFU); mixed streams with equal numbers of instructions: 6 FP32x2 FMA +
+ * FP32 FMA, 7 FP32x2 FMA + FP16x2 FMA, 8 FP32 FMA + FP16x2 FMA, 9 FP32x2 FMA
+ * + twice as many FP32 FMA.  *ops_per_clk_sm (host) receives lane-operations per SM clock,
  * from clock64() deltas; *seconds the kernel's wall time.  Synchronous. */
 int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds);
 

@@ -78,26 +78,45 @@ __device__ double seg_box_d2(const double p0[3], const double p1[3], const doubl
   return best;
 }
 
-__global__ void label_kernel(const ChainD c, const Boxes bx, const float *__restrict__ q, int64_t n,
-                             int8_t *__restrict__ y) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  PoseD P;
-  pose_base(c, P);
-  bool hit = false;
-  for (int i = 0; i < c.D && !hit; ++i) {
-    const double o0[3] = {P.T[3], P.T[7], P.T[11]};
-    pose_step(c, i, (double)q[k * c.D + i], P);
-    const double o1[3] = {P.T[3], P.T[7], P.T[11]};
-    for (int b = 0; b < bx.nb && !hit; ++b)
-      if (seg_box_d2(o0, o1, bx.b[b], bx.b[b] + 3) <= bx.r2) hit = true;
+// One warp per configuration: lane 0 runs the FP64 chain and leaves the D+1
+// frame origins in shared memory, then the lanes split the D x nb (link, box)
+// pairs and a ballot gives the label.
+constexpr int kLabelWarps = 8;
+
+__global__ void __launch_bounds__(kLabelWarps * 32) label_kernel(const ChainD c, const Boxes bx,
+                                                                  const float *__restrict__ q, int64_t n,
+                                                                  int8_t *__restrict__ y) {
+  __shared__ double org[kLabelWarps][FK_MAX_DOF + 1][3];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t k = blockIdx.x * (int64_t)kLabelWarps + wl;
+  if (k >= n) return;  // whole warp
+  if (lane == 0) {
+    PoseD P;
+    pose_base(c, P);
+    org[wl][0][0] = P.T[3];
+    org[wl][0][1] = P.T[7];
+    org[wl][0][2] = P.T[11];
+    for (int i = 0; i < c.D; ++i) {
+      pose_step(c, i, (double)q[k * c.D + i], P);
+      org[wl][i + 1][0] = P.T[3];
+      org[wl][i + 1][1] = P.T[7];
+      org[wl][i + 1][2] = P.T[11];
+    }
   }
-  y[k] = hit ? 1 : -1;
+  __syncwarp();
+  bool hit = false;
+  const int pairs = c.D * bx.nb;
+  for (int e = lane; e < pairs && !hit; e += 32) {
+    const int i = e / bx.nb, b = e % bx.nb;
+    hit = seg_box_d2(org[wl][i], org[wl][i + 1], bx.b[b], bx.b[b] + 3) <= bx.r2;
+  }
+  const unsigned any = __ballot_sync(0xffffffffu, hit);
+  if (lane == 0) y[k] = any ? 1 : -1;
 }
 
 cudaError_t launch_label(const ChainD &c, const Boxes &bx, const float *q, int64_t n, int8_t *y, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  label_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, bx, q, n, y);
+  label_kernel<<<(unsigned)((n + kLabelWarps - 1) / kLabelWarps), kLabelWarps * 32, 0, s>>>(c, bx, q, n, y);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,7 @@
 namespace fk {
 bool score_supported(int mv);
 int probe_iters(int kind);
-int probe_ops_per_instr(int kind);
-int probe_instr_per_iter();
+int probe_ops_per_iter(int kind);
 }  // namespace fk
 
 using namespace fk;
@@ -436,7 +435,7 @@ extern "C" int fk_label(const fk_chain_t *c, const double *boxes, int64_t nb, do
 
 // -------------------------------------------------------------- probe ---
 extern "C" int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds) {
-  if (kind < 0 || kind > 5) return fail(FK_ERR_ARG, "fk_probe_pipe: unknown kind %d", kind);
+  if (kind < 0 || kind > 9) return fail(FK_ERR_ARG, "fk_probe_pipe: unknown kind %d", kind);
   if (!ops_per_clk_sm) return fail(FK_ERR_ARG, "fk_probe_pipe: NULL pointer");
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
@@ -469,7 +468,7 @@ extern "C" int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds) 
     if (hi[sm] < 0 || t1 > hi[sm]) hi[sm] = t1;
     ++nblk[sm];
   }
-  const double per_block = (double)threads * probe_iters(kind) * probe_instr_per_iter() * probe_ops_per_instr(kind);
+  const double per_block = (double)threads * probe_iters(kind) * probe_ops_per_iter(kind);
   double sum = 0.0;
   int used = 0;
   for (size_t i = 0; i < lo.size(); ++i)
