@@ -203,6 +203,16 @@ int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double ra
  * synchronised with calls in flight on other threads. */
 void fk_set_wait_limit(uint32_t polls);
 
+/* ---- tensor-core GEMM ---------------------------------------------------
+ * C_z = A B^T over the z-th of `splits` equal K ranges, on tcgen05 tensor
+ * cores: A device bf16 M x K (row stride lda elements), B device bf16 N x K
+ * (row stride ldb), C device float splits x M x N.  M % 128 == 0, N % 64 ==
+ * 0, K % (64 splits) == 0, lda, ldb >= K and multiples of 8, pointers 16-byte
+ * aligned.  The building block of the surrogate's layers, exposed for
+ * testing.  Synchronous (checks the kernel's timeout flag). */
+int fk_tc_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int M, int N, int K, int splits,
+                    float *C, void *stream);
+
 /* ---- pipe throughput probes --------------------------------------------
  * Measures sustained per-SM throughput of one instruction class with a
  * register-only loop on all SMs: kind 0 FP32 FMA, 1 packed FP32x2 FMA,

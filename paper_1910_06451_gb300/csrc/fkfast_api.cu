@@ -8,8 +8,11 @@
 #include <vector>
 
 #include "fk_internal.h"
+#include "tc_gemm.cuh"
 
 namespace fk {
+struct GemmArgs;
+cudaError_t launch_gemm_f32(const GemmArgs &g, int splits, cudaStream_t s);
 bool score_supported(int mv);
 int probe_iters(int kind);
 int probe_ops_per_iter(int kind);
@@ -430,6 +433,41 @@ extern "C" int fk_label(const fk_chain_t *c, const double *boxes, int64_t nb, do
   for (int64_t b = 0; b < nb; ++b)
     for (int k = 0; k < 6; ++k) bx.b[b][k] = boxes[6 * b + k];
   CK(launch_label(c->cd, bx, q, n, y, (cudaStream_t)stream));
+  return FK_OK;
+}
+
+// --------------------------------------------------------- tensor GEMM ---
+extern "C" int fk_tc_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int M, int N, int K,
+                               int splits, float *C, void *stream) {
+  if (!A || !B || !C) return fail(FK_ERR_ARG, "fk_tc_gemm_bf16: NULL pointer");
+  if (M <= 0 || N <= 0 || K <= 0 || splits <= 0 || M % 128 || N % 64 || K % (64 * splits))
+    return fail(FK_ERR_ARG, "fk_tc_gemm_bf16: need M %% 128 == 0, N %% 64 == 0, K %% (64 splits) == 0");
+  if (lda < K || ldb < K || lda % 8 || ldb % 8)
+    return fail(FK_ERR_ARG, "fk_tc_gemm_bf16: leading dimensions must be >= K and multiples of 8");
+  if (((uintptr_t)A | (uintptr_t)B) % 16 || (uintptr_t)C % 16)
+    return fail(FK_ERR_ARG, "fk_tc_gemm_bf16: pointers must be 16-byte aligned");
+  static DevBuf err;
+  CK(err.ensure(sizeof(int32_t)));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(err.p, 0, sizeof(int32_t), s));
+  GemmArgs g{};
+  g.A = reinterpret_cast<const bf16 *>(A);
+  g.lda = lda;
+  g.B = reinterpret_cast<const bf16 *>(B);
+  g.ldb = ldb;
+  g.M = M;
+  g.N = N;
+  g.K = K / splits;
+  g.Cf = C;
+  g.ldcf = N;
+  g.zstride = (int64_t)M * N;
+  g.err = err.as<int32_t>();
+  g.wait_limit = g_wait_limit;
+  CK(launch_gemm_f32(g, splits, s));
+  int32_t h = 0;
+  CK(cudaMemcpyAsync(&h, err.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_tc_gemm_bf16: an MMA completion wait timed out");
   return FK_OK;
 }
 

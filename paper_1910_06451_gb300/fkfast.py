@@ -30,7 +30,7 @@ EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
     "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
-    "fk_probe_pipe",
+    "fk_probe_pipe", "fk_tc_gemm_bf16",
 )
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
+            "fk_tc_gemm_bf16": ([P, I64, P, I64, I, I, I, I, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -289,6 +290,23 @@ def fk_label(chain, boxes, radius, q, y, stream=None):
 
 def fk_set_wait_limit(polls: int):
     load().fk_set_wait_limit(int(polls))
+
+
+def fk_tc_gemm_bf16(A, B, splits=1, stream=None):
+    """D = A B^T on the tensor cores: A (M, K) and B (N, K) bfloat16 CUDA
+    tensors (row stride may exceed K); returns float32 partials (splits, M, N)
+    whose sum over the first axis is D."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or not A.is_cuda or not B.is_cuda:
+        raise ValueError("A and B must be bfloat16 CUDA tensors")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("A and B rows must be contiguous")
+    C = torch.empty((splits, M, N), dtype=torch.float32, device=A.device)
+    _check(load().fk_tc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                                  B.stride(0), M, N, K, splits, ctypes.c_void_p(C.data_ptr()), _stream(stream)))
+    return C
 
 
 def fk_probe_pipe(kind: int):
