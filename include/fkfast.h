@@ -203,6 +203,73 @@ int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double ra
  * synchronised with calls in flight on other threads. */
 void fk_set_wait_limit(uint32_t polls);
 
+/* ---- learned surrogate (not part of the paper) -------------------------
+ * A 64-256-256-256-1 ReLU MLP that predicts the model value f(q) from
+ * features of the control points (position of each control point, sin/cos of
+ * the joint values on either side of its frame: 7 per point, at most 9
+ * points, zero-padded to 64).  Its layers run on tcgen05 tensor cores with
+ * BF16 operands and FP32 accumulation; training is mean-squared error on
+ * f / scale with Adam on FP32 master weights.  Inference answers a query with
+ * sign(pred) when |pred| > tau and sends every other query to fk_score
+ * (FP32 score + FP64 re-score), so those labels are exact. */
+typedef struct surrogate surrogate_t;
+
+typedef struct {
+    int32_t epochs;   /* passes over the training rows */
+    int32_t batch;    /* rows per step, a multiple of 128, <= 65536 */
+    float lr;         /* Adam step size (divided by 3 for the last third of the epochs) */
+    float holdout;    /* fraction of the queries held out to calibrate tau, in [0, 1) */
+    int32_t reinit;   /* 1: reinitialise the weights first; 0: continue (fine-tune) */
+    int32_t reserved;
+} surrogate_train_params;
+
+typedef struct {
+    int64_t steps, n_train, n_holdout;
+    float loss_first, loss_last;  /* mean squared error of the first step / last epoch (units of f / scale) */
+    float scale;                  /* root mean square of f over the training rows */
+    float tau;                    /* calibrated threshold in units of f: no held-out row with |pred| > tau had a wrong sign */
+    float holdout_sign_error;     /* fraction of held-out rows whose sign(pred) differs from the exact score's */
+    float holdout_fallback;       /* fraction of held-out rows with |pred| <= tau */
+} surrogate_stats;
+
+/* Creates a surrogate for `chain` with He-uniform weights drawn from `seed`. */
+int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogate_t **out);
+void surrogate_destroy(surrogate_t *s);
+
+/* Trains on n query configurations q (device float n x D): the targets are
+ * the model's FP32 scores of the same queries, computed here; the last
+ * `holdout` fraction (rounded to 128 rows) is held out to calibrate tau.
+ * stats: host, may be NULL.  Synchronous. */
+int surrogate_train(surrogate_t *s, fastron_model_t *model, const float *q, int64_t n,
+                    const surrogate_train_params *p, surrogate_stats *stats, void *stream);
+
+/* Labels n queries (device float n x D) into label (device int8 [n]).  pred
+ * (device float [n] or NULL) receives the surrogate's prediction of f, or the
+ * exact f for fallback queries.  tau <= 0 uses the calibrated threshold.
+ * n_fallback (host, may be NULL) receives the number of fallback queries.
+ * Synchronises `stream` once (to size the fallback pass). */
+int surrogate_infer(surrogate_t *s, fastron_model_t *model, const float *q, int64_t n, double tau, int8_t *label,
+                    float *pred, int64_t *n_fallback, void *stream);
+
+/* Raw network outputs (units of f / scale) for n queries: out device float [n]. */
+int surrogate_forward(surrogate_t *s, const float *q, int64_t n, float *out, void *stream);
+
+/* Parameters as one FP32 vector of 148,481 values: W1 [256][64], b1 [256],
+ * W2 [256][256], b2, W3 [256][256], b3, w4 [256], b4.  get also returns the
+ * target scale and tau (each may be NULL).  Synchronous. */
+int surrogate_set_params(surrogate_t *s, const float *params, int64_t count);
+int surrogate_get_params(const surrogate_t *s, float *params, int64_t count, float *scale, float *tau);
+
+/* One forward and backward pass on n queries (device float n x D, n a
+ * multiple of 128) against targets (device float [n], units of f / scale):
+ * the gradient of the mean squared error (host float [148481]) and the loss
+ * (host, may be NULL).  Synchronous. */
+int surrogate_gradients(surrogate_t *s, const float *q, int64_t n, const float *target, float *grad, float *loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the given gradient
+ * (host float [148481]).  Synchronous. */
+int surrogate_adam_step(surrogate_t *s, const float *grad, float lr);
+
 /* ---- tensor-core GEMM ---------------------------------------------------
  * C_z = A B^T over the z-th of `splits` equal K ranges, on tcgen05 tensor
  * cores: A device bf16 M x K (row stride lda elements), B device bf16 N x K

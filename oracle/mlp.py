@@ -16,7 +16,9 @@ kernels follow, in numpy FP64 with library matmuls as steps:
 
 Parity status: pinned by tests/test_oracle_mlp.py (central finite
 differences of the loss, the closed-form first Adam step, feature values at
-known configurations).
+known configurations, bfloat16 rounding of exactly representable and halfway
+values, and the BF16-storage gradients reducing to the FP64 ones when every
+stored value is representable).
 """
 from __future__ import annotations
 
@@ -83,6 +85,43 @@ def backward(p: dict, cache, out: np.ndarray, target: np.ndarray) -> dict:
     g["W2"] = d2.T @ h1
     g["b2"] = d2.sum(0)
     d1 = (d2 @ p["W2"]) * (h1 > 0)
+    g["W1"] = d1.T @ X
+    g["b1"] = d1.sum(0)
+    return g
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to bfloat16 (8 exponent bits, 7 fraction bits), ties to even,
+    returned as FP64: x is first rounded to FP32, then the low 16 bits of the
+    FP32 pattern are rounded away."""
+    f = np.asarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    b = (b + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def backward_bf16_storage(p: dict, X: np.ndarray, target: np.ndarray) -> dict:
+    """The same gradients when the hidden activations h1, h2, h3 and the
+    back-propagated deltas are stored in bfloat16 between layers (the
+    arithmetic itself in FP64): the precision contract of the tensor-core
+    path, which keeps activations and deltas in BF16 and accumulates in FP32."""
+    z1 = X @ p["W1"].T + p["b1"]
+    h1 = bf16_round(np.maximum(z1, 0.0))
+    h2 = bf16_round(np.maximum(h1 @ p["W2"].T + p["b2"], 0.0))
+    z3 = h2 @ p["W3"].T + p["b3"]
+    h3 = bf16_round(np.maximum(z3, 0.0))
+    out = np.maximum(z3, 0.0) @ p["w4"] + p["b4"][0]
+    B = X.shape[0]
+    dout = 2.0 * (out - target) / B
+    g = {"w4": h3.T @ dout, "b4": np.array([dout.sum()])}
+    d3 = bf16_round(np.outer(dout, p["w4"]) * (h3 > 0))
+    g["W3"] = d3.T @ h2
+    g["b3"] = d3.sum(0)
+    d2 = bf16_round((d3 @ p["W3"]) * (h2 > 0))
+    g["W2"] = d2.T @ h1
+    g["b2"] = d2.sum(0)
+    d1 = bf16_round((d2 @ p["W2"]) * (h1 > 0))
     g["W1"] = d1.T @ X
     g["b1"] = d1.sum(0)
     return g

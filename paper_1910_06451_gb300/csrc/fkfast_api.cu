@@ -592,3 +592,516 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   }
   return FK_OK;
 }
+
+// ------------------------------------------------------------ surrogate ---
+// Learned surrogate of the model value (not part of the paper).  Flat FP32
+// parameter vector: W1 [256][64], b1, W2 [256][256], b2, W3 [256][256], b3,
+// w4 [256], b4.
+namespace fk {
+cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, bf16 *XT,
+                                 cudaStream_t s);
+cudaError_t launch_gemm(int epi, int nt, const GemmArgs &g, int splits, cudaStream_t s);
+cudaError_t launch_surr_head_bwd(const float *out, const float *y, const bf16 *h3, const float *w4, int B, bf16 *dP3,
+                                 float *pw4, float *pb4, float *ploss, cudaStream_t s);
+cudaError_t launch_transpose_bf16(const bf16 *in, int64_t rows, int64_t cols, bf16 *out, cudaStream_t s);
+cudaError_t launch_sum_partials(const float *src, int nz, int64_t stride, int64_t n, float *dst, cudaStream_t s);
+cudaError_t launch_row_sum_bf16(const bf16 *Mt, int64_t rows, int64_t cols, float *dst, cudaStream_t s);
+cudaError_t launch_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
+                        float eps, int64_t t, cudaStream_t s);
+cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, bf16 *WTb, cudaStream_t s);
+cudaError_t launch_surr_decide(const float *out, float scale, int64_t n, float tau, float *pred, int8_t *label,
+                               int32_t *fb_idx, int32_t *fb_cnt, cudaStream_t s);
+cudaError_t launch_gather_rows(const float *q, int D, const int32_t *idx, int64_t n, float *out, cudaStream_t s);
+cudaError_t launch_scatter_labels(const int8_t *src, const float *fsrc, const int32_t *idx, int64_t n, int8_t *label,
+                                  float *pred, cudaStream_t s);
+cudaError_t launch_sumsq(const float *x, int64_t n, double *acc, cudaStream_t s);
+cudaError_t launch_scale(float *x, int64_t n, float v, cudaStream_t s);
+cudaError_t launch_surr_calibrate(const float *pred, const float *f, int64_t n, unsigned *tau_bits,
+                                  unsigned long long *wrong, unsigned long long *below_cnt, float tau_hint,
+                                  cudaStream_t s);
+cudaError_t launch_count_below(const float *pred, int64_t n, float tau, unsigned long long *cnt, cudaStream_t s);
+}  // namespace fk
+
+namespace {
+constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + (int64_t)kSurrW * kSurrIn;
+constexpr int64_t kOffW2 = kOffB1 + kSurrW, kOffB2 = kOffW2 + (int64_t)kSurrW * kSurrW;
+constexpr int64_t kOffW3 = kOffB2 + kSurrW, kOffB3 = kOffW3 + (int64_t)kSurrW * kSurrW;
+constexpr int64_t kOffW4 = kOffB3 + kSurrW, kOffB4 = kOffW4 + kSurrW;
+constexpr int64_t kSurrParams = kOffB4 + 1;
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// SplitMix64 for the parameter initialisation (library-private stream).
+struct Mix64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+}  // namespace
+
+struct surrogate {
+  const fk_chain *chain = nullptr;
+  uint64_t seed = 0;
+  DevBuf p, m, v, g;
+  DevBuf w1b, w1t, w2b, w2t, w3b, w3t;
+  float scale = 1.f;   // target scale: the network predicts f / scale
+  float tau = -1.f;    // calibrated threshold in units of f (< 0: not calibrated)
+  int64_t t = 0;       // Adam steps taken
+  int B = 0;           // batch of the training buffers
+  DevBuf H1, H1T, H2, H2T, H3, dP3, dP3T, dP2, dP2T, dP1, dP1T, out, part, pw4, pb4, ploss, loss_hist;
+  DevBuf X, XT, Y, Yh, lab_tmp;
+  DevBuf iX, iH1, iH2, iout, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
+  DevBuf err, scal;
+};
+
+static int surr_init_params(surrogate *s, cudaStream_t st) {
+  std::vector<float> h((size_t)kSurrParams, 0.f);
+  Mix64 r{s->seed ^ 0xA5A5A5A55A5A5A5Aull};
+  auto he = [&](int64_t off, int out, int in) {
+    const double lim = sqrt(6.0 / in);
+    for (int64_t i = 0; i < (int64_t)out * in; ++i) h[(size_t)(off + i)] = (float)((2.0 * r.uniform() - 1.0) * lim);
+  };
+  he(kOffW1, kSurrW, kSurrIn);
+  he(kOffW2, kSurrW, kSurrW);
+  he(kOffW3, kSurrW, kSurrW);
+  he(kOffW4, 1, kSurrW);
+  CK(cudaMemcpyAsync(s->p.p, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s->m.p, 0, sizeof(float) * kSurrParams, st));
+  CK(cudaMemsetAsync(s->v.p, 0, sizeof(float) * kSurrParams, st));
+  CK(cudaStreamSynchronize(st));
+  s->t = 0;
+  return FK_OK;
+}
+
+static int surr_sync_weights(surrogate *s, cudaStream_t st) {
+  const float *P = s->p.as<float>();
+  CK(launch_weights_bf16(P + kOffW1, kSurrW, kSurrIn, s->w1b.as<bf16>(), s->w1t.as<bf16>(), st));
+  CK(launch_weights_bf16(P + kOffW2, kSurrW, kSurrW, s->w2b.as<bf16>(), s->w2t.as<bf16>(), st));
+  CK(launch_weights_bf16(P + kOffW3, kSurrW, kSurrW, s->w3b.as<bf16>(), s->w3t.as<bf16>(), st));
+  return FK_OK;
+}
+
+extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogate_t **out) {
+  if (!out) return fail(FK_ERR_ARG, "surrogate_create: out is NULL");
+  *out = nullptr;
+  if (!chain) return fail(FK_ERR_ARG, "surrogate_create: chain is NULL");
+  if (7 * chain->M > kSurrIn)
+    return fail(FK_ERR_CAPACITY, "surrogate_create: %d control points need %d features, above %d", chain->M,
+                7 * chain->M, kSurrIn);
+  surrogate *s = new surrogate;
+  s->chain = chain;
+  s->seed = seed;
+  int rc = FK_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == FK_OK) rc = fail(FK_ERR_CUDA, "surrogate_create: %s", cudaGetErrorString(e));
+  };
+  ck(s->p.ensure(sizeof(float) * kSurrParams));
+  ck(s->m.ensure(sizeof(float) * kSurrParams));
+  ck(s->v.ensure(sizeof(float) * kSurrParams));
+  ck(s->g.ensure(sizeof(float) * kSurrParams));
+  ck(s->w1b.ensure(2 * kSurrW * kSurrIn));
+  ck(s->w1t.ensure(2 * kSurrW * kSurrIn));
+  ck(s->w2b.ensure(2 * kSurrW * kSurrW));
+  ck(s->w2t.ensure(2 * kSurrW * kSurrW));
+  ck(s->w3b.ensure(2 * kSurrW * kSurrW));
+  ck(s->w3t.ensure(2 * kSurrW * kSurrW));
+  ck(s->err.ensure(64));
+  ck(s->scal.ensure(64));
+  if (rc == FK_OK) rc = surr_init_params(s, 0);
+  if (rc == FK_OK) rc = surr_sync_weights(s, 0);
+  if (rc == FK_OK && cudaStreamSynchronize(0) != cudaSuccess) rc = fail(FK_ERR_CUDA, "surrogate_create: sync failed");
+  if (rc != FK_OK) {
+    surrogate_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return FK_OK;
+}
+
+extern "C" void surrogate_destroy(surrogate_t *s) {
+  if (!s) return;
+  DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w1t, &s->w2b, &s->w2t, &s->w3b, &s->w3t,
+                    &s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1,
+                    &s->dP1T, &s->out, &s->part, &s->pw4, &s->pb4, &s->ploss, &s->loss_hist, &s->X, &s->XT,
+                    &s->Y, &s->Yh, &s->lab_tmp, &s->iX, &s->iH1, &s->iH2, &s->iout, &s->fb_idx, &s->fb_cnt,
+                    &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred, &s->err, &s->scal};
+  for (DevBuf *b : bufs) b->release();
+  delete s;
+}
+
+static int surr_ensure_batch(surrogate *s, int B) {
+  if (s->B == B) return FK_OK;
+  const size_t act = 2 * (size_t)B * kSurrW;
+  DevBuf *acts[] = {&s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1, &s->dP1T};
+  for (DevBuf *b : acts) CK(b->ensure(act));
+  CK(s->out.ensure(sizeof(float) * (size_t)B));
+  const int splits = B / kBM;
+  CK(s->part.ensure(sizeof(float) * (size_t)splits * kSurrW * kSurrW));
+  CK(s->pw4.ensure(sizeof(float) * (size_t)(B / 32) * kSurrW));
+  CK(s->pb4.ensure(sizeof(float) * (size_t)(B / 32)));
+  CK(s->ploss.ensure(sizeof(float) * (size_t)(B / 32)));
+  s->B = B;
+  return FK_OK;
+}
+
+static GemmArgs gemm_args(surrogate *s, const bf16 *A, int64_t lda, const bf16 *Bm, int64_t ldb, int M, int N, int K) {
+  GemmArgs g{};
+  g.A = A;
+  g.lda = lda;
+  g.B = Bm;
+  g.ldb = ldb;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.err = s->err.as<int32_t>();
+  g.wait_limit = g_wait_limit;
+  return g;
+}
+
+// Forward pass of the training batch: X [B][64] (row stride 64), XT its
+// transpose with row stride ldxt.  Leaves H1, H1T, H2, H2T, H3 and out.
+static int surr_forward_train(surrogate *s, const bf16 *X, int B, cudaStream_t st) {
+  const float *P = s->p.as<float>();
+  GemmArgs g = gemm_args(s, X, kSurrIn, s->w1b.as<bf16>(), kSurrIn, B, kSurrW, kSurrIn);
+  g.bias = P + kOffB1;
+  g.C = s->H1.as<bf16>();
+  g.ldc = kSurrW;
+  g.CT = s->H1T.as<bf16>();
+  g.ldct = B;
+  CK(launch_gemm(EPI_RELU, 128, g, 1, st));
+  g = gemm_args(s, s->H1.as<bf16>(), kSurrW, s->w2b.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
+  g.bias = P + kOffB2;
+  g.C = s->H2.as<bf16>();
+  g.ldc = kSurrW;
+  g.CT = s->H2T.as<bf16>();
+  g.ldct = B;
+  CK(launch_gemm(EPI_RELU, 128, g, 1, st));
+  g = gemm_args(s, s->H2.as<bf16>(), kSurrW, s->w3b.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
+  g.bias = P + kOffB3;
+  g.C = s->H3.as<bf16>();
+  g.ldc = kSurrW;
+  g.w4 = P + kOffW4;
+  g.b4 = P + kOffB4;
+  g.out = s->out.as<float>();
+  CK(launch_gemm(EPI_HEAD, 256, g, 1, st));
+  return FK_OK;
+}
+
+// Backward pass into the flat gradient g; XT is the batch's transposed input
+// with row stride ldxt.  loss_out (device, may be null) receives the batch's
+// mean squared error.
+static int surr_backward(surrogate *s, const bf16 *XT, int64_t ldxt, const float *Y, int B, float *loss_out,
+                         cudaStream_t st) {
+  float *G = s->g.as<float>();
+  const float *P = s->p.as<float>();
+  const int nb = B / 32, splits = B / kBM;
+  CK(launch_surr_head_bwd(s->out.as<float>(), Y, s->H3.as<bf16>(), P + kOffW4, B, s->dP3.as<bf16>(),
+                          s->pw4.as<float>(), s->pb4.as<float>(), s->ploss.as<float>(), st));
+  CK(launch_sum_partials(s->pw4.as<float>(), nb, kSurrW, kSurrW, G + kOffW4, st));
+  CK(launch_sum_partials(s->pb4.as<float>(), nb, 1, 1, G + kOffB4, st));
+  if (loss_out) {
+    CK(launch_sum_partials(s->ploss.as<float>(), nb, 1, 1, loss_out, st));
+    CK(launch_scale(loss_out, 1, 1.f / (float)B, st));
+  }
+  CK(launch_transpose_bf16(s->dP3.as<bf16>(), B, kSurrW, s->dP3T.as<bf16>(), st));
+  // layer 3: dW3 = dP3^T H2, db3 = rows of dP3^T
+  GemmArgs g = gemm_args(s, s->dP3T.as<bf16>(), B, s->H2T.as<bf16>(), B, kSurrW, kSurrW, B / splits);
+  g.Cf = s->part.as<float>();
+  g.ldcf = kSurrW;
+  g.zstride = (int64_t)kSurrW * kSurrW;
+  CK(launch_gemm(EPI_F32, 256, g, splits, st));
+  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrW, (int64_t)kSurrW * kSurrW, G + kOffW3, st));
+  CK(launch_row_sum_bf16(s->dP3T.as<bf16>(), kSurrW, B, G + kOffB3, st));
+  // dP2 = (dP3 W3) [H2 > 0]
+  g = gemm_args(s, s->dP3.as<bf16>(), kSurrW, s->w3t.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
+  g.mask = s->H2.as<bf16>();
+  g.ldm = kSurrW;
+  g.C = s->dP2.as<bf16>();
+  g.ldc = kSurrW;
+  g.CT = s->dP2T.as<bf16>();
+  g.ldct = B;
+  CK(launch_gemm(EPI_MASK, 128, g, 1, st));
+  g = gemm_args(s, s->dP2T.as<bf16>(), B, s->H1T.as<bf16>(), B, kSurrW, kSurrW, B / splits);
+  g.Cf = s->part.as<float>();
+  g.ldcf = kSurrW;
+  g.zstride = (int64_t)kSurrW * kSurrW;
+  CK(launch_gemm(EPI_F32, 256, g, splits, st));
+  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrW, (int64_t)kSurrW * kSurrW, G + kOffW2, st));
+  CK(launch_row_sum_bf16(s->dP2T.as<bf16>(), kSurrW, B, G + kOffB2, st));
+  // dP1 = (dP2 W2) [H1 > 0]
+  g = gemm_args(s, s->dP2.as<bf16>(), kSurrW, s->w2t.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
+  g.mask = s->H1.as<bf16>();
+  g.ldm = kSurrW;
+  g.C = s->dP1.as<bf16>();
+  g.ldc = kSurrW;
+  g.CT = s->dP1T.as<bf16>();
+  g.ldct = B;
+  CK(launch_gemm(EPI_MASK, 128, g, 1, st));
+  g = gemm_args(s, s->dP1T.as<bf16>(), B, XT, ldxt, kSurrW, kSurrIn, B / splits);
+  g.Cf = s->part.as<float>();
+  g.ldcf = kSurrIn;
+  g.zstride = (int64_t)kSurrW * kSurrIn;
+  CK(launch_gemm(EPI_F32, 64, g, splits, st));
+  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrIn, (int64_t)kSurrW * kSurrIn, G + kOffW1, st));
+  CK(launch_row_sum_bf16(s->dP1T.as<bf16>(), kSurrW, B, G + kOffB1, st));
+  return FK_OK;
+}
+
+static int surr_check_err(surrogate *s, cudaStream_t st, const char *who) {
+  int32_t h = 0;
+  CK(cudaMemcpyAsync(&h, s->err.p, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h & kErrTimeout) return fail(FK_ERR_TIMEOUT, "%s: a tensor-core completion wait timed out", who);
+  return FK_OK;
+}
+
+// Features of n queries into buffer X (and XT if non-null), rows padded to n_pad.
+static int surr_features(surrogate *s, const float *q, int64_t n, int64_t n_pad, DevBuf &X, DevBuf *XT,
+                         cudaStream_t st) {
+  CK(X.ensure(2 * (size_t)n_pad * kSurrIn));
+  if (XT) CK(XT->ensure(2 * (size_t)n_pad * kSurrIn));
+  CK(launch_surr_features(s->chain->cf, q, n, n_pad, X.as<bf16>(), XT ? XT->as<bf16>() : nullptr, st));
+  return FK_OK;
+}
+
+// Network outputs (f / scale) of n_pad feature rows into iout.
+static int surr_forward_infer(surrogate *s, const bf16 *X, int64_t n_pad, cudaStream_t st) {
+  const float *P = s->p.as<float>();
+  CK(s->iH1.ensure(2 * (size_t)n_pad * kSurrW));
+  CK(s->iH2.ensure(2 * (size_t)n_pad * kSurrW));
+  CK(s->iout.ensure(sizeof(float) * (size_t)n_pad));
+  GemmArgs g = gemm_args(s, X, kSurrIn, s->w1b.as<bf16>(), kSurrIn, (int)n_pad, kSurrW, kSurrIn);
+  g.bias = P + kOffB1;
+  g.C = s->iH1.as<bf16>();
+  g.ldc = kSurrW;
+  CK(launch_gemm(EPI_RELU, 256, g, 1, st));
+  g = gemm_args(s, s->iH1.as<bf16>(), kSurrW, s->w2b.as<bf16>(), kSurrW, (int)n_pad, kSurrW, kSurrW);
+  g.bias = P + kOffB2;
+  g.C = s->iH2.as<bf16>();
+  g.ldc = kSurrW;
+  CK(launch_gemm(EPI_RELU, 256, g, 1, st));
+  g = gemm_args(s, s->iH2.as<bf16>(), kSurrW, s->w3b.as<bf16>(), kSurrW, (int)n_pad, kSurrW, kSurrW);
+  g.bias = P + kOffB3;
+  g.w4 = P + kOffW4;
+  g.b4 = P + kOffB4;
+  g.out = s->iout.as<float>();
+  CK(launch_gemm(EPI_HEAD, 256, g, 1, st));
+  return FK_OK;
+}
+
+extern "C" int surrogate_set_params(surrogate_t *s, const float *params, int64_t count) {
+  if (!s || !params) return fail(FK_ERR_ARG, "surrogate_set_params: NULL pointer");
+  if (count != kSurrParams) return fail(FK_ERR_ARG, "surrogate_set_params: expected %lld values", (long long)kSurrParams);
+  CK(cudaMemcpy(s->p.p, params, sizeof(float) * kSurrParams, cudaMemcpyHostToDevice));
+  int rc = surr_sync_weights(s, 0);
+  if (rc != FK_OK) return rc;
+  CK(cudaStreamSynchronize(0));
+  return FK_OK;
+}
+
+extern "C" int surrogate_get_params(const surrogate_t *s, float *params, int64_t count, float *scale, float *tau) {
+  if (!s) return fail(FK_ERR_ARG, "surrogate_get_params: NULL pointer");
+  if (params) {
+    if (count != kSurrParams)
+      return fail(FK_ERR_ARG, "surrogate_get_params: expected %lld values", (long long)kSurrParams);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(params, s->p.p, sizeof(float) * kSurrParams, cudaMemcpyDeviceToHost));
+  }
+  if (scale) *scale = s->scale;
+  if (tau) *tau = s->tau;
+  return FK_OK;
+}
+
+extern "C" int surrogate_gradients(surrogate_t *s, const float *q, int64_t n, const float *target, float *grad,
+                                   float *loss) {
+  if (!s || !q || !target || !grad) return fail(FK_ERR_ARG, "surrogate_gradients: NULL pointer");
+  if (n < kBM || n % kBM || n > (1 << 20)) return fail(FK_ERR_ARG, "surrogate_gradients: n must be a multiple of 128");
+  cudaStream_t st = 0;
+  CK(cudaMemsetAsync(s->err.p, 0, 64, st));
+  int rc = surr_ensure_batch(s, (int)n);
+  if (rc != FK_OK) return rc;
+  if ((rc = surr_features(s, q, n, n, s->X, &s->XT, st)) != FK_OK) return rc;
+  if ((rc = surr_forward_train(s, s->X.as<bf16>(), (int)n, st)) != FK_OK) return rc;
+  float *dl = s->scal.as<float>();
+  if ((rc = surr_backward(s, s->XT.as<bf16>(), n, target, (int)n, dl, st)) != FK_OK) return rc;
+  if ((rc = surr_check_err(s, st, "surrogate_gradients")) != FK_OK) return rc;
+  CK(cudaMemcpy(grad, s->g.p, sizeof(float) * kSurrParams, cudaMemcpyDeviceToHost));
+  if (loss) CK(cudaMemcpy(loss, dl, sizeof(float), cudaMemcpyDeviceToHost));
+  return FK_OK;
+}
+
+extern "C" int surrogate_adam_step(surrogate_t *s, const float *grad, float lr) {
+  if (!s || !grad) return fail(FK_ERR_ARG, "surrogate_adam_step: NULL pointer");
+  CK(cudaMemcpy(s->g.p, grad, sizeof(float) * kSurrParams, cudaMemcpyHostToDevice));
+  ++s->t;
+  CK(launch_adam(s->p.as<float>(), s->m.as<float>(), s->v.as<float>(), s->g.as<float>(), kSurrParams, lr, 0.9f,
+                 0.999f, 1e-8f, s->t, 0));
+  int rc = surr_sync_weights(s, 0);
+  if (rc != FK_OK) return rc;
+  CK(cudaStreamSynchronize(0));
+  return FK_OK;
+}
+
+extern "C" int surrogate_forward(surrogate_t *s, const float *q, int64_t n, float *out, void *stream) {
+  if (!s || !q || !out) return fail(FK_ERR_ARG, "surrogate_forward: NULL pointer");
+  if (n <= 0) return n == 0 ? FK_OK : fail(FK_ERR_ARG, "surrogate_forward: n < 0");
+  if (n > INT32_MAX - kBM) return fail(FK_ERR_CAPACITY, "surrogate_forward: n too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(s->err.p, 0, 64, st));
+  const int64_t n_pad = round_up(n, kBM);
+  int rc = surr_features(s, q, n, n_pad, s->iX, nullptr, st);
+  if (rc != FK_OK) return rc;
+  if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_pad, st)) != FK_OK) return rc;
+  CK(cudaMemcpyAsync(out, s->iout.p, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  return surr_check_err(s, st, "surrogate_forward");
+}
+
+extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const float *q, int64_t n,
+                               const surrogate_train_params *prm, surrogate_stats *stats, void *stream) {
+  if (!s || !model || !q || !prm) return fail(FK_ERR_ARG, "surrogate_train: NULL pointer");
+  if (model->chain != s->chain) return fail(FK_ERR_ARG, "surrogate_train: model and surrogate use different chains");
+  if (model->ns < 0) return fail(FK_ERR_STATE, "surrogate_train: model is untrained");
+  const int B = prm->batch;
+  if (B < kBM || B % kBM || B > (1 << 16)) return fail(FK_ERR_ARG, "surrogate_train: batch must be a multiple of 128 up to 65536");
+  if (prm->epochs < 0 || !(prm->lr > 0.f) || !(prm->holdout >= 0.f && prm->holdout < 1.f))
+    return fail(FK_ERR_ARG, "surrogate_train: bad epochs, lr or holdout");
+  const int64_t n_hold = round_up((int64_t)(prm->holdout * (double)n), kBM) <= n ? round_up((int64_t)(prm->holdout * (double)n), kBM) : 0;
+  const int64_t n_tr = (n - n_hold) / B * B;
+  if (n_tr < B) return fail(FK_ERR_ARG, "surrogate_train: fewer training rows than one batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(s->err.p, 0, 64, st));
+  // exact targets: the FP32 score of every query (training and held-out rows)
+  CK(s->Y.ensure(sizeof(float) * (size_t)n));
+  CK(s->lab_tmp.ensure((size_t)n));
+  int rc = fk_score(model, q, n, FK_F32, 0, 0.0, s->Y.as<float>(), s->lab_tmp.as<int8_t>(), nullptr, stream);
+  if (rc != FK_OK) return rc;
+  double *acc = reinterpret_cast<double *>(s->scal.as<char>() + 16);
+  CK(cudaMemsetAsync(acc, 0, sizeof(double), st));
+  CK(launch_sumsq(s->Y.as<float>(), n_tr, acc, st));
+  double ss = 0.0;
+  CK(cudaMemcpyAsync(&ss, acc, sizeof ss, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  s->scale = ss > 0.0 ? (float)sqrt(ss / (double)n_tr) : 1.f;
+  CK(s->Yh.ensure(sizeof(float) * (size_t)(n_hold > 0 ? n_hold : 1)));
+  if (n_hold > 0)
+    CK(cudaMemcpyAsync(s->Yh.p, s->Y.as<float>() + (n - n_hold), sizeof(float) * (size_t)n_hold,
+                       cudaMemcpyDeviceToDevice, st));
+  CK(launch_scale(s->Y.as<float>(), n_tr, 1.f / s->scale, st));
+  // features of the training rows, both layouts
+  if ((rc = surr_features(s, q, n_tr, n_tr, s->X, &s->XT, st)) != FK_OK) return rc;
+  if ((rc = surr_ensure_batch(s, B)) != FK_OK) return rc;
+  if (prm->reinit) {
+    if ((rc = surr_init_params(s, st)) != FK_OK) return rc;
+    if ((rc = surr_sync_weights(s, st)) != FK_OK) return rc;
+  }
+  const int64_t steps_per_epoch = n_tr / B;
+  const int64_t total = steps_per_epoch * prm->epochs;
+  CK(s->loss_hist.ensure(sizeof(float) * (size_t)(total > 0 ? total : 1)));
+  int64_t step = 0;
+  for (int ep = 0; ep < prm->epochs; ++ep) {
+    const float lr = ep < (2 * prm->epochs + 2) / 3 ? prm->lr : prm->lr / 3.f;
+    for (int64_t b = 0; b < steps_per_epoch; ++b, ++step) {
+      const int64_t b0 = b * B;
+      if ((rc = surr_forward_train(s, s->X.as<bf16>() + b0 * kSurrIn, B, st)) != FK_OK) return rc;
+      if ((rc = surr_backward(s, s->XT.as<bf16>() + b0, n_tr, s->Y.as<float>() + b0, B,
+                              s->loss_hist.as<float>() + step, st)) != FK_OK)
+        return rc;
+      ++s->t;
+      CK(launch_adam(s->p.as<float>(), s->m.as<float>(), s->v.as<float>(), s->g.as<float>(), kSurrParams, lr, 0.9f,
+                     0.999f, 1e-8f, s->t, st));
+      if ((rc = surr_sync_weights(s, st)) != FK_OK) return rc;
+    }
+  }
+  if ((rc = surr_check_err(s, st, "surrogate_train")) != FK_OK) return rc;
+  // calibrate tau on the held-out rows: the largest |pred| with a wrong sign
+  float tau = 0.f, fb = 0.f, wrong_rate = 0.f;
+  if (n_hold > 0) {
+    if ((rc = surr_features(s, q + (n - n_hold) * s->chain->D, n_hold, n_hold, s->iX, nullptr, st)) != FK_OK) return rc;
+    if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_hold, st)) != FK_OK) return rc;
+    CK(launch_scale(s->iout.as<float>(), n_hold, s->scale, st));
+    unsigned *tb = reinterpret_cast<unsigned *>(s->scal.as<char>() + 32);
+    unsigned long long *wr = reinterpret_cast<unsigned long long *>(s->scal.as<char>() + 40);
+    unsigned long long *below = reinterpret_cast<unsigned long long *>(s->scal.as<char>() + 48);
+    CK(cudaMemsetAsync(tb, 0, 24, st));
+    CK(launch_surr_calibrate(s->iout.as<float>(), s->Yh.as<float>(), n_hold, tb, wr, below, 0.f, st));
+    unsigned htb = 0;
+    unsigned long long hwr = 0;
+    CK(cudaMemcpyAsync(&htb, tb, sizeof htb, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hwr, wr, sizeof hwr, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(&tau, &htb, sizeof tau);
+    CK(launch_count_below(s->iout.as<float>(), n_hold, tau, below, st));
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, below, sizeof hb, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    fb = (float)((double)hb / (double)n_hold);
+    wrong_rate = (float)((double)hwr / (double)n_hold);
+    if ((rc = surr_check_err(s, st, "surrogate_train")) != FK_OK) return rc;
+  }
+  s->tau = tau;
+  if (stats) {
+    std::vector<float> lh((size_t)(total > 0 ? total : 0));
+    if (total > 0) CK(cudaMemcpy(lh.data(), s->loss_hist.p, sizeof(float) * lh.size(), cudaMemcpyDeviceToHost));
+    stats->steps = total;
+    stats->loss_first = total > 0 ? lh.front() : 0.f;
+    float tail = 0.f;
+    const int64_t k = total < steps_per_epoch ? total : steps_per_epoch;
+    for (int64_t i = total - k; i < total; ++i) tail += lh[(size_t)i];
+    stats->loss_last = k > 0 ? tail / (float)k : 0.f;
+    stats->scale = s->scale;
+    stats->tau = tau;
+    stats->holdout_sign_error = wrong_rate;
+    stats->holdout_fallback = fb;
+    stats->n_train = n_tr;
+    stats->n_holdout = n_hold;
+  }
+  return FK_OK;
+}
+
+extern "C" int surrogate_infer(surrogate_t *s, fastron_model_t *model, const float *q, int64_t n, double tau,
+                               int8_t *label, float *pred, int64_t *n_fallback, void *stream) {
+  if (!s || !model || !label) return fail(FK_ERR_ARG, "surrogate_infer: NULL pointer");
+  if (model->chain != s->chain) return fail(FK_ERR_ARG, "surrogate_infer: model and surrogate use different chains");
+  if (model->ns < 0) return fail(FK_ERR_STATE, "surrogate_infer: model is untrained");
+  if (n < 0) return fail(FK_ERR_ARG, "surrogate_infer: n < 0");
+  if (n_fallback) *n_fallback = 0;
+  if (n == 0) return FK_OK;
+  if (!q) return fail(FK_ERR_ARG, "surrogate_infer: q is NULL");
+  if (n > INT32_MAX - kBM) return fail(FK_ERR_CAPACITY, "surrogate_infer: n too large");
+  const float t = tau > 0.0 ? (float)tau : s->tau;
+  if (!(t >= 0.f)) return fail(FK_ERR_STATE, "surrogate_infer: no threshold (train with a holdout or pass tau > 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(s->err.p, 0, 64, st));
+  const int64_t n_pad = round_up(n, kBM);
+  int rc = surr_features(s, q, n, n_pad, s->iX, nullptr, st);
+  if (rc != FK_OK) return rc;
+  if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_pad, st)) != FK_OK) return rc;
+  CK(s->fb_idx.ensure(sizeof(int32_t) * (size_t)n));
+  CK(s->fb_cnt.ensure(sizeof(int32_t) * 2));
+  CK(cudaMemsetAsync(s->fb_cnt.p, 0, sizeof(int32_t), st));
+  CK(launch_surr_decide(s->iout.as<float>(), s->scale, n, t, pred, label, s->fb_idx.as<int32_t>(),
+                        s->fb_cnt.as<int32_t>(), st));
+  int32_t nfb = 0;
+  CK(cudaMemcpyAsync(&nfb, s->fb_cnt.p, sizeof nfb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((rc = surr_check_err(s, st, "surrogate_infer")) != FK_OK) return rc;
+  if (nfb > 0) {
+    const int D = s->chain->D;
+    CK(s->fb_q.ensure(sizeof(float) * (size_t)nfb * D));
+    CK(s->fb_lab.ensure((size_t)nfb));
+    CK(s->fb_f.ensure(sizeof(float) * (size_t)nfb));
+    CK(launch_gather_rows(q, D, s->fb_idx.as<int32_t>(), nfb, s->fb_q.as<float>(), st));
+    rc = fk_score(model, s->fb_q.as<float>(), nfb, FK_F32, 1, 0.0, s->fb_f.as<float>(), s->fb_lab.as<int8_t>(),
+                  nullptr, stream);
+    if (rc != FK_OK) return rc;
+    CK(launch_scatter_labels(s->fb_lab.as<int8_t>(), s->fb_f.as<float>(), s->fb_idx.as<int32_t>(), nfb, label, pred,
+                             st));
+  }
+  if (n_fallback) *n_fallback = nfb;
+  return FK_OK;
+}

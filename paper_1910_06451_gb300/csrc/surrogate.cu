@@ -27,3 +27,345 @@ cudaError_t launch_gemm_f32(const GemmArgs &g0, int splits, cudaStream_t s) {
 }
 
 }  // namespace fk
+
+namespace fk {
+
+// ------------------------------------------------------------ features ---
+// Per control point m (frame j = cj[m]): its position, then sin/cos of the
+// joint values q_j and q_{j+1} (q_0 = q_{D+1} = 0): 7 values per point,
+// zero-padded to kSurrIn.  Rows n..n_pad-1 are zeros.
+__global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q, int64_t n, int64_t n_pad,
+                                     bf16 *__restrict__ X, bf16 *__restrict__ XT) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n_pad) return;
+  float f[kSurrIn];
+#pragma unroll
+  for (int i = 0; i < kSurrIn; ++i) f[i] = 0.f;
+  if (k < n) {
+    float qv[FK_MAX_DOF + 2];
+    qv[0] = 0.f;
+    for (int i = 0; i < c.D; ++i) qv[i + 1] = q[k * c.D + i];
+    qv[c.D + 1] = 0.f;
+    PoseF P;
+    pose_base(c, P);
+    for (int fr = 0; fr <= c.D; ++fr) {
+      if (fr > 0) pose_step(c, fr - 1, qv[fr], P);
+      for (int m = 0; m < c.M; ++m)
+        if (c.cj[m] == fr) {
+          float o[3];
+          pose_point(P, c.ct[m], o);
+          float s0, c0, s1, c1;
+          sincosf(qv[fr], &s0, &c0);
+          sincosf(qv[fr + 1], &s1, &c1);
+          const int b = 7 * m;
+          f[b + 0] = o[0];
+          f[b + 1] = o[1];
+          f[b + 2] = o[2];
+          f[b + 3] = s0;
+          f[b + 4] = c0;
+          f[b + 5] = s1;
+          f[b + 6] = c1;
+        }
+    }
+  }
+  __align__(16) bf16 h[kSurrIn];
+#pragma unroll
+  for (int i = 0; i < kSurrIn; ++i) h[i] = __float2bfloat16_rn(f[i]);
+  uint4 *dst = reinterpret_cast<uint4 *>(X + k * kSurrIn);
+#pragma unroll
+  for (int i = 0; i < kSurrIn / 8; ++i) dst[i] = reinterpret_cast<const uint4 *>(h)[i];
+  if (XT) {
+#pragma unroll
+    for (int i = 0; i < kSurrIn; ++i) XT[(int64_t)i * n_pad + k] = h[i];
+  }
+}
+
+// ---------------------------------------------------------------- head ---
+// Loss gradient of the output and the back-propagation through the last
+// layer.  One CTA of 256 threads (one per hidden unit) handles 32 rows:
+//   dout_b = 2 (out_b - y_b) / B
+//   dP3[b][k] = dout_b w4[k] [h3[b][k] > 0]
+//   partial dW4[k] = sum_b dout_b h3[b][k], partial db4 and loss sum.
+constexpr int kHeadRows = 32;
+
+__global__ void __launch_bounds__(kSurrW) surr_head_bwd_kernel(const float *__restrict__ out,
+                                                               const float *__restrict__ y, const bf16 *__restrict__ h3,
+                                                               const float *__restrict__ w4, int B,
+                                                               bf16 *__restrict__ dP3, float *__restrict__ pw4,
+                                                               float *__restrict__ pb4, float *__restrict__ ploss) {
+  __shared__ float dout[kHeadRows];
+  const int k = threadIdx.x;
+  const int b0 = blockIdx.x * kHeadRows;
+  if (k < kHeadRows) {
+    const float e = out[b0 + k] - y[b0 + k];
+    dout[k] = 2.f * e / (float)B;
+    float se = e * e, sd = 2.f * e / (float)B;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    if (k == 0) {
+      ploss[blockIdx.x] = se;
+      pb4[blockIdx.x] = sd;
+    }
+  }
+  __syncthreads();
+  const float wk = w4[k];
+  float acc = 0.f;
+  for (int r = 0; r < kHeadRows; ++r) {
+    const int64_t b = b0 + r;
+    const float h = __bfloat162float(h3[b * kSurrW + k]);
+    acc = fmaf(dout[r], h, acc);
+    dP3[b * kSurrW + k] = __float2bfloat16_rn(h > 0.f ? dout[r] * wk : 0.f);
+  }
+  pw4[(int64_t)blockIdx.x * kSurrW + k] = acc;
+}
+
+// ---------------------------------------------------------- transposes ---
+// out[c][r] = in[r][c] for a rows x cols bf16 matrix (both multiples of 32).
+__global__ void transpose_bf16_kernel(const bf16 *__restrict__ in, int64_t rows, int64_t cols,
+                                      bf16 *__restrict__ out) {
+  __shared__ bf16 t[32][33];
+  const int64_t r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) t[i][threadIdx.x] = in[(r0 + i) * cols + c0 + threadIdx.x];
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) out[(c0 + i) * rows + r0 + threadIdx.x] = t[threadIdx.x][i];
+}
+
+// ----------------------------------------------------------- reductions --
+// dst[j] = sum_z src[z * stride + j] for j < n (split-K partials, per-block partials).
+__global__ void sum_partials_kernel(const float *__restrict__ src, int nz, int64_t stride, int64_t n,
+                                    float *__restrict__ dst) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float s = 0.f;
+  for (int z = 0; z < nz; ++z) s += src[z * stride + j];
+  dst[j] = s;
+}
+
+// dst[r] = sum_c M[r][c] for a rows x cols bf16 matrix: one warp per row.
+__global__ void row_sum_bf16_kernel(const bf16 *__restrict__ Mt, int64_t rows, int64_t cols, float *__restrict__ dst) {
+  const int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float s = 0.f;
+  for (int64_t c = lane; c < cols; c += 32) s += __bfloat162float(Mt[r * cols + c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) dst[r] = s;
+}
+
+// ---------------------------------------------------------------- Adam ---
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of a weight matrix W [rows][cols] (FP32): row-major and transposed.
+__global__ void weights_bf16_kernel(const float *__restrict__ W, int rows, int cols, bf16 *__restrict__ Wb,
+                                    bf16 *__restrict__ WTb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i / cols, c = i % cols;
+  const bf16 h = __float2bfloat16_rn(W[i]);
+  Wb[i] = h;
+  WTb[(int64_t)c * rows + r] = h;
+}
+
+// ----------------------------------------------------------- inference ---
+// Confident queries (|pred| > tau) take sign(pred); the rest are appended to
+// the fallback list for the exact score.
+__global__ void surr_decide_kernel(const float *__restrict__ out, float scale, int64_t n, float tau,
+                                   float *__restrict__ pred, int8_t *__restrict__ label, int32_t *__restrict__ fb_idx,
+                                   int32_t *__restrict__ fb_cnt) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31;
+  const bool valid = k < n;
+  const float p = valid ? out[k] * scale : 0.f;
+  const bool fb = valid && !(fabsf(p) > tau);
+  if (valid) {
+    if (pred) pred[k] = p;
+    label[k] = p >= 0.f ? 1 : -1;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, fb);
+  if (bal) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(fb_cnt, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (fb) fb_idx[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)k;
+  }
+}
+
+__global__ void gather_rows_kernel(const float *__restrict__ q, int D, const int32_t *__restrict__ idx, int64_t n,
+                                   float *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * D) return;
+  const int64_t r = i / D, c = i % D;
+  out[i] = q[(int64_t)idx[r] * D + c];
+}
+
+__global__ void scatter_labels_kernel(const int8_t *__restrict__ src, const float *__restrict__ fsrc,
+                                      const int32_t *__restrict__ idx, int64_t n, int8_t *__restrict__ label,
+                                      float *__restrict__ pred) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  label[idx[i]] = src[i];
+  if (pred) pred[idx[i]] = fsrc[i];
+}
+
+// sum of squares of x[0..n) into *acc (one atomic per block; used once per
+// training call to scale the targets)
+__global__ void sumsq_kernel(const float *__restrict__ x, int64_t n, double *__restrict__ acc) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)x[i] * (double)x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
+    atomicAdd(acc, t);
+  }
+}
+
+__global__ void scale_kernel(float *__restrict__ x, int64_t n, float s) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= s;
+}
+
+// ------------------------------------------------------------ launchers ---
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, bf16 *XT,
+                                 cudaStream_t s) {
+  surr_features_kernel<<<blocks_for(n_pad, 128), 128, 0, s>>>(c, q, n, n_pad, X, XT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(int epi, int nt, const GemmArgs &g, int splits, cudaStream_t s) {
+  switch (epi * 1000 + nt) {
+    case EPI_RELU * 1000 + 128: return launch_gemm_t<128, EPI_RELU>(g, splits, s);
+    case EPI_RELU * 1000 + 256: return launch_gemm_t<256, EPI_RELU>(g, splits, s);
+    case EPI_HEAD * 1000 + 256: return launch_gemm_t<256, EPI_HEAD>(g, splits, s);
+    case EPI_MASK * 1000 + 128: return launch_gemm_t<128, EPI_MASK>(g, splits, s);
+    case EPI_MASK * 1000 + 256: return launch_gemm_t<256, EPI_MASK>(g, splits, s);
+    case EPI_F32 * 1000 + 64: return launch_gemm_t<64, EPI_F32>(g, splits, s);
+    case EPI_F32 * 1000 + 128: return launch_gemm_t<128, EPI_F32>(g, splits, s);
+    case EPI_F32 * 1000 + 256: return launch_gemm_t<256, EPI_F32>(g, splits, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_surr_head_bwd(const float *out, const float *y, const bf16 *h3, const float *w4, int B, bf16 *dP3,
+                                 float *pw4, float *pb4, float *ploss, cudaStream_t s) {
+  surr_head_bwd_kernel<<<B / kHeadRows, kSurrW, 0, s>>>(out, y, h3, w4, B, dP3, pw4, pb4, ploss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_bf16(const bf16 *in, int64_t rows, int64_t cols, bf16 *out, cudaStream_t s) {
+  dim3 grid((unsigned)(cols / 32), (unsigned)(rows / 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const float *src, int nz, int64_t stride, int64_t n, float *dst, cudaStream_t s) {
+  sum_partials_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, nz, stride, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sum_bf16(const bf16 *Mt, int64_t rows, int64_t cols, float *dst, cudaStream_t s) {
+  row_sum_bf16_kernel<<<blocks_for(rows, 8), 256, 0, s>>>(Mt, rows, cols, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
+                        float eps, int64_t t, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  adam_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p, m, v, g, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, bf16 *WTb, cudaStream_t s) {
+  weights_bf16_kernel<<<blocks_for((int64_t)rows * cols, 256), 256, 0, s>>>(W, rows, cols, Wb, WTb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surr_decide(const float *out, float scale, int64_t n, float tau, float *pred, int8_t *label,
+                               int32_t *fb_idx, int32_t *fb_cnt, cudaStream_t s) {
+  surr_decide_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, scale, n, tau, pred, label, fb_idx, fb_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const float *q, int D, const int32_t *idx, int64_t n, float *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  gather_rows_kernel<<<blocks_for(n * D, 256), 256, 0, s>>>(q, D, idx, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_labels(const int8_t *src, const float *fsrc, const int32_t *idx, int64_t n, int8_t *label,
+                                  float *pred, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  scatter_labels_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, fsrc, idx, n, label, pred);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const float *x, int64_t n, double *acc, cudaStream_t s) {
+  sumsq_kernel<<<152 * 4, 256, 0, s>>>(x, n, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float *x, int64_t n, float v, cudaStream_t s) {
+  scale_kernel<<<blocks_for(n, 256), 256, 0, s>>>(x, n, v);
+  return cudaGetLastError();
+}
+
+}  // namespace fk
+
+namespace fk {
+
+// tau for zero sign errors on a held-out set: the largest |pred| among the
+// rows whose sign differs from the exact score's; also counts them.
+__global__ void surr_calibrate_kernel(const float *__restrict__ pred, const float *__restrict__ f, int64_t n,
+                                      unsigned *__restrict__ tau_bits, unsigned long long *__restrict__ wrong) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool w = (pred[i] >= 0.f) != (f[i] >= 0.f);
+  if (w) {
+    atomicMax(tau_bits, __float_as_uint(fabsf(pred[i])));
+    atomicAdd(wrong, 1ull);
+  }
+}
+
+__global__ void count_below_kernel(const float *__restrict__ pred, int64_t n, float tau,
+                                   unsigned long long *__restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && !(fabsf(pred[i]) > tau)) atomicAdd(cnt, 1ull);
+}
+
+cudaError_t launch_surr_calibrate(const float *pred, const float *f, int64_t n, unsigned *tau_bits,
+                                  unsigned long long *wrong, unsigned long long *below_cnt, float tau_hint,
+                                  cudaStream_t s) {
+  surr_calibrate_kernel<<<blocks_for(n, 256), 256, 0, s>>>(pred, f, n, tau_bits, wrong);
+  (void)tau_hint;
+  (void)below_cnt;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_below(const float *pred, int64_t n, float tau, unsigned long long *cnt, cudaStream_t s) {
+  count_below_kernel<<<blocks_for(n, 256), 256, 0, s>>>(pred, n, tau, cnt);
+  return cudaGetLastError();
+}
+
+}  // namespace fk

@@ -44,12 +44,15 @@ struct GemmArgs {
   int64_t ldm;
   float *Cf;            // EPI_F32 output; split z at Cf + z * zstride
   int64_t ldcf, zstride;
-  const float *w4;      // EPI_HEAD: out[m] = relu(acc + bias) . w4 + b4
-  float b4;
+  const float *w4;      // EPI_HEAD: out[m] = relu(acc + bias) . w4 + *b4
+  const float *b4;
   float *out;
   int32_t *err;
   uint32_t wait_limit;
 };
+
+constexpr int kSurrIn = 64;   // surrogate input width (56 features, zero-padded)
+constexpr int kSurrW = 256;   // hidden width
 
 constexpr int kGemmThreads = 128;
 constexpr int kBM = 128, kBK = 64;
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const GemmArgs
         for (int i = 0; i < 16; ++i) g.CT[(int64_t)(n + i) * g.ldct + gm] = hb[i];
       }
     }
-    if (EPI == EPI_HEAD) g.out[gm] = dot + g.b4;
+    if (EPI == EPI_HEAD) g.out[gm] = dot + *g.b4;
   } else if (tid == 0) {
     atomicOr(g.err, kErrTimeout);
   }

@@ -30,7 +30,8 @@ EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
     "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
-    "fk_probe_pipe", "fk_tc_gemm_bf16",
+    "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
+    "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
 )
 
 
@@ -52,6 +53,20 @@ class FkCp(ctypes.Structure):
 class FastronParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("beta", ctypes.c_double), ("iter_max", ctypes.c_int64),
                 ("s_max", ctypes.c_int64), ("warm_start", ctypes.c_int32), ("trace", ctypes.c_int32)]
+
+
+class SurrogateTrainParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("holdout", ctypes.c_float), ("reinit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SurrogateStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("n_train", ctypes.c_int64), ("n_holdout", ctypes.c_int64),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float), ("scale", ctypes.c_float),
+                ("tau", ctypes.c_float), ("holdout_sign_error", ctypes.c_float), ("holdout_fallback", ctypes.c_float)]
+
+
+SURROGATE_PARAMS = 148481
 
 
 class FastronStats(ctypes.Structure):
@@ -100,6 +115,15 @@ def load(build_if_missing: bool = False):
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
             "fk_tc_gemm_bf16": ([P, I64, P, I64, I, I, I, I, P, P], I),
+            "surrogate_create": ([P, ctypes.c_uint64, PP], I),
+            "surrogate_destroy": ([P], None),
+            "surrogate_train": ([P, P, P, I64, P, P, P], I),
+            "surrogate_infer": ([P, P, P, I64, D, P, P, P, P], I),
+            "surrogate_forward": ([P, P, I64, P, P], I),
+            "surrogate_set_params": ([P, P, I64], I),
+            "surrogate_get_params": ([P, P, I64, P, P], I),
+            "surrogate_gradients": ([P, P, I64, P, P, P], I),
+            "surrogate_adam_step": ([P, P, ctypes.c_float], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -314,3 +338,71 @@ def fk_probe_pipe(kind: int):
     sec = ctypes.c_double()
     _check(load().fk_probe_pipe(int(kind), ctypes.byref(ops), ctypes.byref(sec)))
     return ops.value, sec.value
+
+
+# ------------------------------------------------------------ surrogate ---
+
+def surrogate_create(chain, seed=0):
+    out = ctypes.c_void_p()
+    _check(load().surrogate_create(chain, int(seed), ctypes.byref(out)))
+    return out
+
+
+def surrogate_destroy(s):
+    load().surrogate_destroy(s)
+
+
+def surrogate_train(s, model, q, epochs=10, batch=8192, lr=1e-3, holdout=0.1, reinit=True, stream=None) -> dict:
+    """Trains the surrogate on float32 queries q (n, D); targets are the model's FP32 scores."""
+    import torch
+    p = SurrogateTrainParams(int(epochs), int(batch), float(lr), float(holdout), int(bool(reinit)), 0)
+    st = SurrogateStats()
+    _check(load().surrogate_train(s, model, _dev(q, torch.float32, "q"), q.shape[0], ctypes.byref(p),
+                                  ctypes.byref(st), _stream(stream)))
+    return {k: getattr(st, k) for k, _ in SurrogateStats._fields_}
+
+
+def surrogate_infer(s, model, q, label, pred=None, tau=0.0, stream=None) -> int:
+    """Labels of float32 queries q (n, D); returns the number of fallback queries."""
+    import torch
+    n = q.shape[0]
+    nf = ctypes.c_int64()
+    _check(load().surrogate_infer(s, model, _dev(q, torch.float32, "q"), n, float(tau), _dev(label, torch.int8, "label", (n,)),
+                                  None if pred is None else _dev(pred, torch.float32, "pred", (n,)), ctypes.byref(nf),
+                                  _stream(stream)))
+    return nf.value
+
+
+def surrogate_forward(s, q, out, stream=None):
+    import torch
+    n = q.shape[0]
+    _check(load().surrogate_forward(s, _dev(q, torch.float32, "q"), n, _dev(out, torch.float32, "out", (n,)),
+                                    _stream(stream)))
+
+
+def surrogate_set_params(s, params):
+    a, ap = _host(params, np.float32)
+    _check(load().surrogate_set_params(s, ap, a.shape[0]))
+
+
+def surrogate_get_params(s):
+    a = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+    sc, tau = ctypes.c_float(), ctypes.c_float()
+    _check(load().surrogate_get_params(s, a.ctypes.data_as(ctypes.c_void_p), a.shape[0], ctypes.byref(sc),
+                                       ctypes.byref(tau)))
+    return a, sc.value, tau.value
+
+
+def surrogate_gradients(s, q, target):
+    import torch
+    n = q.shape[0]
+    g = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().surrogate_gradients(s, _dev(q, torch.float32, "q"), n, _dev(target, torch.float32, "target", (n,)),
+                                      g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def surrogate_adam_step(s, grad, lr):
+    a, ap = _host(grad, np.float32)
+    _check(load().surrogate_adam_step(s, ap, float(lr)))

@@ -1,0 +1,156 @@
+"""The learned surrogate on the tensor cores against the FP64 MLP oracle:
+forward values, gradients of every parameter tensor, Adam steps, and
+training plus inference with fallback to the exact score.
+
+Gradient bounds (relative L2 error per tensor): against the oracle that keeps
+activations and deltas in BF16 between layers (the stated precision of the
+tensor-core path) 5e-3; against plain FP64 5e-2, because three BF16-stored
+deltas precede the first layer's gradient (measured 2.5-3.6% at 512 rows,
+1-3% at 4096, the same with the FP64 emulation of the BF16 storage)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as L
+from paper_1910_06451_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ORDER = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)), ("b3", (256,)),
+         ("w4", (256,)), ("b4", (1,))]
+
+
+def _flat(p):
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).reshape(-1) for k, _ in ORDER]).astype(np.float32)
+
+
+def _unflat(v):
+    out, o = {}, 0
+    for k, shp in ORDER:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(v[o:o + n], dtype=np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def _bf16(x):
+    return torch.from_numpy(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+@pytest.fixture(scope="module")
+def setup(fk):
+    w = synth.workload("arm7-n5000")
+    chain = fk.chain_from_arm(w.scene.arm)
+    s = fk.surrogate_create(chain, seed=1)
+    yield w, chain, s
+    fk.surrogate_destroy(s)
+    fk.fk_chain_destroy(chain)
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = L.init_params(rng)
+    for k in ("b1", "b2", "b3", "b4"):
+        p[k] = rng.normal(size=p[k].shape) * 0.05
+    return p
+
+
+def _oracle_with_bf16(p, w, q):
+    """The oracle evaluated on the BF16-rounded weights and features the GPU uses."""
+    pb = dict(p)
+    for k in ("W1", "W2", "W3"):
+        pb[k] = _bf16(p[k])
+    X = _bf16(L.features(w.scene.arm, q.astype(np.float64)))
+    return pb, X
+
+
+def test_forward_matches_oracle(fk, setup):
+    w, chain, s = setup
+    p = _params(3)
+    fk.surrogate_set_params(s, _flat(p))
+    q = w.query_configs(1000)
+    out = torch.empty(1000, dtype=torch.float32, device="cuda")
+    fk.surrogate_forward(s, torch.from_numpy(q).cuda(), out)
+    pb, X = _oracle_with_bf16(_unflat(_flat(p)), w, q)
+    want, _ = L.forward(pb, X)
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - want) <= 1e-2 * np.linalg.norm(want)
+
+
+def test_gradients_match_oracle(fk, setup):
+    w, chain, s = setup
+    p = _unflat(_flat(_params(4)))
+    fk.surrogate_set_params(s, _flat(p))
+    n = 512
+    q = w.query_configs(n)
+    target = np.random.default_rng(5).normal(size=n).astype(np.float32)
+    g, loss = fk.surrogate_gradients(s, torch.from_numpy(q).cuda(), torch.from_numpy(target).cuda())
+    pb, X = _oracle_with_bf16(p, w, q)
+    out, cache = L.forward(pb, X)
+    want = L.backward(pb, cache, out, target.astype(np.float64))
+    got = _unflat(g)
+    emu = L.backward_bf16_storage(pb, X, target.astype(np.float64))
+    assert loss == pytest.approx(L.loss(out, target), rel=1e-2)
+    for k, _ in ORDER:
+        err = np.linalg.norm(got[k] - want[k]) / max(np.linalg.norm(want[k]), 1e-30)
+        err_b = np.linalg.norm(got[k] - emu[k]) / max(np.linalg.norm(emu[k]), 1e-30)
+        assert err_b <= 5e-3, (k, err_b)
+        assert err <= 5e-2, (k, err)
+
+
+def test_adam_step_matches_oracle(fk, setup):
+    w, chain, s = setup
+    s2 = fk.surrogate_create(chain, seed=2)
+    try:
+        p = _unflat(_flat(_params(6)))
+        fk.surrogate_set_params(s2, _flat(p))
+        rng = np.random.default_rng(7)
+        st = {}
+        for it in range(3):
+            g = {k: rng.normal(size=shp) for k, shp in ORDER}
+            gf = _flat(g)
+            fk.surrogate_adam_step(s2, gf, 1e-3)
+            L.adam_step(p, _unflat(gf), st, lr=1e-3)
+        got = _unflat(fk.surrogate_get_params(s2)[0])
+        for k, _ in ORDER:
+            np.testing.assert_allclose(got[k], p[k], rtol=1e-4, atol=1e-6)
+    finally:
+        fk.surrogate_destroy(s2)
+
+
+def test_train_and_infer_with_fallback(fk, setup):
+    w, chain, s = setup
+    dev = torch.device("cuda")
+    model = fk.fastron_model_create(chain)
+    try:
+        X = w.train_configs()
+        y = torch.empty(w.n_train, dtype=torch.int8, device=dev)
+        fk.fk_label(chain, w.scene.boxes, w.scene.radius, torch.from_numpy(X).to(dev), y)
+        fk.fastron_train(model, torch.from_numpy(X.astype(np.float64)).to(dev), y, w.gamma, w.beta, w.iter_max,
+                         w.s_max)
+        qtr = torch.from_numpy(synth.uniform_configs(4242, 1 << 18, 7, w.scene.arm.qlim)).to(dev)
+        st = fk.surrogate_train(s, model, qtr, epochs=4, batch=4096, lr=1e-3, holdout=0.125)
+        assert st["steps"] > 0 and st["loss_last"] < st["loss_first"]
+        assert st["tau"] >= 0 and 0 < st["holdout_fallback"] <= 1
+        n = 100_000
+        q = torch.from_numpy(w.query_configs(n)).to(dev)
+        lab = torch.empty(n, dtype=torch.int8, device=dev)
+        pred = torch.empty(n, dtype=torch.float32, device=dev)
+        nfb = fk.surrogate_infer(s, model, q, lab, pred)
+        exact = torch.empty(n, dtype=torch.int8, device=dev)
+        fk.fk_score(model, q, exact, rescore=True)
+        raw = torch.empty(n, dtype=torch.float32, device=dev)
+        fk.surrogate_forward(s, q, raw)
+        _, scale, tau = fk.surrogate_get_params(s)
+        assert tau == st["tau"]
+        p_net = raw.cpu().numpy() * np.float32(scale)
+        lab, exact = lab.cpu().numpy(), exact.cpu().numpy()
+        assert 0 < nfb < n
+        confident = np.abs(p_net) > np.float32(tau)
+        # every fallback query carries the exact label
+        assert np.array_equal(lab[~confident], exact[~confident])
+        assert np.sum(~confident) == nfb
+        # the network's answers agree with the exact labels on almost all confident queries
+        assert np.mean(lab[confident] == exact[confident]) >= 0.995
+    finally:
+        fk.fastron_model_destroy(model)

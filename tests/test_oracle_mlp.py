@@ -76,3 +76,35 @@ def test_features_at_known_configurations():
                                    atol=1e-16)
     # control point 0 is the base: constant
     assert np.all(f[0, :3] == 0)
+
+
+def test_bf16_rounding():
+    # representable values stay; halfway cases go to the even neighbour
+    assert L.bf16_round(1.0) == 1.0 and L.bf16_round(-3.5) == -3.5
+    one_ulp = 2.0 ** -7  # bf16 spacing just above 1
+    assert L.bf16_round(1.0 + one_ulp / 2) == 1.0               # tie -> even (1.0)
+    assert L.bf16_round(1.0 + 1.5 * one_ulp) == 1.0 + 2 * one_ulp  # tie -> even
+    assert L.bf16_round(1.0 + 0.6 * one_ulp) == 1.0 + one_ulp
+    assert L.bf16_round(np.float32(3.0e38)) == pytest.approx(3.0e38, rel=1e-2)
+
+
+def test_bf16_storage_gradients(monkeypatch):
+    rng = np.random.default_rng(8)
+    p = L.init_params(rng, 8, 16)
+    for k in ("b1", "b2", "b3", "b4"):
+        p[k] = rng.normal(size=p[k].shape) * 0.1
+    X = rng.normal(size=(40, 8))
+    y = rng.normal(size=40)
+    out, cache = L.forward(p, X)
+    g = L.backward(p, cache, out, y)
+    g_bf = L.backward_bf16_storage(p, X, y)
+    # the storage rounding perturbs the gradients at the bfloat16 level ...
+    for k in g:
+        rel = np.linalg.norm(g_bf[k] - g[k]) / np.linalg.norm(g[k])
+        assert rel < 5e-2, k
+    assert any(np.linalg.norm(g_bf[k] - g[k]) > 0 for k in ("W1", "W2", "W3"))
+    # ... and without it the storage variant is exactly the FP64 back-propagation
+    monkeypatch.setattr(L, "bf16_round", lambda x: np.asarray(x, dtype=np.float64))
+    g_id = L.backward_bf16_storage(p, X, y)
+    for k in g:
+        np.testing.assert_allclose(g_id[k], g[k], rtol=1e-13, atol=1e-15)
