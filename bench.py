@@ -151,6 +151,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=N_QUERY, help="query batch size (profiling runs use a smaller one)")
+    ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
+    ap.add_argument("--surrogate-epochs", type=int, default=12)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -280,6 +282,45 @@ def main():
     h2d = Qh.numel() * 4 + Xh.numel() * 8 + X32h.numel() * 4
     d2h = labh.numel()
 
+    # query-pass alternatives on the same batch (not part of the step):
+    # the learned surrogate with exact fallback, against the exact path
+    paths = {"fp32_exact": {"checks_per_s": nq / (query_ms * 1e-3), "ms": query_ms, "label_mismatch": 0,
+                            "rescored": nres}}
+    if args.surrogate_train > 0:
+        sur = fk.surrogate_create(chain, seed=rank + 1)
+        try:
+            qtr = torch.from_numpy(synth.uniform_configs(w.seed + 7, args.surrogate_train, arm.D, arm.qlim)).to(dev)
+            t0 = time.perf_counter()
+            sst = fk.surrogate_train(sur, model, qtr, epochs=args.surrogate_epochs, batch=8192, lr=1e-3,
+                                     holdout=0.0625)
+            torch.cuda.synchronize()
+            train_s = time.perf_counter() - t0
+            del qtr
+            slab = torch.empty(nq, dtype=torch.int8, device=dev)
+            ex = torch.empty(nq, dtype=torch.int8, device=dev)
+            fk.fk_score(model, Q, ex, rescore=True)
+            nfb = fk.surrogate_infer(sur, model, Q, slab)
+            times_s = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fk.surrogate_infer(sur, model, Q, slab)
+                b.record()
+                b.synchronize()
+                times_s.append(a.elapsed_time(b))
+            sms = statistics.median(times_s)
+            mism = int((slab != ex).sum().item())
+            paths["surrogate"] = {"checks_per_s": nq / (sms * 1e-3), "ms": sms, "fallback": nfb / nq,
+                                  "label_mismatch": mism, "label_mismatch_rate": mism / nq,
+                                  "tau": sst["tau"], "holdout_fallback": sst["holdout_fallback"],
+                                  "holdout_sign_error": sst["holdout_sign_error"], "train_s": train_s,
+                                  "train_rows": sst["n_train"], "epochs": args.surrogate_epochs,
+                                  "loss_last": sst["loss_last"], "speedup_vs_fp32_exact": query_ms / sms}
+            del slab, ex
+        finally:
+            fk.surrogate_destroy(sur)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(w, args.cpu_sample, os.cpu_count() or 1)
@@ -296,6 +337,7 @@ def main():
             "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
                           "rescored_queries": nres},
             "query_only_checks_per_s": nq / (query_ms * 1e-3),
+            "query_paths": paths,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
