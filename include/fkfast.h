@@ -203,6 +203,37 @@ int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double ra
  * synchronised with calls in flight on other threads. */
 void fk_set_wait_limit(uint32_t polls);
 
+/* ---- many scenes in one launch -----------------------------------------
+ * A batch groups trained models (one per scene, each with its own chain,
+ * support set and kernel width; all with the same DOF and number of
+ * configuration-dependent control points).  fk_score_batched scores every
+ * scene's queries in one persistent launch: work items (scene, block of
+ * queries) sorted by cost |S| x queries, longest first, handed out by an
+ * atomic counter; then one FP64 re-score launch for all band queries.  The
+ * launches are captured once in a CUDA graph and replayed while q, f, label,
+ * rescore, q_off and the tuned variant stay the same.  The models must stay
+ * alive and unchanged while the batch exists (recreate it after retraining).
+ * The paper's evaluation scores one scene at a time; this is the multi-scene
+ * form of Sec. III-B's check. */
+typedef struct fk_batch fk_batch_t;
+int fk_batch_create(fastron_model_t *const *models, int n_scenes, fk_batch_t **out);
+void fk_batch_destroy(fk_batch_t *batch);
+
+/* q: device float, all scenes' queries concatenated, scene i at rows
+ * q_off[i] .. q_off[i+1]-1 (q_off: host int64 [n_scenes + 1], q_off[0] = 0).
+ * label (device int8 [total]) and f (device float [total] or NULL) in the same
+ * order; rescore and n_rescored as in fk_score.  A change of q_off rebuilds
+ * the work list (the device is synchronised, then the list is uploaded). */
+int fk_score_batched(fk_batch_t *batch, const float *q, const int64_t *q_off, int rescore, float *f, int8_t *label,
+                     int64_t *n_rescored, void *stream);
+
+/* Autotuner: times every compiled tile variant (queries per thread, support
+ * pairs per shared-memory tile, threads per CTA) on this batch and keeps the
+ * fastest for later calls.  ms (host, may be NULL) receives up to cap times;
+ * best (host, may be NULL) the chosen variant.  Synchronous. */
+int fk_batch_tune(fk_batch_t *batch, const float *q, const int64_t *q_off, int8_t *label, float *ms, int cap,
+                  int *best);
+
 /* ---- learned surrogate (not part of the paper) -------------------------
  * A 64-256-256-256-1 ReLU MLP that predicts the model value f(q) from
  * features of the control points (position of each control point, sin/cos of

@@ -1,0 +1,241 @@
+// Many independent scenes (own chain, own support set, own query batch) in
+// one persistent launch.  Work items are (scene, block of queries); the host
+// sorts them by cost, |S_scene| x queries, longest first, and CTAs take them
+// in that order from an atomic counter, so the long items start first and the
+// short ones fill the tail.  Each item stages its scene's chain in shared
+// memory and runs the same score_block as the per-call kernel; the band
+// queries of every scene are then re-scored in FP64 by one launch.
+#include <cstring>
+
+#include "fk_internal.h"
+#include "fk_ptx.cuh"
+#include "score_core.cuh"
+
+namespace fk {
+
+// Per-scene description in device memory.
+struct SceneDev {
+  ChainF cf;
+  ChainD cd;
+  const float4 *rec;
+  const double *cp64;
+  const double *alpha;
+  int64_t ns;
+  float gs;
+  double gamma;
+  int64_t q_off;  // first query of the scene in the concatenated batch
+  int64_t n;      // its number of queries
+};
+
+struct WorkItem {
+  int32_t scene;
+  int32_t block;  // block of NTHR * Q queries within the scene
+};
+
+struct BatchArgs {
+  const SceneDev *scenes;
+  const WorkItem *items;
+  int32_t n_items;
+  int32_t *counter;
+  const float *q;
+  float *f;
+  int8_t *label;
+  float eps;
+  int32_t *band_idx;
+  int32_t *band_scene;
+  int32_t *band_cnt;
+  int32_t *err;
+  uint32_t wait_limit;
+};
+
+template <int MV, int Q, int TP, int NTHR>
+__global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) {
+  extern __shared__ __align__(128) float4 tiles[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) ChainF cs;
+  __shared__ int item_sh;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) item_sh = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int it = item_sh;
+    if (it >= a.n_items) break;
+    const WorkItem w = a.items[it];
+    const SceneDev *sc = a.scenes + w.scene;
+    {
+      const int *src = reinterpret_cast<const int *>(&sc->cf);
+      int *dst = reinterpret_cast<int *>(&cs);
+      for (int i = tid; i < (int)(sizeof(ChainF) / sizeof(int)); i += NTHR) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int64_t off = sc->q_off;
+    const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, a.eps, a.band_idx, a.band_scene, w.scene, off,
+                     a.band_cnt, a.err, a.wait_limit};
+    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->ns, sc->gs, a.q + off * sc->cf.D, sc->n,
+                                                 (int64_t)w.block * (NTHR * Q), o, tiles, bar);
+    if (!ok) break;   // identical in every thread
+    __syncthreads();  // item_sh, cs and the tiles are reused by the next item
+  }
+}
+
+// FP64 re-score of the band queries of all scenes: one warp per entry.
+constexpr int kBRescoreWarps = 8;
+
+__global__ void __launch_bounds__(kBRescoreWarps * 32) batched_rescore_kernel(const SceneDev *__restrict__ scenes,
+                                                                             const float *__restrict__ q,
+                                                                             const int32_t *__restrict__ band_idx,
+                                                                             const int32_t *__restrict__ band_scene,
+                                                                             const int32_t *__restrict__ band_cnt,
+                                                                             float *__restrict__ f,
+                                                                             int8_t *__restrict__ label) {
+  __shared__ double qcp[kBRescoreWarps][FK_MAX_CP][3];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t gw = blockIdx.x * (int64_t)kBRescoreWarps + wl;
+  const int64_t nw = (int64_t)gridDim.x * kBRescoreWarps;
+  const int64_t cnt = *band_cnt;
+  for (int64_t e = gw; e < cnt; e += nw) {
+    const int64_t k = band_idx[e];
+    const SceneDev *sc = scenes + band_scene[e];
+    const ChainD &c = sc->cd;
+    if (lane == 0) {
+      PoseD P;
+      pose_base(c, P);
+      for (int m = 0; m < c.M; ++m)
+        if (c.cj[m] == 0) pose_point(P, c.ct[m], qcp[wl][m]);
+      for (int i = 0; i < c.D; ++i) {
+        pose_step(c, i, (double)q[k * c.D + i], P);
+        for (int m = 0; m < c.M; ++m)
+          if (c.cj[m] == i + 1) pose_point(P, c.ct[m], qcp[wl][m]);
+      }
+    }
+    __syncwarp();
+    const double hg = 0.5 * sc->gamma, invM = 1.0 / c.M;
+    const int64_t ns = sc->ns;
+    double acc = 0.0;
+    for (int64_t s = lane; s < ns; s += 32) {
+      double ks = (double)c.n_const;
+      for (int v = 0; v < c.Mv; ++v) {
+        const int m = c.vidx[v];
+        const double sp[3] = {sc->cp64[(m * 3 + 0) * ns + s], sc->cp64[(m * 3 + 1) * ns + s],
+                              sc->cp64[(m * 3 + 2) * ns + s]};
+        ks += k_rq_f64(hg, sp, qcp[wl][m]);
+      }
+      acc = fma(sc->alpha[s] * invM, ks, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      if (f) f[k] = (float)acc;
+      label[k] = acc >= 0.0 ? 1 : -1;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------- variants ---
+// Tile shapes the autotuner chooses among: queries per thread, support pairs
+// per shared-memory tile, threads per CTA.
+struct Variant {
+  int Q, TP, NTHR;
+};
+constexpr Variant kVariants[] = {{2, 64, 256}, {1, 64, 256}, {2, 32, 256}, {2, 128, 256}, {1, 32, 128}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int batched_num_variants() { return kNumVariants; }
+int batched_block_queries(int v) { return kVariants[v].Q * kVariants[v].NTHR; }
+
+template <int MV, int Q, int TP, int NTHR>
+static cudaError_t launch_bv(const BatchArgs &a, cudaStream_t s, bool prepare_only) {
+  auto kern = batched_score_kernel<MV, Q, TP, NTHR>;
+  const size_t smem = 2 * (size_t)TP * rec_len(MV) * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess || prepare_only) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHR, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > a.n_items) grid = a.n_items > 0 ? a.n_items : 1;
+  kern<<<grid, NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MV>
+static cudaError_t launch_bmv(int v, const BatchArgs &a, cudaStream_t s, bool prep) {
+  switch (v) {
+    case 0: return launch_bv<MV, 2, 64, 256>(a, s, prep);
+    case 1: return launch_bv<MV, 1, 64, 256>(a, s, prep);
+    case 2: return launch_bv<MV, 2, 32, 256>(a, s, prep);
+    case 3: return launch_bv<MV, 2, 128, 256>(a, s, prep);
+    case 4: return launch_bv<MV, 1, 32, 128>(a, s, prep);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool batched_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
+
+cudaError_t launch_batched_score(int mv, int variant, const BatchArgs &a, cudaStream_t s, bool prepare_only) {
+  switch (mv) {
+    case 3: return launch_bmv<3>(variant, a, s, prepare_only);
+    case 7: return launch_bmv<7>(variant, a, s, prepare_only);
+    case 11: return launch_bmv<11>(variant, a, s, prepare_only);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_batched_rescore(const SceneDev *scenes, const float *q, const int32_t *band_idx,
+                                   const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
+                                   cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  batched_rescore_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 304), kBRescoreWarps * 32, 0, s>>>(
+      scenes, q, band_idx, band_scene, band_cnt, f, label);
+  return cudaGetLastError();
+}
+
+size_t scene_dev_size() { return sizeof(SceneDev); }
+size_t work_item_size() { return sizeof(WorkItem); }
+
+// Host-side filling of a SceneDev record (the layout stays private to this file).
+void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const double *cp64,
+                    const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n) {
+  SceneDev d;
+  memset(&d, 0, sizeof d);
+  d.cf = cf;
+  d.cd = cd;
+  d.rec = static_cast<const float4 *>(rec);
+  d.cp64 = cp64;
+  d.alpha = alpha;
+  d.ns = ns;
+  d.gs = (float)sqrt(0.5 * gamma);
+  d.gamma = gamma;
+  d.q_off = q_off;
+  d.n = n;
+  memcpy(dst, &d, sizeof d);
+}
+
+void fill_work_item(void *dst, int32_t scene, int32_t block) {
+  WorkItem w{scene, block};
+  memcpy(dst, &w, sizeof w);
+}
+
+cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
+                                      int32_t *counter, const float *q, float *f, int8_t *label, float eps,
+                                      int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
+                                      uint32_t wait_limit, cudaStream_t s, bool prepare_only) {
+  BatchArgs a{static_cast<const SceneDev *>(scenes), static_cast<const WorkItem *>(items), n_items, counter, q, f,
+              label, eps, band_idx, band_scene, band_cnt, err, wait_limit};
+  return launch_batched_score(mv, variant, a, s, prepare_only);
+}
+
+cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,
+                                        const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
+                                        cudaStream_t s) {
+  return launch_batched_rescore(static_cast<const SceneDev *>(scenes), q, band_idx, band_scene, band_cnt, f, label,
+                                s);
+}
+
+}  // namespace fk

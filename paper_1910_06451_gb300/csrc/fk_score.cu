@@ -22,6 +22,7 @@
 //            support set, a fixed-order warp sum; f and the label are replaced.
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
+#include "score_core.cuh"
 
 namespace fk {
 
@@ -85,202 +86,18 @@ cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackAr
 }
 
 // --------------------------------------------------------------- score ---
-// Packed FP32x2 arithmetic: each 64-bit register holds the same quantity for
-// the two support points of a pair.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2 rcp2(f2 x) {
-  float lo, hi;
-  upk(x, lo, hi);
-  return pk(rcp_approx(lo), rcp_approx(hi));
-}
-
 constexpr int kScoreThreads = 256;
 constexpr int kQ = 2;                          // queries per thread
 constexpr int kQueriesPerCta = kScoreThreads * kQ;
 constexpr int kTilePairs = 64;                 // support pairs per shared-memory tile
-constexpr uint32_t kDrainLimit = 1u << 22;     // polls while draining copies after a timeout
-
-// Number of control-point pairs that share one reciprocal: the rest take one
-// MUFU reciprocal each.  About a sixth of the points paired balances the FP32
-// pipe (128 lanes/clk/SM) against the MUFU pipe (16 lanes/clk/SM).
-template <int MV>
-struct RcpPlan {
-  static constexpr int NP = (MV + 3) / 7;
-};
 
 template <int MV>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
-  extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][REC]
+  extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
-  constexpr int REC = MV + (MV + 1) / 2 + 1;
-  constexpr int NP = RcpPlan<MV>::NP;
-
-  const int tid = threadIdx.x;
-  const int64_t npair = (a.ns + 1) / 2;
-  const int ntiles = (int)((npair + kTilePairs - 1) / kTilePairs);
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  auto issue = [&](int t) {
-    const int64_t p0 = (int64_t)t * kTilePairs;
-    const int64_t cnt = npair - p0 < kTilePairs ? npair - p0 : kTilePairs;
-    const uint32_t bytes = (uint32_t)(cnt * REC * sizeof(float4));
-    uint64_t *b = &bar[t & 1];
-    mbar_arrive_expect_tx(b, bytes);
-    tma_bulk_load(tiles + (size_t)(t & 1) * kTilePairs * REC, a.rec + p0 * REC, bytes, b);
-  };
-  if (tid == 0) {
-    if (ntiles > 0) issue(0);
-    if (ntiles > 1) issue(1);
-  }
-
-  // forward kinematics of this thread's queries, scaled by sqrt(gamma/2) so
-  // that t = 1 + |p - s|^2, duplicated into both halves of a packed register
-  const int64_t qbase = (int64_t)blockIdx.x * kQueriesPerCta + tid;
-  f2 P[kQ][MV][3];
-#pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    const int64_t qi = qbase + k * kScoreThreads;
-    float qv[FK_MAX_DOF];
-    for (int i = 0; i < c.D; ++i) qv[i] = qi < a.n ? a.q[qi * c.D + i] : 0.f;
-    float cp[MV][3];
-    fk_points_f32<MV>(c, qv, cp);
-#pragma unroll
-    for (int m = 0; m < MV; ++m)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float v = a.gs * cp[m][r];
-        P[k][m][r] = pk(v, v);
-      }
-  }
-  const f2 one2 = pk(1.f, 1.f);
-  const float nc = (float)c.n_const;
-  const f2 nc2 = pk(nc, nc);
-
-  f2 F[kQ], B[kQ];
-#pragma unroll
-  for (int k = 0; k < kQ; ++k) F[k] = B[k] = pk(0.f, 0.f);
-  int t_fail = -1;
-  for (int t = 0; t < ntiles; ++t) {
-    const bool got = mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, a.wait_limit);
-    if (!__syncthreads_and(got)) {
-      t_fail = t;
-      break;
-    }
-    const float4 *tile = tiles + (size_t)(t & 1) * kTilePairs * REC;
-    const int64_t p0 = (int64_t)t * kTilePairs;
-    const int cnt = (int)(npair - p0 < kTilePairs ? npair - p0 : kTilePairs);
-#pragma unroll 1
-    for (int j = 0; j < cnt; ++j) {
-      const float4 *r = tile + j * REC;
-      f2 acc[kQ];
-#pragma unroll
-      for (int k = 0; k < kQ; ++k) acc[k] = nc2;
-      f2 tv[kQ][MV];
-#pragma unroll
-      for (int m = 0; m < MV; ++m) {
-        const float4 xy = r[m];
-        const float4 zz = r[MV + m / 2];
-        const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
-        const f2 sz = (m & 1) ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) {
-          const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
-          tv[k][m] = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kQ; ++k) {
-        // pairs: 1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2
-#pragma unroll
-        for (int pp = 0; pp < NP; ++pp) {
-          const f2 t1 = tv[k][2 * pp], t2 = tv[k][2 * pp + 1];
-          const f2 pr = mul2(t1, t2);
-          const f2 num = fma2(t1, t1, mul2(t2, t2));
-          acc[k] = fma2(num, rcp2(mul2(pr, pr)), acc[k]);
-        }
-#pragma unroll
-        for (int m = 2 * NP; m < MV; ++m) {
-          const f2 rr = rcp2(tv[k][m]);
-          acc[k] = fma2(rr, rr, acc[k]);
-        }
-      }
-      const float4 W = r[REC - 1];
-      const f2 w = pk(W.x, W.y), aw = pk(W.z, W.w);
-#pragma unroll
-      for (int k = 0; k < kQ; ++k) {
-        F[k] = fma2(w, acc[k], F[k]);
-        B[k] = fma2(aw, acc[k], B[k]);
-      }
-    }
-    __syncthreads();  // every thread is done with this buffer
-    if (tid == 0 && t + 2 < ntiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + 2);
-    }
-  }
-  if (t_fail >= 0) {
-    // give the copies still in flight (tiles t_fail and t_fail + 1) a
-    // bounded chance to land before the CTA exits, then report
-    if (tid == 0) {
-      for (int t = t_fail; t < ntiles && t < t_fail + 2; ++t)
-        mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, kDrainLimit);
-      atomicOr(a.err, kErrTimeout);
-    }
-    return;
-  }
-
-  const unsigned lane = tid & 31;
-#pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    float f0, f1, b0, b1;
-    upk(F[k], f0, f1);
-    upk(B[k], b0, b1);
-    const float f = f0 + f1, bq = b0 + b1;
-    const int64_t qi = qbase + k * kScoreThreads;
-    const bool valid = qi < a.n;
-    if (valid) {
-      if (a.f) a.f[qi] = f;
-      a.label[qi] = f >= 0.f ? 1 : -1;
-    }
-    if (a.band_idx) {
-      const bool flag = valid && fabsf(f) <= a.eps * bq;
-      const unsigned bal = __ballot_sync(0xffffffffu, flag);
-      if (bal) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(a.band_cnt, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (flag) a.band_idx[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)qi;
-      }
-    }
-  }
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
+  score_block<MV, kQ, kTilePairs, kScoreThreads>(c, a.rec, a.ns, a.gs, a.q, a.n,
+                                                 (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
 }
 
 }  // namespace fk

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -1103,5 +1104,232 @@ extern "C" int surrogate_infer(surrogate_t *s, fastron_model_t *model, const flo
                              st));
   }
   if (n_fallback) *n_fallback = nfb;
+  return FK_OK;
+}
+
+// ------------------------------------------------------ batched scenes ---
+namespace fk {
+int batched_num_variants();
+int batched_block_queries(int v);
+bool batched_supported(int mv);
+size_t scene_dev_size();
+size_t work_item_size();
+void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const double *cp64,
+                    const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n);
+void fill_work_item(void *dst, int32_t scene, int32_t block);
+cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
+                                      int32_t *counter, const float *q, float *f, int8_t *label, float eps,
+                                      int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
+                                      uint32_t wait_limit, cudaStream_t s, bool prepare_only);
+cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,
+                                        const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
+                                        cudaStream_t s);
+}  // namespace fk
+
+struct fk_batch {
+  int n_scenes = 0, mv = 0, D = 0;
+  std::vector<fastron_model *> models;
+  DevBuf scenes, items, flags, band_idx, band_scene;
+  std::vector<char> scenes_h, items_h;
+  int32_t n_items = 0;
+  std::vector<int64_t> off;  // query offsets of the current work list
+  int variant = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const float *g_q = nullptr;
+  float *g_f = nullptr;
+  int8_t *g_label = nullptr;
+  int g_rescore = -1, g_variant = -1;
+};
+
+static void batch_drop_graph(fk_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+}
+
+extern "C" int fk_batch_create(fastron_model_t *const *models, int n_scenes, fk_batch_t **out) {
+  if (!out) return fail(FK_ERR_ARG, "fk_batch_create: out is NULL");
+  *out = nullptr;
+  if (!models || n_scenes < 1) return fail(FK_ERR_ARG, "fk_batch_create: need at least one model");
+  const fastron_model *m0 = models[0];
+  if (!m0) return fail(FK_ERR_ARG, "fk_batch_create: model 0 is NULL");
+  for (int i = 0; i < n_scenes; ++i) {
+    const fastron_model *m = models[i];
+    if (!m) return fail(FK_ERR_ARG, "fk_batch_create: model %d is NULL", i);
+    if (m->ns < 0) return fail(FK_ERR_STATE, "fk_batch_create: model %d is untrained", i);
+    if (m->chain->D != m0->chain->D || m->chain->cf.Mv != m0->chain->cf.Mv)
+      return fail(FK_ERR_ARG, "fk_batch_create: model %d has another DOF or control-point count", i);
+    if (m->gamma > 1e7) return fail(FK_ERR_ARG, "fk_batch_create: model %d gamma out of range", i);
+  }
+  if (!batched_supported(m0->chain->cf.Mv))
+    return fail(FK_ERR_ARG, "fk_batch_create: %d configuration-dependent control points is not a compiled shape",
+                m0->chain->cf.Mv);
+  fk_batch *b = new fk_batch;
+  b->n_scenes = n_scenes;
+  b->mv = m0->chain->cf.Mv;
+  b->D = m0->chain->D;
+  b->models.assign(models, models + n_scenes);
+  b->scenes_h.resize(scene_dev_size() * (size_t)n_scenes);
+  cudaError_t e = b->scenes.ensure(b->scenes_h.size());
+  if (e == cudaSuccess) e = b->flags.ensure(sizeof(int32_t) * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    fk_batch_destroy(b);
+    return fail(FK_ERR_CUDA, "fk_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return FK_OK;
+}
+
+extern "C" void fk_batch_destroy(fk_batch_t *b) {
+  if (!b) return;
+  batch_drop_graph(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->scenes.release();
+  b->items.release();
+  b->flags.release();
+  b->band_idx.release();
+  b->band_scene.release();
+  delete b;
+}
+
+// Rebuilds the scene records and the cost-sorted work list for new offsets.
+static int batch_plan(fk_batch *b, const int64_t *q_off) {
+  const int bq = batched_block_queries(b->variant);
+  std::vector<std::pair<int64_t, std::pair<int32_t, int32_t>>> it;
+  for (int i = 0; i < b->n_scenes; ++i) {
+    const fastron_model *m = b->models[i];
+    const int64_t n = q_off[i + 1] - q_off[i];
+    fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p,
+                   m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, q_off[i], n);
+    for (int64_t blk = 0; blk * bq < n; ++blk) {
+      const int64_t qn = n - blk * bq < bq ? n - blk * bq : bq;
+      it.push_back({(m->ns + 1) * qn, {i, (int32_t)blk}});
+    }
+  }
+  std::stable_sort(it.begin(), it.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+  b->n_items = (int32_t)it.size();
+  b->items_h.resize(work_item_size() * (it.size() > 0 ? it.size() : 1));
+  for (size_t k = 0; k < it.size(); ++k) fill_work_item(b->items_h.data() + work_item_size() * k, it[k].second.first, it[k].second.second);
+  CK(cudaDeviceSynchronize());  // earlier launches may still read the old plan
+  CK(b->items.ensure(b->items_h.size()));
+  CK(cudaMemcpy(b->scenes.p, b->scenes_h.data(), b->scenes_h.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->items.p, b->items_h.data(), b->items_h.size(), cudaMemcpyHostToDevice));
+  b->off.assign(q_off, q_off + b->n_scenes + 1);
+  batch_drop_graph(b);
+  return FK_OK;
+}
+
+// Enqueues the batched work on stream s (flags cleared, score, re-score).
+static int batch_enqueue(fk_batch *b, const float *q, float *f, int8_t *label, int rescore, cudaStream_t s) {
+  int32_t *fl = b->flags.as<int32_t>();
+  CK(cudaMemsetAsync(fl, 0, sizeof(int32_t) * 4, s));
+  CK(launch_batched_score_args(b->mv, b->variant, b->scenes.p, b->items.p, b->n_items, fl, q, f, label,
+                               (float)kDefaultEps, rescore ? b->band_idx.as<int32_t>() : nullptr,
+                               rescore ? b->band_scene.as<int32_t>() : nullptr, fl + 1, fl + 2, g_wait_limit, s,
+                               false));
+  if (rescore)
+    CK(launch_batched_rescore_args(b->scenes.p, q, b->band_idx.as<int32_t>(), b->band_scene.as<int32_t>(), fl + 1, f,
+                                   label, s));
+  return FK_OK;
+}
+
+extern "C" int fk_score_batched(fk_batch_t *b, const float *q, const int64_t *q_off, int rescore, float *f,
+                                int8_t *label, int64_t *n_rescored, void *stream) {
+  if (!b || !q_off) return fail(FK_ERR_ARG, "fk_score_batched: NULL pointer");
+  if (q_off[0] != 0) return fail(FK_ERR_ARG, "fk_score_batched: q_off[0] must be 0");
+  for (int i = 0; i < b->n_scenes; ++i)
+    if (q_off[i + 1] < q_off[i]) return fail(FK_ERR_ARG, "fk_score_batched: q_off must not decrease");
+  const int64_t total = q_off[b->n_scenes];
+  if (total > (int64_t)INT32_MAX) return fail(FK_ERR_CAPACITY, "fk_score_batched: more than 2^31 - 1 queries");
+  if (n_rescored) *n_rescored = 0;
+  if (total == 0) return FK_OK;
+  if (!q || !label) return fail(FK_ERR_ARG, "fk_score_batched: q and label must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->off.size() != (size_t)b->n_scenes + 1 || !std::equal(b->off.begin(), b->off.end(), q_off)) {
+    int rc = batch_plan(b, q_off);
+    if (rc != FK_OK) return rc;
+  }
+  if (rescore) {
+    const size_t cap_before = b->band_idx.cap;
+    CK(b->band_idx.ensure(sizeof(int32_t) * (size_t)total));
+    CK(b->band_scene.ensure(sizeof(int32_t) * (size_t)total));
+    if (b->band_idx.cap != cap_before) batch_drop_graph(b);
+  }
+  // replay the captured graph when nothing it depends on has changed
+  if (!b->exec || b->g_q != q || b->g_f != f || b->g_label != label || b->g_rescore != (rescore != 0) ||
+      b->g_variant != b->variant) {
+    batch_drop_graph(b);
+    CK(launch_batched_score_args(b->mv, b->variant, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0.f,
+                                 nullptr, nullptr, nullptr, nullptr, 0, s, true));
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_enqueue(b, q, f, label, rescore, b->cap);
+    cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != FK_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(FK_ERR_CUDA, "fk_score_batched: capture failed: %s", cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+      b->exec = nullptr;
+      return fail(FK_ERR_CUDA, "fk_score_batched: instantiate failed: %s", cudaGetErrorString(ec));
+    }
+    b->g_q = q;
+    b->g_f = f;
+    b->g_label = label;
+    b->g_rescore = rescore != 0;
+    b->g_variant = b->variant;
+  }
+  CK(cudaGraphLaunch(b->exec, s));
+  if (n_rescored) {
+    int32_t h[4];
+    CK(cudaMemcpyAsync(h, b->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h[2] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score_batched: a shared-memory tile wait timed out");
+    *n_rescored = rescore ? h[1] : 0;
+  }
+  return FK_OK;
+}
+
+extern "C" int fk_batch_tune(fk_batch_t *b, const float *q, const int64_t *q_off, int8_t *label, float *ms,
+                             int cap, int *best) {
+  if (!b || !q || !q_off || !label) return fail(FK_ERR_ARG, "fk_batch_tune: NULL pointer");
+  const int nv = batched_num_variants();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best_ms = 0.f;
+  int best_v = 0;
+  for (int v = 0; v < nv; ++v) {
+    b->variant = v;
+    b->off.clear();  // block size depends on the variant: rebuild the plan
+    int rc = fk_score_batched(b, q, q_off, 1, nullptr, label, nullptr, b->cap);
+    if (rc != FK_OK) return rc;
+    float t = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      CK(cudaEventRecord(e0, b->cap));
+      rc = fk_score_batched(b, q, q_off, 1, nullptr, label, nullptr, b->cap);
+      if (rc != FK_OK) return rc;
+      CK(cudaEventRecord(e1, b->cap));
+      CK(cudaEventSynchronize(e1));
+      float x = 0.f;
+      CK(cudaEventElapsedTime(&x, e0, e1));
+      t = x < t ? x : t;
+    }
+    if (ms && v < cap) ms[v] = t;
+    if (v == 0 || t < best_ms) {
+      best_ms = t;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = best_v;
+  b->off.clear();
+  batch_drop_graph(b);
+  if (best) *best = best_v;
   return FK_OK;
 }

@@ -32,6 +32,7 @@ EXPORTS = (
     "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
+    "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune",
 )
 
 
@@ -115,6 +116,10 @@ def load(build_if_missing: bool = False):
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
             "fk_tc_gemm_bf16": ([P, I64, P, I64, I, I, I, I, P, P], I),
+            "fk_batch_create": ([P, I, PP], I),
+            "fk_batch_destroy": ([P], None),
+            "fk_score_batched": ([P, P, P, I, P, P, P, P], I),
+            "fk_batch_tune": ([P, P, P, P, P, I, P], I),
             "surrogate_create": ([P, ctypes.c_uint64, PP], I),
             "surrogate_destroy": ([P], None),
             "surrogate_train": ([P, P, P, I64, P, P, P], I),
@@ -406,3 +411,40 @@ def surrogate_gradients(s, q, target):
 def surrogate_adam_step(s, grad, lr):
     a, ap = _host(grad, np.float32)
     _check(load().surrogate_adam_step(s, ap, float(lr)))
+
+
+# ------------------------------------------------------- batched scenes ---
+
+def fk_batch_create(models):
+    arr = (ctypes.c_void_p * len(models))(*[m.value for m in models])
+    out = ctypes.c_void_p()
+    _check(load().fk_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(models), ctypes.byref(out)))
+    return out
+
+
+def fk_batch_destroy(b):
+    load().fk_batch_destroy(b)
+
+
+def fk_score_batched(b, q, q_off, label, f=None, rescore=True, count=False, stream=None):
+    """Scores the concatenated queries q (total, D) of all scenes; q_off (host
+    int64, n_scenes + 1) gives each scene's rows."""
+    import torch
+    off, offp = _host(q_off, np.int64)
+    total = int(off[-1])
+    nr = ctypes.c_int64()
+    _check(load().fk_score_batched(b, _dev(q, torch.float32, "q"), offp, int(bool(rescore)),
+                                   None if f is None else _dev(f, torch.float32, "f", (total,)),
+                                   _dev(label, torch.int8, "label", (total,)), ctypes.byref(nr) if count else None,
+                                   _stream(stream)))
+    return nr.value if count else None
+
+
+def fk_batch_tune(b, q, q_off, label):
+    import torch
+    off, offp = _host(q_off, np.int64)
+    ms = np.zeros(16, dtype=np.float32)
+    best = ctypes.c_int()
+    _check(load().fk_batch_tune(b, _dev(q, torch.float32, "q"), offp, _dev(label, torch.int8, "label"),
+                                ms.ctypes.data_as(ctypes.c_void_p), 16, ctypes.byref(best)))
+    return best.value, ms

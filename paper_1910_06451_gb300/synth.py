@@ -189,3 +189,40 @@ def workload(name: str, trial: int = 0, **over) -> Workload:
     else:
         raise KeyError(name)
     return dataclasses.replace(w, **over)
+
+
+@dataclasses.dataclass
+class BatchScene:
+    scene: Scene
+    support: np.ndarray   # (ns, D) FP32 support configurations
+    alpha: np.ndarray     # (ns,) weights
+    queries: np.ndarray   # (nq, D) FP32 queries
+    gamma: float
+
+
+def _log_uniform_int(st: Stream, lo: int, hi: int) -> int:
+    return int(round(math.exp(st.uniform(1, math.log(lo), math.log(hi))[0])))
+
+
+def batch_scenes(seed: int, n_scenes: int, support=(200, 6000), queries=(1000, 65536), boxes=(4, 20),
+                 gamma: float = 40.0) -> list[BatchScene]:
+    """Independent 7-DOF scenes with uneven sizes: support-set and query-batch
+    sizes log-uniform in the given ranges, 4-20 boxes.  The support sets are
+    random configurations with normal weights (scale 5, like the trained
+    7-DOF model's): the scoring work and its parity do not depend on how the
+    weights were found."""
+    st = Stream(seed ^ 0xB47C4)
+    out = []
+    for i in range(n_scenes):
+        s = seed * 1000 + i
+        arm = arm_7dof(s)
+        nb = int(st.uniform(1, boxes[0], boxes[1] + 1)[0])
+        ns = _log_uniform_int(st, *support)
+        nq = _log_uniform_int(st, *queries)
+        sc = Scene(arm, random_boxes(s, nb), 0.03)
+        sup = uniform_configs(s + 11, ns, arm.D, arm.qlim)
+        alpha = Stream(s + 13).uniform(ns, -1.0, 1.0)
+        alpha = _f32(np.sign(alpha) * (0.5 + 5.0 * np.abs(alpha)))
+        q = uniform_configs(s + 17, nq, arm.D, arm.qlim)
+        out.append(BatchScene(sc, sup, alpha, q, gamma))
+    return out

@@ -1,0 +1,77 @@
+"""Many scenes in one persistent launch: labels equal those of per-scene
+fk_score calls and of the FP64 oracle, f within the FP32 bound, for uneven
+scenes including empty query batches and single support points; every
+autotuner variant gives the same labels."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1910_06451_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def batch(fk):
+    scenes = synth.batch_scenes(7, 9, support=(1, 700), queries=(1, 3000))
+    scenes[2].queries = scenes[2].queries[:0]       # a scene without queries
+    scenes[4].support = scenes[4].support[:1]       # a single support point
+    scenes[4].alpha = scenes[4].alpha[:1]
+    chains, models = [], []
+    for sc in scenes:
+        ch = fk.chain_from_arm(sc.scene.arm)
+        m = fk.fastron_model_create(ch)
+        fk.fastron_model_set(m, sc.support.astype(np.float64), sc.alpha, sc.gamma)
+        chains.append(ch)
+        models.append(m)
+    b = fk.fk_batch_create(models)
+    off = np.concatenate([[0], np.cumsum([len(sc.queries) for sc in scenes])]).astype(np.int64)
+    q = torch.from_numpy(np.concatenate([sc.queries for sc in scenes])).cuda()
+    yield scenes, models, b, off, q
+    fk.fk_batch_destroy(b)
+    for m in models:
+        fk.fastron_model_destroy(m)
+    for ch in chains:
+        fk.fk_chain_destroy(ch)
+
+
+def test_batched_matches_per_scene_and_oracle(fk, batch):
+    scenes, models, b, off, q = batch
+    total = int(off[-1])
+    lab = torch.empty(total, dtype=torch.int8, device="cuda")
+    f = torch.empty(total, dtype=torch.float32, device="cuda")
+    fk.fk_score_batched(b, q, off, lab, f, count=True)
+    # the second call replays the captured graph
+    lab2 = torch.empty_like(lab)
+    fk.fk_score_batched(b, q, off, lab2, f)
+    torch.cuda.synchronize()
+    lab, lab2, f = lab.cpu().numpy(), lab2.cpu().numpy(), f.cpu().numpy()
+    for i, (sc, m) in enumerate(zip(scenes, models)):
+        a, z = off[i], off[i + 1]
+        if z == a:
+            continue
+        qi = q[a:z].contiguous()
+        ref = torch.empty(z - a, dtype=torch.int8, device="cuda")
+        fk.fk_score(m, qi, ref, rescore=True)
+        want = O.score(sc.scene.arm, sc.support.astype(np.float64), sc.alpha, sc.queries.astype(np.float64),
+                       sc.gamma, nthreads=8)
+        B = O.score(sc.scene.arm, sc.support.astype(np.float64), np.abs(sc.alpha), sc.queries.astype(np.float64),
+                    sc.gamma, nthreads=8)
+        assert np.array_equal(lab[a:z], ref.cpu().numpy()), i
+        assert np.array_equal(lab[a:z], O.labels_from_f(want)), i
+        assert np.array_equal(lab2[a:z], lab[a:z])
+        assert np.all(np.abs(f[a:z] - want) <= 3e-6 * B + 1e-30), i
+
+
+def test_every_tuned_variant_agrees(fk, batch):
+    scenes, models, b, off, q = batch
+    total = int(off[-1])
+    ref = torch.empty(total, dtype=torch.int8, device="cuda")
+    fk.fk_score_batched(b, q, off, ref)
+    best, ms = fk.fk_batch_tune(b, q, off, torch.empty(total, dtype=torch.int8, device="cuda"))
+    assert 0 <= best < 5 and np.all(ms[:5] > 0)
+    lab = torch.empty(total, dtype=torch.int8, device="cuda")
+    fk.fk_score_batched(b, q, off, lab)
+    torch.cuda.synchronize()
+    assert torch.equal(lab, ref)
