@@ -153,6 +153,7 @@ def main():
     ap.add_argument("--queries", type=int, default=N_QUERY, help="query batch size (profiling runs use a smaller one)")
     ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
     ap.add_argument("--surrogate-epochs", type=int, default=12)
+    ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the multi-scene measurement (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -321,6 +322,60 @@ def main():
         finally:
             fk.surrogate_destroy(sur)
 
+    # many scenes: one persistent graph-captured launch (tuned) against one
+    # fk_score call per scene, same queries, same exact labels
+    batched = None
+    if args.batch_scenes > 0:
+        scenes = synth.batch_scenes(100 + rank, args.batch_scenes)
+        bchains, bmodels = [], []
+        for sc in scenes:
+            ch = fk.chain_from_arm(sc.scene.arm)
+            m = fk.fastron_model_create(ch)
+            fk.fastron_model_set(m, sc.support.astype(np.float64), sc.alpha, sc.gamma)
+            bchains.append(ch)
+            bmodels.append(m)
+        bb = fk.fk_batch_create(bmodels)
+        try:
+            off = np.concatenate([[0], np.cumsum([len(sc.queries) for sc in scenes])]).astype(np.int64)
+            bq = torch.from_numpy(np.concatenate([sc.queries for sc in scenes])).to(dev)
+            btot = int(off[-1])
+            blab = torch.empty(btot, dtype=torch.int8, device=dev)
+            best, tms = fk.fk_batch_tune(bb, bq, off, blab)
+            fk.fk_score_batched(bb, bq, off, blab)
+            def timed(fn, reps=5):
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    fn()
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                return statistics.median(ts)
+            t_batch = timed(lambda: fk.fk_score_batched(bb, bq, off, blab))
+            plab = torch.empty(btot, dtype=torch.int8, device=dev)
+            views = [(bq[off[i]:off[i + 1]], plab[off[i]:off[i + 1]]) for i in range(len(scenes))]
+            def per_scene():
+                for m, (qv, lv) in zip(bmodels, views):
+                    if qv.shape[0]:
+                        fk.fk_score(m, qv, lv, rescore=True)
+            per_scene()
+            t_per = timed(per_scene)
+            same = bool(torch.equal(blab, plab))
+            evals_b = sum(len(sc.support) * len(sc.queries) for sc in scenes) * Mv
+            batched = {"scenes": len(scenes), "queries": btot, "support_min": min(len(sc.support) for sc in scenes),
+                       "support_max": max(len(sc.support) for sc in scenes), "ms_persistent_graph": t_batch,
+                       "ms_per_scene_launches": t_per, "speedup": t_per / t_batch,
+                       "checks_per_s": btot / (t_batch * 1e-3), "teval_per_s": evals_b / (t_batch * 1e-3) / 1e12,
+                       "tuned_variant": best, "variant_ms": [float(x) for x in tms[:5]], "labels_identical": same}
+        finally:
+            fk.fk_batch_destroy(bb)
+            for m in bmodels:
+                fk.fastron_model_destroy(m)
+            for ch in bchains:
+                fk.fk_chain_destroy(ch)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(w, args.cpu_sample, os.cpu_count() or 1)
@@ -338,6 +393,7 @@ def main():
                           "rescored_queries": nres},
             "query_only_checks_per_s": nq / (query_ms * 1e-3),
             "query_paths": paths,
+            "batched_scenes": batched,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
