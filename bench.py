@@ -287,6 +287,25 @@ def main():
     # the learned surrogate with exact fallback, against the exact path
     paths = {"fp32_exact": {"checks_per_s": nq / (query_ms * 1e-3), "ms": query_ms, "label_mismatch": 0,
                             "rescored": nres}}
+    # packed-half distances, band through the FP32 path and its FP64 re-score
+    hlab = torch.empty(nq, dtype=torch.int8, device=dev)
+    ex16 = torch.empty(nq, dtype=torch.int8, device=dev)
+    fk.fk_score(model, Q, ex16, rescore=True)
+    nb16 = fk.fk_score(model, Q, hlab, rescore=True, count=True, precision=fk.FK_F16)
+    ht = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fk.fk_score(model, Q, hlab, rescore=True, precision=fk.FK_F16)
+        b.record()
+        b.synchronize()
+        ht.append(a.elapsed_time(b))
+    hms = statistics.median(ht)
+    paths["half2_exact"] = {"checks_per_s": nq / (hms * 1e-3), "ms": hms, "band_to_fp32": nb16 / nq,
+                            "label_mismatch": int((hlab != ex16).sum().item()),
+                            "speedup_vs_fp32_exact": query_ms / hms}
+    del hlab, ex16
     if args.surrogate_train > 0:
         sur = fk.surrogate_create(chain, seed=rank + 1)
         try:

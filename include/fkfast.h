@@ -44,6 +44,7 @@ extern "C" {
 
 #define FK_F32 0  /* FP32 arithmetic */
 #define FK_F64 1  /* FP64 arithmetic */
+#define FK_F16 2  /* packed FP16 distances, FP32 reciprocals and sums (fk_score only) */
 
 #define FK_MAX_DOF 16
 #define FK_MAX_CP 32
@@ -160,7 +161,13 @@ int fastron_model_get(const fastron_model_t *model, int64_t *idx, double *alpha,
  * again in FP64 (FK and kernel), and its f and label are replaced, so that
  * labels equal an FP64 evaluation.  rescore_eps <= 0 selects the library
  * default.  n_rescored (host, may be NULL) receives the number of queries
- * re-evaluated; filling it synchronises `stream`. */
+ * re-evaluated; filling it synchronises `stream`.
+ * precision FK_F16: the differences and t = 1 + gamma/2 |p - s|^2 are
+ * computed in packed half precision, the rest in FP32; with rescore != 0 every
+ * query with |f| <= rescore_eps * B(q) (default 2e-3) goes through the FP32
+ * path above (and its FP64 re-score), so the labels are again those of an
+ * FP64 evaluation; n_rescored then counts the queries of the half pass's
+ * band.  The call synchronises `stream` once when rescore != 0. */
 int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, int rescore, double rescore_eps,
              float *f, int8_t *label, int64_t *n_rescored, void *stream);
 

@@ -100,9 +100,42 @@ __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const Chain
                                                  (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
 }
 
+// The packed-half variant of the same block (differences and t in FP16).
+template <int MV>
+__global__ void __launch_bounds__(kScoreThreads, 2) score_f16_kernel(const ChainF c, const ScoreArgs a) {
+  extern __shared__ __align__(128) float4 tiles[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
+  score_block<MV, kQ, kTilePairs, kScoreThreads, true>(c, a.rec, a.ns, a.gs, a.q, a.n,
+                                                       (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
+}
+
 }  // namespace fk
 
 namespace fk {
+
+template <int MV>
+static cudaError_t launch_score_h_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
+  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(score_f16_kernel<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  score_f16_kernel<MV><<<grid, kScoreThreads, smem, s>>>(c, a);
+  return cudaGetLastError();
+}
+
+bool score_f16_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
+
+cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (c.Mv) {
+    case 3: return launch_score_h_mv<3>(c, a, s);
+    case 7: return launch_score_h_mv<7>(c, a, s);
+    case 11: return launch_score_h_mv<11>(c, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 template <int MV>
 static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {

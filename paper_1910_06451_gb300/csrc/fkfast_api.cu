@@ -12,6 +12,11 @@
 #include "tc_gemm.cuh"
 
 namespace fk {
+cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
+bool score_f16_supported(int mv);
+cudaError_t launch_gather_rows(const float *q, int D, const int32_t *idx, int64_t n, float *out, cudaStream_t s);
+cudaError_t launch_scatter_labels(const int8_t *src, const float *fsrc, const int32_t *idx, int64_t n, int8_t *label,
+                                  float *pred, cudaStream_t s);
 struct GemmArgs;
 cudaError_t launch_gemm_f32(const GemmArgs &g, int splits, cudaStream_t s);
 bool score_supported(int mv);
@@ -206,6 +211,7 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
 // -------------------------------------------------------------- model ---
 static constexpr int64_t kMaxTrainN = 8192;
 static constexpr double kDefaultEps = 6e-6;
+static constexpr double kDefaultEpsF16 = 2e-3;
 static constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // about a quarter second of polling
 static uint32_t g_wait_limit = kDefaultWaitLimit;
 
@@ -225,6 +231,7 @@ struct fastron_model {
   bool host_idx_valid = false;
   // score scratch
   DevBuf band_idx, flags;  // flags: [0] band count, [1] error bits
+  DevBuf fb_idx, fb_q, fb_lab, fb_f;  // band of the half pass, re-scored by the FP32 path
 };
 
 extern "C" int fastron_model_create(const fk_chain_t *chain, fastron_model_t **out) {
@@ -244,7 +251,7 @@ extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
   DevBuf *bufs[] = {&m->cpX, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
                     &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin,
-                    &m->band_idx, &m->flags};
+                    &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
   for (DevBuf *b : bufs) b->release();
   delete m;
 }
@@ -388,13 +395,48 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   if (m->ns < 0) return fail(FK_ERR_STATE, "fk_score: model is untrained");
   if (n < 0) return fail(FK_ERR_ARG, "fk_score: n < 0");
   if (n > (int64_t)INT32_MAX) return fail(FK_ERR_CAPACITY, "fk_score: n exceeds 2^31 - 1");
-  if (precision != FK_F32) return fail(FK_ERR_ARG, "fk_score: unsupported precision %d", precision);
+  if (precision != FK_F32 && precision != FK_F16) return fail(FK_ERR_ARG, "fk_score: unsupported precision %d", precision);
   if (n_rescored) *n_rescored = 0;
   if (n == 0) return FK_OK;
   if (!q || !label) return fail(FK_ERR_ARG, "fk_score: q and label must not be NULL");
   if (m->gamma > 1e7) return fail(FK_ERR_ARG, "fk_score: gamma above the FP32 range of the score kernel");
   cudaStream_t s = (cudaStream_t)stream;
   const fk_chain *c = m->chain;
+  if (precision == FK_F16) {
+    if (!score_f16_supported(c->cf.Mv))
+      return fail(FK_ERR_ARG, "fk_score: no half-precision kernel for %d control points", c->cf.Mv);
+    CK(m->flags.ensure(sizeof(int32_t) * 2));
+    CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
+    if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
+    const double eps16 = rescore_eps > 0.0 ? rescore_eps : kDefaultEpsF16;
+    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps16, f, label,
+                 rescore ? m->band_idx.as<int32_t>() : nullptr, m->flags.as<int32_t>(), m->flags.as<int32_t>() + 1,
+                 g_wait_limit};
+    CK(launch_score_f16(c->cf, sa, s));
+    int32_t h[2] = {0, 0};
+    if (rescore || n_rescored) {
+      CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score: a shared-memory tile wait timed out");
+    }
+    if (!rescore) return FK_OK;
+    const int64_t nb = h[0];
+    if (nb > 0) {
+      // the half pass's band goes through the FP32 score and its FP64 re-score
+      CK(m->fb_idx.ensure(sizeof(int32_t) * (size_t)nb));
+      CK(m->fb_q.ensure(sizeof(float) * (size_t)nb * c->D));
+      CK(m->fb_lab.ensure((size_t)nb));
+      CK(m->fb_f.ensure(sizeof(float) * (size_t)nb));
+      CK(cudaMemcpyAsync(m->fb_idx.p, m->band_idx.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, s));
+      CK(launch_gather_rows(q, c->D, m->fb_idx.as<int32_t>(), nb, m->fb_q.as<float>(), s));
+      int rc = fk_score(m, m->fb_q.as<float>(), nb, FK_F32, 1, 0.0, m->fb_f.as<float>(), m->fb_lab.as<int8_t>(),
+                        nullptr, stream);
+      if (rc != FK_OK) return rc;
+      CK(launch_scatter_labels(m->fb_lab.as<int8_t>(), m->fb_f.as<float>(), m->fb_idx.as<int32_t>(), nb, label, f, s));
+    }
+    if (n_rescored) *n_rescored = nb;
+    return FK_OK;
+  }
   CK(m->flags.ensure(sizeof(int32_t) * 2));
   CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1;

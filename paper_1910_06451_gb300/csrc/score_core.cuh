@@ -3,6 +3,8 @@
 // kernel.  See fk_score.cu for the arithmetic.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
 
@@ -64,13 +66,17 @@ struct BlockOut {
   uint32_t wait_limit;
 };
 
+// HALF = true: the differences and t = 1 + |d|^2 are computed in packed
+// FP16 (HSUB2/HFMA2, query coordinates and the support pair's coordinates
+// rounded to half), then widened to FP32 for the reciprocals and the
+// accumulation.  HALF = false: all FP32.
 // Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
 // (n x D) against the support records rec (ns points, (ns+1)/2 pair records)
 // with chain c.  tiles: 2 * TP * rec_len(MV) float4 of shared memory; bar: two
 // mbarriers.  Every thread of the CTA must call it.  Returns false (in every
 // thread) if a tile wait gave up; the caller must then stop using the CTA's
 // barriers.
-template <int MV, int Q, int TP, int NTHR>
+template <int MV, int Q, int TP, int NTHR, bool HALF = false>
 __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, float gs,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
                                             float4 *tiles, uint64_t *bar) {
@@ -103,6 +109,7 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
   // that t = 1 + |p - s|^2, duplicated into both halves of a packed register
   const int64_t qbase = q0 + tid;
   f2 P[Q][MV][3];
+  __half2 Ph[HALF ? Q : 1][HALF ? MV : 1][3];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int64_t qi = qbase + k * NTHR;
@@ -115,9 +122,13 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const float v = gs * cp[m][r];
-        P[k][m][r] = pk(v, v);
+        if (HALF)
+          Ph[HALF ? k : 0][HALF ? m : 0][r] = __float2half2_rn(v);
+        else
+          P[k][m][r] = pk(v, v);
       }
   }
+  const __half2 one_h = __float2half2_rn(1.f);
   const f2 one2 = pk(1.f, 1.f);
   const float nc = (float)c.n_const;
   const f2 nc2 = pk(nc, nc);
@@ -146,12 +157,25 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
       for (int m = 0; m < MV; ++m) {
         const float4 xy = r[m];
         const float4 zz = r[MV + m / 2];
-        const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
-        const f2 sz = (m & 1) ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+        if (HALF) {
+          const __half2 hx = __floats2half2_rn(xy.x, xy.y), hy = __floats2half2_rn(xy.z, xy.w);
+          const __half2 hz = (m & 1) ? __floats2half2_rn(zz.z, zz.w) : __floats2half2_rn(zz.x, zz.y);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
-          tv[k][m] = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
+          for (int k = 0; k < Q; ++k) {
+            const int kk = HALF ? k : 0, mm = HALF ? m : 0;
+            const __half2 dx = __hsub2(Ph[kk][mm][0], hx), dy = __hsub2(Ph[kk][mm][1], hy),
+                          dz = __hsub2(Ph[kk][mm][2], hz);
+            const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
+            tv[k][m] = pk(tf.x, tf.y);
+          }
+        } else {
+          const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
+          const f2 sz = (m & 1) ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
+            tv[k][m] = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
+          }
         }
       }
 #pragma unroll

@@ -23,6 +23,7 @@ FK_ERR_TIMEOUT = -4
 FK_ERR_STATE = -5
 FK_F32 = 0
 FK_F64 = 1
+FK_F16 = 2
 FK_MAX_DOF = 16
 FK_MAX_CP = 32
 
@@ -280,13 +281,13 @@ def fastron_model_get(model):
 
 # ---------------------------------------------------------------- score ---
 
-def fk_score(model, q, label, f=None, rescore=True, eps=0.0, count=False, stream=None):
+def fk_score(model, q, label, f=None, rescore=True, eps=0.0, count=False, stream=None, precision=FK_F32):
     """Labels (and optionally f) of float32 queries q (n, D).  With count=True
-    the call synchronises and returns the number of FP64 re-evaluations."""
+    the call synchronises and returns the number of re-evaluated queries."""
     import torch
     n = q.shape[0]
     nr = ctypes.c_int64()
-    _check(load().fk_score(model, _dev(q, torch.float32, "q"), n, FK_F32, int(bool(rescore)), float(eps),
+    _check(load().fk_score(model, _dev(q, torch.float32, "q"), n, int(precision), int(bool(rescore)), float(eps),
                            None if f is None else _dev(f, torch.float32, "f", (n,)),
                            _dev(label, torch.int8, "label", (n,)), ctypes.byref(nr) if count else None,
                            _stream(stream)))

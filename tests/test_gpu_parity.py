@@ -273,3 +273,35 @@ def test_argument_errors(fk, arm3, dev):
             fk.fk_score(m, q.double(), lab)
     finally:
         fk.fastron_model_destroy(m)
+
+
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_score_half_precision_path(fk, arm3, arm7, dev, which):
+    """Packed-half distances: the half pass stays within its band bound and,
+    after its band goes through the FP32 path and the FP64 re-score, every
+    label equals the oracle's."""
+    w, ch = arm3 if which == "arm3" else arm7
+    X = w.train_configs().astype(np.float64)
+    y = O.check(w.scene, X)
+    r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+    S, alpha = X[r.support], r.alpha[r.support]
+    Q = w.query_configs(20000)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, alpha, w.gamma)
+        tq = torch.from_numpy(Q).to(dev)
+        f16 = torch.empty(len(Q), dtype=torch.float32, device=dev)
+        l16 = torch.empty(len(Q), dtype=torch.int8, device=dev)
+        fk.fk_score(m, tq, l16, f16, rescore=False, precision=fk.FK_F16)
+        lab = torch.empty(len(Q), dtype=torch.int8, device=dev)
+        nb = fk.fk_score(m, tq, lab, rescore=True, count=True, precision=fk.FK_F16)
+        torch.cuda.synchronize()
+    finally:
+        fk.fastron_model_destroy(m)
+    cps, cpq = O.fk_points(w.scene.arm, S), O.fk_points(w.scene.arm, Q.astype(np.float64))
+    want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
+    B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=8)
+    err = np.abs(f16.cpu().numpy().astype(np.float64) - want) / B
+    print(f"half pass: max |df|/B = {err.max():.3e}, band = {nb} of {len(Q)}")
+    assert err.max() <= 0.5 * 2e-3
+    assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
