@@ -16,7 +16,11 @@
 //      CTA of the cluster (distributed shared memory) and, one cluster
 //      barrier later, every warp reduces the C slots itself.  Slots are
 //      double-buffered by pass parity, so one cluster barrier per pass
-//      suffices.
+//      suffices.  Each warp-level step is three redux.sync reductions and
+//      one shuffle rather than a shuffle butterfly.
+// The row of the argmin candidate is requested before the decision is taken
+// (an add step is the common case), so its latency overlaps the decision;
+// the decision's FP64 arithmetic runs in one lane per warp and is broadcast.
 // Comparisons run on int64 keys that order like the doubles (sign-magnitude
 // folded to two's complement, zeros made +0), so the argmin/argmax work stays
 // off the FP64 pipe, which on this part runs at 1/64 of the FP32 rate; ties
@@ -38,6 +42,7 @@ constexpr int kTrainThreads = 256;
 constexpr int kTrainWarps = kTrainThreads / 32;
 constexpr int kMaxCluster = 16;
 constexpr long long kMag = 0x7fffffffffffffffLL;
+constexpr long long kSign = (long long)0x8000000000000000ULL;
 
 struct Cand {
   long long key;  // ordered key of the margin (argmin) or removal margin (argmax)
@@ -64,25 +69,49 @@ __device__ __forceinline__ bool better_max(const Cand &a, const Cand &b) {
   return a.key > b.key || (a.key == b.key && cidx(a) < cidx(b));
 }
 
-__device__ __forceinline__ Cand shfl_cand(const Cand &c, int lane_mask) {
-  Cand o;
-  o.key = __shfl_xor_sync(0xffffffffu, c.key, lane_mask);
-  o.alpha = __shfl_xor_sync(0xffffffffu, c.alpha, lane_mask);
-  o.iy = __shfl_xor_sync(0xffffffffu, c.iy, lane_mask);
-  return o;
+// Warp-wide argmin / argmax with the single-instruction warp reductions
+// (redux.sync): first the high 32 bits of the key (signed), then the low 32
+// bits among the lanes that tie on the high part (unsigned), then the lowest
+// index among full ties; the winner's alpha and label come from its lane by
+// one shuffle.  Every lane of the warp gets the same candidate.
+__device__ __forceinline__ Cand warp_argmin(const Cand &c) {
+  const unsigned full = 0xffffffffu;
+  const int hi = (int)(c.key >> 32);
+  const unsigned lo = (unsigned)c.key, ix = (unsigned)cidx(c);
+  const int mh = __reduce_min_sync(full, hi);
+  const unsigned ml = __reduce_min_sync(full, hi == mh ? lo : 0xffffffffu);
+  const bool tie = hi == mh && lo == ml;
+  const unsigned mi = __reduce_min_sync(full, tie ? ix : 0xffffffffu);
+  const int src = __ffs(__ballot_sync(full, tie && ix == mi)) - 1;
+  Cand r;
+  r.key = ((long long)mh << 32) | (long long)ml;
+  r.alpha = __shfl_sync(full, c.alpha, src);
+  r.iy = __shfl_sync(full, c.iy, src);
+  return r;
 }
 
-// Full 32-lane butterfly: afterwards every lane holds the best candidate of
-// the whole warp.  (Every decision below must be identical in every thread of
-// the cluster, because every thread then meets the same barriers; a narrower
-// butterfly would leave the upper lanes with a different answer.)
+__device__ __forceinline__ Cand warp_argmax(const Cand &c) {
+  const unsigned full = 0xffffffffu;
+  const int hi = (int)(c.key >> 32);
+  const unsigned lo = (unsigned)c.key, ix = (unsigned)cidx(c);
+  const int mh = __reduce_max_sync(full, hi);
+  const unsigned ml = __reduce_max_sync(full, hi == mh ? lo : 0u);
+  const bool tie = hi == mh && lo == ml;
+  const unsigned mi = __reduce_min_sync(full, tie ? ix : 0xffffffffu);
+  const int src = __ffs(__ballot_sync(full, tie && ix == mi)) - 1;
+  Cand r;
+  r.key = ((long long)mh << 32) | (long long)ml;
+  r.alpha = __shfl_sync(full, c.alpha, src);
+  r.iy = __shfl_sync(full, c.iy, src);
+  return r;
+}
+
+// Every decision below must be identical in every thread of the cluster,
+// because every thread then meets the same barriers; the warp reductions give
+// every lane the same answer.
 __device__ __forceinline__ void warp_reduce(Cand &mn, Cand &mx) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const Cand a = shfl_cand(mn, o), b = shfl_cand(mx, o);
-    if (better_min(a, mn)) mn = a;
-    if (better_max(b, mx)) mx = b;
-  }
+  mn = warp_argmin(mn);
+  mx = warp_argmax(mx);
 }
 
 __device__ __forceinline__ Cand no_min() { return {LLONG_MAX, 0.0, INT_MAX}; }
@@ -198,22 +227,44 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
   long long iters = 0, adds = 0, removes = 0;
   int converged = 0;
   for (long long iter = 1; iter <= a.iter_max; ++iter) {
+    // request the argmin's row first: an add step is the common case
+    double gk[KMAX];
+    const int imin = cidx(mn);
+    const bool min_valid = imin != INT_MAX;
+    if (min_valid) {
+      const double *row = a.G + (long long)imin * N;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int j = g + stride * k;
+        gk[k] = j < N ? row[j] : 0.0;
+      }
+    }
     int kind, i;
     double coef, delta;
-    if (cidx(mn) != INT_MAX && mn.key <= 0 && (nnz < a.s_max || nonzero(mn.alpha))) {
-      // add / adjust support point i: delta = b_i y_i - F_i (Eq. 6)
+    if (min_valid && mn.key <= 0 && (nnz < a.s_max || nonzero(mn.alpha))) {
+      // add / adjust support point i: delta = b_i y_i - F_i (Eq. 6); the FP64
+      // arithmetic runs in lane 0 and is broadcast to the warp
       kind = 1;
-      i = cidx(mn);
-      const bool yn = mn.iy < 0;
-      const double m = key_value(mn.key);  // y_i F_i
-      const double Fi = yn ? -m : m;
-      const double by = yn ? -1.0 : a.beta;  // b_i y_i with b_i = beta^(0.5 (y_i + 1))
-      delta = __dsub_rn(by, Fi);
+      i = imin;
+      double dl = 0.0;
+      int nz_new = 0;
+      if (lane == 0) {
+        const bool yn = mn.iy < 0;
+        // F_i = y_i * (y_i F_i): a sign flip of the margin's bit pattern
+        const double Fi = __longlong_as_double(__double_as_longlong(key_value(mn.key)) ^ (yn ? kSign : 0LL));
+        const double by = yn ? -1.0 : a.beta;  // b_i y_i with b_i = beta^(0.5 (y_i + 1))
+        dl = __dsub_rn(by, Fi);
+        // alpha_i + delta (Eq. 7) is zero exactly when delta == -alpha_i
+        const long long bd = __double_as_longlong(dl), ba = __double_as_longlong(mn.alpha);
+        nz_new = !(((bd ^ kSign) == ba) || (!nonzero(dl) && !nonzero(mn.alpha)));
+      }
+      delta = __shfl_sync(0xffffffffu, dl, 0);
+      nz_new = __shfl_sync(0xffffffffu, nz_new, 0);
       coef = delta;
-      const double anew = __dadd_rn(mn.alpha, delta);  // Eq. 7
-      nnz += (long long)nonzero(anew) - (long long)nonzero(mn.alpha);
+      nnz += (long long)nz_new - (long long)nonzero(mn.alpha);
       const int gi = i % stride;
-      if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = anew;
+      if (gi / kTrainThreads == rank && gi % kTrainThreads == tid)
+        alpha[(i / stride) * kTrainThreads + tid] = __dadd_rn(mn.alpha, delta);
       ++adds;
     } else if (cidx(mx) != INT_MAX && mx.key > 0) {
       // remove the redundant support point i
@@ -225,6 +276,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = 0.0;
       --nnz;
       ++removes;
+      const double *row = a.G + (long long)i * N;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int j = g + stride * k;
+        gk[k] = j < N ? row[j] : 0.0;
+      }
     } else {
       converged = 1;
       break;
@@ -234,13 +291,6 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       a.trace_kind[iter - 1] = (int8_t)kind;
       a.trace_idx[iter - 1] = i;
       a.trace_delta[iter - 1] = delta;
-    }
-    const double *row = a.G + (long long)i * N;
-    double gk[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      const int j = g + stride * k;
-      gk[k] = j < N ? row[j] : 0.0;
     }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
