@@ -45,6 +45,7 @@ extern "C" {
 #define FK_F32 0  /* FP32 arithmetic */
 #define FK_F64 1  /* FP64 arithmetic */
 #define FK_F16 2  /* packed FP16 distances, FP32 reciprocals and sums (fk_score only) */
+#define FK_DF64 3 /* FP64 inputs and outputs, double-float arithmetic on the FP32 pipes (fk_gram, training) */
 
 #define FK_MAX_DOF 16
 #define FK_MAX_CP 32
@@ -90,7 +91,11 @@ int fk_forward_f64(const fk_chain_t *chain, const double *q, int64_t n, double *
 /* ---- kernel matrix (Sec. II-B with the FK kernel of Eq. 4) -------------
  * K[i][j] = K_FK(Xa_i, Xb_j) = (1/M) sum_m (1 + gamma/2 |FK_m(Xa_i) - FK_m(Xb_j)|^2)^-2.
  * precision FK_F64: Xa, Xb are device double arrays (na x D, nb x D) and K a
- * device double array na x nb.  FK_F32: float inputs and a float K.  gamma > 0.
+ * device double array na x nb.  FK_DF64: the same FP64 inputs and output,
+ * computed in double-float arithmetic (pairs of FP32 values, error-free
+ * transformations; entries within about 1e-13 of the FP64 ones, some ten
+ * times faster on this part, whose FP64 rate is 1/64 of its FP32 rate).
+ * FK_F32: float inputs and a float K.  gamma > 0.
  * Control points are computed into the chain's workspace first. */
 int fk_gram(const fk_chain_t *chain, const void *Xa, int64_t na, const void *Xb, int64_t nb, double gamma,
             int precision, void *K, void *stream);
@@ -105,6 +110,9 @@ typedef struct {
                           same training set (loadPreviousModel); 0: alpha = F = 0 */
     int32_t trace;     /* 1: record every pass (kind, index, change of alpha) for
                           fastron_model_trace; 0: do not */
+    int32_t gram;      /* arithmetic of the training kernel matrix: FK_DF64 (0 selects it)
+                          or FK_F64 */
+    int32_t reserved;
 } fastron_params;
 
 typedef struct {

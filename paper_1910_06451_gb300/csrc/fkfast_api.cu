@@ -186,19 +186,23 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
   if (!c) return fail(FK_ERR_ARG, "fk_gram: chain is NULL");
   if (na < 0 || nb < 0) return fail(FK_ERR_ARG, "fk_gram: negative size");
   if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(FK_ERR_ARG, "fk_gram: gamma must be finite and > 0");
-  if (precision != FK_F32 && precision != FK_F64) return fail(FK_ERR_ARG, "fk_gram: unknown precision %d", precision);
+  if (precision != FK_F32 && precision != FK_F64 && precision != FK_DF64)
+    return fail(FK_ERR_ARG, "fk_gram: unknown precision %d", precision);
   if (na == 0 || nb == 0) return FK_OK;
   if (!Xa || !Xb || !K) return fail(FK_ERR_ARG, "fk_gram: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const bool sym = Xa == Xb && na == nb;
-  const size_t el = precision == FK_F64 ? sizeof(double) : sizeof(float);
+  const size_t el = precision == FK_F32 ? sizeof(float) : sizeof(double);
   CK(c->ws_a.ensure(el * (size_t)c->M * 3 * (size_t)na));
   if (!sym) CK(c->ws_b.ensure(el * (size_t)c->M * 3 * (size_t)nb));
-  if (precision == FK_F64) {
+  if (precision == FK_F64 || precision == FK_DF64) {
     double *A = c->ws_a.as<double>(), *B = sym ? A : c->ws_b.as<double>();
     CK(launch_fk_forward_f64(c->cd, (const double *)Xa, na, A, s));
     if (!sym) CK(launch_fk_forward_f64(c->cd, (const double *)Xb, nb, B, s));
-    CK(launch_gram_f64(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
+    if (precision == FK_F64)
+      CK(launch_gram_f64(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
+    else
+      CK(launch_gram_df(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
   } else {
     float *A = c->ws_a.as<float>(), *B = sym ? A : c->ws_b.as<float>();
     CK(launch_fk_forward_f32(c->cf, (const float *)Xa, na, A, s));
@@ -281,6 +285,8 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   if (!(p->beta >= 1.0) || !std::isfinite(p->beta)) return fail(FK_ERR_ARG, "fastron_train: beta must be >= 1");
   if (p->iter_max < 0) return fail(FK_ERR_ARG, "fastron_train: iter_max < 0");
   if (p->s_max < 1) return fail(FK_ERR_ARG, "fastron_train: s_max < 1");
+  if (p->gram != 0 && p->gram != FK_F64 && p->gram != FK_DF64)
+    return fail(FK_ERR_ARG, "fastron_train: gram must be FK_DF64 or FK_F64");
   if (p->warm_start && (m->N != N || m->alpha.p == nullptr))
     return fail(FK_ERR_STATE, "fastron_train: warm start needs a previous training call with the same N");
   cudaStream_t s = (cudaStream_t)stream;
@@ -306,7 +312,10 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   }
   m->N = N;
   CK(launch_fk_forward_f64(c->cd, X, N, m->cpX.as<double>(), s));
-  CK(launch_gram_f64(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
+  if (p->gram == FK_F64)
+    CK(launch_gram_f64(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
+  else
+    CK(launch_gram_df(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
   TrainArgs ta{m->G.as<double>(), y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
                m->stats.as<int64_t>(), m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(),
                trace ? m->trace_kind.as<int8_t>() : nullptr, trace ? m->trace_idx.as<int32_t>() : nullptr,

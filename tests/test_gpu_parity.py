@@ -83,6 +83,13 @@ def test_gram(fk, arm3, dev, na, nb):
     if na == nb:
         assert np.array_equal(got, got.T)
         assert np.all(np.diag(got) == 1.0)
+    Kd = torch.empty((na, nb), dtype=torch.float64, device=dev)
+    fk.fk_gram(ch, ta, tb, w.gamma, Kd, double_float=True)
+    gotd = Kd.cpu().numpy()
+    assert np.max(np.abs(gotd - want)) <= 2e-13
+    if na == nb:
+        assert np.array_equal(gotd, gotd.T)
+        assert np.all(np.diag(gotd) == 1.0)
     K32 = torch.empty((na, nb), dtype=torch.float32, device=dev)
     t32a = ta.float()
     fk.fk_gram(ch, t32a, t32a if na == nb else tb.float(), w.gamma, K32)
@@ -101,22 +108,23 @@ def test_labels(fk, arm3, arm7, dev, which):
     assert 0 < np.sum(want == 1) < len(want)
 
 
-def _train_both(fk, w, ch, dev, n=None, beta=None):
+def _train_both(fk, w, ch, dev, n=None, beta=None, gram=None):
     X = w.train_configs()[:n].astype(np.float64)
     y = O.check(w.scene, X)
     beta = w.beta if beta is None else beta
     r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, beta, w.iter_max, w.s_max, trace=True)
     m = fk.fastron_model_create(ch)
     st = fk.fastron_train(m, torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev), w.gamma, beta,
-                          w.iter_max, w.s_max, trace=True)
+                          w.iter_max, w.s_max, trace=True, gram=fk.FK_DF64 if gram is None else gram)
     return X, y, r, m, st
 
 
+@pytest.mark.parametrize("gram", ["df64", "f64"])
 @pytest.mark.parametrize("which,n,beta", [("arm3", 1000, 1.0), ("arm3", 1000, 1.5), ("arm3", 333, 1.0),
                                           ("arm7", 5000, 1.0)])
-def test_fastron_train_matches_oracle(fk, arm3, arm7, dev, which, n, beta):
+def test_fastron_train_matches_oracle(fk, arm3, arm7, dev, which, n, beta, gram):
     w, ch = arm3 if which == "arm3" else arm7
-    X, y, r, m, st = _train_both(fk, w, ch, dev, n, beta)
+    X, y, r, m, st = _train_both(fk, w, ch, dev, n, beta, fk.FK_DF64 if gram == "df64" else fk.FK_F64)
     try:
         assert st["iterations"] == r.iters and st["adds"] == r.adds and st["removes"] == r.removes
         assert st["converged"] == r.converged and st["n_support"] == r.n_support
