@@ -207,7 +207,10 @@ int fk_score_noalloc(fastron_model_t *model, const float *q, int64_t n, double r
  * link comes within `radius` of any axis-aligned box, else -1.  Stands in for
  * the geometric checker used to label training data (Sec. III-B active
  * learning, Sec. IV).  boxes: host double nb x 6 (lo xyz, hi xyz), nb <= 64.
- * q: device float n x D.  y: device int8 [n].  Computed in FP64. */
+ * q: device float n x D.  y: device int8 [n].  The labels are those of an
+ * FP64 evaluation: pairs are first decided in FP32 when their distance is
+ * more than 1e-5 m from the radius, and a configuration with a pair closer
+ * than that to the radius (and no clear hit) is evaluated again in FP64. */
 int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double radius, const float *q, int64_t n,
              int8_t *y, void *stream);
 

@@ -101,14 +101,15 @@ struct RescoreArgs {
 };
 cudaError_t launch_rescore_f64(const ChainD &c, const RescoreArgs &a, cudaStream_t s);
 
-// FP64 geometric labels.
+// Geometric labels: FP32 filter, FP64 for configurations too close to call.
 constexpr int kMaxBoxes = 64;
 struct Boxes {
   int nb;
   double r2;
   double b[kMaxBoxes][6];
 };
-cudaError_t launch_label(const ChainD &c, const Boxes &bx, const float *q, int64_t n, int8_t *y, cudaStream_t s);
+cudaError_t launch_label(const ChainF &cf, const ChainD &c, const Boxes &bx, const float *q, int64_t n, int8_t *y,
+                         cudaStream_t s);
 
 // Throughput probe; fills per-block (smid, start, end) records.
 cudaError_t launch_probe(int kind, int blocks, int threads, long long *rec, cudaStream_t s);

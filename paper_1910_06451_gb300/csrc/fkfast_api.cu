@@ -484,7 +484,7 @@ extern "C" int fk_label(const fk_chain_t *c, const double *boxes, int64_t nb, do
   bx.r2 = radius * radius;
   for (int64_t b = 0; b < nb; ++b)
     for (int k = 0; k < 6; ++k) bx.b[b][k] = boxes[6 * b + k];
-  CK(launch_label(c->cd, bx, q, n, y, (cudaStream_t)stream));
+  CK(launch_label(c->cf, c->cd, bx, q, n, y, (cudaStream_t)stream));
   return FK_OK;
 }
 

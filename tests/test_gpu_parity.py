@@ -108,6 +108,21 @@ def test_labels(fk, arm3, arm7, dev, which):
     assert 0 < np.sum(want == 1) < len(want)
 
 
+@pytest.mark.parametrize("gap", [0.0, 1e-7, -1e-7, 3e-6, 2e-5])
+def test_labels_at_the_radius(fk, arm3, dev, gap):
+    # the first link of the 3-DOF arm lies in the plane z = 0; a box whose
+    # lower face is at z = radius + gap puts every configuration within |gap|
+    # of the decision, so the FP32 filter must hand them to FP64
+    w, ch = arm3
+    q = w.query_configs(4000)
+    boxes = np.array([[-0.6, -0.6, 0.03 + gap, 0.6, 0.6, 0.6]])
+    sc = synth.Scene(w.scene.arm, boxes, 0.03)
+    want = O.check(sc, q.astype(np.float64))
+    y = torch.empty(len(q), dtype=torch.int8, device=dev)
+    fk.fk_label(ch, boxes, 0.03, torch.from_numpy(q).to(dev), y)
+    assert np.array_equal(y.cpu().numpy(), want)
+
+
 def _train_both(fk, w, ch, dev, n=None, beta=None, gram=None):
     X = w.train_configs()[:n].astype(np.float64)
     y = O.check(w.scene, X)
