@@ -190,11 +190,16 @@ int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *
 
 /* ----------------------------------------------------------- Fastron ---- */
 
-/* Column i of the kernel matrix over the training set (computeKernelMatrixColumn). */
-static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col)
+/* Column i of the kernel matrix over the training set (computeKernelMatrixColumn).
+ * store32 != 0: every entry is rounded to the nearest FP32 value, the kernel
+ * matrix as it is held when it is stored in single precision (65,536
+ * training points take 17.2 GB in FP32); the margins and weights stay FP64. */
+static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col, int store32)
 {
-    for (int64_t j = 0; j < N; ++j)
-        col[j] = orc_k_fk(M, cpX + j * M * 3, cpX + i * M * 3, gamma);
+    for (int64_t j = 0; j < N; ++j) {
+        double k = orc_k_fk(M, cpX + j * M * 3, cpX + i * M * 3, gamma);
+        col[j] = store32 ? (double)(float)k : k;
+    }
 }
 
 /*
@@ -218,11 +223,12 @@ static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int
  * for a warm start, loadPreviousModel).  stats = {iterations, adds, removals,
  * converged (1 if the loop ended by break), support size}.  If trace_kind is
  * not NULL, pass k records kind (1 add, 2 removal), index and delta (the
- * change of alpha_i) in trace_kind/trace_idx/trace_delta[k].
+ * change of alpha_i) in trace_kind/trace_idx/trace_delta[k].  store32: see
+ * kernel_column.
  */
-int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
-                      int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
-                      int8_t *trace_kind, int64_t *trace_idx, double *trace_delta)
+int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                            int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                            int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32)
 {
     double *col = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     if (!col)
@@ -244,7 +250,7 @@ int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const i
             }
         }
         if (i >= 0 && mmin <= 0.0) {
-            kernel_column(M, gamma, N, cpX, i, col);
+            kernel_column(M, gamma, N, cpX, i, col, store32);
             if (nnz < s_max || alpha[i] != 0.0) {
                 double b = y[i] > 0 ? beta : 1.0;
                 double delta = b * y[i] - F[i];
@@ -276,7 +282,7 @@ int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const i
             }
         }
         if (r >= 0 && mmax > 0.0) {
-            kernel_column(M, gamma, N, cpX, r, col);
+            kernel_column(M, gamma, N, cpX, r, col, store32);
             double a = alpha[r];
             for (int64_t j = 0; j < N; ++j)
                 F[j] -= a * col[j];
@@ -301,6 +307,14 @@ int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const i
     stats[3] = converged;
     stats[4] = nnz;
     return 0;
+}
+
+int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                      int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                      int8_t *trace_kind, int64_t *trace_idx, double *trace_delta)
+{
+    return orc_fastron_train_store(M, gamma, N, cpX, y, beta, iter_max, s_max, alpha, F, stats, trace_kind,
+                                   trace_idx, trace_delta, 0);
 }
 
 /* --------------------------------------------------- geometric checker -- */

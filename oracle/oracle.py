@@ -71,6 +71,8 @@ def _load():
         lib.orc_score.restype = I
         lib.orc_fastron_train.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P]
         lib.orc_fastron_train.restype = I
+        lib.orc_fastron_train_store.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I]
+        lib.orc_fastron_train_store.restype = I
         lib.orc_seg_box_dist2.argtypes = [P, P, P, P]
         lib.orc_seg_box_dist2.restype = Dbl
         lib.orc_check.argtypes = [I, P, P, I64, P, Dbl, I64, P, P]
@@ -173,10 +175,12 @@ class TrainResult:
 
 
 def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000, s_max: int | None = None,
-                  alpha0=None, F0=None, trace: bool = False) -> TrainResult:
+                  alpha0=None, F0=None, trace: bool = False, store32: bool = False) -> TrainResult:
     """Algorithm 1 (Sec. III-B) on training control points cpX (N, M, 3) and labels y in {+1, -1}.
 
-    alpha0/F0 warm-start the model (loadPreviousModel); zeros otherwise."""
+    alpha0/F0 warm-start the model (loadPreviousModel); zeros otherwise.
+    store32: kernel-matrix entries rounded to the nearest FP32 value (the
+    matrix held in single precision); margins and weights stay FP64."""
     cpX = _d(cpX)
     N, M = cpX.shape[0], cpX.shape[1]
     y = np.ascontiguousarray(y, dtype=np.int8)
@@ -191,8 +195,8 @@ def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000,
         tr = (_p(tk), _p(ti), _p(td))
     else:
         tr = (None, None, None)
-    rc = _load().orc_fastron_train(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
-                                   _p(alpha), _p(F), _p(stats), *tr)
+    rc = _load().orc_fastron_train_store(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
+                                         _p(alpha), _p(F), _p(stats), *tr, int(bool(store32)))
     if rc != 0:
         raise RuntimeError("orc_fastron_train failed")
     tr_out = None

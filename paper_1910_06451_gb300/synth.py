@@ -126,6 +126,25 @@ def arm_7dof(seed: int) -> Arm:
     return random_arm(seed, 7, (0.1, 0.4), (0.0, 0.1), math.radians(170.0))
 
 
+def arm_7dof_m12(seed: int) -> Arm:
+    """The 7-DOF arm of ``arm_7dof(seed)`` with 12 control points: the origins
+    of frames 0..7 and the midpoints of the four links with the largest
+    sqrt(a^2 + d^2).  Link j joins the origins of frames j-1 and j; in frame j
+    its midpoint sits at the constant offset -(a_j, d_j sin alpha_j,
+    d_j cos alpha_j) / 2 (the DH step of Eq. 1 walked back by half), rounded
+    to FP32 like every other input."""
+    arm = arm_7dof(seed)
+    a, al, d = arm.dh[:, 0], arm.dh[:, 1], arm.dh[:, 2]
+    length = np.sqrt(a * a + d * d)
+    longest = np.sort(np.argsort(-length, kind="stable")[:4])  # DH rows, ascending
+    cj = list(arm.cp_joint)
+    co = [row for row in arm.cp_off]
+    for r in longest:
+        cj.append(int(r) + 1)
+        co.append(_f32(-0.5 * np.array([a[r], d[r] * math.sin(al[r]), d[r] * math.cos(al[r])])))
+    return dataclasses.replace(arm, cp_joint=np.array(cj, dtype=np.int32), cp_off=np.array(co))
+
+
 def random_boxes(seed: int, nb: int, centre=(-0.8, 0.8), half=(0.05, 0.15),
                  keep_clear: float = 0.1) -> np.ndarray:
     """Axis-aligned boxes; a draw whose box comes within ``keep_clear`` of the
@@ -141,6 +160,46 @@ def random_boxes(seed: int, nb: int, centre=(-0.8, 0.8), half=(0.05, 0.15),
             continue
         out.append(np.concatenate([lo, hi]))
     return np.array(out)
+
+
+def moving_boxes(seed: int, boxes0: np.ndarray, n_frames: int, vmax: float = 0.05, region=(-0.8, 0.8),
+                 keep_clear: float = 0.1) -> np.ndarray:
+    """Box positions over n_frames frames, shape (n_frames, nb, 6); frame 0 is
+    boxes0.  Each box moves along a straight line at a constant speed drawn
+    uniformly in [0, vmax] per frame, in a direction uniform on the sphere;
+    its centre is reflected at the faces of the region cube, and a step that
+    would bring the box within keep_clear of the base origin is undone and the
+    velocity reversed.  Positions are tracked in FP64 and each frame's box is
+    rounded to FP32."""
+    st = Stream(seed ^ 0x30B1E5)
+    b0 = np.asarray(boxes0, dtype=np.float64)
+    nb = b0.shape[0]
+    c = 0.5 * (b0[:, :3] + b0[:, 3:])
+    h = 0.5 * (b0[:, 3:] - b0[:, :3])
+    z = st.uniform(nb, -1.0, 1.0)
+    phi = st.uniform(nb, 0.0, 2.0 * math.pi)
+    speed = st.uniform(nb, 0.0, vmax)
+    r = np.sqrt(np.maximum(1.0 - z * z, 0.0))
+    v = (speed * np.stack([r * np.cos(phi), r * np.sin(phi), z])).T
+    lo_r, hi_r = region
+    out = np.empty((n_frames, nb, 6))
+    out[0] = b0
+    for k in range(1, n_frames):
+        nxt = c + v
+        for ax in range(3):
+            over = nxt[:, ax] > hi_r
+            under = nxt[:, ax] < lo_r
+            nxt[over, ax] = 2 * hi_r - nxt[over, ax]
+            nxt[under, ax] = 2 * lo_r - nxt[under, ax]
+            v[over | under, ax] *= -1.0
+        lo, hi = nxt - h, nxt + h
+        gap = np.maximum(np.maximum(lo, -hi), 0.0)
+        near = np.sqrt(np.sum(gap * gap, axis=1)) <= keep_clear
+        nxt[near] = c[near]
+        v[near] *= -1.0
+        c = nxt
+        out[k] = np.concatenate([_f32(c - h), _f32(c + h)], axis=1)
+    return out
 
 
 def uniform_configs(seed: int, n: int, D: int, qlim: float) -> np.ndarray:
@@ -177,6 +236,10 @@ def workload(name: str, trial: int = 0, **over) -> Workload:
     ``arm7-n5000``: 7-DOF arm, 8 control points, 10 boxes, N = 5000, 4M
     queries, gamma = 40 (the paper picks its kernel parameters by grid search,
     Sec. IV; 40 gave the best held-out accuracy of 5, 10, 20, 40, 80, 160).
+    ``arm7m12-n65536``: the changing environment: 7-DOF arm with 12 control
+    points (``arm_7dof_m12``), 10 boxes that move (``moving_boxes``, up to
+    0.05 m per frame), N = 65,536 training configurations, 16,777,216 queries
+    per frame, gamma = 40, S_max = 20,000, up to 100,000 iterations.
     """
     if name == "arm3-n1000":
         s = 1000 * 0 + trial
@@ -186,6 +249,10 @@ def workload(name: str, trial: int = 0, **over) -> Workload:
         s = 1000 * 1 + trial
         sc = Scene(arm_7dof(s), random_boxes(s, 10), 0.03)
         w = Workload(name, sc, 40.0, 1.0, 5000, 4_000_000, 5000, 5000, s)
+    elif name == "arm7m12-n65536":
+        s = 1000 * 4 + trial
+        sc = Scene(arm_7dof_m12(s), random_boxes(s, 10), 0.03)
+        w = Workload(name, sc, 40.0, 1.0, 65_536, 16_777_216, 100_000, 20_000, s)
     else:
         raise KeyError(name)
     return dataclasses.replace(w, **over)

@@ -141,3 +141,30 @@ def test_workloads_train_to_positive_margins():
     r = O.fastron_train(cp, y, w.gamma, iter_max=w.iter_max)
     assert r.converged and np.all(y * r.F > 0)
     assert 0 < r.n_support < 1000
+
+
+def test_fp32_stored_kernel_two_points_closed_form():
+    # the same two passes as above with K_01 rounded to FP32
+    g = 10.0
+    cp = _two_points(0.3)
+    k = O.k_fk(cp[0], cp[1], g)
+    k32 = float(np.float32(k))
+    assert k32 != k
+    r = O.fastron_train(cp, np.array([1, -1]), g, iter_max=100, trace=True, store32=True)
+    kind, idx, delta = r.trace
+    assert list(kind) == [1, 1] and list(idx) == [0, 1]
+    assert delta[1] == -1.0 - k32
+    assert r.alpha[1] == -1.0 - k32 and r.F[0] == 1.0 + (-1.0 - k32) * k32 and r.F[1] == -1.0
+    r64 = O.fastron_train(cp, np.array([1, -1]), g, iter_max=100, store32=False)
+    assert r64.alpha[1] != r.alpha[1]
+
+
+def test_fp32_stored_kernel_margins_are_k32_alpha():
+    # F = K32 alpha throughout, with K32 the FP64 Gram rounded entry by entry
+    w, X, y, cp = _small_problem(200, seed=3, name="arm7-n5000")
+    K32 = O.gram(cp, cp, w.gamma).astype(np.float32).astype(np.float64)
+    r = O.fastron_train(cp, y, w.gamma, iter_max=5000, store32=True)
+    assert r.converged and np.all(y * r.F > 0)
+    np.testing.assert_allclose(r.F, K32 @ r.alpha, rtol=1e-11, atol=1e-11)
+    K = O.gram(cp, cp, w.gamma)
+    assert np.max(np.abs(K32 @ r.alpha - K @ r.alpha)) > 0

@@ -49,3 +49,33 @@ def test_workload_shapes():
         gap = np.maximum(np.maximum(b[:, :3], -b[:, 3:]), 0.0)
         assert np.all(np.linalg.norm(gap, axis=1) > 0.1)
     assert np.array_equal(synth.workload("arm7-n5000").query_configs(100), w7.query_configs(100))
+
+
+def test_twelve_control_point_arm_adds_link_midpoints():
+    from oracle import oracle as O
+    arm = synth.arm_7dof_m12(4000)
+    assert arm.M == 12 and list(arm.cp_joint[:8]) == list(range(8))
+    length = np.hypot(arm.dh[:, 0], arm.dh[:, 2])
+    assert sorted(arm.cp_joint[8:] - 1) == sorted(np.argsort(-length)[:4])
+    q = synth.uniform_configs(7, 50, arm.D, arm.qlim).astype(np.float64)
+    cp = O.fk_points(arm, q)
+    for m in range(8, 12):
+        j = int(arm.cp_joint[m])
+        mid = 0.5 * (cp[:, j - 1] + cp[:, j])  # frame origins j-1 and j are control points j-1 and j
+        np.testing.assert_allclose(cp[:, m], mid, atol=1e-7)
+
+
+def test_moving_boxes_stay_in_bounds_and_move_slowly():
+    w = synth.workload("arm7m12-n65536")
+    b = synth.moving_boxes(w.seed, w.scene.boxes, 100)
+    assert b.shape == (100, 10, 6)
+    np.testing.assert_array_equal(b[0], w.scene.boxes)
+    c = 0.5 * (b[..., :3] + b[..., 3:])
+    h = b[..., 3:] - b[..., :3]
+    step = np.linalg.norm(np.diff(c, axis=0), axis=2)
+    assert step.max() <= 0.05 * 1.0001 and step.max() > 0.01
+    np.testing.assert_allclose(h, h[0:1].repeat(100, axis=0), atol=1e-6)  # sizes fixed
+    assert np.all(np.abs(c) <= 0.8 + 1e-6)
+    gap = np.maximum(np.maximum(b[..., :3], -b[..., 3:]), 0.0)
+    assert np.all(np.linalg.norm(gap, axis=2) > 0.1)
+    np.testing.assert_array_equal(b, synth.moving_boxes(w.seed, w.scene.boxes, 100))
