@@ -46,6 +46,8 @@ extern "C" {
 #define FK_F64 1  /* FP64 arithmetic */
 #define FK_F16 2  /* packed FP16 distances, FP32 reciprocals and sums (fk_score only) */
 #define FK_DF64 3 /* FP64 inputs and outputs, double-float arithmetic on the FP32 pipes (fk_gram, training) */
+#define FK_DF32 4 /* as FK_DF64, each result rounded to FP32 once: the kernel matrix stored in
+                     single precision (fk_gram: float K; training: half the memory) */
 
 #define FK_MAX_DOF 16
 #define FK_MAX_CP 32
@@ -95,7 +97,8 @@ int fk_forward_f64(const fk_chain_t *chain, const double *q, int64_t n, double *
  * computed in double-float arithmetic (pairs of FP32 values, error-free
  * transformations; entries within about 1e-13 of the FP64 ones, some ten
  * times faster on this part, whose FP64 rate is 1/64 of its FP32 rate).
- * FK_F32: float inputs and a float K.  gamma > 0.
+ * FK_DF32: FP64 inputs, a device float K holding each FK_DF64 entry rounded to
+ * FP32 once.  FK_F32: float inputs and a float K.  gamma > 0.
  * Control points are computed into the chain's workspace first. */
 int fk_gram(const fk_chain_t *chain, const void *Xa, int64_t na, const void *Xb, int64_t nb, double gamma,
             int precision, void *K, void *stream);
@@ -110,9 +113,13 @@ typedef struct {
                           same training set (loadPreviousModel); 0: alpha = F = 0 */
     int32_t trace;     /* 1: record every pass (kind, index, change of alpha) for
                           fastron_model_trace; 0: do not */
-    int32_t gram;      /* arithmetic of the training kernel matrix: FK_DF64 (0 selects it)
-                          or FK_F64 */
-    int32_t reserved;
+    int32_t gram;      /* arithmetic and storage of the training kernel matrix: FK_DF64
+                          (0 selects it) or FK_F64, both stored in FP64 (N^2 doubles), or
+                          FK_DF32, stored in FP32 (N^2 floats; 17.2 GB at N = 65,536) */
+    int32_t reuse_gram;/* 1: X is the training set of this model's previous call, with the same
+                          N and gram: its stored kernel matrix is used again instead of being
+                          rebuilt (a changing environment relabels a fixed training set);
+                          0: build it */
 } fastron_params;
 
 typedef struct {
@@ -138,7 +145,10 @@ void fastron_model_destroy(fastron_model_t *model);
  * applies or after iter_max passes.  alpha and F are FP64.  The support set
  * (ascending training indices with alpha != 0) and its weights become the
  * model.  stats: host, may be NULL; filling it synchronises `stream`.
- * Requires N <= 8192 (the FP64 kernel matrix is N^2 doubles), else FK_ERR_CAPACITY. */
+ * The kernel matrix is stored (N^2 entries of 8 or 4 bytes, see gram) and
+ * kept with the model.  Requires N <= 65,536, else FK_ERR_CAPACITY; the
+ * matrix must fit in device memory, else FK_ERR_CUDA.  Sizes above 32,768
+ * need a 16-CTA thread-block cluster. */
 int fastron_train(fastron_model_t *model, const double *X, const int8_t *y, int64_t N, const fastron_params *p,
                   fastron_stats *stats, void *stream);
 
@@ -165,11 +175,14 @@ int fastron_model_get(const fastron_model_t *model, int64_t *idx, double *alpha,
  * q: device float, n x D.  label: device int8 [n].  f: device float [n] or NULL.
  * precision FK_F32: FK of each query and the kernel sums run in FP32; a bound
  * B(q) = sum_s |alpha_s| K_FK(S_s, q) is accumulated beside f.
- * rescore != 0: every query with |f| <= rescore_eps * B(q) is evaluated
- * again in FP64 (FK and kernel), and its f and label are replaced, so that
- * labels equal an FP64 evaluation.  rescore_eps <= 0 selects the library
- * default.  n_rescored (host, may be NULL) receives the number of queries
- * re-evaluated; filling it synchronises `stream`.
+ * rescore != 0: every query with |f| <= rescore_eps * B(q) (the FP32 band)
+ * is evaluated again, and its f and label are replaced, so that labels equal
+ * an FP64 evaluation: first in double-float arithmetic (FP64 kinematics,
+ * summands and sums as FP32 pairs, ~1e-13 relative), then, for the queries
+ * it leaves within 1e-9 B(q) of zero, in FP64 (FK and kernel).  The call
+ * reads the band size back, so it synchronises `stream` once.  rescore_eps
+ * <= 0 selects the library default.  n_rescored (host, may be NULL) receives
+ * the size of the FP32 band; filling it synchronises `stream`.
  * precision FK_F16: the differences and t = 1 + gamma/2 |p - s|^2 are
  * computed in packed half precision, the rest in FP32; with rescore != 0 every
  * query with |f| <= rescore_eps * B(q) (default 2e-3) goes through the FP32

@@ -1,0 +1,64 @@
+// Double-float arithmetic: a value is the unevaluated sum h + l of two FP32
+// numbers (about 48 significant bits), manipulated with the error-free
+// transformations two-sum (Knuth, TAOCP vol. 2, 4.2.2) and two-product by
+// FMA (Dekker, Numer. Math. 18, 1971, with the splitting replaced by the
+// fused product), so FP64-class accuracy comes from the FP32 pipes.
+#pragma once
+
+#include "fk_ptx.cuh"
+
+namespace fk {
+
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// a - b, accurate when the two cancel
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
+  dfl s = two_sum(a.h, -b.h);
+  s.l += a.l - b.l;
+  return quick_two_sum(s.h, s.l);
+}
+// (h + l)^2 = h^2 + 2 h l (l^2 is below the precision); h^2 exactly by FMA
+__device__ __forceinline__ dfl df_sqr(dfl a) {
+  const float p = a.h * a.h;
+  const float e = fmaf(a.h, a.h, -p);
+  return quick_two_sum(p, fmaf(2.f * a.h, a.l, e));
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p);
+  return quick_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+// sum of two non-negative values (no cancellation)
+__device__ __forceinline__ dfl df_add_pos(dfl a, dfl b) {
+  dfl s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return quick_two_sum(s.h, s.l);
+}
+// 1 / a for a >= 1: y = rcp(a.h) with relative error about 2^-23, then
+// y + y (1 - a y) with the residual 1 - a y formed exactly (a.h y = p + pe by
+// FMA, 1 - p exact since p is within a factor 2 of 1): error about 2^-46
+__device__ __forceinline__ dfl df_rcp(dfl a) {
+  const float y = rcp_approx(a.h);
+  const float p = a.h * y;
+  const float pe = fmaf(a.h, y, -p);
+  const float e = ((1.f - p) - pe) - a.l * y;
+  return quick_two_sum(y, y * e);
+}
+
+
+}  // namespace fk

@@ -10,7 +10,8 @@
 //      label and alpha, and takes the same decision: add/adjust (Eqs. 6-8),
 //      removal, or stop;
 //   2. every thread updates its F_j with row i of the stored kernel matrix
-//      (symmetric, so row i is column i); the owner of i updates alpha_i;
+//      (symmetric, so row i is column i; FP64, or FP32 entries widened to
+//      FP64 exactly); the owner of i updates alpha_i;
 //   3. candidates are reduced: per thread, warp shuffles, one __syncthreads
 //      for the CTA, then warp 0 stores the CTA's pair into a slot of every
 //      CTA of the cluster (distributed shared memory) and, one cluster
@@ -60,6 +61,18 @@ __device__ __forceinline__ long long bits_key(long long b) {
 }
 __device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k >= 0 ? k : (k ^ kMag)); }
 __device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) & kMag) != 0; }
+
+// Exact FP32 -> FP64 widening.  Positive normal values (every kernel-matrix
+// entry: 0 < K <= 1, far above the FP32 normal range's lower end) get their
+// exponent rebiased (127 -> 1023) and fraction shifted by integer operations,
+// keeping the conversion off the FP64 pipe; anything else takes the ordinary
+// conversion.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  if (b - 0x00800000u < 0x7f000000u) return __longlong_as_double(((long long)b << 29) + (896LL << 52));
+  return (double)x;
+}
+__device__ __forceinline__ double widen(double x) { return x; }
 
 __device__ __forceinline__ int cidx(const Cand &c) { return c.iy & 0x7fffffff; }
 __device__ __forceinline__ bool better_min(const Cand &a, const Cand &b) {
@@ -123,8 +136,10 @@ struct TrainShared {
   int slot_cnt[kMaxCluster], wcnt[kTrainWarps];
 };
 
-template <int KMAX>
+template <int KMAX, typename GT>
 __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const TrainArgs a) {
+  static_assert(KMAX <= 32, "labels are kept as a bit mask");
+  const GT *__restrict__ G = static_cast<const GT *>(a.G);
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TrainShared sh;
@@ -138,17 +153,16 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
   const int N = (int)a.N;
 
   double F[KMAX];
-  int yneg[KMAX];
+  unsigned yneg = 0;  // bit k: label of point g + stride k is -1
   int nnz_local = 0;
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     const int j = g + stride * k;
     F[k] = 0.0;
-    yneg[k] = 0;
     double aj = 0.0;
     if (j < N) {
       F[k] = a.F[j];
-      yneg[k] = a.y[j] > 0 ? 0 : 1;
+      yneg |= (a.y[j] > 0 ? 0u : 1u) << k;
       aj = a.alpha[j];
       nnz_local += nonzero(aj);
     }
@@ -187,8 +201,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
     for (int k = 0; k < KMAX; ++k) {
       const int j = g + stride * k;
       if (j < N) {
-        const long long sign = (long long)yneg[k] << 63;
-        const int iy = j | (yneg[k] << 31);
+        const unsigned yn = (yneg >> k) & 1u;
+        const long long sign = (long long)yn << 63;
+        const int iy = j | (int)(yn << 31);
         const double aj = alpha[k * kTrainThreads + tid];
         const long long km = bits_key(__double_as_longlong(F[k]) ^ sign);  // key of y_j F_j
         if (km < mn.key) mn = {km, aj, iy};  // j ascends within a thread
@@ -228,15 +243,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
   int converged = 0;
   for (long long iter = 1; iter <= a.iter_max; ++iter) {
     // request the argmin's row first: an add step is the common case
-    double gk[KMAX];
+    GT gk[KMAX];
     const int imin = cidx(mn);
     const bool min_valid = imin != INT_MAX;
     if (min_valid) {
-      const double *row = a.G + (long long)imin * N;
+      const GT *row = G + (long long)imin * N;
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         const int j = g + stride * k;
-        gk[k] = j < N ? row[j] : 0.0;
+        gk[k] = j < N ? row[j] : GT(0);
       }
     }
     int kind, i;
@@ -276,11 +291,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = 0.0;
       --nnz;
       ++removes;
-      const double *row = a.G + (long long)i * N;
+      const GT *row = G + (long long)i * N;
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         const int j = g + stride * k;
-        gk[k] = j < N ? row[j] : 0.0;
+        gk[k] = j < N ? row[j] : GT(0);
       }
     } else {
       converged = 1;
@@ -292,12 +307,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       a.trace_idx[iter - 1] = i;
       a.trace_delta[iter - 1] = delta;
     }
+    // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal).  Round
+    // to nearest is symmetric in sign, so F - fl(alpha_i K) equals
+    // F + fl((-alpha_i) K) bit for bit: one signed multiply and one add.
+    const double c = kind == 1 ? coef : -coef;
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal)
-      const double p = __dmul_rn(coef, gk[k]);
-      F[k] = kind == 1 ? __dadd_rn(F[k], p) : __dsub_rn(F[k], p);
-    }
+    for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, widen(gk[k])));  // FP32 entries widen exactly
     local_candidates();
     reduce_cluster();
   }
@@ -353,9 +368,9 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(const double *
   if (tid == 0) stats[4] = base;
 }
 
-template <int KMAX>
+template <int KMAX, typename GT>
 static cudaError_t launch_k(const TrainArgs &a, int C, cudaStream_t s) {
-  auto kern = fastron_train_kernel<KMAX>;
+  auto kern = fastron_train_kernel<KMAX, GT>;
   const size_t smem = sizeof(double) * KMAX * kTrainThreads;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
@@ -378,24 +393,30 @@ static cudaError_t launch_k(const TrainArgs &a, int C, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+template <typename GT>
 static cudaError_t launch_c(const TrainArgs &a, int C, cudaStream_t s) {
   const int64_t per = (int64_t)kTrainThreads * C;
   const int64_t kneed = (a.N + per - 1) / per;
-  if (kneed <= 1) return launch_k<1>(a, C, s);
-  if (kneed <= 2) return launch_k<2>(a, C, s);
-  if (kneed <= 4) return launch_k<4>(a, C, s);
-  if (kneed <= 8) return launch_k<8>(a, C, s);
+  if (kneed <= 1) return launch_k<1, GT>(a, C, s);
+  if (kneed <= 2) return launch_k<2, GT>(a, C, s);
+  if (kneed <= 4) return launch_k<4, GT>(a, C, s);
+  if (kneed <= 8) return launch_k<8, GT>(a, C, s);
+  if (kneed <= 16) return launch_k<16, GT>(a, C, s);
   return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_any(const TrainArgs &a, int C, cudaStream_t s) {
+  return a.g32 ? launch_c<float>(a, C, s) : launch_c<double>(a, C, s);
 }
 
 cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s) {
   // as many CTAs as the points need (at least 2 per thread below 16 CTAs)
   int C = 1;
   while (C < kMaxCluster && (int64_t)kTrainThreads * C * 2 < a.N) C *= 2;
-  cudaError_t e = launch_c(a, C, s);
-  if (e != cudaSuccess && C > 8) {
+  cudaError_t e = launch_any(a, C, s);
+  if (e != cudaSuccess && C > 8 && a.N <= (int64_t)kTrainThreads * 8 * 16) {
     cudaGetLastError();  // the non-portable size may be unavailable: fall back to 8
-    e = launch_c(a, 8, s);
+    e = launch_any(a, 8, s);
   }
   if (e != cudaSuccess) return e;
   compact_kernel<<<1, kCompactThreads, 0, s>>>(a.alpha, (int)a.N, a.sup_idx, a.sup_alpha, a.stats);

@@ -25,12 +25,17 @@ cudaError_t launch_gram_f64(const ChainD &c, double gamma, const double *cpa, in
 // Double-float (FP32 pair) evaluation of the FP64 kernel matrix.
 cudaError_t launch_gram_df(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
                            int sym, double *K, cudaStream_t s);
+// The same, each entry rounded to FP32 once (the stored single-precision matrix).
+cudaError_t launch_gram_df32(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
+                             int64_t nb, int sym, float *K, cudaStream_t s);
 cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
                             int sym, float *K, cudaStream_t s);
 
-// Fastron Algorithm 1 on a stored FP64 kernel matrix G [N][N].
+// Fastron Algorithm 1 on a stored kernel matrix G [N][N], FP64 or FP32
+// (g32 != 0), N <= 65,536.
 struct TrainArgs {
-  const double *G;
+  const void *G;
+  int g32;
   const int8_t *y;
   int64_t N;
   double beta;
@@ -53,6 +58,12 @@ cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s);
 // by sqrt(gamma / 2).
 __host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 1; }
 
+// floats of one support point's double-float record (the band re-score): for
+// each configuration-dependent control point (x_h, x_l, y_h, y_l, z_h, z_l) of
+// sqrt(gamma/2) times its FP64 position, then (w_h, w_l, |w|, 0) with
+// w = alpha / M as a pair, padded to a multiple of four.
+__host__ __device__ constexpr int rec_df_len(int mv) { return (6 * mv + 4 + 3) / 4 * 4; }
+
 // Packs a support set for scoring: gathers X[idx[s]] (FP64 configurations,
 // idx may be null for identity), computes their FP64 control points and
 // writes the FP32 score records and the FP64 SoA control points.
@@ -66,6 +77,7 @@ struct PackArgs {
   double *cp64;       // SoA [M][3][ns]
   double *alpha_out;  // [ns] (copy of alpha, compacted)
   double *q_out;      // [ns][D] support configurations
+  float *sdf;         // [ns][rec_df_len(Mv)] double-float records
 };
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s);
 
@@ -100,6 +112,30 @@ struct RescoreArgs {
   int8_t *label;
 };
 cudaError_t launch_rescore_f64(const ChainD &c, const RescoreArgs &a, cudaStream_t s);
+
+// Double-float re-evaluation of the band (host-known size nb); queries whose
+// |f| <= eps2 B(q) are appended to band2 for the FP64 re-score.
+constexpr int kMaxDfChunks = 64;
+struct DfRescoreArgs {
+  const float *q;
+  const int32_t *band_idx;  // [nb]
+  int64_t nb;
+  const float *sdf;         // [ns][rec_df_len(Mv)]
+  int64_t ns;
+  int n_const;              // control points fixed to the base (summand exactly 1)
+  double gs;                // sqrt(gamma / 2)
+  float2 *qdf;              // [Mv * 3][nb] scratch: band control points as pairs
+  float4 *part;             // [chunks][nb] scratch: (f_h, f_l, B, 0) per chunk
+  int chunks;
+  int64_t chunk_len;
+  double eps2;
+  float *f;
+  int8_t *label;
+  int32_t *band2_idx;       // [nb]
+  int32_t *band2_cnt;       // [1], zeroed by the caller
+};
+int rescore_df_chunks(int64_t nb, int64_t ns, int sms);
+cudaError_t launch_rescore_df(const ChainD &c, const DfRescoreArgs &a, cudaStream_t s);
 
 // Geometric labels: FP32 filter, FP64 for configurations too close to call.
 constexpr int kMaxBoxes = 64;

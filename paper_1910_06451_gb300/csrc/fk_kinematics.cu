@@ -1,5 +1,6 @@
 // Forward kinematics (Sec. II-A, Eqs. 1-2) and the FK-kernel matrix
 // (Sec. II-B with Eq. 4) on the GPU.
+#include "df_arith.cuh"
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
 
@@ -177,75 +178,22 @@ cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int6
 }
 
 // ------------------------------------------------- double-float Gram ---
-// The same matrix in double-float arithmetic: a value is an unevaluated sum
-// h + l of two FP32 numbers (about 48 significant bits), manipulated with the
-// error-free transformations two-sum (Knuth) and two-product by FMA (Dekker's
-// splitting replaced by the fused product), so the work runs on the FP32
-// pipes (128 lanes/clk/SM) instead of the FP64 pipe (1.7 lanes/clk/SM on this
-// part).  Inputs are the FP64 control points split into h + l; the reciprocal
-// is a MUFU estimate refined by one Newton step carried in double-float.  The
-// entries come out within about 1e-13 of the FP64 ones.
-struct dfl {
-  float h, l;
-};
-
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ dfl quick_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ dfl df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-// a - b, accurate when the two cancel
-__device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
-  dfl s = two_sum(a.h, -b.h);
-  s.l += a.l - b.l;
-  return quick_two_sum(s.h, s.l);
-}
-// (h + l)^2 = h^2 + 2 h l (l^2 is below the precision); h^2 exactly by FMA
-__device__ __forceinline__ dfl df_sqr(dfl a) {
-  const float p = a.h * a.h;
-  const float e = fmaf(a.h, a.h, -p);
-  return quick_two_sum(p, fmaf(2.f * a.h, a.l, e));
-}
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.h, -p);
-  return quick_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
-}
-// sum of two non-negative values (no cancellation)
-__device__ __forceinline__ dfl df_add_pos(dfl a, dfl b) {
-  dfl s = two_sum(a.h, b.h);
-  s.l += a.l + b.l;
-  return quick_two_sum(s.h, s.l);
-}
-// 1 / a for a >= 1: y = rcp(a.h) with relative error about 2^-23, then
-// y + y (1 - a y) with the residual 1 - a y formed exactly (a.h y = p + pe by
-// FMA, 1 - p exact since p is within a factor 2 of 1): error about 2^-46
-__device__ __forceinline__ dfl df_rcp(dfl a) {
-  const float y = rcp_approx(a.h);
-  const float p = a.h * y;
-  const float pe = fmaf(a.h, y, -p);
-  const float e = ((1.f - p) - pe) - a.l * y;
-  return quick_two_sum(y, y * e);
-}
-
+// The same matrix in double-float arithmetic (df_arith.cuh): the work runs on
+// the FP32 pipes (128 lanes/clk/SM) instead of the FP64 pipe (1.7 lanes/clk/SM
+// on this part).  Inputs are the FP64 control points split into h + l; the
+// reciprocal is a MUFU estimate refined by one Newton step carried in
+// double-float.  The entries come out within about 1e-13 of the FP64 ones.
+template <typename OT>
 __global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, double gamma, const double *__restrict__ cpa,
                                                      int64_t na, const double *__restrict__ cpb, int64_t nb, int sym,
-                                                     double *__restrict__ K) {
+                                                     OT *__restrict__ K) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = g.M;
   dfl *A = reinterpret_cast<dfl *>(smem_raw);
   dfl *B = A + M * 3 * kGT;
-  double *O = reinterpret_cast<double *>(B + M * 3 * kGT);  // [kGT][kGT + 1]
+  OT *O = reinterpret_cast<OT *>(B + M * 3 * kGT);  // [kGT][kGT + 1]
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)bi * kGT, j0 = (int64_t)bj * kGT;
   for (int e = threadIdx.x; e < M * 3 * kGT; e += blockDim.x) {
@@ -271,7 +219,7 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, double ga
       const dfl t = df_add_pos(one, df_mul(hg, d2));
       s = df_add_pos(s, df_rcp(df_sqr(t)));
     }
-    const double v = ((double)s.h + (double)s.l) * invM;
+    const OT v = (OT)(((double)s.h + (double)s.l) * invM);  // FP32: one more rounding
     if (i0 + il < na && j0 + tx < nb) K[(i0 + il) * nb + j0 + tx] = v;
     if (mirror) O[il * (kGT + 1) + tx] = v;
   }
@@ -284,19 +232,30 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, double ga
   }
 }
 
-cudaError_t launch_gram_df(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
-                           int sym, double *K, cudaStream_t s) {
+template <typename OT>
+static cudaError_t launch_gram_df_t(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
+                                    int64_t nb, int sym, OT *K, cudaStream_t s) {
   if (na <= 0 || nb <= 0) return cudaSuccess;
   GramCps g{c.M, c.Mv, c.n_const, {}};
   for (int v = 0; v < c.Mv; ++v) g.vidx[v] = c.vidx[v];
-  const size_t smem = sizeof(dfl) * 2 * (size_t)c.M * 3 * kGT + sizeof(double) * kGT * (kGT + 1);
+  const size_t smem = sizeof(dfl) * 2 * (size_t)c.M * 3 * kGT + sizeof(OT) * kGT * (kGT + 1);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gram_df_kernel<OT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(grid_for(nb, kGT), grid_for(na, kGT));
-  gram_df_kernel<<<grid, 256, smem, s>>>(g, gamma, cpa, na, cpb, nb, sym, K);
+  gram_df_kernel<OT><<<grid, 256, smem, s>>>(g, gamma, cpa, na, cpb, nb, sym, K);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gram_df(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
+                           int sym, double *K, cudaStream_t s) {
+  return launch_gram_df_t<double>(c, gamma, cpa, na, cpb, nb, sym, K, s);
+}
+
+cudaError_t launch_gram_df32(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
+                             int64_t nb, int sym, float *K, cudaStream_t s) {
+  return launch_gram_df_t<float>(c, gamma, cpa, na, cpb, nb, sym, K, s);
 }
 
 }  // namespace fk

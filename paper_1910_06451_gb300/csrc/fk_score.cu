@@ -20,6 +20,7 @@
 //   rescore  FP64, one warp per band query: FK and Eq. 3/4 in FP64 with the
 //            operation order of the plain definition, lanes splitting the
 //            support set, a fixed-order warp sum; f and the label are replaced.
+#include "df_arith.cuh"
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
 #include "score_core.cuh"
@@ -68,6 +69,20 @@ __global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) 
     const double wd = al / cd.M;
     w[h] = (float)wd;
     aw[h] = (float)fabs(wd);
+    if (a.sdf) {
+      float *r = a.sdf + s * rec_df_len(MV);
+      for (int v = 0; v < MV; ++v)
+        for (int c3 = 0; c3 < 3; ++c3) {
+          const dfl x = df_from_double(gs * cp[cf.vidx[v]][c3]);
+          r[v * 6 + 2 * c3] = x.h;
+          r[v * 6 + 2 * c3 + 1] = x.l;
+        }
+      const dfl wp = df_from_double(wd);
+      r[6 * MV] = wp.h;
+      r[6 * MV + 1] = wp.l;
+      r[6 * MV + 2] = (float)fabs(wd);
+      for (int i = 6 * MV + 3; i < rec_df_len(MV); ++i) r[i] = 0.f;
+    }
   }
   for (int v = 0; v < MV; ++v) rec[v] = make_float4(cpv[0][v][0], cpv[1][v][0], cpv[0][v][1], cpv[1][v][1]);
   for (int v = 0; v < MV; v += 2) {

@@ -186,7 +186,7 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
   if (!c) return fail(FK_ERR_ARG, "fk_gram: chain is NULL");
   if (na < 0 || nb < 0) return fail(FK_ERR_ARG, "fk_gram: negative size");
   if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(FK_ERR_ARG, "fk_gram: gamma must be finite and > 0");
-  if (precision != FK_F32 && precision != FK_F64 && precision != FK_DF64)
+  if (precision != FK_F32 && precision != FK_F64 && precision != FK_DF64 && precision != FK_DF32)
     return fail(FK_ERR_ARG, "fk_gram: unknown precision %d", precision);
   if (na == 0 || nb == 0) return FK_OK;
   if (!Xa || !Xb || !K) return fail(FK_ERR_ARG, "fk_gram: NULL pointer");
@@ -195,12 +195,14 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
   const size_t el = precision == FK_F32 ? sizeof(float) : sizeof(double);
   CK(c->ws_a.ensure(el * (size_t)c->M * 3 * (size_t)na));
   if (!sym) CK(c->ws_b.ensure(el * (size_t)c->M * 3 * (size_t)nb));
-  if (precision == FK_F64 || precision == FK_DF64) {
+  if (precision == FK_F64 || precision == FK_DF64 || precision == FK_DF32) {
     double *A = c->ws_a.as<double>(), *B = sym ? A : c->ws_b.as<double>();
     CK(launch_fk_forward_f64(c->cd, (const double *)Xa, na, A, s));
     if (!sym) CK(launch_fk_forward_f64(c->cd, (const double *)Xb, nb, B, s));
     if (precision == FK_F64)
       CK(launch_gram_f64(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
+    else if (precision == FK_DF32)
+      CK(launch_gram_df32(c->cd, gamma, A, na, B, nb, sym, (float *)K, s));
     else
       CK(launch_gram_df(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
   } else {
@@ -213,8 +215,9 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
 }
 
 // -------------------------------------------------------------- model ---
-static constexpr int64_t kMaxTrainN = 8192;
+static constexpr int64_t kMaxTrainN = 65536;
 static constexpr double kDefaultEps = 6e-6;
+static constexpr double kDefaultEpsDf = 1e-9;  // band of the double-float re-score, relative to B(q)
 static constexpr double kDefaultEpsF16 = 2e-3;
 static constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // about a quarter second of polling
 static uint32_t g_wait_limit = kDefaultWaitLimit;
@@ -225,16 +228,18 @@ struct fastron_model {
   const fk_chain *chain = nullptr;
   // training state (full training set)
   int64_t N = 0;
+  int gram = -1;  // arithmetic/storage of G for the training set of the last call (-1: none)
   DevBuf cpX, G, alpha, F, stats, sup_idx, sup_alpha, trace_kind, trace_idx, trace_delta;
   int64_t trace_len = 0;
   // support set packed for scoring
   int64_t ns = -1;  // -1 = untrained
   double gamma = 0.0;
-  DevBuf rec, cp64, alpha_s, q_s, qin;
+  DevBuf rec, cp64, alpha_s, q_s, qin, sdf;
   std::vector<int64_t> host_idx;  // training indices of the support points (model_set: positions)
   bool host_idx_valid = false;
   // score scratch
-  DevBuf band_idx, flags;  // flags: [0] band count, [1] error bits
+  DevBuf band_idx, flags;  // flags: [0] band count, [1] error bits, [2] FP64 band count
+  DevBuf qdf, part, band2_idx;  // double-float re-score scratch
   DevBuf fb_idx, fb_q, fb_lab, fb_f;  // band of the half pass, re-scored by the FP32 path
 };
 
@@ -254,7 +259,8 @@ extern "C" int fastron_model_create(const fk_chain_t *chain, fastron_model_t **o
 extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
   DevBuf *bufs[] = {&m->cpX, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
-                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin,
+                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf,
+                    &m->qdf, &m->part, &m->band2_idx,
                     &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
   for (DevBuf *b : bufs) b->release();
   delete m;
@@ -267,8 +273,9 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   CK(m->cp64.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->M * 3));
   CK(m->alpha_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
+  CK(m->sdf.ensure(sizeof(float) * (size_t)(ns > 0 ? ns : 1) * rec_df_len(c->cf.Mv)));
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
-              m->q_s.as<double>()};
+              m->q_s.as<double>(), m->sdf.as<float>()};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
   m->gamma = gamma;
@@ -285,15 +292,20 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   if (!(p->beta >= 1.0) || !std::isfinite(p->beta)) return fail(FK_ERR_ARG, "fastron_train: beta must be >= 1");
   if (p->iter_max < 0) return fail(FK_ERR_ARG, "fastron_train: iter_max < 0");
   if (p->s_max < 1) return fail(FK_ERR_ARG, "fastron_train: s_max < 1");
-  if (p->gram != 0 && p->gram != FK_F64 && p->gram != FK_DF64)
-    return fail(FK_ERR_ARG, "fastron_train: gram must be FK_DF64 or FK_F64");
+  const int gram = p->gram == 0 ? FK_DF64 : p->gram;
+  if (gram != FK_F64 && gram != FK_DF64 && gram != FK_DF32)
+    return fail(FK_ERR_ARG, "fastron_train: gram must be FK_DF64, FK_F64 or FK_DF32");
   if (p->warm_start && (m->N != N || m->alpha.p == nullptr))
     return fail(FK_ERR_STATE, "fastron_train: warm start needs a previous training call with the same N");
+  if (p->reuse_gram && (m->N != N || m->gram != gram))
+    return fail(FK_ERR_STATE, "fastron_train: reuse_gram needs a previous call with the same N and gram");
   cudaStream_t s = (cudaStream_t)stream;
   const fk_chain *c = m->chain;
   const bool keep = p->warm_start != 0;
+  const bool reuse = p->reuse_gram != 0;
   CK(m->cpX.ensure(sizeof(double) * (size_t)N * c->M * 3));
-  CK(m->G.ensure(sizeof(double) * (size_t)N * (size_t)N));
+  if (!reuse) m->gram = -1;  // the stored matrix is invalid until rebuilt below
+  CK(m->G.ensure((gram == FK_DF32 ? sizeof(float) : sizeof(double)) * (size_t)N * (size_t)N));
   if (!keep) {
     CK(m->alpha.ensure(sizeof(double) * (size_t)N));
     CK(m->F.ensure(sizeof(double) * (size_t)N));
@@ -311,12 +323,18 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     CK(m->trace_delta.ensure(sizeof(double) * L));
   }
   m->N = N;
-  CK(launch_fk_forward_f64(c->cd, X, N, m->cpX.as<double>(), s));
-  if (p->gram == FK_F64)
-    CK(launch_gram_f64(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
-  else
-    CK(launch_gram_df(c->cd, p->gamma, m->cpX.as<double>(), N, m->cpX.as<double>(), N, 1, m->G.as<double>(), s));
-  TrainArgs ta{m->G.as<double>(), y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
+  if (!reuse) {
+    CK(launch_fk_forward_f64(c->cd, X, N, m->cpX.as<double>(), s));
+    const double *cp = m->cpX.as<double>();
+    if (gram == FK_F64)
+      CK(launch_gram_f64(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), s));
+    else if (gram == FK_DF32)
+      CK(launch_gram_df32(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<float>(), s));
+    else
+      CK(launch_gram_df(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), s));
+    m->gram = gram;
+  }
+  TrainArgs ta{m->G.p, gram == FK_DF32 ? 1 : 0, y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
                m->stats.as<int64_t>(), m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(),
                trace ? m->trace_kind.as<int8_t>() : nullptr, trace ? m->trace_idx.as<int32_t>() : nullptr,
                trace ? m->trace_delta.as<double>() : nullptr};
@@ -446,26 +464,37 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
     if (n_rescored) *n_rescored = nb;
     return FK_OK;
   }
-  CK(m->flags.ensure(sizeof(int32_t) * 2));
-  CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
-  int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1;
+  CK(m->flags.ensure(sizeof(int32_t) * 4));
+  CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 4, s));
+  int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1, *cnt2 = cnt + 2;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
   const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
   ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
                rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit};
   CK(launch_score_f32(c->cf, sa, s));
-  if (rescore) {
-    RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
-                   m->gamma, f, label};
-    CK(launch_rescore_f64(c->cd, ra, s));
-  }
-  if (n_rescored) {
-    int32_t h[2];
-    CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score: a shared-memory tile wait timed out");
-    *n_rescored = rescore ? h[0] : 0;
-  }
+  if (!rescore && !n_rescored) return FK_OK;
+  int32_t h[2];
+  CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score: a shared-memory tile wait timed out");
+  if (n_rescored) *n_rescored = rescore ? h[0] : 0;
+  if (!rescore || h[0] == 0) return FK_OK;
+  // the band: double-float first, FP64 for what it cannot decide
+  const int64_t nb = h[0];
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int chunks = rescore_df_chunks(nb, m->ns, sms);
+  CK(m->qdf.ensure(sizeof(float2) * (size_t)nb * c->cf.Mv * 3));
+  CK(m->part.ensure(sizeof(float4) * (size_t)nb * chunks));
+  CK(m->band2_idx.ensure(sizeof(int32_t) * (size_t)nb));
+  DfRescoreArgs da{q, m->band_idx.as<int32_t>(), nb, m->sdf.as<float>(), m->ns, c->cd.n_const,
+                   sqrt(0.5 * m->gamma), m->qdf.as<float2>(), m->part.as<float4>(), chunks,
+                   (m->ns + chunks - 1) / chunks, kDefaultEpsDf, f, label, m->band2_idx.as<int32_t>(), cnt2};
+  CK(launch_rescore_df(c->cd, da, s));
+  RescoreArgs ra{q, m->band2_idx.as<int32_t>(), cnt2, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
+                 m->gamma, f, label};
+  CK(launch_rescore_f64(c->cd, ra, s));
   return FK_OK;
 }
 

@@ -25,6 +25,7 @@ FK_F32 = 0
 FK_F64 = 1
 FK_F16 = 2
 FK_DF64 = 3
+FK_DF32 = 4
 FK_MAX_DOF = 16
 FK_MAX_CP = 32
 
@@ -56,7 +57,7 @@ class FkCp(ctypes.Structure):
 class FastronParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("beta", ctypes.c_double), ("iter_max", ctypes.c_int64),
                 ("s_max", ctypes.c_int64), ("warm_start", ctypes.c_int32), ("trace", ctypes.c_int32),
-                ("gram", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("gram", ctypes.c_int32), ("reuse_gram", ctypes.c_int32)]
 
 
 class SurrogateTrainParams(ctypes.Structure):
@@ -219,14 +220,19 @@ def fk_forward_f64(chain, q, cp, stream=None):
 
 def fk_gram(chain, Xa, Xb, gamma, K, stream=None, double_float=False):
     """K[i][j] = K_FK(Xa_i, Xb_j); float64 inputs -> FP64 (double-float
-    arithmetic with double_float=True), float32 -> FP32."""
+    arithmetic with double_float=True; a float32 K then receives each entry
+    rounded to FP32), float32 -> FP32."""
     import torch
     dt = Xa.dtype
-    prec = (FK_DF64 if double_float else FK_F64) if dt == torch.float64 else FK_F32
+    kt = dt
+    if dt == torch.float64 and double_float and K.dtype == torch.float32:
+        prec, kt = FK_DF32, torch.float32
+    else:
+        prec = (FK_DF64 if double_float else FK_F64) if dt == torch.float64 else FK_F32
     pa = _dev(Xa, dt, "Xa")
     pb = pa if Xb is Xa else _dev(Xb, dt, "Xb")
     _check(load().fk_gram(chain, pa, Xa.shape[0], pb, Xb.shape[0], float(gamma), prec,
-                          _dev(K, dt, "K", (Xa.shape[0], Xb.shape[0])), _stream(stream)))
+                          _dev(K, kt, "K", (Xa.shape[0], Xb.shape[0])), _stream(stream)))
 
 
 # ---------------------------------------------------------------- model ---
@@ -242,12 +248,12 @@ def fastron_model_destroy(model):
 
 
 def fastron_train(model, X, y, gamma, beta=1.0, iter_max=5000, s_max=None, warm_start=False, trace=False,
-                  gram=FK_DF64, stream=None) -> dict:
+                  gram=FK_DF64, reuse_gram=False, stream=None) -> dict:
     """Algorithm 1 on device training data X (float64, (N, D)) and y (int8, (N,))."""
     import torch
     N = X.shape[0]
     p = FastronParams(float(gamma), float(beta), int(iter_max), int(N if s_max is None else s_max),
-                      int(bool(warm_start)), int(bool(trace)), int(gram), 0)
+                      int(bool(warm_start)), int(bool(trace)), int(gram), int(bool(reuse_gram)))
     st = FastronStats()
     _check(load().fastron_train(model, _dev(X, torch.float64, "X"), _dev(y, torch.int8, "y", (N,)), N,
                                 ctypes.byref(p), ctypes.byref(st), _stream(stream)))

@@ -253,6 +253,63 @@ def test_score_query_equal_to_support_point(fk, arm7, dev):
     assert abs(f_raw[0] + 0.75) <= 1e-6 and lab[0] == -1
 
 
+def _ulps32(a, b):
+    ia = np.asarray(a, dtype=np.float32).view(np.int32).astype(np.int64)
+    ib = np.asarray(b, dtype=np.float32).view(np.int32).astype(np.int64)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_score_double_float_tier_on_every_query(fk, arm3, arm7, dev, which):
+    # a band of eps = 1 holds every query (|f| <= B(q) always), so the
+    # double-float tier evaluates all of them: its f, rounded to FP32, is the
+    # FP64 value rounded to FP32 (1 ulp where the FP64 value sits on a
+    # rounding boundary within the pair error)
+    w, ch = arm3 if which == "arm3" else arm7
+    X = w.train_configs()[:1500].astype(np.float64)
+    y = O.check(w.scene, X)
+    r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+    S, alpha = X[r.support], r.alpha[r.support]
+    Q = w.query_configs(6000)
+    want = O.score(w.scene.arm, S, alpha, Q.astype(np.float64), w.gamma, nthreads=8)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, alpha, w.gamma)
+        tq = torch.from_numpy(Q).to(dev)
+        f = torch.empty(len(Q), dtype=torch.float32, device=dev)
+        lab = torch.empty(len(Q), dtype=torch.int8, device=dev)
+        nres = fk.fk_score(m, tq, lab, f, rescore=True, eps=1.0, count=True)
+        torch.cuda.synchronize()
+    finally:
+        fk.fastron_model_destroy(m)
+    assert nres == len(Q)
+    u = _ulps32(f.cpu().numpy(), want.astype(np.float32))
+    assert u.max() <= 1 and np.mean(u > 0) <= 1e-3
+    assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
+
+
+def test_score_cancelling_support_points_reach_fp64(fk, arm7, dev):
+    # the same configuration twice with weights +1 and -1: f = 0 exactly for
+    # every query, which no reduced precision can decide; the FP64 re-score
+    # returns 0 and the label of f = 0, +1
+    w, ch = arm7
+    x = w.train_configs()[:1].astype(np.float64)
+    S = np.concatenate([x, x])
+    Q = w.query_configs(1000)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, np.array([1.0, -1.0]), w.gamma)
+        tq = torch.from_numpy(Q).to(dev)
+        f = torch.full((len(Q),), 7.0, dtype=torch.float32, device=dev)
+        lab = torch.zeros(len(Q), dtype=torch.int8, device=dev)
+        nres = fk.fk_score(m, tq, lab, f, rescore=True, count=True)
+        torch.cuda.synchronize()
+    finally:
+        fk.fastron_model_destroy(m)
+    assert nres == len(Q)
+    assert np.all(f.cpu().numpy() == 0.0) and np.all(lab.cpu().numpy() == 1)
+
+
 def test_score_timeout_path_reports_and_recovers(fk, arm7, dev):
     # a tile wait that gives up at once returns FK_ERR_TIMEOUT; the context
     # stays usable and the next call with the normal limit succeeds
@@ -285,8 +342,8 @@ def test_argument_errors(fk, arm3, dev):
         with pytest.raises(fk.FkError) as e:
             fk.fk_score(m, q, lab)
         assert e.value.code == fk.FK_ERR_STATE
-        X = torch.zeros((9000, 3), dtype=torch.float64, device=dev)
-        y = torch.ones(9000, dtype=torch.int8, device=dev)
+        X = torch.zeros((65537, 3), dtype=torch.float64, device=dev)
+        y = torch.ones(65537, dtype=torch.int8, device=dev)
         with pytest.raises(fk.FkError) as e:
             fk.fastron_train(m, X, y, 10.0)
         assert e.value.code == fk.FK_ERR_CAPACITY
