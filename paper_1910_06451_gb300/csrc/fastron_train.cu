@@ -5,20 +5,22 @@
 // g = rank * 256 + tid owns the training points j = g + 256 C k.  Its
 // margins F_j (FP64) live in registers, its weights alpha_j (FP64) in its
 // CTA's shared memory (read and written only by the owner).  Each pass:
-//   1. every thread holds the same two candidates, the argmin of y_j F_j and
-//      the argmax over alpha_j != 0 of y_j (F_j - alpha_j), each with its
-//      label and alpha, and takes the same decision: add/adjust (Eqs. 6-8),
-//      removal, or stop;
+//   1. every thread holds the same candidate, the argmin of y_j F_j with its
+//      label and alpha, and takes the same decision: add/adjust (Eqs. 6-8)
+//      or, when no add applies, form the removal candidate (the argmax over
+//      alpha_j != 0 of y_j (F_j - alpha_j)) and remove it or stop;
 //   2. every thread updates its F_j with row i of the stored kernel matrix
 //      (symmetric, so row i is column i; FP64, or FP32 entries widened to
 //      FP64 exactly); the owner of i updates alpha_i;
-//   3. candidates are reduced: per thread, warp shuffles, one __syncthreads
-//      for the CTA, then warp 0 stores the CTA's pair into a slot of every
-//      CTA of the cluster (distributed shared memory) and, one cluster
+//   3. the argmin candidate is reduced: per thread, warp, one __syncthreads
+//      for the CTA, then warp 0 stores the CTA's candidate into a slot of
+//      every CTA of the cluster (distributed shared memory) and, one cluster
 //      barrier later, every warp reduces the C slots itself.  Slots are
-//      double-buffered by pass parity, so one cluster barrier per pass
+//      double-buffered by round parity, so one cluster barrier per round
 //      suffices.  Each warp-level step is three redux.sync reductions and
-//      one shuffle rather than a shuffle butterfly.
+//      one shuffle rather than a shuffle butterfly.  The removal candidate
+//      (argmax) is formed and reduced the same way, but only in a pass where
+//      no add applies.
 // The row of the argmin candidate is requested before the decision is taken
 // (an add step is the common case), so its latency overlaps the decision;
 // the decision's FP64 arithmetic runs in one lane per warp and is broadcast.
@@ -62,26 +64,24 @@ __device__ __forceinline__ long long bits_key(long long b) {
 __device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k >= 0 ? k : (k ^ kMag)); }
 __device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) & kMag) != 0; }
 
-// Exact FP32 -> FP64 widening.  Positive normal values (every kernel-matrix
-// entry: 0 < K <= 1, far above the FP32 normal range's lower end) get their
-// exponent rebiased (127 -> 1023) and fraction shifted by integer operations,
-// keeping the conversion off the FP64 pipe; anything else takes the ordinary
-// conversion.
-__device__ __forceinline__ double widen(float x) {
+// Exact FP32 -> FP64 widening of kernel-matrix entries by integer operations,
+// keeping the conversion off the FP64 pipe: a positive normal value gets its
+// exponent rebiased (127 -> 1023) and its fraction shifted; zero stays zero.
+// Other values (subnormal entries, possible only for enormous gamma without a
+// base control point) are flagged by needs_cast and take the ordinary
+// conversion instead.
+__device__ __forceinline__ double widen_fast(float x) {
   const unsigned b = __float_as_uint(x);
-  if (b - 0x00800000u < 0x7f000000u) return __longlong_as_double(((long long)b << 29) + (896LL << 52));
-  return (double)x;
+  return b ? __longlong_as_double(((long long)b << 29) + (896LL << 52)) : 0.0;
 }
-__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ bool needs_cast(float x) {
+  const unsigned b = __float_as_uint(x);
+  return b != 0u && b - 0x00800000u >= 0x7f000000u;
+}
+__device__ __forceinline__ double widen_fast(double x) { return x; }
+__device__ __forceinline__ bool needs_cast(double) { return false; }
 
 __device__ __forceinline__ int cidx(const Cand &c) { return c.iy & 0x7fffffff; }
-__device__ __forceinline__ bool better_min(const Cand &a, const Cand &b) {
-  return a.key < b.key || (a.key == b.key && cidx(a) < cidx(b));
-}
-__device__ __forceinline__ bool better_max(const Cand &a, const Cand &b) {
-  return a.key > b.key || (a.key == b.key && cidx(a) < cidx(b));
-}
-
 // Warp-wide argmin / argmax with the single-instruction warp reductions
 // (redux.sync): first the high 32 bits of the key (signed), then the low 32
 // bits among the lanes that tie on the high part (unsigned), then the lowest
@@ -122,11 +122,6 @@ __device__ __forceinline__ Cand warp_argmax(const Cand &c) {
 // Every decision below must be identical in every thread of the cluster,
 // because every thread then meets the same barriers; the warp reductions give
 // every lane the same answer.
-__device__ __forceinline__ void warp_reduce(Cand &mn, Cand &mx) {
-  mn = warp_argmin(mn);
-  mx = warp_argmax(mx);
-}
-
 __device__ __forceinline__ Cand no_min() { return {LLONG_MAX, 0.0, INT_MAX}; }
 __device__ __forceinline__ Cand no_max() { return {LLONG_MIN, 0.0, INT_MAX}; }
 
@@ -194,51 +189,67 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
 
   int parity = 0;
   Cand mn, mx;
-  auto local_candidates = [&]() {
+  // argmin of the margins y_j F_j (every pass)
+  auto local_min = [&]() {
     mn = no_min();
-    mx = no_max();
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int j = g + stride * k;
       if (j < N) {
         const unsigned yn = (yneg >> k) & 1u;
-        const long long sign = (long long)yn << 63;
-        const int iy = j | (int)(yn << 31);
+        const long long km = bits_key(__double_as_longlong(F[k]) ^ ((long long)yn << 63));  // key of y_j F_j
+        if (km < mn.key) mn = {km, alpha[k * kTrainThreads + tid], j | (int)(yn << 31)};  // j ascends
+      }
+    }
+  };
+  // argmax over alpha_j != 0 of y_j (F_j - alpha_j): only in passes where
+  // no add applies, which are few (removals and the final check)
+  auto local_max = [&]() {
+    mx = no_max();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int j = g + stride * k;
+      if (j < N) {
         const double aj = alpha[k * kTrainThreads + tid];
-        const long long km = bits_key(__double_as_longlong(F[k]) ^ sign);  // key of y_j F_j
-        if (km < mn.key) mn = {km, aj, iy};  // j ascends within a thread
         if (nonzero(aj)) {
-          const long long kr = bits_key(__double_as_longlong(__dsub_rn(F[k], aj)) ^ sign);
-          if (kr > mx.key) mx = {kr, aj, iy};
+          const unsigned yn = (yneg >> k) & 1u;
+          const long long kr = bits_key(__double_as_longlong(__dsub_rn(F[k], aj)) ^ ((long long)yn << 63));
+          if (kr > mx.key) mx = {kr, aj, j | (int)(yn << 31)};
         }
       }
     }
   };
-  auto reduce_cluster = [&]() {
-    warp_reduce(mn, mx);
-    if (lane == 0) {
-      sh.wmin[warp] = mn;
-      sh.wmax[warp] = mx;
-    }
+  // warp, then CTA through shared memory, then cluster through one slot per
+  // CTA in every CTA (distributed shared memory) and one cluster barrier;
+  // the slots alternate by round parity, so a fast CTA's next round cannot
+  // overwrite a slot another CTA has yet to read
+  auto reduce_min = [&]() {
+    mn = warp_argmin(mn);
+    if (lane == 0) sh.wmin[warp] = mn;
     __syncthreads();
     if (warp == 0) {
-      mn = lane < kTrainWarps ? sh.wmin[lane] : no_min();
-      mx = lane < kTrainWarps ? sh.wmax[lane] : no_max();
-      warp_reduce(mn, mx);
-      if (lane < C) {
-        *cluster.map_shared_rank(&sh.slot_min[parity][rank], lane) = mn;
-        *cluster.map_shared_rank(&sh.slot_max[parity][rank], lane) = mx;
-      }
+      mn = warp_argmin(lane < kTrainWarps ? sh.wmin[lane] : no_min());
+      if (lane < C) *cluster.map_shared_rank(&sh.slot_min[parity][rank], lane) = mn;
     }
     cluster.sync();
-    mn = lane < C ? sh.slot_min[parity][lane] : no_min();
-    mx = lane < C ? sh.slot_max[parity][lane] : no_max();
-    warp_reduce(mn, mx);
+    mn = warp_argmin(lane < C ? sh.slot_min[parity][lane] : no_min());
+    parity ^= 1;
+  };
+  auto reduce_max = [&]() {
+    mx = warp_argmax(mx);
+    if (lane == 0) sh.wmax[warp] = mx;
+    __syncthreads();
+    if (warp == 0) {
+      mx = warp_argmax(lane < kTrainWarps ? sh.wmax[lane] : no_max());
+      if (lane < C) *cluster.map_shared_rank(&sh.slot_max[parity][rank], lane) = mx;
+    }
+    cluster.sync();
+    mx = warp_argmax(lane < C ? sh.slot_max[parity][lane] : no_max());
     parity ^= 1;
   };
 
-  local_candidates();
-  reduce_cluster();
+  local_min();
+  reduce_min();
   long long iters = 0, adds = 0, removes = 0;
   int converged = 0;
   for (long long iter = 1; iter <= a.iter_max; ++iter) {
@@ -281,7 +292,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       if (gi / kTrainThreads == rank && gi % kTrainThreads == tid)
         alpha[(i / stride) * kTrainThreads + tid] = __dadd_rn(mn.alpha, delta);
       ++adds;
-    } else if (cidx(mx) != INT_MAX && mx.key > 0) {
+    } else {
+      local_max();
+      reduce_max();
+      if (cidx(mx) == INT_MAX || mx.key <= 0) {
+        converged = 1;
+        break;
+      }
       // remove the redundant support point i
       kind = 2;
       i = cidx(mx);
@@ -297,9 +314,6 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
         const int j = g + stride * k;
         gk[k] = j < N ? row[j] : GT(0);
       }
-    } else {
-      converged = 1;
-      break;
     }
     ++iters;
     if (rank == 0 && tid == 0 && a.trace_kind) {
@@ -311,10 +325,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
     // to nearest is symmetric in sign, so F - fl(alpha_i K) equals
     // F + fl((-alpha_i) K) bit for bit: one signed multiply and one add.
     const double c = kind == 1 ? coef : -coef;
+    bool cast = false;
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, widen(gk[k])));  // FP32 entries widen exactly
-    local_candidates();
-    reduce_cluster();
+    for (int k = 0; k < KMAX; ++k) cast |= needs_cast(gk[k]);
+    if (!__any_sync(0xffffffffu, cast)) {
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, widen_fast(gk[k])));
+    } else {
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, (double)gk[k]));
+    }
+    local_min();
+    reduce_min();
   }
 
 #pragma unroll
