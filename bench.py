@@ -142,6 +142,73 @@ def run_reference(args):
     return 0
 
 
+def changing_environment(fk, dev, rank, frames, nq):
+    """The 12-control-point arm among moving boxes: a fixed training set of
+    65,536 configurations relabelled every frame, Algorithm 1 on the stored
+    FP32 kernel matrix (built once), then the query batch scored.  Each frame
+    runs twice over the same box path: warm-started from the previous frame's
+    model (loadPreviousModel) and from zero; per-frame device times."""
+    import torch
+    wd = synth.workload("arm7m12-n65536", trial=rank)
+    ch = fk.chain_from_arm(wd.scene.arm)
+    m = fk.fastron_model_create(ch)
+    try:
+        X = torch.from_numpy(wd.train_configs().astype(np.float64)).to(dev)
+        X32 = X.float()
+        Q = torch.from_numpy(wd.query_configs(nq)).to(dev)
+        boxes = synth.moving_boxes(wd.seed, wd.scene.boxes, frames)
+        y = torch.empty(X.shape[0], dtype=torch.int8, device=dev)
+        lab = torch.empty(nq, dtype=torch.int8, device=dev)
+
+        def ev():
+            e = torch.cuda.Event(enable_timing=True)
+            e.record()
+            return e
+
+        torch.cuda.synchronize()
+        e0 = ev()
+        fk.fk_label(ch, boxes[0], wd.scene.radius, X32, y)
+        st0 = fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32)
+        e1 = ev()
+        torch.cuda.synchronize()
+        setup_ms = e0.elapsed_time(e1)
+        out = {"workload": wd.name, "n_train": X.shape[0], "control_points": wd.scene.arm.M, "queries_per_frame": nq,
+               "frames": frames, "kernel_matrix": "fp32 (double-float entries rounded once), built once",
+               "frame0_cold_with_matrix_ms": setup_ms, "frame0_support": st0["n_support"],
+               "frame0_iterations": st0["iterations"]}
+        for mode in ("warm", "cold"):
+            # both modes start from the frame-0 model
+            fk.fk_label(ch, boxes[0], wd.scene.radius, X32, y)
+            fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32, reuse_gram=True)
+            upd, qry, its, sup, conv, nres = [], [], [], [], [], []
+            for k in range(1, frames):
+                torch.cuda.synchronize()
+                a = ev()
+                fk.fk_label(ch, boxes[k], wd.scene.radius, X32, y)
+                st = fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, warm_start=mode == "warm",
+                                      gram=fk.FK_DF32, reuse_gram=True)
+                b = ev()
+                nr = fk.fk_score(m, Q, lab, rescore=True, count=True)
+                c = ev()
+                torch.cuda.synchronize()
+                upd.append(a.elapsed_time(b))
+                qry.append(b.elapsed_time(c))
+                its.append(st["iterations"])
+                sup.append(st["n_support"])
+                conv.append(bool(st["converged"]))
+                nres.append(nr)
+            tot = [u + q for u, q in zip(upd, qry)]
+            out[mode] = {"update_ms_p50": float(np.percentile(upd, 50)), "update_ms_p99": float(np.percentile(upd, 99)),
+                         "query_ms_p50": float(np.percentile(qry, 50)), "query_ms_p99": float(np.percentile(qry, 99)),
+                         "frame_ms_p50": float(np.percentile(tot, 50)), "frame_ms_p99": float(np.percentile(tot, 99)),
+                         "iterations": its, "support": sup, "converged": conv, "rescored": nres,
+                         "checks_per_s_p50": nq / (float(np.percentile(tot, 50)) * 1e-3)}
+        return out
+    finally:
+        fk.fastron_model_destroy(m)
+        fk.fk_chain_destroy(ch)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +221,9 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
     ap.add_argument("--surrogate-epochs", type=int, default=12)
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the multi-scene measurement (0: skip)")
+    ap.add_argument("--dynamic-frames", type=int, default=8,
+                    help="frames of the changing-environment measurement (0: skip)")
+    ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -236,6 +306,10 @@ def main():
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = ws * nq / (ms_per_step * 1e-3)
+    # kernels of this library per step: label; FK, kernel matrix, Algorithm 1,
+    # compaction, packing; FP32 score, then band FK, double-float summands,
+    # their finish and the FP64 re-score when the band is not empty
+    launches = 7 + (4 if nres > 0 else 0)
 
     # roofline of the dominant kernel: the FP32 score, one launch per step.
     # Algorithmic work = |S| * Mv RQ evaluations per query.
@@ -395,6 +469,10 @@ def main():
             for ch in bchains:
                 fk.fk_chain_destroy(ch)
 
+    dynamic = None
+    if args.dynamic_frames > 1:
+        dynamic = changing_environment(fk, dev, rank, args.dynamic_frames, args.dynamic_queries)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(w, args.cpu_sample, os.cpu_count() or 1)
@@ -403,23 +481,26 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 score, f64 band re-score and training", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "f32 score; double-float then f64 band re-score; f64 training (double-float kernel matrix)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": arm.D, "control_points": arm.M, "boxes": len(w.scene.boxes),
                        "n_train": w.n_train, "n_query": nq, "gamma": w.gamma,
                        "support": st["n_support"], "iterations": st["iterations"],
-                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+fp64-rescore"},
+                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+df+fp64-rescore"},
             "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
                           "rescored_queries": nres},
             "query_only_checks_per_s": nq / (query_ms * 1e-3),
             "query_paths": paths,
             "batched_scenes": batched,
+            "changing_environment": dynamic,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": ws * nq / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": launches * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line))
