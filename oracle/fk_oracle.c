@@ -317,6 +317,29 @@ int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const i
                                    trace_idx, trace_delta, 0);
 }
 
+/*
+ * Margins of a carried-over model on a new training set (loadPreviousModel
+ * when the training set has changed, Sec. III-B): the first ns training
+ * points are the previous support set with weights alpha[0..ns); the rest
+ * start at 0, so F_j = sum_{s < ns} alpha_s K(X_s, X_j), summed in ascending
+ * s with separately rounded products and sums.  store32: kernel entries
+ * rounded to FP32 as in kernel_column.
+ */
+void orc_margins(int M, double gamma, int64_t N, const double *cpX, int64_t ns, const double *alpha, int store32,
+                 double *F)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        double f = 0.0;
+        for (int64_t s = 0; s < ns; ++s) {
+            double k = orc_k_fk(M, cpX + s * M * 3, cpX + j * M * 3, gamma);
+            if (store32)
+                k = (double)(float)k;
+            f += alpha[s] * k;
+        }
+        F[j] = f;
+    }
+}
+
 /* --------------------------------------------------- geometric checker -- */
 
 /* Squared distance from point p to the box [lo, hi]. */

@@ -18,6 +18,8 @@ import threading
 
 import numpy as np
 
+from paper_1910_06451_gb300 import synth  # the seeded generator (draws only)
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fk_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
@@ -73,6 +75,8 @@ def _load():
         lib.orc_fastron_train.restype = I
         lib.orc_fastron_train_store.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I]
         lib.orc_fastron_train_store.restype = I
+        lib.orc_margins.argtypes = [I, Dbl, I64, P, I64, P, I, P]
+        lib.orc_margins.restype = None
         lib.orc_seg_box_dist2.argtypes = [P, P, P, P]
         lib.orc_seg_box_dist2.restype = Dbl
         lib.orc_check.argtypes = [I, P, P, I64, P, Dbl, I64, P, P]
@@ -204,6 +208,41 @@ def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000,
         k = int(stats[0])
         tr_out = (tk[:k].copy(), ti[:k].copy(), td[:k].copy())
     return TrainResult(alpha, F, stats, tr_out)
+
+
+def margins(cpX, ns: int, alpha_s, gamma: float, store32: bool = False) -> np.ndarray:
+    """F = K alpha0 for a training set whose first ns points carry weights
+    alpha_s and the rest 0 (loadPreviousModel on a changed training set),
+    summed in ascending support order."""
+    cpX = _d(cpX)
+    N, M = cpX.shape[0], cpX.shape[1]
+    a = _d(alpha_s)
+    assert a.shape[0] == ns <= N
+    F = np.empty(N)
+    _load().orc_margins(M, float(gamma), N, _p(cpX), int(ns), _p(a), int(bool(store32)), _p(F))
+    return F
+
+
+def active_samples(support_q, k_near: int, sigma: float, n_uniform: int, qlim: float, seed: int) -> np.ndarray:
+    """Two-stage active learning (Sec. III-B, after Algorithm 1): the support
+    configurations, then k_near random samples near each of them (uniform in
+    +-sigma per joint, clipped to the joint limits), then n_uniform samples
+    uniform in the joint limits.  Draw ((c ns + s) D + d) of SplitMix64 stream
+    `seed` perturbs joint d of support point s in copy c; draw
+    (k_near ns D + i D + d) gives joint d of uniform sample i.  Every new
+    value is computed in FP64 (lo + (hi - lo) u, then the sum and the clip)
+    and rounded to FP32 once."""
+    S = _d(support_q)
+    ns, D = S.shape
+    st = synth.Stream(seed)
+    near = st.uniform(k_near * ns * D, -sigma, sigma).reshape(k_near, ns, D)
+    out = [S]
+    for c in range(k_near):
+        v = np.clip(S + near[c], -qlim, qlim)
+        out.append(v.astype(np.float32).astype(np.float64))
+    uni = st.uniform(n_uniform * D, -qlim, qlim).reshape(n_uniform, D)
+    out.append(uni.astype(np.float32).astype(np.float64))
+    return np.concatenate(out, axis=0)
 
 
 # -------------------------------------------------------------- checker ---

@@ -168,3 +168,50 @@ def test_fp32_stored_kernel_margins_are_k32_alpha():
     np.testing.assert_allclose(r.F, K32 @ r.alpha, rtol=1e-11, atol=1e-11)
     K = O.gram(cp, cp, w.gamma)
     assert np.max(np.abs(K32 @ r.alpha - K @ r.alpha)) > 0
+
+
+def test_margins_of_a_carried_model():
+    # F = K alpha0 with the first ns points weighted: against the matrix
+    # product, and exactly for ns = 1 (F_j = alpha_0 K_0j)
+    w, X, y, cp = _small_problem(150, seed=4, name="arm7-n5000")
+    alpha = np.linspace(-2.0, 3.0, 40)
+    K = O.gram(cp, cp, w.gamma)
+    F = O.margins(cp, 40, alpha, w.gamma)
+    np.testing.assert_allclose(F, K[:, :40] @ alpha, rtol=1e-12, atol=1e-12)
+    F1 = O.margins(cp, 1, alpha[:1], w.gamma)
+    assert np.array_equal(F1, alpha[0] * K[:, 0])
+    F32 = O.margins(cp, 40, alpha, w.gamma, store32=True)
+    np.testing.assert_allclose(F32, K[:, :40].astype(np.float32).astype(np.float64) @ alpha, rtol=1e-12,
+                               atol=1e-12)
+    # a carried model is a warm start: training resumes from it, and a model
+    # carried onto its own training set with its own F changes nothing
+    r = O.fastron_train(cp, y, w.gamma, iter_max=5000)
+    order = np.concatenate([r.support, np.setdiff1d(np.arange(len(y)), r.support)])
+    cpo, yo = cp[order], y[order]
+    F0 = O.margins(cpo, len(r.support), r.alpha[r.support], w.gamma)
+    np.testing.assert_allclose(F0, r.F[order], rtol=1e-10, atol=1e-10)
+    a0 = np.zeros(len(y))
+    a0[:len(r.support)] = r.alpha[r.support]
+    r2 = O.fastron_train(cpo, yo, w.gamma, iter_max=5000, alpha0=a0, F0=F0)
+    assert r2.converged and r2.iters == 0
+
+
+def test_active_samples_layout_and_bounds():
+    w = synth.workload("arm7m12-n65536")
+    arm = w.scene.arm
+    S = w.train_configs()[:50].astype(np.float64)
+    X = O.active_samples(S, 2, 0.1, 300, arm.qlim, seed=77)
+    assert X.shape == (50 + 100 + 300, 7)
+    assert np.array_equal(X[:50], S)
+    assert np.array_equal(X, X.astype(np.float32).astype(np.float64))  # FP32 values
+    for c in range(2):
+        d = X[50 + 50 * c:100 + 50 * c] - S
+        assert np.all(np.abs(d) <= 0.1 + 1e-6) and np.abs(d).max() > 0.05
+    assert np.all(np.abs(X) <= arm.qlim)
+    U = X[150:]
+    assert np.abs(U).max() > 0.9 * arm.qlim and abs(U.mean()) < 0.2
+    # the draws are those of the shared generator, in the stated order
+    u = synth.Stream(77).uniform(2 * 50 * 7, -0.1, 0.1).reshape(2, 50, 7)
+    want = np.clip(S + u[1], -arm.qlim, arm.qlim).astype(np.float32).astype(np.float64)
+    assert np.array_equal(X[100:150], want)
+    assert np.array_equal(X, O.active_samples(S, 2, 0.1, 300, arm.qlim, seed=77))
