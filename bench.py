@@ -147,7 +147,11 @@ def changing_environment(fk, dev, rank, frames, nq):
     65,536 configurations relabelled every frame, Algorithm 1 on the stored
     FP32 kernel matrix (built once), then the query batch scored.  Each frame
     runs twice over the same box path: warm-started from the previous frame's
-    model (loadPreviousModel) and from zero; per-frame device times."""
+    model (loadPreviousModel) and from zero; then a third time as the paper's
+    loop, two-stage active learning: the next training set (65,536 rows) is
+    the support set, one copy of it moved by up to 0.1 rad per joint, and
+    uniform samples; it is relabelled, its kernel matrix rebuilt, and
+    Algorithm 1 starts from the carried weights.  Per-frame device times."""
     import torch
     wd = synth.workload("arm7m12-n65536", trial=rank)
     ch = fk.chain_from_arm(wd.scene.arm)
@@ -176,17 +180,30 @@ def changing_environment(fk, dev, rank, frames, nq):
                "frames": frames, "kernel_matrix": "fp32 (double-float entries rounded once), built once",
                "frame0_cold_with_matrix_ms": setup_ms, "frame0_support": st0["n_support"],
                "frame0_iterations": st0["iterations"]}
-        for mode in ("warm", "cold"):
-            # both modes start from the frame-0 model
+        n_max = X.shape[0]
+        Xa = torch.empty_like(X)
+        Xa32 = torch.empty_like(X32)
+        for mode in ("warm", "cold", "active"):
+            # every mode starts from the frame-0 model
             fk.fk_label(ch, boxes[0], wd.scene.radius, X32, y)
             fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32, reuse_gram=True)
+            ns = st0["n_support"]
             upd, qry, its, sup, conv, nres = [], [], [], [], [], []
             for k in range(1, frames):
                 torch.cuda.synchronize()
                 a = ev()
-                fk.fk_label(ch, boxes[k], wd.scene.radius, X32, y)
-                st = fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, warm_start=mode == "warm",
-                                      gram=fk.FK_DF32, reuse_gram=True)
+                if mode == "active":
+                    kn = 1 if 2 * ns <= n_max else 0
+                    nu = max(0, n_max - (1 + kn) * ns)
+                    n = fk.fk_active_samples(m, kn, 0.1, nu, wd.scene.arm.qlim, wd.seed * 7919 + k, Xa, Xa32)
+                    fk.fk_label(ch, boxes[k], wd.scene.radius, Xa32[:n], y[:n])
+                    st = fk.fastron_train(m, Xa[:n], y[:n], wd.gamma, wd.beta, wd.iter_max, wd.s_max, warm_start=2,
+                                          gram=fk.FK_DF32)
+                    ns = st["n_support"]
+                else:
+                    fk.fk_label(ch, boxes[k], wd.scene.radius, X32, y)
+                    st = fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max,
+                                          warm_start=mode == "warm", gram=fk.FK_DF32, reuse_gram=True)
                 b = ev()
                 nr = fk.fk_score(m, Q, lab, rescore=True, count=True)
                 c = ev()

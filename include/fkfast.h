@@ -109,8 +109,12 @@ typedef struct {
     double beta;       /* conditional bias, >= 1 (Eq. 5): b_i = beta for y_i = +1, 1 otherwise */
     int64_t iter_max;  /* iteration limit of Algorithm 1, >= 0 */
     int64_t s_max;     /* support-set size limit S_max of Algorithm 1, >= 1 */
-    int32_t warm_start;/* 1: start from this model's alpha and F of the previous call on the
-                          same training set (loadPreviousModel); 0: alpha = F = 0 */
+    int32_t warm_start;/* loadPreviousModel: 1: start from this model's alpha and F of the
+                          previous call on the same training set; 2: the training set has
+                          changed and its first |S| rows are this model's support points in
+                          the model's order (as fk_active_samples writes them): they keep
+                          their weights, the other rows start at 0, and F = K alpha is
+                          computed on the device; 0: alpha = F = 0 */
     int32_t trace;     /* 1: record every pass (kind, index, change of alpha) for
                           fastron_model_trace; 0: do not */
     int32_t gram;      /* arithmetic and storage of the training kernel matrix: FK_DF64
@@ -151,6 +155,29 @@ void fastron_model_destroy(fastron_model_t *model);
  * need a 16-CTA thread-block cluster. */
 int fastron_train(fastron_model_t *model, const double *X, const int8_t *y, int64_t N, const fastron_params *p,
                   fastron_stats *stats, void *stream);
+
+/* Two-stage active learning (Sec. III-B, after Algorithm 1): the next
+ * training set from this model's support set S (|S| = ns rows).  X: device
+ * double [rows][D], rows = ns (1 + k_near) + n_uniform, laid out as
+ *   rows [0, ns)                    the support configurations, in the
+ *                                   model's order (for warm_start = 2);
+ *   rows ns + c ns + s, c < k_near  support point s with every joint moved by
+ *                                   a draw uniform in [-sigma, sigma] and
+ *                                   clipped to [-qlim, qlim] (stage 1: small
+ *                                   changes of the C-space obstacles);
+ *   the last n_uniform rows         configurations uniform in [-qlim, qlim]
+ *                                   (stage 2: obstacles entering the workspace).
+ * Draws: SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) as a counter-based
+ * generator; draw k of stream `seed` is the finaliser of
+ * seed + (k + 1) * 0x9E3779B97F4A7C15, top 53 bits scaled to [0, 1), mapped to
+ * [lo, hi) as lo + (hi - lo) u in FP64.  Draw (c ns + s) D + d moves joint d
+ * of support point s in copy c; draw k_near ns D + i D + d is joint d of
+ * uniform sample i.  New values are rounded to FP32 once (so the FP32 copy
+ * X32, device float [rows][D] or NULL, holds the same configurations).
+ * cap: rows X can hold; *n_out (host) receives rows; rows > cap is
+ * FK_ERR_CAPACITY.  The model must be trained or set (FK_ERR_STATE). */
+int fk_active_samples(const fastron_model_t *model, int32_t k_near, double sigma, int64_t n_uniform, double qlim,
+                      uint64_t seed, double *X, float *X32, int64_t cap, int64_t *n_out, void *stream);
 
 /* Copies the per-pass record of the last fastron_train call made with
  * p->trace = 1: kind (host int8: 1 add/adjust, 2 removal), idx (host int64,

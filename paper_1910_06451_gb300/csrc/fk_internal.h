@@ -51,6 +51,23 @@ struct TrainArgs {
 };
 cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s);
 
+// Two-stage active-learning samples and the margins of a carried-over model.
+struct ActiveArgs {
+  const double *S;  // [ns][D] support configurations
+  int64_t ns;
+  int D;
+  int k_near;
+  double sigma, qlim;
+  int64_t n_uniform;
+  uint64_t seed;
+  double *X;        // [ns (1 + k_near) + n_uniform][D]
+  float *X32;       // same, FP32, or null
+};
+cudaError_t launch_active_samples(const ActiveArgs &a, cudaStream_t s);
+// F[j] = sum_{s < ns} alpha[s] G[s][j], G [N][N] FP64 or FP32 (g32 != 0).
+cudaError_t launch_margins(const void *G, int g32, int64_t N, const double *alpha, int64_t ns, double *F,
+                           cudaStream_t s);
+
 // float4 entries of one support-pair record of the FP32 score: for each of
 // the Mv configuration-dependent control points (x_a, x_b, y_a, y_b), then
 // the z coordinates two points at a time (z_a, z_b, z_a', z_b'), then the

@@ -295,13 +295,19 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   const int gram = p->gram == 0 ? FK_DF64 : p->gram;
   if (gram != FK_F64 && gram != FK_DF64 && gram != FK_DF32)
     return fail(FK_ERR_ARG, "fastron_train: gram must be FK_DF64, FK_F64 or FK_DF32");
-  if (p->warm_start && (m->N != N || m->alpha.p == nullptr))
+  if (p->warm_start < 0 || p->warm_start > 2) return fail(FK_ERR_ARG, "fastron_train: warm_start must be 0, 1 or 2");
+  if (p->warm_start == 1 && (m->N != N || m->alpha.p == nullptr))
     return fail(FK_ERR_STATE, "fastron_train: warm start needs a previous training call with the same N");
+  const int64_t ns_carry = m->ns;
+  if (p->warm_start == 2 && (ns_carry < 0 || ns_carry > N))
+    return fail(FK_ERR_STATE, "fastron_train: carrying the support set needs a trained model with |S| <= N");
+  if (p->warm_start == 2 && p->reuse_gram)
+    return fail(FK_ERR_ARG, "fastron_train: a carried support set means a new training set: reuse_gram must be 0");
   if (p->reuse_gram && (m->N != N || m->gram != gram))
     return fail(FK_ERR_STATE, "fastron_train: reuse_gram needs a previous call with the same N and gram");
   cudaStream_t s = (cudaStream_t)stream;
   const fk_chain *c = m->chain;
-  const bool keep = p->warm_start != 0;
+  const bool keep = p->warm_start == 1;
   const bool reuse = p->reuse_gram != 0;
   CK(m->cpX.ensure(sizeof(double) * (size_t)N * c->M * 3));
   if (!reuse) m->gram = -1;  // the stored matrix is invalid until rebuilt below
@@ -333,6 +339,13 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     else
       CK(launch_gram_df(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), s));
     m->gram = gram;
+  }
+  if (p->warm_start == 2) {
+    // loadPreviousModel on a changed training set: the first ns rows are the
+    // previous support points with their weights; F = K alpha
+    if (ns_carry > 0)
+      CK(cudaMemcpyAsync(m->alpha.p, m->alpha_s.p, sizeof(double) * (size_t)ns_carry, cudaMemcpyDeviceToDevice, s));
+    CK(launch_margins(m->G.p, gram == FK_DF32 ? 1 : 0, N, m->alpha.as<double>(), ns_carry, m->F.as<double>(), s));
   }
   TrainArgs ta{m->G.p, gram == FK_DF32 ? 1 : 0, y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
                m->stats.as<int64_t>(), m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(),
@@ -412,6 +425,27 @@ extern "C" int fastron_model_get(const fastron_model_t *cm, int64_t *idx, double
       for (int64_t i = 0; i < k; ++i) idx[i] = tmp[(size_t)i];
     }
   }
+  return FK_OK;
+}
+
+// ---------------------------------------------------- active learning ---
+extern "C" int fk_active_samples(const fastron_model_t *m, int32_t k_near, double sigma, int64_t n_uniform,
+                                 double qlim, uint64_t seed, double *X, float *X32, int64_t cap, int64_t *n_out,
+                                 void *stream) {
+  if (!m || !n_out) return fail(FK_ERR_ARG, "fk_active_samples: NULL pointer");
+  *n_out = 0;
+  if (m->ns < 0) return fail(FK_ERR_STATE, "fk_active_samples: model is untrained");
+  if (k_near < 0 || n_uniform < 0) return fail(FK_ERR_ARG, "fk_active_samples: negative count");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma) || !(qlim > 0.0) || !std::isfinite(qlim))
+    return fail(FK_ERR_ARG, "fk_active_samples: sigma must be >= 0 and qlim > 0, both finite");
+  const int64_t rows = m->ns * (1 + (int64_t)k_near) + n_uniform;
+  *n_out = rows;
+  if (rows > cap) return fail(FK_ERR_CAPACITY, "fk_active_samples: %lld rows exceed cap %lld", (long long)rows,
+                              (long long)cap);
+  if (rows == 0) return FK_OK;
+  if (!X) return fail(FK_ERR_ARG, "fk_active_samples: X is NULL");
+  ActiveArgs aa{m->q_s.as<double>(), m->ns, m->chain->D, k_near, sigma, qlim, n_uniform, seed, X, X32};
+  CK(launch_active_samples(aa, (cudaStream_t)stream));
   return FK_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
-    "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune",
+    "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune", "fk_active_samples",
 )
 
 
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = False):
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
             "fk_score_noalloc": ([P, P, I64, D, P, P, P, P], I),
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
+            "fk_active_samples": ([P, ctypes.c_int32, D, I64, D, ctypes.c_uint64, P, P, I64, P, P], I),
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
             "fk_probe_pipe": ([I, P, P], I),
             "fk_tc_gemm_bf16": ([P, I64, P, I64, I, I, I, I, P, P], I),
@@ -249,16 +250,32 @@ def fastron_model_destroy(model):
 
 def fastron_train(model, X, y, gamma, beta=1.0, iter_max=5000, s_max=None, warm_start=False, trace=False,
                   gram=FK_DF64, reuse_gram=False, stream=None) -> dict:
-    """Algorithm 1 on device training data X (float64, (N, D)) and y (int8, (N,))."""
+    """Algorithm 1 on device training data X (float64, (N, D)) and y (int8, (N,)).
+    warm_start: False/0, True/1 (same training set), or 2 (the first |S|
+    rows are the model's support points, carried with their weights)."""
     import torch
     N = X.shape[0]
     p = FastronParams(float(gamma), float(beta), int(iter_max), int(N if s_max is None else s_max),
-                      int(bool(warm_start)), int(bool(trace)), int(gram), int(bool(reuse_gram)))
+                      int(warm_start), int(bool(trace)), int(gram), int(bool(reuse_gram)))
     st = FastronStats()
     _check(load().fastron_train(model, _dev(X, torch.float64, "X"), _dev(y, torch.int8, "y", (N,)), N,
                                 ctypes.byref(p), ctypes.byref(st), _stream(stream)))
     return {"iterations": st.iterations, "adds": st.adds, "removes": st.removes, "n_support": st.n_support,
             "converged": bool(st.converged)}
+
+
+def fk_active_samples(model, k_near, sigma, n_uniform, qlim, seed, X, X32=None, stream=None) -> int:
+    """Two-stage active-learning training set from the model's support set
+    into device X (float64, (cap, D)) and optionally X32 (float32, same
+    shape); returns the number of rows written."""
+    import torch
+    cap = X.shape[0]
+    n = ctypes.c_int64()
+    _check(load().fk_active_samples(model, int(k_near), float(sigma), int(n_uniform), float(qlim),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, _dev(X, torch.float64, "X"),
+                                    None if X32 is None else _dev(X32, torch.float32, "X32", tuple(X.shape)), cap,
+                                    ctypes.byref(n), _stream(stream)))
+    return n.value
 
 
 def fastron_model_trace(model, cap: int):

@@ -1,8 +1,9 @@
 """The changing-environment workload through the C ABI: the 7-DOF arm with 12
 control points, a kernel matrix stored in FP32 (FK_DF32), training sets up to
 65,536 points, warm-started Algorithm 1 on a fixed training set relabelled as
-the boxes move (reuse_gram), and scoring with 11 configuration-dependent
-control points.  Tolerances:
+the boxes move (reuse_gram), the paper's two-stage active learning with
+carried-over weights (fk_active_samples, warm_start = 2), and scoring with 11
+configuration-dependent control points.  Tolerances:
 
   FP32-stored kernel matrix   each entry the FP32 rounding of the FP64 entry;
                               1 ulp where the FP64 value lies within the
@@ -10,6 +11,8 @@ control points.  Tolerances:
                               boundary (at most 1e-4 of the entries)
   training                    pass sequence identical to the oracle's with
                               FP32-rounded columns; alpha within 1e-9 relative
+  active-learning samples     bit-identical to the oracle's (same SplitMix64
+                              draws, same FP64 operations, one FP32 rounding)
   large N                     the first 40 passes identical; converged margins
                               positive and no removal applicable, on sampled
                               points recomputed by the oracle
@@ -190,3 +193,77 @@ def test_score_twelve_control_points(fk, arm12, dev):
     err = np.abs(f_raw.cpu().numpy().astype(np.float64) - want)
     assert np.all(err <= 3e-6 * B + 1e-30)
     assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
+
+
+def test_active_samples_match_oracle(fk, arm12, dev):
+    w, ch = arm12
+    X = w.train_configs()[:1500].astype(np.float64)
+    y = O.check(w.scene, X)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_train(m, torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev), w.gamma, w.beta, 20000,
+                         w.s_max)
+        sup, _ = fk.fastron_model_get(m)
+        ns = len(sup)
+        rows = ns * 3 + 700
+        Xd = torch.empty((rows + 5, 7), dtype=torch.float64, device=dev)
+        X32 = torch.empty((rows + 5, 7), dtype=torch.float32, device=dev)
+        n = fk.fk_active_samples(m, 2, 0.1, 700, w.scene.arm.qlim, 0xC0FFEE, Xd, X32)
+        assert n == rows
+        want = O.active_samples(X[sup], 2, 0.1, 700, w.scene.arm.qlim, 0xC0FFEE)
+        got = Xd[:rows].cpu().numpy()
+        assert np.array_equal(got, want)
+        assert np.array_equal(X32[:rows].cpu().numpy().astype(np.float64), want)
+        small = torch.empty((rows - 1, 7), dtype=torch.float64, device=dev)
+        with pytest.raises(fk.FkError):
+            fk.fk_active_samples(m, 2, 0.1, 700, w.scene.arm.qlim, 1, small)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
+@pytest.mark.parametrize("gram", ["df32", "df64"])
+def test_active_learning_frames_match_oracle(fk, arm12, dev, gram):
+    # the paper's update loop: the next training set is the support set, one
+    # perturbed copy of it and uniform samples up to n_max; labels from the
+    # moved boxes; Algorithm 1 from the carried weights (F = K alpha)
+    w, ch = arm12
+    n_max, frames, sigma = 3000, 3, 0.1
+    qlim = w.scene.arm.qlim
+    store32 = gram == "df32"
+    code = fk.FK_DF32 if store32 else fk.FK_DF64
+    path = synth.moving_boxes(w.seed, w.scene.boxes, frames)
+    X = w.train_configs()[:2000].astype(np.float64)
+    y = O.check(synth.Scene(w.scene.arm, path[0], 0.03), X)
+    r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, w.beta, 20000, w.s_max, store32=store32)
+    m = fk.fastron_model_create(ch)
+    Xd = torch.empty((n_max, 7), dtype=torch.float64, device=dev)
+    X32 = torch.empty((n_max, 7), dtype=torch.float32, device=dev)
+    try:
+        st = fk.fastron_train(m, torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev), w.gamma, w.beta, 20000,
+                              w.s_max, gram=code)
+        assert st["n_support"] == r.n_support
+        S, aS = X[r.support], r.alpha[r.support]
+        for k in range(1, frames):
+            ns = len(S)
+            nu = max(0, n_max - 2 * ns)
+            seed = 1000 + k
+            n = fk.fk_active_samples(m, 1, sigma, nu, qlim, seed, Xd, X32)
+            Xk = O.active_samples(S, 1, sigma, nu, qlim, seed)
+            assert n == len(Xk) and np.array_equal(Xd[:n].cpu().numpy(), Xk)
+            yk = O.check(synth.Scene(w.scene.arm, path[k], 0.03), Xk)
+            ty = torch.empty(n, dtype=torch.int8, device=dev)
+            fk.fk_label(ch, path[k], 0.03, X32[:n], ty)
+            assert np.array_equal(ty.cpu().numpy(), yk)
+            cp = O.fk_points(w.scene.arm, Xk)
+            F0 = O.margins(cp, ns, aS, w.gamma, store32=store32)
+            a0 = np.zeros(n)
+            a0[:ns] = aS
+            r = O.fastron_train(cp, yk, w.gamma, w.beta, 20000, w.s_max, alpha0=a0, F0=F0, trace=True,
+                                store32=store32)
+            st = fk.fastron_train(m, Xd[:n], ty, w.gamma, w.beta, 20000, w.s_max, warm_start=2, trace=True,
+                                  gram=code)
+            assert (st["iterations"], st["n_support"], st["converged"]) == (r.iters, r.n_support, r.converged)
+            _compare_trace(fk, m, r)
+            S, aS = Xk[r.support], r.alpha[r.support]
+    finally:
+        fk.fastron_model_destroy(m)
