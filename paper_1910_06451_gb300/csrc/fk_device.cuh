@@ -27,6 +27,12 @@ struct ChainF {
   int vidx[FK_MAX_CP];          // its index among all M points
   int cj[FK_MAX_CP];            // frame of every point (fk_forward output order)
   float ct[FK_MAX_CP][3];
+  // The first configuration-dependent point rides on frame 1 of a revolute
+  // joint 1 (and the base rotation is orthonormal): it moves on a circle of
+  // radius rho about joint 1's axis, so its squared distance between
+  // configurations is rho^2 (2 - 2 cos(theta_q - theta_s)), theta = q_1 + theta0_1.
+  int cp1;
+  double cp1_rho2;
 };
 
 // The same chain for the FP64 kernels.  cos/sin of the link twists are taken

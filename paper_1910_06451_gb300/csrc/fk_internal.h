@@ -95,6 +95,10 @@ struct PackArgs {
   double *alpha_out;  // [ns] (copy of alpha, compacted)
   double *q_out;      // [ns][D] support configurations
   float *sdf;         // [ns][rec_df_len(Mv)] double-float records
+  float4 *rec1;       // or null: the records again with entry 0 holding
+                      // (U_a, U_b, V_a, V_b), U = k cos theta, V = k sin theta
+                      // of joint 1, k = gamma rho^2 (see ChainF::cp1)
+  double cp1_k;
 };
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s);
 
@@ -104,6 +108,8 @@ struct ScoreArgs {
   int64_t n;
   const float4 *rec;
   int64_t ns;
+  const float4 *rec1;  // or null; with it the first point's t = A - U cos theta_q - V sin theta_q
+  float cp1_A;         // 1 + k
   float gs;           // sqrt(gamma / 2): scale of the control points
   float eps;          // band: |f| <= eps * B(q)
   float *f;           // [n] or null

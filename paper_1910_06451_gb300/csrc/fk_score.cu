@@ -40,6 +40,7 @@ __global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) 
   const double gs = sqrt(0.5 * a.gamma);
   float cpv[2][FK_MAX_CP][3];
   float w[2], aw[2];
+  float uv[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int h = 0; h < 2; ++h) {
     const int64_t s = 2 * j + h;
     if (s >= a.ns) {
@@ -69,6 +70,12 @@ __global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) 
     const double wd = al / cd.M;
     w[h] = (float)wd;
     aw[h] = (float)fabs(wd);
+    if (a.rec1) {
+      // circle form of point 0: U = k cos theta, V = k sin theta, theta = q_1 + theta0_1
+      const double th = x[0] + cd.th0[0];
+      uv[h][0] = (float)(a.cp1_k * cos(th));
+      uv[h][1] = (float)(a.cp1_k * sin(th));
+    }
     if (a.sdf) {
       float *r = a.sdf + s * rec_df_len(MV);
       for (int v = 0; v < MV; ++v)
@@ -91,6 +98,11 @@ __global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) 
                                   two ? cpv[1][v + 1][2] : 0.f);
   }
   rec[REC - 1] = make_float4(w[0], w[1], aw[0], aw[1]);
+  if (a.rec1) {
+    float4 *r1 = a.rec1 + j * REC;
+    for (int e = 0; e < REC; ++e) r1[e] = rec[e];
+    r1[0] = make_float4(uv[0][0], uv[1][0], uv[0][1], uv[1][1]);
+  }
 }
 
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s) {
@@ -106,13 +118,14 @@ constexpr int kQ = 2;                          // queries per thread
 constexpr int kQueriesPerCta = kScoreThreads * kQ;
 constexpr int kTilePairs = 64;                 // support pairs per shared-memory tile
 
-template <int MV>
+template <int MV, bool CP1>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
   const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
-  score_block<MV, kQ, kTilePairs, kScoreThreads>(c, a.rec, a.ns, a.gs, a.q, a.n,
-                                                 (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
+  score_block<MV, kQ, kTilePairs, kScoreThreads, false, CP1>(c, CP1 ? a.rec1 : a.rec, a.ns, a.gs, a.q, a.n,
+                                                             (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar,
+                                                             a.cp1_A);
 }
 
 // The packed-half variant of the same block (differences and t in FP16).
@@ -152,16 +165,20 @@ cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s
   }
 }
 
-template <int MV>
+template <int MV, bool CP1 = false>
 static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   constexpr int REC = MV + (MV + 1) / 2 + 1;
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(score_f32_kernel<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = score_f32_kernel<MV, CP1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
-  score_f32_kernel<MV><<<grid, kScoreThreads, smem, s>>>(c, a);
+  kern<<<grid, kScoreThreads, smem, s>>>(c, a);
   return cudaGetLastError();
 }
+
+// Shapes with a compiled circle-form kernel (the 3- and 7-DOF workloads).
+bool score_cp1_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
 
 // Shapes with a compiled score kernel: the number of configuration-dependent
 // control points.
@@ -176,6 +193,14 @@ bool score_supported(int mv) {
 
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (a.rec1) {
+    switch (c.Mv) {
+      case 3: return launch_score_mv<3, true>(c, a, s);
+      case 7: return launch_score_mv<7, true>(c, a, s);
+      case 11: return launch_score_mv<11, true>(c, a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (c.Mv) {
     case 1: return launch_score_mv<1>(c, a, s);
     case 2: return launch_score_mv<2>(c, a, s);

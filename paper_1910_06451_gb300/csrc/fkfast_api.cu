@@ -20,6 +20,7 @@ cudaError_t launch_scatter_labels(const int8_t *src, const float *fsrc, const in
 struct GemmArgs;
 cudaError_t launch_gemm_f32(const GemmArgs &g, int splits, cudaStream_t s);
 bool score_supported(int mv);
+bool score_cp1_supported(int mv);
 int probe_iters(int kind);
 int probe_ops_per_iter(int kind);
 }  // namespace fk
@@ -135,6 +136,28 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
     for (int k = 0; k < 3; ++k) f.R0[3 * r + k] = (float)base[4 * r + k];
     f.p0[r] = (float)base[4 * r + 3];
   }
+  // the circle of the first configuration-dependent point (see ChainF::cp1):
+  // in frame 1 the point is Rz(theta) w with w = (a, 0, d) + Rx(alpha) t
+  {
+    int first = -1;
+    for (int m = 0; m < M && first < 0; ++m)
+      if (cps[m].joint != 0) first = m;
+    double orth = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double g = 0.0;
+        for (int k = 0; k < 3; ++k) g += base[4 * k + i] * base[4 * k + j];
+        orth = fmax(orth, fabs(g - (i == j ? 1.0 : 0.0)));
+      }
+    f.cp1 = 0;
+    f.cp1_rho2 = 0.0;
+    if (first >= 0 && cps[first].joint == 1 && dh[0].type == FK_REVOLUTE && orth < 1e-12) {
+      const double ca = cos(dh[0].alpha), sa = sin(dh[0].alpha);
+      const double wx = dh[0].a + cps[first].t[0], wy = ca * cps[first].t[1] - sa * cps[first].t[2];
+      f.cp1 = 1;
+      f.cp1_rho2 = wx * wx + wy * wy;
+    }
+  }
   int v = 0;
   for (int m = 0; m < M; ++m) {
     d.cj[m] = f.cj[m] = cps[m].joint;
@@ -235,6 +258,9 @@ struct fastron_model {
   int64_t ns = -1;  // -1 = untrained
   double gamma = 0.0;
   DevBuf rec, cp64, alpha_s, q_s, qin, sdf;
+  DevBuf rec1;        // records with the circle form of point 0 (used when use_cp1)
+  bool use_cp1 = false;
+  float cp1_A = 0.f;
   std::vector<int64_t> host_idx;  // training indices of the support points (model_set: positions)
   bool host_idx_valid = false;
   // score scratch
@@ -259,7 +285,7 @@ extern "C" int fastron_model_create(const fk_chain_t *chain, fastron_model_t **o
 extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
   DevBuf *bufs[] = {&m->cpX, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
-                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf,
+                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf, &m->rec1,
                     &m->qdf, &m->part, &m->band2_idx,
                     &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
   for (DevBuf *b : bufs) b->release();
@@ -274,8 +300,15 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   CK(m->alpha_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
   CK(m->sdf.ensure(sizeof(float) * (size_t)(ns > 0 ? ns : 1) * rec_df_len(c->cf.Mv)));
+  // the circle form of point 0 where it is as accurate as the direct form
+  // on the far points: A = 1 + gamma rho^2 below 8
+  const double k1 = gamma * c->cf.cp1_rho2;
+  m->use_cp1 = c->cf.cp1 && score_cp1_supported(c->cf.Mv) && 1.0 + k1 < 8.0;
+  m->cp1_A = (float)(1.0 + k1);
+  if (m->use_cp1)
+    CK(m->rec1.ensure(sizeof(float4) * (size_t)((ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1) * rec_len(c->cf.Mv)));
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
-              m->q_s.as<double>(), m->sdf.as<float>()};
+              m->q_s.as<double>(), m->sdf.as<float>(), m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
   m->gamma = gamma;
@@ -470,7 +503,7 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
     CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
     if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
     const double eps16 = rescore_eps > 0.0 ? rescore_eps : kDefaultEpsF16;
-    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps16, f, label,
+    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, nullptr, 0.f, (float)sqrt(0.5 * m->gamma), (float)eps16, f, label,
                  rescore ? m->band_idx.as<int32_t>() : nullptr, m->flags.as<int32_t>(), m->flags.as<int32_t>() + 1,
                  g_wait_limit};
     CK(launch_score_f16(c->cf, sa, s));
@@ -503,7 +536,8 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1, *cnt2 = cnt + 2;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
   const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
-  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
+  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
+               (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
                rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit};
   CK(launch_score_f32(c->cf, sa, s));
   if (!rescore && !n_rescored) return FK_OK;
@@ -693,7 +727,8 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   // word must start at zero (the band list is written before it is read)
   CK(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2, s));
   const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
-  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
+  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
+               (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
                band, cnt, err, g_wait_limit};
   CK(launch_score_f32(c->cf, sa, s));
   RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};

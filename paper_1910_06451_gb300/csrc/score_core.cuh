@@ -70,16 +70,22 @@ struct BlockOut {
 // FP16 (HSUB2/HFMA2, query coordinates and the support pair's coordinates
 // rounded to half), then widened to FP32 for the reciprocals and the
 // accumulation.  HALF = false: all FP32.
+// CP1 = true (FP32 only): record entry 0 holds (U_a, U_b, V_a, V_b) of the
+// circle form of the first point (ChainF::cp1), t = A - U cos theta_q -
+// V sin theta_q with A = 1 + k: two FMAs instead of three differences and
+// three FMAs.  Its FP32 error for A < 8 stays within that of the direct
+// form on the points farther out.
 // Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
 // (n x D) against the support records rec (ns points, (ns+1)/2 pair records)
 // with chain c.  tiles: 2 * TP * rec_len(MV) float4 of shared memory; bar: two
 // mbarriers.  Every thread of the CTA must call it.  Returns false (in every
 // thread) if a tile wait gave up; the caller must then stop using the CTA's
 // barriers.
-template <int MV, int Q, int TP, int NTHR, bool HALF = false>
+template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false>
 __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, float gs,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
-                                            float4 *tiles, uint64_t *bar) {
+                                            float4 *tiles, uint64_t *bar, float cp1_A = 0.f) {
+  static_assert(!(HALF && CP1), "the circle form is an FP32 path");
   constexpr int REC = MV + (MV + 1) / 2 + 1;
   constexpr int NP = RcpPlan<MV>::NP;
 
@@ -110,11 +116,18 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
   const int64_t qbase = q0 + tid;
   f2 P[Q][MV][3];
   __half2 Ph[HALF ? Q : 1][HALF ? MV : 1][3];
+  f2 ncq[CP1 ? Q : 1], nsq[CP1 ? Q : 1];  // -cos theta_q, -sin theta_q of joint 1
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int64_t qi = qbase + k * NTHR;
     float qv[FK_MAX_DOF];
     for (int i = 0; i < c.D; ++i) qv[i] = qi < n ? q[qi * c.D + i] : 0.f;
+    if (CP1) {
+      float sn, cs;
+      sincosf(qv[0] + c.th0[0], &sn, &cs);
+      ncq[CP1 ? k : 0] = pk(-cs, -cs);
+      nsq[CP1 ? k : 0] = pk(-sn, -sn);
+    }
     float cp[MV][3];
     fk_points_f32<MV>(c, qv, cp);
 #pragma unroll
@@ -130,6 +143,7 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
   }
   const __half2 one_h = __float2half2_rn(1.f);
   const f2 one2 = pk(1.f, 1.f);
+  const f2 A2 = pk(cp1_A, cp1_A);
   const float nc = (float)c.n_const;
   const f2 nc2 = pk(nc, nc);
 
@@ -157,7 +171,11 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
       for (int m = 0; m < MV; ++m) {
         const float4 xy = r[m];
         const float4 zz = r[MV + m / 2];
-        if (HALF) {
+        if (CP1 && m == 0) {
+          const f2 u = pk(xy.x, xy.y), v = pk(xy.z, xy.w);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) tv[k][0] = fma2(u, ncq[CP1 ? k : 0], fma2(v, nsq[CP1 ? k : 0], A2));
+        } else if (HALF) {
           const __half2 hx = __floats2half2_rn(xy.x, xy.y), hy = __floats2half2_rn(xy.z, xy.w);
           const __half2 hz = (m & 1) ? __floats2half2_rn(zz.z, zz.w) : __floats2half2_rn(zz.x, zz.y);
 #pragma unroll
