@@ -142,6 +142,56 @@ def run_reference(args):
     return 0
 
 
+def obstacle_sweep(fk, dev, rank, counts, Q, X32, X, flush):
+    """Query cost of the proxy check against the geometric checker as the
+    number of boxes grows (the sweep of Sec. IV-A, 1-50 random boxes): per box
+    count, the 7-DOF arm's 5000 training configurations are labelled and the
+    model trained; then the query batch is labelled by the checker and scored
+    by the model (FP32 with the band re-score), each timed alone; the model's
+    labels are compared with the checker's (accuracy, TPR, TNR of Sec. IV-A)."""
+    import torch
+    w = synth.workload(WORKLOAD, trial=rank)
+    ch = fk.chain_from_arm(w.scene.arm)
+    m = fk.fastron_model_create(ch)
+    nq = Q.shape[0]
+    y = torch.empty(X.shape[0], dtype=torch.int8, device=dev)
+    truth = torch.empty(nq, dtype=torch.int8, device=dev)
+    lab = torch.empty(nq, dtype=torch.int8, device=dev)
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = []
+    try:
+        for nb in counts:
+            boxes = synth.random_boxes(w.seed * 97 + nb, nb)
+            fk.fk_label(ch, boxes, w.scene.radius, X32, y)
+            st = fk.fastron_train(m, X, y, w.gamma, w.beta, w.iter_max, w.s_max)
+            t_chk = timed(lambda: fk.fk_label(ch, boxes, w.scene.radius, Q, truth))
+            t_fk = timed(lambda: fk.fk_score(m, Q, lab, rescore=True))
+            pos, pred = truth == 1, lab == 1
+            tp = int((pos & pred).sum().item())
+            tn = int((~pos & ~pred).sum().item())
+            npos = int(pos.sum().item())
+            out.append({"boxes": nb, "in_collision": npos / nq, "support": st["n_support"],
+                        "iterations": st["iterations"], "proxy_checks_per_s": nq / t_fk * 1e3,
+                        "checker_checks_per_s": nq / t_chk * 1e3, "accuracy": (tp + tn) / nq,
+                        "tpr": tp / max(npos, 1), "tnr": tn / max(nq - npos, 1)})
+    finally:
+        fk.fastron_model_destroy(m)
+        fk.fk_chain_destroy(ch)
+    return out
+
+
 def changing_environment(fk, dev, rank, frames, nq):
     """The 12-control-point arm among moving boxes: a fixed training set of
     65,536 configurations relabelled every frame, Algorithm 1 on the stored
@@ -241,6 +291,8 @@ def main():
     ap.add_argument("--dynamic-frames", type=int, default=8,
                     help="frames of the changing-environment measurement (0: skip)")
     ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
+    ap.add_argument("--obstacle-sweep", default="1,2,5,10,20,35,50",
+                    help="box counts of the obstacle sweep (empty: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -486,6 +538,11 @@ def main():
             for ch in bchains:
                 fk.fk_chain_destroy(ch)
 
+    sweep = None
+    if args.obstacle_sweep:
+        counts = [int(x) for x in args.obstacle_sweep.split(",") if x.strip()]
+        sweep = obstacle_sweep(fk, dev, rank, counts, Q, Xq32, X, flush)
+
     dynamic = None
     if args.dynamic_frames > 1:
         dynamic = changing_environment(fk, dev, rank, args.dynamic_frames, args.dynamic_queries)
@@ -511,6 +568,7 @@ def main():
             "query_paths": paths,
             "batched_scenes": batched,
             "changing_environment": dynamic,
+            "obstacle_sweep": sweep,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},

@@ -267,8 +267,10 @@ void fk_set_wait_limit(uint32_t polls);
  * configuration-dependent control points).  fk_score_batched scores every
  * scene's queries in one persistent launch: work items (scene, block of
  * queries) sorted by cost |S| x queries, longest first, handed out by an
- * atomic counter; then one FP64 re-score launch for all band queries.  The
- * launches are captured once in a CUDA graph and replayed while q, f, label,
+ * atomic counter; then the band queries of all scenes are evaluated again
+ * in double-float (one warp per query) and those still within 1e-9 B(q) of
+ * zero in FP64, band sizes kept on the device.  The launches are captured
+ * once in a CUDA graph and replayed while q, f, label,
  * rescore, q_off and the tuned variant stay the same.  The models must stay
  * alive and unchanged while the batch exists (recreate it after retraining).
  * The paper's evaluation scores one scene at a time; this is the multi-scene

@@ -61,4 +61,37 @@ __device__ __forceinline__ dfl df_rcp(dfl a) {
 }
 
 
+// One summand t^-2 of the FK kernel in pair arithmetic, t = 1 + |q - s|^2 in
+// coordinates scaled by sqrt(gamma/2); q = qh + ql and s = (s[0] + s[1],
+// s[2] + s[3], s[4] + s[5]) per axis.  Every step keeps its rounding error:
+//   d = q - s      (dh, e) = two_sum(qh, -sh), dl = e + (ql - sl)
+//   d^2            p = dh^2, e' = fma(dh, dh, -p) + dl (2 dh + dl)
+//   t              th + tl = 1 + p_x + p_y + p_z (three two-sums) + sum of e'
+//   t^2            uh = th^2, ul = fma(th, th, -uh) + 2 th tl
+//   t^-2           y = rcp(uh), r = y + y (1 - uh y - ul y)
+// Returns the unnormalised pair (y, y res); relative error ~1e-13 (the
+// neglected square of the Newton residual is 2^-44).
+__device__ __forceinline__ void df_rq_term(const float qh[3], const float ql[3], const float *s, float &rh,
+                                           float &rl) {
+  float p[3], ep[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const dfl d = two_sum(qh[r], -s[2 * r]);
+    const float dl = d.l + (ql[r] - s[2 * r + 1]);
+    p[r] = d.h * d.h;
+    ep[r] = fmaf(dl, fmaf(2.f, d.h, dl), fmaf(d.h, d.h, -p[r]));
+  }
+  const dfl t1 = two_sum(1.f, p[0]);
+  const dfl t2 = two_sum(t1.h, p[1]);
+  const dfl t3 = two_sum(t2.h, p[2]);
+  const float th = t3.h;
+  const float tl = ((t1.l + t2.l) + t3.l) + ((ep[0] + ep[1]) + ep[2]);
+  const float uh = th * th;
+  const float ul = fmaf(2.f * th, tl, fmaf(th, th, -uh));
+  const float y = rcp_approx(uh);
+  const float res = fmaf(-ul, y, fmaf(-uh, y, 1.f));
+  rh = y;
+  rl = y * res;
+}
+
 }  // namespace fk

@@ -4,9 +4,13 @@
 // in that order from an atomic counter, so the long items start first and the
 // short ones fill the tail.  Each item stages its scene's chain in shared
 // memory and runs the same score_block as the per-call kernel; the band
-// queries of every scene are then re-scored in FP64 by one launch.
+// queries of every scene are then re-scored in double-float by one launch
+// (one warp per band query, the lanes over the scene's support set) and
+// those it cannot decide in FP64 by another.  Band sizes stay on the device,
+// so the whole sequence is one CUDA graph.
 #include <cstring>
 
+#include "df_arith.cuh"
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
 #include "score_core.cuh"
@@ -18,6 +22,7 @@ struct SceneDev {
   ChainF cf;
   ChainD cd;
   const float4 *rec;
+  const float *sdf;    // double-float records [ns][rec_df_len(Mv)]
   const double *cp64;
   const double *alpha;
   int64_t ns;
@@ -78,8 +83,104 @@ __global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) 
   }
 }
 
-// FP64 re-score of the band queries of all scenes: one warp per entry.
+// Double-float re-score of the band queries of all scenes: one warp per
+// entry.  Lane 0 computes the query's control points in FP64; they are split
+// into pairs in shared memory; each lane sums the summands (df_rq_term) of
+// its share of the support points; a fixed butterfly of two-sums adds the
+// lanes.  |f| > eps2 B(q) decides; the rest go to band2 for FP64.
 constexpr int kBRescoreWarps = 8;
+
+__global__ void __launch_bounds__(kBRescoreWarps * 32) batched_rescore_df_kernel(const SceneDev *__restrict__ scenes,
+                                                                                const float *__restrict__ q,
+                                                                                const int32_t *__restrict__ band_idx,
+                                                                                const int32_t *__restrict__ band_scene,
+                                                                                const int32_t *__restrict__ band_cnt,
+                                                                                double eps2, float *__restrict__ f,
+                                                                                int8_t *__restrict__ label,
+                                                                                int32_t *__restrict__ band2_idx,
+                                                                                int32_t *__restrict__ band2_scene,
+                                                                                int32_t *__restrict__ band2_cnt) {
+  __shared__ double qcp[kBRescoreWarps][FK_MAX_CP][3];
+  __shared__ float qd[kBRescoreWarps][FK_MAX_CP][6];  // (h, l) per axis of each configuration-dependent point
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t gw = blockIdx.x * (int64_t)kBRescoreWarps + wl;
+  const int64_t nw = (int64_t)gridDim.x * kBRescoreWarps;
+  const int64_t cnt = *band_cnt;
+  for (int64_t e = gw; e < cnt; e += nw) {
+    const int64_t k = band_idx[e];
+    const int scene = band_scene[e];
+    const SceneDev *sc = scenes + scene;
+    const ChainD &c = sc->cd;
+    if (lane == 0) {
+      PoseD P;
+      pose_base(c, P);
+      for (int m = 0; m < c.M; ++m)
+        if (c.cj[m] == 0) pose_point(P, c.ct[m], qcp[wl][m]);
+      for (int i = 0; i < c.D; ++i) {
+        pose_step(c, i, (double)q[k * c.D + i], P);
+        for (int m = 0; m < c.M; ++m)
+          if (c.cj[m] == i + 1) pose_point(P, c.ct[m], qcp[wl][m]);
+      }
+    }
+    __syncwarp();
+    const double gs = sqrt(0.5 * sc->gamma);
+    for (int i = lane; i < 3 * c.Mv; i += 32) {
+      const int v = i / 3, r = i % 3;
+      const dfl x = df_from_double(gs * qcp[wl][c.vidx[v]][r]);
+      qd[wl][v][2 * r] = x.h;
+      qd[wl][v][2 * r + 1] = x.l;
+    }
+    __syncwarp();
+    const int Mv = c.Mv, RL = rec_df_len(Mv);
+    const float n_const = (float)c.n_const;
+    float fh = 0.f, fl = 0.f, B = 0.f;
+    for (int64_t s = lane; s < sc->ns; s += 32) {
+      const float *S = sc->sdf + s * RL;
+      float kh = n_const, kl = 0.f;
+      for (int v = 0; v < Mv; ++v) {
+        const float qh[3] = {qd[wl][v][0], qd[wl][v][2], qd[wl][v][4]};
+        const float ql[3] = {qd[wl][v][1], qd[wl][v][3], qd[wl][v][5]};
+        float rh, rl;
+        df_rq_term(qh, ql, S + v * 6, rh, rl);
+        const dfl ks = two_sum(kh, rh);
+        kh = ks.h;
+        kl += ks.l + rl;
+      }
+      const float wh = S[6 * Mv], wlo = S[6 * Mv + 1];
+      const float ph = wh * kh;
+      const float pe = fmaf(wh, kl, fmaf(wlo, kh, fmaf(wh, kh, -ph)));
+      const dfl fs = two_sum(fh, ph);
+      fh = fs.h;
+      fl += fs.l + pe;
+      B = fmaf(S[6 * Mv + 2], kh, B);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, fh, o), ol = __shfl_xor_sync(0xffffffffu, fl, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, B, o);
+      // the same operands in the same order in both lanes of a pair (lower lane first)
+      const bool low = (lane & o) == 0;
+      const dfl t = two_sum(low ? fh : oh, low ? oh : fh);
+      fl = t.l + (low ? fl + ol : ol + fl);
+      fh = t.h;
+      B = low ? B + ob : ob + B;
+    }
+    if (lane == 0) {
+      const double fv = (double)fh + (double)fl;
+      if (fabs(fv) > eps2 * (double)B) {
+        if (f) f[k] = (float)fv;
+        label[k] = fv >= 0.0 ? 1 : -1;
+      } else {
+        const int pos = atomicAdd(band2_cnt, 1);
+        band2_idx[pos] = (int32_t)k;
+        band2_scene[pos] = scene;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// FP64 re-score of the entries the double-float pass left: one warp per entry.
 
 __global__ void __launch_bounds__(kBRescoreWarps * 32) batched_rescore_kernel(const SceneDev *__restrict__ scenes,
                                                                              const float *__restrict__ q,
@@ -185,6 +286,18 @@ cudaError_t launch_batched_score(int mv, int variant, const BatchArgs &a, cudaSt
   }
 }
 
+cudaError_t launch_batched_rescore_df(const SceneDev *scenes, const float *q, const int32_t *band_idx,
+                                      const int32_t *band_scene, const int32_t *band_cnt, double eps2, float *f,
+                                      int8_t *label, int32_t *band2_idx, int32_t *band2_scene, int32_t *band2_cnt,
+                                      cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  batched_rescore_df_kernel<<<(unsigned)(sms > 0 ? 4 * sms : 608), kBRescoreWarps * 32, 0, s>>>(
+      scenes, q, band_idx, band_scene, band_cnt, eps2, f, label, band2_idx, band2_scene, band2_cnt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batched_rescore(const SceneDev *scenes, const float *q, const int32_t *band_idx,
                                    const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
                                    cudaStream_t s) {
@@ -200,13 +313,14 @@ size_t scene_dev_size() { return sizeof(SceneDev); }
 size_t work_item_size() { return sizeof(WorkItem); }
 
 // Host-side filling of a SceneDev record (the layout stays private to this file).
-void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const double *cp64,
-                    const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n) {
+void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
+                    const double *cp64, const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n) {
   SceneDev d;
   memset(&d, 0, sizeof d);
   d.cf = cf;
   d.cd = cd;
   d.rec = static_cast<const float4 *>(rec);
+  d.sdf = sdf;
   d.cp64 = cp64;
   d.alpha = alpha;
   d.ns = ns;
@@ -229,6 +343,14 @@ cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, c
   BatchArgs a{static_cast<const SceneDev *>(scenes), static_cast<const WorkItem *>(items), n_items, counter, q, f,
               label, eps, band_idx, band_scene, band_cnt, err, wait_limit};
   return launch_batched_score(mv, variant, a, s, prepare_only);
+}
+
+cudaError_t launch_batched_rescore_df_args(const void *scenes, const float *q, const int32_t *band_idx,
+                                           const int32_t *band_scene, const int32_t *band_cnt, double eps2, float *f,
+                                           int8_t *label, int32_t *band2_idx, int32_t *band2_scene,
+                                           int32_t *band2_cnt, cudaStream_t s) {
+  return launch_batched_rescore_df(static_cast<const SceneDev *>(scenes), q, band_idx, band_scene, band_cnt, eps2, f,
+                                   label, band2_idx, band2_scene, band2_cnt, s);
 }
 
 cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,

@@ -7,7 +7,7 @@
 //               scaled by sqrt(gamma/2) in FP64 and split into FP32 pairs;
 //   df          per (query, support point, control point) the summand
 //               t^-2, t = 1 + |p - s|^2 in scaled coordinates, from pair
-//               arithmetic (below), summed per support point, weighted by
+//               arithmetic (df_rq_term), summed per support point, weighted by
 //               alpha_s / M and summed over a chunk of the support set;
 //               the support set is cut into chunks when the band is small,
 //               so that every SM has work;
@@ -15,13 +15,7 @@
 //               |f| > eps2 B(q) decides the label (the double-float error is
 //               far below eps2 B(q)); the rest go to the FP64 re-score.
 //
-// Summand arithmetic (q, s are pairs h + l; every step keeps its rounding
-// error, so the pair carries ~2^-46 relative accuracy):
-//   d = q - s:     (dh, e) = two_sum(qh, -sh),  dl = e + (ql - sl)
-//   d^2:           p = dh^2, e' = fma(dh, dh, -p) + dl (2 dh + dl)
-//   t:             th + tl = 1 + p_x + p_y + p_z (three two-sums) + sum of e'
-//   t^2:           uh = th^2, ul = fma(th, th, -uh) + 2 th tl
-//   t^-2:          y = rcp(uh), r = y + y (1 - uh y - ul y), the residual by FMA
+// Summand arithmetic: df_rq_term (df_arith.cuh).
 // Error budget per query: coordinates 2^-48 relative (the pair split),
 // summands ~1e-13 relative (the neglected square of the Newton residual is
 // 2^-44), the unnormalised low words of the sums n 2^-48 of B(q) for n
@@ -90,26 +84,11 @@ __global__ void __launch_bounds__(kDfThreads) rescore_df_kernel(const DfRescoreA
       float kh = n_const, kl = 0.f;
 #pragma unroll
       for (int v = 0; v < MV; ++v) {
-        float p[3], ep[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const dfl d = two_sum(qh[v][r], -S[v * 6 + 2 * r]);
-          const float dl = d.l + (ql[v][r] - S[v * 6 + 2 * r + 1]);
-          p[r] = d.h * d.h;
-          ep[r] = fmaf(dl, fmaf(2.f, d.h, dl), fmaf(d.h, d.h, -p[r]));
-        }
-        const dfl t1 = two_sum(1.f, p[0]);
-        const dfl t2 = two_sum(t1.h, p[1]);
-        const dfl t3 = two_sum(t2.h, p[2]);
-        const float th = t3.h;
-        const float tl = ((t1.l + t2.l) + t3.l) + ((ep[0] + ep[1]) + ep[2]);
-        const float uh = th * th;
-        const float ul = fmaf(2.f * th, tl, fmaf(th, th, -uh));
-        const float y = rcp_approx(uh);
-        const float res = fmaf(-ul, y, fmaf(-uh, y, 1.f));
-        const dfl ks = two_sum(kh, y);
+        float rh, rl;
+        df_rq_term(qh[v], ql[v], S + v * 6, rh, rl);
+        const dfl ks = two_sum(kh, rh);
         kh = ks.h;
-        kl += ks.l + y * res;
+        kl += ks.l + rl;
       }
       // f += w_s * ks, with w_s = alpha_s / M as a pair
       const float wh = S[6 * MV], wl = S[6 * MV + 1];

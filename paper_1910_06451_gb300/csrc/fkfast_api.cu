@@ -1263,8 +1263,8 @@ int batched_block_queries(int v);
 bool batched_supported(int mv);
 size_t scene_dev_size();
 size_t work_item_size();
-void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const double *cp64,
-                    const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n);
+void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
+                    const double *cp64, const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n);
 void fill_work_item(void *dst, int32_t scene, int32_t block);
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
                                       int32_t *counter, const float *q, float *f, int8_t *label, float eps,
@@ -1273,12 +1273,16 @@ cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, c
 cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,
                                         const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
                                         cudaStream_t s);
+cudaError_t launch_batched_rescore_df_args(const void *scenes, const float *q, const int32_t *band_idx,
+                                           const int32_t *band_scene, const int32_t *band_cnt, double eps2, float *f,
+                                           int8_t *label, int32_t *band2_idx, int32_t *band2_scene,
+                                           int32_t *band2_cnt, cudaStream_t s);
 }  // namespace fk
 
 struct fk_batch {
   int n_scenes = 0, mv = 0, D = 0;
   std::vector<fastron_model *> models;
-  DevBuf scenes, items, flags, band_idx, band_scene;
+  DevBuf scenes, items, flags, band_idx, band_scene, band2_idx, band2_scene;
   std::vector<char> scenes_h, items_h;
   int32_t n_items = 0;
   std::vector<int64_t> off;  // query offsets of the current work list
@@ -1339,6 +1343,8 @@ extern "C" void fk_batch_destroy(fk_batch_t *b) {
   b->flags.release();
   b->band_idx.release();
   b->band_scene.release();
+  b->band2_idx.release();
+  b->band2_scene.release();
   delete b;
 }
 
@@ -1349,7 +1355,7 @@ static int batch_plan(fk_batch *b, const int64_t *q_off) {
   for (int i = 0; i < b->n_scenes; ++i) {
     const fastron_model *m = b->models[i];
     const int64_t n = q_off[i + 1] - q_off[i];
-    fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p,
+    fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p, m->sdf.as<float>(),
                    m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, q_off[i], n);
     for (int64_t blk = 0; blk * bq < n; ++blk) {
       const int64_t qn = n - blk * bq < bq ? n - blk * bq : bq;
@@ -1377,9 +1383,14 @@ static int batch_enqueue(fk_batch *b, const float *q, float *f, int8_t *label, i
                                (float)kDefaultEps, rescore ? b->band_idx.as<int32_t>() : nullptr,
                                rescore ? b->band_scene.as<int32_t>() : nullptr, fl + 1, fl + 2, g_wait_limit, s,
                                false));
-  if (rescore)
-    CK(launch_batched_rescore_args(b->scenes.p, q, b->band_idx.as<int32_t>(), b->band_scene.as<int32_t>(), fl + 1, f,
-                                   label, s));
+  if (rescore) {
+    // double-float first; what it cannot decide goes to FP64 (count in fl[3])
+    CK(launch_batched_rescore_df_args(b->scenes.p, q, b->band_idx.as<int32_t>(), b->band_scene.as<int32_t>(), fl + 1,
+                                      kDefaultEpsDf, f, label, b->band2_idx.as<int32_t>(),
+                                      b->band2_scene.as<int32_t>(), fl + 3, s));
+    CK(launch_batched_rescore_args(b->scenes.p, q, b->band2_idx.as<int32_t>(), b->band2_scene.as<int32_t>(), fl + 3,
+                                   f, label, s));
+  }
   return FK_OK;
 }
 
@@ -1400,10 +1411,13 @@ extern "C" int fk_score_batched(fk_batch_t *b, const float *q, const int64_t *q_
     if (rc != FK_OK) return rc;
   }
   if (rescore) {
-    const size_t cap_before = b->band_idx.cap;
+    const void *before[4] = {b->band_idx.p, b->band_scene.p, b->band2_idx.p, b->band2_scene.p};
     CK(b->band_idx.ensure(sizeof(int32_t) * (size_t)total));
     CK(b->band_scene.ensure(sizeof(int32_t) * (size_t)total));
-    if (b->band_idx.cap != cap_before) batch_drop_graph(b);
+    CK(b->band2_idx.ensure(sizeof(int32_t) * (size_t)total));
+    CK(b->band2_scene.ensure(sizeof(int32_t) * (size_t)total));
+    const void *after[4] = {b->band_idx.p, b->band_scene.p, b->band2_idx.p, b->band2_scene.p};
+    if (!std::equal(before, before + 4, after)) batch_drop_graph(b);  // the captured graph holds the old pointers
   }
   // replay the captured graph when nothing it depends on has changed
   if (!b->exec || b->g_q != q || b->g_f != f || b->g_label != label || b->g_rescore != (rescore != 0) ||
