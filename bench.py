@@ -32,6 +32,11 @@ from paper_1910_06451_gb300 import synth  # noqa: E402
 
 WORKLOAD = "arm7-n5000"
 N_QUERY = 1 << 22
+# DRAM bytes read + written by one launch of the FP32 score kernel on this
+# workload (4,194,304 queries, 800 support points), from an ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum): the
+# queries in and the labels out, no re-reads
+SCORE_TRAFFIC_BYTES = 117_568_000 + 4_515_072
 METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -292,7 +297,7 @@ def main():
                     help="frames of the changing-environment measurement (0: skip)")
     ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
     ap.add_argument("--obstacle-sweep", default="1,2,5,10,20,35,50",
-                    help="box counts of the obstacle sweep (empty: skip)")
+                    help="box counts of the obstacle sweep (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -539,8 +544,8 @@ def main():
                 fk.fk_chain_destroy(ch)
 
     sweep = None
-    if args.obstacle_sweep:
-        counts = [int(x) for x in args.obstacle_sweep.split(",") if x.strip()]
+    counts = [int(x) for x in args.obstacle_sweep.split(",") if x.strip() and int(x) > 0]
+    if counts:
         sweep = obstacle_sweep(fk, dev, rank, counts, Q, Xq32, X, flush)
 
     dynamic = None
@@ -570,7 +575,8 @@ def main():
             "changing_environment": dynamic,
             "obstacle_sweep": sweep,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": SCORE_TRAFFIC_BYTES if nq == N_QUERY and Mv == 7 else None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": ws * nq / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
