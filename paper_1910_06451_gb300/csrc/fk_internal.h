@@ -22,12 +22,14 @@ cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t
 // added without evaluation.
 cudaError_t launch_gram_f64(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
                             int64_t nb, int sym, double *K, cudaStream_t s);
-// Double-float (FP32 pair) evaluation of the FP64 kernel matrix.
+// Double-float (FP32 pair) evaluation of the FP64 kernel matrix.  wa, wb:
+// workspaces of Mv * 3 * na (nb) float2 for the split control points (wb
+// unused when sym != 0).
 cudaError_t launch_gram_df(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
-                           int sym, double *K, cudaStream_t s);
+                           int sym, double *K, float2 *wa, float2 *wb, cudaStream_t s);
 // The same, each entry rounded to FP32 once (the stored single-precision matrix).
 cudaError_t launch_gram_df32(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
-                             int64_t nb, int sym, float *K, cudaStream_t s);
+                             int64_t nb, int sym, float *K, float2 *wa, float2 *wb, cudaStream_t s);
 cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int64_t na, const float *cpb, int64_t nb,
                             int sym, float *K, cudaStream_t s);
 

@@ -178,48 +178,82 @@ cudaError_t launch_gram_f32(const ChainD &c, float gamma, const float *cpa, int6
 }
 
 // ------------------------------------------------- double-float Gram ---
-// The same matrix in double-float arithmetic (df_arith.cuh): the work runs on
-// the FP32 pipes (128 lanes/clk/SM) instead of the FP64 pipe (1.7 lanes/clk/SM
-// on this part).  Inputs are the FP64 control points split into h + l; the
-// reciprocal is a MUFU estimate refined by one Newton step carried in
-// double-float.  The entries come out within about 1e-13 of the FP64 ones.
+// The same matrix in double-float arithmetic (df_arith.cuh), on the FP32
+// pipes (128 lanes/clk/SM) instead of the FP64 pipe (1.7 lanes/clk/SM on this
+// part).  The FP64 control points are scaled by sqrt(gamma/2) and split into
+// FP32 pairs once per point (df_split_kernel), so t = 1 + |p - s|^2 and each
+// summand is df_rq_term; per entry only the final value touches FP64: the
+// pair is widened exactly by integer operations and added (one DADD), then
+// scaled by 1/M (one DMUL), the order of the FP64 definition, so a diagonal
+// entry (every summand exactly 1) is exactly 1.  Entries come out within
+// about 1e-13 of the FP64 ones.
+
+// (h, l) of sqrt(gamma/2) cp for the configuration-dependent points:
+// cp SoA [M][3][n] FP64 -> out SoA [Mv*3][n] float2.
+__global__ void __launch_bounds__(256) df_split_kernel(const GramCps g, double gs, const double *__restrict__ cp,
+                                                      int64_t n, float2 *__restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)g.Mv * 3 * n) return;
+  const int row = (int)(e / n);
+  const int64_t j = e % n;
+  const int v = row / 3, r = row % 3;
+  const dfl x = df_from_double(gs * cp[(g.vidx[v] * 3 + r) * n + j]);
+  out[e] = make_float2(x.h, x.l);
+}
+
+// Exact FP32 -> FP64 widening of a normal value by integer operations (sign,
+// rebiased exponent, shifted fraction); zero and subnormal values give 0,
+// which for the low word of a pair whose high word is >= 1e-30 changes the
+// sum by less than 1e-38.
+__device__ __forceinline__ double widen_flush(float x) {
+  const unsigned b = __float_as_uint(x), mag = b & 0x7fffffffu;
+  if (mag < 0x00800000u) return 0.0;
+  return __longlong_as_double((long long)((unsigned long long)(b >> 31) << 63) | (((long long)mag << 29) + (896LL << 52)));
+}
+
 template <typename OT>
-__global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, double gamma, const double *__restrict__ cpa,
-                                                     int64_t na, const double *__restrict__ cpb, int64_t nb, int sym,
+__global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, const float2 *__restrict__ da, int64_t na,
+                                                     const float2 *__restrict__ db, int64_t nb, int sym,
                                                      OT *__restrict__ K) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int M = g.M;
-  dfl *A = reinterpret_cast<dfl *>(smem_raw);
-  dfl *B = A + M * 3 * kGT;
-  OT *O = reinterpret_cast<OT *>(B + M * 3 * kGT);  // [kGT][kGT + 1]
+  const int Mv = g.Mv;
+  // [Mv * 6][kGT]: for point v the words x_h, x_l, y_h, y_l, z_h, z_l, each a
+  // row over the tile's configurations (consecutive lanes, consecutive words)
+  float *A = reinterpret_cast<float *>(smem_raw);
+  float *B = A + Mv * 6 * kGT;
+  OT *O = reinterpret_cast<OT *>(B + Mv * 6 * kGT);  // [kGT][kGT + 1]
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)bi * kGT, j0 = (int64_t)bj * kGT;
-  for (int e = threadIdx.x; e < M * 3 * kGT; e += blockDim.x) {
-    const int row = e / kGT, col = e % kGT;
-    A[e] = df_from_double((i0 + col < na) ? cpa[row * na + i0 + col] : 0.0);
-    B[e] = df_from_double((j0 + col < nb) ? cpb[row * nb + j0 + col] : 0.0);
+  for (int e = threadIdx.x; e < Mv * 3 * kGT; e += blockDim.x) {
+    const int row = e / kGT, col = e % kGT;  // row = v * 3 + axis
+    const float2 x = (i0 + col < na) ? da[row * na + i0 + col] : make_float2(0.f, 0.f);
+    const float2 y = (j0 + col < nb) ? db[row * nb + j0 + col] : make_float2(0.f, 0.f);
+    A[(2 * row) * kGT + col] = x.x;
+    A[(2 * row + 1) * kGT + col] = x.y;
+    B[(2 * row) * kGT + col] = y.x;
+    B[(2 * row + 1) * kGT + col] = y.y;
   }
   __syncthreads();
-  const dfl hg = df_from_double(0.5 * gamma);
-  const dfl one = {1.f, 0.f};
-  const double invM = 1.0 / (double)M;
+  const double invM = 1.0 / (double)g.M;
   const bool mirror = sym && bi != bj;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int il = ty + 8 * r;
-    dfl s = {(float)g.n_const, 0.f};
-    for (int v = 0; v < g.Mv; ++v) {
-      const int m = g.vidx[v];
-      const dfl dx = df_sub(A[(m * 3 + 0) * kGT + il], B[(m * 3 + 0) * kGT + tx]);
-      const dfl dy = df_sub(A[(m * 3 + 1) * kGT + il], B[(m * 3 + 1) * kGT + tx]);
-      const dfl dz = df_sub(A[(m * 3 + 2) * kGT + il], B[(m * 3 + 2) * kGT + tx]);
-      const dfl d2 = df_add_pos(df_add_pos(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
-      const dfl t = df_add_pos(one, df_mul(hg, d2));
-      s = df_add_pos(s, df_rcp(df_sqr(t)));
+    float kh = (float)g.n_const, kl = 0.f;
+    for (int v = 0; v < Mv; ++v) {
+      const float *a6 = A + v * 6 * kGT + il, *b6 = B + v * 6 * kGT + tx;
+      const float qh[3] = {a6[0], a6[2 * kGT], a6[4 * kGT]};
+      const float ql[3] = {a6[kGT], a6[3 * kGT], a6[5 * kGT]};
+      const float sv[6] = {b6[0], b6[kGT], b6[2 * kGT], b6[3 * kGT], b6[4 * kGT], b6[5 * kGT]};
+      float rh, rl;
+      df_rq_term(qh, ql, sv, rh, rl);
+      const dfl ks = two_sum(kh, rh);
+      kh = ks.h;
+      kl += ks.l + rl;
     }
-    const OT v = (OT)(((double)s.h + (double)s.l) * invM);  // FP32: one more rounding
+    const OT v = (OT)(__dadd_rn(widen_flush(kh), widen_flush(kl)) * invM);
     if (i0 + il < na && j0 + tx < nb) K[(i0 + il) * nb + j0 + tx] = v;
     if (mirror) O[il * (kGT + 1) + tx] = v;
   }
@@ -234,28 +268,34 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, double ga
 
 template <typename OT>
 static cudaError_t launch_gram_df_t(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
-                                    int64_t nb, int sym, OT *K, cudaStream_t s) {
+                                    int64_t nb, int sym, OT *K, float2 *wa, float2 *wb, cudaStream_t s) {
   if (na <= 0 || nb <= 0) return cudaSuccess;
   GramCps g{c.M, c.Mv, c.n_const, {}};
   for (int v = 0; v < c.Mv; ++v) g.vidx[v] = c.vidx[v];
-  const size_t smem = sizeof(dfl) * 2 * (size_t)c.M * 3 * kGT + sizeof(OT) * kGT * (kGT + 1);
+  const double gs = sqrt(0.5 * gamma);
+  const int64_t ea = (int64_t)c.Mv * 3 * na, eb = (int64_t)c.Mv * 3 * nb;
+  if (ea > 0) df_split_kernel<<<(unsigned)((ea + 255) / 256), 256, 0, s>>>(g, gs, cpa, na, wa);
+  if (!sym && eb > 0) df_split_kernel<<<(unsigned)((eb + 255) / 256), 256, 0, s>>>(g, gs, cpb, nb, wb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(float) * 2 * (size_t)c.Mv * 6 * kGT + sizeof(OT) * kGT * (kGT + 1);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gram_df_kernel<OT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(gram_df_kernel<OT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(grid_for(nb, kGT), grid_for(na, kGT));
-  gram_df_kernel<OT><<<grid, 256, smem, s>>>(g, gamma, cpa, na, cpb, nb, sym, K);
+  gram_df_kernel<OT><<<grid, 256, smem, s>>>(g, wa, na, sym ? wa : wb, nb, sym, K);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_df(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb, int64_t nb,
-                           int sym, double *K, cudaStream_t s) {
-  return launch_gram_df_t<double>(c, gamma, cpa, na, cpb, nb, sym, K, s);
+                           int sym, double *K, float2 *wa, float2 *wb, cudaStream_t s) {
+  return launch_gram_df_t<double>(c, gamma, cpa, na, cpb, nb, sym, K, wa, wb, s);
 }
 
 cudaError_t launch_gram_df32(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
-                             int64_t nb, int sym, float *K, cudaStream_t s) {
-  return launch_gram_df_t<float>(c, gamma, cpa, na, cpb, nb, sym, K, s);
+                             int64_t nb, int sym, float *K, float2 *wa, float2 *wb, cudaStream_t s) {
+  return launch_gram_df_t<float>(c, gamma, cpa, na, cpb, nb, sym, K, wa, wb, s);
 }
 
 }  // namespace fk

@@ -78,7 +78,8 @@ struct fk_chain {
   int D = 0, M = 0;
   ChainF cf{};
   ChainD cd{};
-  DevBuf ws_a, ws_b;  // control-point workspaces of fk_gram
+  DevBuf ws_a, ws_b;    // control-point workspaces of fk_gram
+  DevBuf ws_da, ws_db;  // their double-float splits
 };
 
 extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, const fk_cp *cps, int M,
@@ -180,6 +181,8 @@ extern "C" void fk_chain_destroy(fk_chain_t *c) {
   if (!c) return;
   c->ws_a.release();
   c->ws_b.release();
+  c->ws_da.release();
+  c->ws_db.release();
   delete c;
 }
 
@@ -224,10 +227,15 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
     if (!sym) CK(launch_fk_forward_f64(c->cd, (const double *)Xb, nb, B, s));
     if (precision == FK_F64)
       CK(launch_gram_f64(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
-    else if (precision == FK_DF32)
-      CK(launch_gram_df32(c->cd, gamma, A, na, B, nb, sym, (float *)K, s));
-    else
-      CK(launch_gram_df(c->cd, gamma, A, na, B, nb, sym, (double *)K, s));
+    else {
+      CK(c->ws_da.ensure(sizeof(float2) * (size_t)(c->cd.Mv > 0 ? c->cd.Mv : 1) * 3 * (size_t)na));
+      if (!sym) CK(c->ws_db.ensure(sizeof(float2) * (size_t)(c->cd.Mv > 0 ? c->cd.Mv : 1) * 3 * (size_t)nb));
+      float2 *wa = c->ws_da.as<float2>(), *wb = sym ? wa : c->ws_db.as<float2>();
+      if (precision == FK_DF32)
+        CK(launch_gram_df32(c->cd, gamma, A, na, B, nb, sym, (float *)K, wa, wb, s));
+      else
+        CK(launch_gram_df(c->cd, gamma, A, na, B, nb, sym, (double *)K, wa, wb, s));
+    }
   } else {
     float *A = c->ws_a.as<float>(), *B = sym ? A : c->ws_b.as<float>();
     CK(launch_fk_forward_f32(c->cf, (const float *)Xa, na, A, s));
@@ -252,7 +260,7 @@ struct fastron_model {
   // training state (full training set)
   int64_t N = 0;
   int gram = -1;  // arithmetic/storage of G for the training set of the last call (-1: none)
-  DevBuf cpX, G, alpha, F, stats, sup_idx, sup_alpha, trace_kind, trace_idx, trace_delta;
+  DevBuf cpX, cpdf, G, alpha, F, stats, sup_idx, sup_alpha, trace_kind, trace_idx, trace_delta;
   int64_t trace_len = 0;
   // support set packed for scoring
   int64_t ns = -1;  // -1 = untrained
@@ -284,7 +292,7 @@ extern "C" int fastron_model_create(const fk_chain_t *chain, fastron_model_t **o
 
 extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
-  DevBuf *bufs[] = {&m->cpX, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
+  DevBuf *bufs[] = {&m->cpX, &m->cpdf, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
                     &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf, &m->rec1,
                     &m->qdf, &m->part, &m->band2_idx,
                     &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
@@ -367,10 +375,14 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     const double *cp = m->cpX.as<double>();
     if (gram == FK_F64)
       CK(launch_gram_f64(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), s));
-    else if (gram == FK_DF32)
-      CK(launch_gram_df32(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<float>(), s));
-    else
-      CK(launch_gram_df(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), s));
+    else {
+      CK(m->cpdf.ensure(sizeof(float2) * (size_t)(c->cd.Mv > 0 ? c->cd.Mv : 1) * 3 * (size_t)N));
+      float2 *w = m->cpdf.as<float2>();
+      if (gram == FK_DF32)
+        CK(launch_gram_df32(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<float>(), w, w, s));
+      else
+        CK(launch_gram_df(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), w, w, s));
+    }
     m->gram = gram;
   }
   if (p->warm_start == 2) {
