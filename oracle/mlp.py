@@ -5,10 +5,11 @@ TEST INFRASTRUCTURE ONLY (test suite, smoke check, benchmark CPU leg).  The
 paper has no learned surrogate; this restates the plain definitions the GPU
 kernels follow, in numpy FP64 with library matmuls as steps:
 
-  features  per control point m = 0..7 of the 7-DOF chain: its position
+  features  per control point m < min(M, D + 1) (on frame j): its position
             (x, y, z) from the FK of Eqs. 1-2, then sin/cos of joint values
-            q_m and q_{m+1} (q_0 = q_{D+1} = 0): 8 x 7 = 56 values, padded
-            with zeros to 64;
+            q_j and q_{j+1} (q_0 = q_{D+1} = 0): for the 7-DOF chain
+            8 x 7 = 56 values, padded with zeros to 64; further points (link
+            midpoints, averages of two frame origins) are left out;
   network   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2),
             h3 = relu(h2 W3^T + b3), out = h3 w4 + b4;
   loss      mean over the batch of (out - target)^2;
@@ -38,12 +39,13 @@ def features(arm, q) -> np.ndarray:
     qq = np.concatenate([np.zeros((n, 1)), q, np.zeros((n, 1))], axis=1)  # q_0 .. q_{D+1}
     out = np.zeros((n, N_IN))
     col = 0
-    for m in range(arm.M):
+    for m in range(min(arm.M, arm.D + 1)):
+        j = int(arm.cp_joint[m])
         out[:, col:col + 3] = cp[:, m]
-        out[:, col + 3] = np.sin(qq[:, m])
-        out[:, col + 4] = np.cos(qq[:, m])
-        out[:, col + 5] = np.sin(qq[:, m + 1])
-        out[:, col + 6] = np.cos(qq[:, m + 1])
+        out[:, col + 3] = np.sin(qq[:, j])
+        out[:, col + 4] = np.cos(qq[:, j])
+        out[:, col + 5] = np.sin(qq[:, j + 1])
+        out[:, col + 6] = np.cos(qq[:, j + 1])
         col += 7
     return out
 

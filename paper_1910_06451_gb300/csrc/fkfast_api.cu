@@ -852,9 +852,10 @@ extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogat
   if (!out) return fail(FK_ERR_ARG, "surrogate_create: out is NULL");
   *out = nullptr;
   if (!chain) return fail(FK_ERR_ARG, "surrogate_create: chain is NULL");
-  if (7 * chain->M > kSurrIn)
-    return fail(FK_ERR_CAPACITY, "surrogate_create: %d control points need %d features, above %d", chain->M,
-                7 * chain->M, kSurrIn);
+  const int nf = chain->M < chain->D + 1 ? chain->M : chain->D + 1;  // feature points
+  if (7 * nf > kSurrIn)
+    return fail(FK_ERR_CAPACITY, "surrogate_create: %d feature points need %d features, above %d", nf, 7 * nf,
+                kSurrIn);
   surrogate *s = new surrogate;
   s->chain = chain;
   s->seed = seed;

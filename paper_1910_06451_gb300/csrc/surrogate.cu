@@ -31,9 +31,11 @@ cudaError_t launch_gemm_f32(const GemmArgs &g0, int splits, cudaStream_t s) {
 namespace fk {
 
 // ------------------------------------------------------------ features ---
-// Per control point m (frame j = cj[m]): its position, then sin/cos of the
-// joint values q_j and q_{j+1} (q_0 = q_{D+1} = 0): 7 values per point,
-// zero-padded to kSurrIn.  Rows n..n_pad-1 are zeros.
+// Per control point m < min(M, D + 1) (frame j = cj[m]): its position, then
+// sin/cos of the joint values q_j and q_{j+1} (q_0 = q_{D+1} = 0): 7 values
+// per point, zero-padded to kSurrIn.  Points beyond the first D + 1 (on the
+// chains here: link midpoints, averages of two frame origins) add no
+// information and are left out.  Rows n..n_pad-1 are zeros.
 __global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q, int64_t n, int64_t n_pad,
                                      bf16 *__restrict__ X, bf16 *__restrict__ XT) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -50,7 +52,7 @@ __global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q
     pose_base(c, P);
     for (int fr = 0; fr <= c.D; ++fr) {
       if (fr > 0) pose_step(c, fr - 1, qv[fr], P);
-      for (int m = 0; m < c.M; ++m)
+      for (int m = 0; m < c.M && m <= c.D; ++m)
         if (c.cj[m] == fr) {
           float o[3];
           pose_point(P, c.ct[m], o);

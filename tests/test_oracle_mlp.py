@@ -108,3 +108,12 @@ def test_bf16_storage_gradients(monkeypatch):
     g_id = L.backward_bf16_storage(p, X, y)
     for k in g:
         np.testing.assert_allclose(g_id[k], g[k], rtol=1e-13, atol=1e-15)
+
+
+def test_features_of_the_twelve_point_arm_use_the_frame_origins():
+    # the four link midpoints are averages of frame origins: the features
+    # are those of the eight frame-origin points, as for the 8-point arm
+    a12 = synth.arm_7dof_m12(4000)
+    a8 = synth.arm_7dof(4000)
+    q = synth.uniform_configs(3, 20, 7, a8.qlim).astype(np.float64)
+    np.testing.assert_array_equal(L.features(a12, q), L.features(a8, q))
