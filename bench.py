@@ -206,7 +206,12 @@ def changing_environment(fk, dev, rank, frames, nq):
     loop, two-stage active learning: the next training set (65,536 rows) is
     the support set, one copy of it moved by up to 0.1 rad per joint, and
     uniform samples; it is relabelled, its kernel matrix rebuilt, and
-    Algorithm 1 starts from the carried weights.  Per-frame device times."""
+    Algorithm 1 starts from the carried weights.  A fourth pass adds the
+    learned surrogate: after each cold update it is fine-tuned (one epoch on
+    a fixed 1M-query set scored by the new model, threshold recalibrated) and
+    answers the frame's queries, falling back to the exact score below the
+    threshold; its labels are compared with the exact path's.  Per-frame
+    device times."""
     import torch
     wd = synth.workload("arm7m12-n65536", trial=rank)
     ch = fk.chain_from_arm(wd.scene.arm)
@@ -275,10 +280,54 @@ def changing_environment(fk, dev, rank, frames, nq):
                          "frame_ms_p50": float(np.percentile(tot, 50)), "frame_ms_p99": float(np.percentile(tot, 99)),
                          "iterations": its, "support": sup, "converged": conv, "rescored": nres,
                          "checks_per_s_p50": nq / (float(np.percentile(tot, 50)) * 1e-3)}
+        out["surrogate"] = surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev)
         return out
     finally:
         fk.fastron_model_destroy(m)
         fk.fk_chain_destroy(ch)
+
+
+def surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev):
+    import torch
+    nq = Q.shape[0]
+    sur = fk.surrogate_create(ch, seed=11)
+    try:
+        qtr = torch.from_numpy(synth.uniform_configs(wd.seed + 9, 1 << 20, wd.scene.arm.D, wd.scene.arm.qlim)).to(dev)
+        fk.fk_label(ch, boxes[0], wd.scene.radius, X32, y)
+        fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32, reuse_gram=True)
+        torch.cuda.synchronize()
+        a = ev()
+        fk.surrogate_train(sur, m, qtr, epochs=6, batch=8192, lr=1e-3, holdout=0.0625, reinit=True)
+        b = ev()
+        torch.cuda.synchronize()
+        first = a.elapsed_time(b)
+        exact = torch.empty(nq, dtype=torch.int8, device=dev)
+        upd, tune, qry, fb, mism = [], [], [], [], []
+        for k in range(1, len(boxes)):
+            torch.cuda.synchronize()
+            e0 = ev()
+            fk.fk_label(ch, boxes[k], wd.scene.radius, X32, y)
+            fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32, reuse_gram=True)
+            e1 = ev()
+            fk.surrogate_train(sur, m, qtr, epochs=1, batch=8192, lr=3e-4, holdout=0.0625, reinit=False)
+            e2 = ev()
+            nfb = fk.surrogate_infer(sur, m, Q, lab)
+            e3 = ev()
+            torch.cuda.synchronize()
+            upd.append(e0.elapsed_time(e1))
+            tune.append(e1.elapsed_time(e2))
+            qry.append(e2.elapsed_time(e3))
+            fb.append(nfb / nq)
+            fk.fk_score(m, Q, exact, rescore=True)
+            mism.append(int((lab != exact).sum().item()))
+        tot = [u + t + q for u, t, q in zip(upd, tune, qry)]
+        return {"first_train_ms": first, "update_ms_p50": float(np.percentile(upd, 50)),
+                "finetune_ms_p50": float(np.percentile(tune, 50)), "query_ms_p50": float(np.percentile(qry, 50)),
+                "query_ms_p99": float(np.percentile(qry, 99)), "frame_ms_p50": float(np.percentile(tot, 50)),
+                "frame_ms_p99": float(np.percentile(tot, 99)), "fallback": fb, "label_mismatch": mism,
+                "checks_per_s_p50": nq / (float(np.percentile(tot, 50)) * 1e-3)}
+    finally:
+        fk.surrogate_destroy(sur)
 
 
 def main():

@@ -154,3 +154,22 @@ def test_train_and_infer_with_fallback(fk, setup):
         assert np.mean(lab[confident] == exact[confident]) >= 0.995
     finally:
         fk.fastron_model_destroy(model)
+
+
+def test_forward_twelve_point_arm_matches_oracle(fk):
+    # the 12-point arm's surrogate reads the frame-origin points' features
+    w = synth.workload("arm7m12-n65536")
+    chain = fk.chain_from_arm(w.scene.arm)
+    s = fk.surrogate_create(chain, seed=2)
+    try:
+        p = _params(4)
+        fk.surrogate_set_params(s, _flat(p))
+        q = w.query_configs(1000)
+        out = torch.empty(1000, dtype=torch.float32, device="cuda")
+        fk.surrogate_forward(s, torch.from_numpy(q).cuda(), out)
+        pb, X = _oracle_with_bf16(_unflat(_flat(p)), w, q)
+        want, _ = L.forward(pb, X)
+        assert np.linalg.norm(out.cpu().numpy() - want) <= 1e-2 * np.linalg.norm(want)
+    finally:
+        fk.surrogate_destroy(s)
+        fk.fk_chain_destroy(chain)
