@@ -217,7 +217,8 @@ static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int
  *
  * Readings where the paper is silent: argmin/argmax ties go to the lowest
  * index; "continue" after an add means a removal is tried only when no add
- * was made in that pass; each pass is one iteration.
+ * was made in that pass; each pass is one iteration; the margin update
+ * F_j + delta K_ji (Eq. 8) is one fused multiply-add, rounded once (C99 fma).
  *
  * alpha and F are in/out (zeros for a cold start, a previous model's values
  * for a warm start, loadPreviousModel).  stats = {iterations, adds, removals,
@@ -257,7 +258,7 @@ int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, c
                 int was_zero = alpha[i] == 0.0;
                 alpha[i] += delta;
                 for (int64_t j = 0; j < N; ++j)
-                    F[j] += delta * col[j];
+                    F[j] = fma(delta, col[j], F[j]);
                 nnz += (alpha[i] != 0.0) - !was_zero;
                 ++adds;
                 ++iters;
@@ -285,7 +286,7 @@ int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, c
             kernel_column(M, gamma, N, cpX, r, col, store32);
             double a = alpha[r];
             for (int64_t j = 0; j < N; ++j)
-                F[j] -= a * col[j];
+                F[j] = fma(-a, col[j], F[j]);
             alpha[r] = 0.0;
             --nnz;
             ++removes;
@@ -322,7 +323,7 @@ int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const i
  * when the training set has changed, Sec. III-B): the first ns training
  * points are the previous support set with weights alpha[0..ns); the rest
  * start at 0, so F_j = sum_{s < ns} alpha_s K(X_s, X_j), summed in ascending
- * s with separately rounded products and sums.  store32: kernel entries
+ * s, each step a fused multiply-add as in the update of Eq. 8.  store32: kernel entries
  * rounded to FP32 as in kernel_column.
  */
 void orc_margins(int M, double gamma, int64_t N, const double *cpX, int64_t ns, const double *alpha, int store32,
@@ -334,7 +335,7 @@ void orc_margins(int M, double gamma, int64_t N, const double *cpX, int64_t ns, 
             double k = orc_k_fk(M, cpX + s * M * 3, cpX + j * M * 3, gamma);
             if (store32)
                 k = (double)(float)k;
-            f += alpha[s] * k;
+            f = fma(alpha[s], k, f);
         }
         F[j] = f;
     }

@@ -154,7 +154,9 @@ def test_fp32_stored_kernel_two_points_closed_form():
     kind, idx, delta = r.trace
     assert list(kind) == [1, 1] and list(idx) == [0, 1]
     assert delta[1] == -1.0 - k32
-    assert r.alpha[1] == -1.0 - k32 and r.F[0] == 1.0 + (-1.0 - k32) * k32 and r.F[1] == -1.0
+    # F_0 = fma(-1 - k32, k32, 1): one rounding of the exact 1 - k32 - k32^2
+    assert r.alpha[1] == -1.0 - k32 and r.F[1] == -1.0
+    assert r.F[0] == pytest.approx(1.0 - k32 - k32 * k32, rel=2e-16, abs=2e-16)
     r64 = O.fastron_train(cp, np.array([1, -1]), g, iter_max=100, store32=False)
     assert r64.alpha[1] != r.alpha[1]
 
