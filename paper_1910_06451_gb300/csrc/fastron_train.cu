@@ -28,8 +28,8 @@
 // folded to two's complement, zeros made +0), so the argmin/argmax work stays
 // off the FP64 pipe, which on this part runs at 1/64 of the FP32 rate; ties
 // go to the lowest index, as in a left-to-right scan.  F and alpha are
-// updated with separately rounded FP64 products and sums, in the order of
-// Eqs. 6-8.  The cluster barrier is a hardware barrier (no polling); the loop
+// updated in FP64 in the order of Eqs. 6-8, F by one fused multiply-add per
+// entry.  The cluster barrier is a hardware barrier (no polling); the loop
 // is bounded by iter_max.
 #include <cooperative_groups.h>
 
@@ -122,6 +122,18 @@ __device__ __forceinline__ Cand warp_argmax(const Cand &c) {
 // Every decision below must be identical in every thread of the cluster,
 // because every thread then meets the same barriers; the warp reductions give
 // every lane the same answer.
+// A cluster barrier whose arrive releases memory only in the warp that wrote
+// to other CTAs' shared memory (warp 0, the slot stores); the other warps
+// arrive relaxed, without a fence.  Every thread's wait acquires, so the slots
+// written before the releasing arrives are visible after it.  Warp-uniform.
+__device__ __forceinline__ void cluster_barrier(bool releases) {
+  if (releases)
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  else
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ Cand no_min() { return {LLONG_MAX, 0.0, INT_MAX}; }
 __device__ __forceinline__ Cand no_max() { return {LLONG_MIN, 0.0, INT_MAX}; }
 
@@ -231,7 +243,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       mn = warp_argmin(lane < kTrainWarps ? sh.wmin[lane] : no_min());
       if (lane < C) *cluster.map_shared_rank(&sh.slot_min[parity][rank], lane) = mn;
     }
-    cluster.sync();
+    cluster_barrier(warp == 0);
     mn = warp_argmin(lane < C ? sh.slot_min[parity][lane] : no_min());
     parity ^= 1;
   };
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       mx = warp_argmax(lane < kTrainWarps ? sh.wmax[lane] : no_max());
       if (lane < C) *cluster.map_shared_rank(&sh.slot_max[parity][rank], lane) = mx;
     }
-    cluster.sync();
+    cluster_barrier(warp == 0);
     mx = warp_argmax(lane < C ? sh.slot_max[parity][lane] : no_max());
     parity ^= 1;
   };
@@ -321,19 +333,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       a.trace_idx[iter - 1] = i;
       a.trace_delta[iter - 1] = delta;
     }
-    // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal).  Round
-    // to nearest is symmetric in sign, so F - fl(alpha_i K) equals
-    // F + fl((-alpha_i) K) bit for bit: one signed multiply and one add.
+    // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal), each
+    // entry one fused multiply-add rounded once, with the signed coefficient
     const double c = kind == 1 ? coef : -coef;
     bool cast = false;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) cast |= needs_cast(gk[k]);
     if (!__any_sync(0xffffffffu, cast)) {
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, widen_fast(gk[k])));
+      for (int k = 0; k < KMAX; ++k) F[k] = __fma_rn(c, widen_fast(gk[k]), F[k]);
     } else {
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) F[k] = __dadd_rn(F[k], __dmul_rn(c, (double)gk[k]));
+      for (int k = 0; k < KMAX; ++k) F[k] = __fma_rn(c, (double)gk[k], F[k]);
     }
     local_min();
     reduce_min();

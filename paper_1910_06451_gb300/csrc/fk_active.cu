@@ -18,8 +18,8 @@
 //                   clip) and rounded to FP32 once; both an FP64 and an FP32
 //                   copy are written.
 //   margins         F_j = sum_{s < ns} alpha_s K_sj over the carried support
-//                   points (the first ns rows), ascending s, separately
-//                   rounded FP64 products and sums; one thread per j reads
+//                   points (the first ns rows), ascending s, one FP64 fused
+//                   multiply-add per term as in Eq. 8; one thread per j reads
 //                   row s of the symmetric stored matrix, so a warp's loads
 //                   are contiguous.
 #include "fk_internal.h"
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) margins_kernel(const GT *__restrict__ G, 
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= N) return;
   double f = 0.0;
-  for (int64_t s = 0; s < ns; ++s) f = __dadd_rn(f, __dmul_rn(alpha[s], (double)G[s * N + j]));
+  for (int64_t s = 0; s < ns; ++s) f = __fma_rn(alpha[s], (double)G[s * N + j], f);
   F[j] = f;
 }
 

@@ -59,15 +59,19 @@ cudaError_t launch_fk_forward_f32(const ChainF &c, const float *q, int64_t n, fl
   return cudaGetLastError();
 }
 
+// The FP64 chain runs at 1/64 of the FP32 rate: one warp per CTA spreads a
+// few thousand configurations over every SM instead of a few dozen.
+constexpr int kFk64Threads = 32;
+
 cudaError_t launch_fk_forward_f64(const ChainD &c, const double *q, int64_t n, double *cp, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  fk_forward_f64_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(c, q, n, cp);
+  fk_forward_f64_kernel<double><<<grid_for(n, kFk64Threads), kFk64Threads, 0, s>>>(c, q, n, cp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t n, double *cp, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  fk_forward_f64_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(c, q, n, cp);
+  fk_forward_f64_kernel<float><<<grid_for(n, kFk64Threads), kFk64Threads, 0, s>>>(c, q, n, cp);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ constexpr int kDfThreads = 128;
 constexpr int kDfTile = 32;  // support points per shared-memory tile
 
 // --------------------------------------------------------- band FK ---
-__global__ void __launch_bounds__(64) band_fk_kernel(const ChainD c, const float *__restrict__ q,
+__global__ void __launch_bounds__(32) band_fk_kernel(const ChainD c, const float *__restrict__ q,
                                                      const int32_t *__restrict__ band_idx, int64_t nb, double gs,
                                                      float2 *__restrict__ qdf) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -143,7 +143,8 @@ int rescore_df_chunks(int64_t nb, int64_t ns, int sms) {
 
 cudaError_t launch_rescore_df(const ChainD &c, const DfRescoreArgs &a, cudaStream_t s) {
   if (a.nb <= 0) return cudaSuccess;
-  band_fk_kernel<<<(unsigned)((a.nb + 63) / 64), 64, 0, s>>>(c, a.q, a.band_idx, a.nb, a.gs, a.qdf);
+  // one warp per CTA: the FP64 kinematics spread over as many SMs as possible
+  band_fk_kernel<<<(unsigned)((a.nb + 31) / 32), 32, 0, s>>>(c, a.q, a.band_idx, a.nb, a.gs, a.qdf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned qblocks = (unsigned)((a.nb + kDfThreads - 1) / kDfThreads);

@@ -28,87 +28,89 @@
 namespace fk {
 
 // ---------------------------------------------------------------- pack ---
-// One thread per pair of support points (2j, 2j+1); an odd count is padded
-// with a point of weight 0.
-__global__ void pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// One thread per support point s, writing its half h = s & 1 of the pair
+// record j = s >> 1 (components h and 2 + h of each float4); an odd count is
+// padded by a thread that writes zeros (weight 0).  The FP64 kinematics run
+// at 1/64 of the FP32 rate, so the CTAs are small (32 threads) and spread
+// over as many SMs as there are support points / 32.
+constexpr int kPackThreads = 32;
+
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t npair = (a.ns + 1) / 2;
-  if (j >= npair) return;
+  if (s >= 2 * npair) return;
   const int MV = cf.Mv;
   const int REC = rec_len(MV);
-  float4 *rec = a.rec + j * REC;
+  const int64_t j = s >> 1;
+  const int h = (int)(s & 1);
+  float *rec = reinterpret_cast<float *>(a.rec + j * REC);
+  float *rec1 = a.rec1 ? reinterpret_cast<float *>(a.rec1 + j * REC) : nullptr;
+  auto put = [&](int e, int c, float v) {  // component c (0..3) of record entry e
+    rec[4 * e + c] = v;
+    if (rec1) rec1[4 * e + c] = v;
+  };
+  if (s >= a.ns) {  // padding half of an odd count
+    for (int e = 0; e < REC; ++e) {
+      put(e, h, 0.f);
+      put(e, 2 + h, 0.f);
+    }
+    return;
+  }
   const double gs = sqrt(0.5 * a.gamma);
-  float cpv[2][FK_MAX_CP][3];
-  float w[2], aw[2];
-  float uv[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int h = 0; h < 2; ++h) {
-    const int64_t s = 2 * j + h;
-    if (s >= a.ns) {
-      for (int v = 0; v < MV; ++v) cpv[h][v][0] = cpv[h][v][1] = cpv[h][v][2] = 0.f;
-      w[h] = aw[h] = 0.f;
-      continue;
-    }
-    const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
-    const double *x = a.X + src * cd.D;
-    double cp[FK_MAX_CP][3];
-    PoseD P;
-    pose_base(cd, P);
+  const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
+  const double *x = a.X + src * cd.D;
+  double cp[FK_MAX_CP][3];
+  PoseD P;
+  pose_base(cd, P);
+  for (int m = 0; m < cd.M; ++m)
+    if (cd.cj[m] == 0) pose_point(P, cd.ct[m], cp[m]);
+  for (int i = 0; i < cd.D; ++i) {
+    a.q_out[s * cd.D + i] = x[i];
+    pose_step(cd, i, x[i], P);
     for (int m = 0; m < cd.M; ++m)
-      if (cd.cj[m] == 0) pose_point(P, cd.ct[m], cp[m]);
-    for (int i = 0; i < cd.D; ++i) {
-      a.q_out[s * cd.D + i] = x[i];
-      pose_step(cd, i, x[i], P);
-      for (int m = 0; m < cd.M; ++m)
-        if (cd.cj[m] == i + 1) pose_point(P, cd.ct[m], cp[m]);
-    }
-    for (int m = 0; m < cd.M; ++m)
-      for (int r = 0; r < 3; ++r) a.cp64[(m * 3 + r) * a.ns + s] = cp[m][r];
-    const double al = a.alpha[s];
-    a.alpha_out[s] = al;
+      if (cd.cj[m] == i + 1) pose_point(P, cd.ct[m], cp[m]);
+  }
+  for (int m = 0; m < cd.M; ++m)
+    for (int r = 0; r < 3; ++r) a.cp64[(m * 3 + r) * a.ns + s] = cp[m][r];
+  const double al = a.alpha[s];
+  a.alpha_out[s] = al;
+  const double wd = al / cd.M;
+  // FP32 record: (x_a, x_b, y_a, y_b) per point, z two points at a time, weights
+  for (int v = 0; v < MV; ++v) {
+    const int m = cf.vidx[v];
+    put(v, h, (float)(gs * cp[m][0]));
+    put(v, 2 + h, (float)(gs * cp[m][1]));
+    put(MV + v / 2, 2 * (v & 1) + h, (float)(gs * cp[m][2]));
+  }
+  if (MV & 1) put(MV + MV / 2, 2 + h, 0.f);  // unused z slot of the last entry
+  put(REC - 1, h, (float)wd);
+  put(REC - 1, 2 + h, (float)fabs(wd));
+  if (rec1) {
+    // circle form of point 0: U = k cos theta, V = k sin theta, theta = q_1 + theta0_1
+    const double th = x[0] + cd.th0[0];
+    rec1[h] = (float)(a.cp1_k * cos(th));
+    rec1[2 + h] = (float)(a.cp1_k * sin(th));
+  }
+  if (a.sdf) {
+    float *r = a.sdf + s * rec_df_len(MV);
     for (int v = 0; v < MV; ++v)
-      for (int r = 0; r < 3; ++r) cpv[h][v][r] = (float)(gs * cp[cf.vidx[v]][r]);
-    const double wd = al / cd.M;
-    w[h] = (float)wd;
-    aw[h] = (float)fabs(wd);
-    if (a.rec1) {
-      // circle form of point 0: U = k cos theta, V = k sin theta, theta = q_1 + theta0_1
-      const double th = x[0] + cd.th0[0];
-      uv[h][0] = (float)(a.cp1_k * cos(th));
-      uv[h][1] = (float)(a.cp1_k * sin(th));
-    }
-    if (a.sdf) {
-      float *r = a.sdf + s * rec_df_len(MV);
-      for (int v = 0; v < MV; ++v)
-        for (int c3 = 0; c3 < 3; ++c3) {
-          const dfl x = df_from_double(gs * cp[cf.vidx[v]][c3]);
-          r[v * 6 + 2 * c3] = x.h;
-          r[v * 6 + 2 * c3 + 1] = x.l;
-        }
-      const dfl wp = df_from_double(wd);
-      r[6 * MV] = wp.h;
-      r[6 * MV + 1] = wp.l;
-      r[6 * MV + 2] = (float)fabs(wd);
-      for (int i = 6 * MV + 3; i < rec_df_len(MV); ++i) r[i] = 0.f;
-    }
-  }
-  for (int v = 0; v < MV; ++v) rec[v] = make_float4(cpv[0][v][0], cpv[1][v][0], cpv[0][v][1], cpv[1][v][1]);
-  for (int v = 0; v < MV; v += 2) {
-    const bool two = v + 1 < MV;
-    rec[MV + v / 2] = make_float4(cpv[0][v][2], cpv[1][v][2], two ? cpv[0][v + 1][2] : 0.f,
-                                  two ? cpv[1][v + 1][2] : 0.f);
-  }
-  rec[REC - 1] = make_float4(w[0], w[1], aw[0], aw[1]);
-  if (a.rec1) {
-    float4 *r1 = a.rec1 + j * REC;
-    for (int e = 0; e < REC; ++e) r1[e] = rec[e];
-    r1[0] = make_float4(uv[0][0], uv[1][0], uv[0][1], uv[1][1]);
+      for (int c3 = 0; c3 < 3; ++c3) {
+        const dfl xv = df_from_double(gs * cp[cf.vidx[v]][c3]);
+        r[v * 6 + 2 * c3] = xv.h;
+        r[v * 6 + 2 * c3 + 1] = xv.l;
+      }
+    const dfl wp = df_from_double(wd);
+    r[6 * MV] = wp.h;
+    r[6 * MV + 1] = wp.l;
+    r[6 * MV + 2] = (float)fabs(wd);
+    for (int i = 6 * MV + 3; i < rec_df_len(MV); ++i) r[i] = 0.f;
   }
 }
 
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s) {
   if (a.ns <= 0) return cudaSuccess;
   const int64_t npair = (a.ns + 1) / 2;
-  pack_kernel<<<(unsigned)((npair + 127) / 128), 128, 0, s>>>(cf, cd, a);
+  pack_kernel<<<(unsigned)((2 * npair + kPackThreads - 1) / kPackThreads), kPackThreads, 0, s>>>(cf, cd, a);
   return cudaGetLastError();
 }
 
