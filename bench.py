@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1910_06451_gb300 import synth  # noqa: E402
+from paper_1910_06451_gb300 import shard, synth  # noqa: E402
 
 WORKLOAD = "arm7-n5000"
 N_QUERY = 1 << 22
@@ -43,8 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    ws, rank, _ = shard.world()
     return ws, rank
 
 
@@ -353,7 +352,7 @@ def main():
 
     import torch
     ws, rank = _dist()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = shard.world()[2]
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -367,7 +366,7 @@ def main():
 
     # every rank runs an independent scene (trial = rank): the path shards by
     # scene and by query batch with no exchange
-    w = synth.workload(WORKLOAD, trial=rank)
+    w = synth.workload(WORKLOAD, trial=shard.rank_trial(rank))
     arm = w.scene.arm
     X = torch.from_numpy(w.train_configs().astype(np.float64)).to(dev)
     Xq32 = torch.from_numpy(w.train_configs()).to(dev)
@@ -422,13 +421,9 @@ def main():
         times.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(sum(times), dev)  # the slowest rank's time
     ms_per_step = total_ms / args.steps
-    value = ws * nq / (ms_per_step * 1e-3)
+    value = shard.aggregate_rate(nq, ws, ms_per_step)
     # kernels of this library per step: label; FK, kernel matrix, Algorithm 1,
     # compaction, packing; FP32 score, then band FK, double-float summands,
     # their finish and the FP64 re-score when the band is not empty
@@ -476,7 +471,7 @@ def main():
         b.synchronize()
         if i >= args.warmup:
             e2e_times.append(a.elapsed_time(b))
-    e2e_ms = sum(e2e_times) / len(e2e_times)
+    e2e_ms = shard.max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
     h2d = Qh.numel() * 4 + Xh.numel() * 8 + X32h.numel() * 4
     d2h = labh.numel()
 
@@ -628,7 +623,7 @@ def main():
                          "traffic": SCORE_TRAFFIC_BYTES if nq == N_QUERY and Mv == 7 else None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": ws * nq / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": shard.aggregate_rate(nq, ws, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches * args.steps,
             "clocks": clocks,
