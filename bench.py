@@ -48,46 +48,65 @@ def _dist():
 
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    """Samples SM clocks and throttle reasons while the timed steps run: one
+    nvidia-smi process streaming a line every 50 ms (its own child process,
+    ended by terminate()); start() returns once the first line has arrived,
+    and only lines that arrive after that are kept."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int = 0):
+    def __init__(self, index: int = 0, period_ms: int = 50):
         self.index = index
-        self.samples = []
-        self._stop = threading.Event()
+        self.period_ms = period_ms
+        self.samples = []  # (time, fields)
+        self.t0 = None
+        self._proc = None
         self._th = None
+        self._first = threading.Event()
 
     def start(self):
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                           "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+
         def run():
-            while not self._stop.is_set():
-                try:
-                    out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                         timeout=5).stdout.strip()
-                    if out:
-                        self.samples.append([x.strip() for x in out.split(",")])
-                except Exception:
-                    pass
-                self._stop.wait(0.2)
+            for line in self._proc.stdout:
+                line = line.strip()
+                if line:
+                    self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+                    self._first.set()
         self._th = threading.Thread(target=run, daemon=True)
         self._th.start()
+        self._first.wait(5.0)
+        self.t0 = time.time()
 
     def stop(self) -> dict:
-        self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._th:
-            self._th.join(timeout=10)
-        if not self.samples:
+            self._th.join(timeout=5)
+        during = [f for t, f in self.samples if self.t0 is not None and t >= self.t0]
+        if not during and self.samples:
+            during = [self.samples[-1][1]]
+        if not during:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        sm = [float(f[0]) for f in during if f[0].replace(".", "").isdigit()]
+        mx = [float(f[1]) for f in during if f[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and "Active" in s[4 + i]
-                          and "Not" not in s[4 + i]})
+        reasons = sorted({names[i] for f in during for i in range(4) if len(f) > 4 + i and "Active" in f[4 + i]
+                          and "Not" not in f[4 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(during)}
 
 
 def _peaks():
@@ -332,7 +351,7 @@ def surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fkfast")
     ap.add_argument("--cpu-sample", type=int, default=16384)
@@ -408,7 +427,10 @@ def main():
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(local)
+    # nvidia-smi numbers GPUs physically: map the local device through
+    # CUDA_VISIBLE_DEVICES (an index or a UUID) when it is set
+    visible = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    sampler = ClockSampler(visible[local].strip() if local < len(visible) else local)
     sampler.start()
     times = []
     for _ in range(args.steps):
