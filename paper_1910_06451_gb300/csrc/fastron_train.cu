@@ -141,7 +141,11 @@ struct TrainShared {
   Cand slot_min[2][kMaxCluster], slot_max[2][kMaxCluster];
   Cand wmin[kTrainWarps], wmax[kTrainWarps];
   int slot_cnt[kMaxCluster], wcnt[kTrainWarps];
+  double dec_delta;  // the add step's delta, computed by one thread of the CTA
+  int dec_nz;        // whether alpha_i + delta is nonzero
 };
+
+__device__ __forceinline__ double neg(double x) { return __longlong_as_double(__double_as_longlong(x) ^ kSign); }
 
 template <int KMAX, typename GT>
 __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const TrainArgs a) {
@@ -158,6 +162,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
   const int stride = kTrainThreads * C;
   const int g = rank * kTrainThreads + tid;
   const int N = (int)a.N;
+  // slice k of this warp holds points j0 + stride k .. + 31: a slice wholly
+  // past N is skipped by the whole warp (no FP64 work on padding)
+  const int j0w = rank * kTrainThreads + warp * 32;
+  auto live = [&](int k) { return j0w + stride * k < N; };
 
   double F[KMAX];
   unsigned yneg = 0;  // bit k: label of point g + stride k is -1
@@ -207,7 +215,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int j = g + stride * k;
-      if (j < N) {
+      if (live(k) && j < N) {
         const unsigned yn = (yneg >> k) & 1u;
         const long long km = bits_key(__double_as_longlong(F[k]) ^ ((long long)yn << 63));  // key of y_j F_j
         if (km < mn.key) mn = {km, alpha[k * kTrainThreads + tid], j | (int)(yn << 31)};  // j ascends
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int j = g + stride * k;
-      if (j < N) {
+      if (live(k) && j < N) {
         const double aj = alpha[k * kTrainThreads + tid];
         if (nonzero(aj)) {
           const unsigned yn = (yneg >> k) & 1u;
@@ -274,30 +282,32 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         const int j = g + stride * k;
-        gk[k] = j < N ? row[j] : GT(0);
+        gk[k] = live(k) && j < N ? row[j] : GT(0);
       }
     }
     int kind, i;
     double coef, delta;
     if (min_valid && mn.key <= 0 && (nnz < a.s_max || nonzero(mn.alpha))) {
       // add / adjust support point i: delta = b_i y_i - F_i (Eq. 6); the FP64
-      // arithmetic runs in lane 0 and is broadcast to the warp
+      // arithmetic runs in one thread of the CTA (an FP64 instruction costs
+      // the whole warp's share of this part's narrow FP64 pipe even with one
+      // lane active) and is shared through shared memory
       kind = 1;
       i = imin;
-      double dl = 0.0;
-      int nz_new = 0;
-      if (lane == 0) {
+      if (tid == 0) {
         const bool yn = mn.iy < 0;
         // F_i = y_i * (y_i F_i): a sign flip of the margin's bit pattern
         const double Fi = __longlong_as_double(__double_as_longlong(key_value(mn.key)) ^ (yn ? kSign : 0LL));
         const double by = yn ? -1.0 : a.beta;  // b_i y_i with b_i = beta^(0.5 (y_i + 1))
-        dl = __dsub_rn(by, Fi);
+        const double dl = __dsub_rn(by, Fi);
         // alpha_i + delta (Eq. 7) is zero exactly when delta == -alpha_i
         const long long bd = __double_as_longlong(dl), ba = __double_as_longlong(mn.alpha);
-        nz_new = !(((bd ^ kSign) == ba) || (!nonzero(dl) && !nonzero(mn.alpha)));
+        sh.dec_delta = dl;
+        sh.dec_nz = !(((bd ^ kSign) == ba) || (!nonzero(dl) && !nonzero(mn.alpha)));
       }
-      delta = __shfl_sync(0xffffffffu, dl, 0);
-      nz_new = __shfl_sync(0xffffffffu, nz_new, 0);
+      __syncthreads();
+      delta = sh.dec_delta;
+      const int nz_new = sh.dec_nz;
       coef = delta;
       nnz += (long long)nz_new - (long long)nonzero(mn.alpha);
       const int gi = i % stride;
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
       kind = 2;
       i = cidx(mx);
       coef = mx.alpha;
-      delta = -mx.alpha;
+      delta = neg(mx.alpha);
       const int gi = i % stride;
       if (gi / kTrainThreads == rank && gi % kTrainThreads == tid) alpha[(i / stride) * kTrainThreads + tid] = 0.0;
       --nnz;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         const int j = g + stride * k;
-        gk[k] = j < N ? row[j] : GT(0);
+        gk[k] = live(k) && j < N ? row[j] : GT(0);
       }
     }
     ++iters;
@@ -335,16 +345,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1) fastron_train_kernel(const T
     }
     // Eq. 8: F += delta K e_i (add), or F -= alpha_i K e_i (removal), each
     // entry one fused multiply-add rounded once, with the signed coefficient
-    const double c = kind == 1 ? coef : -coef;
+    const double c = kind == 1 ? coef : neg(coef);
     bool cast = false;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) cast |= needs_cast(gk[k]);
     if (!__any_sync(0xffffffffu, cast)) {
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) F[k] = __fma_rn(c, widen_fast(gk[k]), F[k]);
+      for (int k = 0; k < KMAX; ++k)
+        if (live(k)) F[k] = __fma_rn(c, widen_fast(gk[k]), F[k]);
     } else {
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) F[k] = __fma_rn(c, (double)gk[k], F[k]);
+      for (int k = 0; k < KMAX; ++k)
+        if (live(k)) F[k] = __fma_rn(c, (double)gk[k], F[k]);
     }
     local_min();
     reduce_min();
