@@ -273,3 +273,44 @@ def test_active_learning_frames_match_oracle(fk, arm12, dev, gram):
             S, aS = Xk[r.support], r.alpha[r.support]
     finally:
         fk.fastron_model_destroy(m)
+
+
+def test_new_entry_points_reject_bad_arguments(fk, arm12, dev):
+    w, ch = arm12
+    X = torch.from_numpy(w.train_configs()[:200].astype(np.float64)).to(dev)
+    y = _labels(fk, ch, w.scene.boxes, X.cpu().numpy(), dev)
+    out = torch.empty((1000, 7), dtype=torch.float64, device=dev)
+    m = fk.fastron_model_create(ch)
+    try:
+        with pytest.raises(fk.FkError) as e:  # untrained model: nothing to carry or sample from
+            fk.fk_active_samples(m, 1, 0.1, 10, w.scene.arm.qlim, 1, out)
+        assert e.value.code == fk.FK_ERR_STATE
+        with pytest.raises(fk.FkError) as e:
+            fk.fastron_train(m, X, y, w.gamma, warm_start=2)
+        assert e.value.code == fk.FK_ERR_STATE
+        fk.fastron_train(m, X, y, w.gamma, gram=fk.FK_DF32)
+        ns = fk.fastron_model_get(m)[0].shape[0]
+        for bad in ((-1, 0.1, 10, w.scene.arm.qlim), (1, -0.1, 10, w.scene.arm.qlim), (1, 0.1, -5, w.scene.arm.qlim),
+                    (1, 0.1, 10, 0.0), (1, float("nan"), 10, w.scene.arm.qlim)):
+            with pytest.raises(fk.FkError) as e:
+                fk.fk_active_samples(m, *bad, 1, out)
+            assert e.value.code == fk.FK_ERR_ARG
+        with pytest.raises(fk.FkError) as e:  # a changed training set cannot reuse the matrix
+            fk.fastron_train(m, X, y, w.gamma, warm_start=2, reuse_gram=True, gram=fk.FK_DF32)
+        assert e.value.code == fk.FK_ERR_ARG
+        with pytest.raises(fk.FkError) as e:  # fewer rows than the carried support set
+            fk.fastron_train(m, X[:ns - 1], y[:ns - 1], w.gamma, warm_start=2)
+        assert e.value.code == fk.FK_ERR_STATE
+        with pytest.raises(fk.FkError):
+            fk.fastron_train(m, X, y, w.gamma, warm_start=3)
+        with pytest.raises(fk.FkError):
+            fk.fastron_train(m, X, y, w.gamma, gram=99)
+        # a carried model on its own support set plus nothing new is a fixed point
+        n = fk.fk_active_samples(m, 0, 0.0, 0, w.scene.arm.qlim, 1, out)
+        assert n == ns
+        sup, alpha = fk.fastron_model_get(m)
+        yy = y[torch.from_numpy(sup).to(dev)]
+        st = fk.fastron_train(m, out[:n], yy.contiguous(), w.gamma, warm_start=2, gram=fk.FK_DF32)
+        assert st["converged"] and st["iterations"] <= ns
+    finally:
+        fk.fastron_model_destroy(m)
