@@ -762,6 +762,7 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
 namespace fk {
 cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, bf16 *XT,
                                  cudaStream_t s);
+
 cudaError_t launch_gemm(int epi, int nt, const GemmArgs &g, int splits, cudaStream_t s);
 cudaError_t launch_surr_head_bwd(const float *out, const float *y, const bf16 *h3, const float *w4, int B, bf16 *dP3,
                                  float *pw4, float *pb4, float *ploss, cudaStream_t s);
@@ -817,7 +818,7 @@ struct surrogate {
   int B = 0;           // batch of the training buffers
   DevBuf H1, H1T, H2, H2T, H3, dP3, dP3T, dP2, dP2T, dP1, dP1T, out, part, pw4, pb4, ploss, loss_hist;
   DevBuf X, XT, Y, Yh, lab_tmp;
-  DevBuf iX, iH1, iH2, iout, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
+  DevBuf iout, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
   DevBuf err, scal;
 };
 
@@ -891,7 +892,7 @@ extern "C" void surrogate_destroy(surrogate_t *s) {
   DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w1t, &s->w2b, &s->w2t, &s->w3b, &s->w3t,
                     &s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1,
                     &s->dP1T, &s->out, &s->part, &s->pw4, &s->pb4, &s->ploss, &s->loss_hist, &s->X, &s->XT,
-                    &s->Y, &s->Yh, &s->lab_tmp, &s->iX, &s->iH1, &s->iH2, &s->iout, &s->fb_idx, &s->fb_cnt,
+                    &s->Y, &s->Yh, &s->lab_tmp, &s->iout, &s->fb_idx, &s->fb_cnt,
                     &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred, &s->err, &s->scal};
   for (DevBuf *b : bufs) b->release();
   delete s;
@@ -1032,28 +1033,34 @@ static int surr_features(surrogate *s, const float *q, int64_t n, int64_t n_pad,
   return FK_OK;
 }
 
-// Network outputs (f / scale) of n_pad feature rows into iout.
-static int surr_forward_infer(surrogate *s, const bf16 *X, int64_t n_pad, cudaStream_t st) {
+// Network outputs (f / scale) of n queries q into out, with the fused
+// inference kernel (features and all layers in one launch); with decide != 0
+// also labels, pred and the fallback list (fb_cnt zeroed by the caller).
+static int surr_forward_fused(surrogate *s, const float *q, int64_t n, float *out, int decide, float tau, float *pred,
+                              int8_t *label, int32_t *fb_idx, int32_t *fb_cnt, cudaStream_t st) {
   const float *P = s->p.as<float>();
-  CK(s->iH1.ensure(2 * (size_t)n_pad * kSurrW));
-  CK(s->iH2.ensure(2 * (size_t)n_pad * kSurrW));
-  CK(s->iout.ensure(sizeof(float) * (size_t)n_pad));
-  GemmArgs g = gemm_args(s, X, kSurrIn, s->w1b.as<bf16>(), kSurrIn, (int)n_pad, kSurrW, kSurrIn);
-  g.bias = P + kOffB1;
-  g.C = s->iH1.as<bf16>();
-  g.ldc = kSurrW;
-  CK(launch_gemm(EPI_RELU, 256, g, 1, st));
-  g = gemm_args(s, s->iH1.as<bf16>(), kSurrW, s->w2b.as<bf16>(), kSurrW, (int)n_pad, kSurrW, kSurrW);
-  g.bias = P + kOffB2;
-  g.C = s->iH2.as<bf16>();
-  g.ldc = kSurrW;
-  CK(launch_gemm(EPI_RELU, 256, g, 1, st));
-  g = gemm_args(s, s->iH2.as<bf16>(), kSurrW, s->w3b.as<bf16>(), kSurrW, (int)n_pad, kSurrW, kSurrW);
-  g.bias = P + kOffB3;
-  g.w4 = P + kOffW4;
-  g.b4 = P + kOffB4;
-  g.out = s->iout.as<float>();
-  CK(launch_gemm(EPI_HEAD, 256, g, 1, st));
+  MlpArgs a{};
+  a.q = q;
+  a.n = n;
+  a.w1 = s->w1b.as<bf16>();
+  a.w2 = s->w2b.as<bf16>();
+  a.w3 = s->w3b.as<bf16>();
+  a.b1 = P + kOffB1;
+  a.b2 = P + kOffB2;
+  a.b3 = P + kOffB3;
+  a.w4 = P + kOffW4;
+  a.b4 = P + kOffB4;
+  a.out = out;
+  a.decide = decide;
+  a.scale = s->scale;
+  a.tau = tau;
+  a.pred = pred;
+  a.label = label;
+  a.fb_idx = fb_idx;
+  a.fb_cnt = fb_cnt;
+  a.err = s->err.as<int32_t>();
+  a.wait_limit = g_wait_limit;
+  CK(launch_mlp_fused(s->chain->cf, a, st));
   return FK_OK;
 }
 
@@ -1116,11 +1123,8 @@ extern "C" int surrogate_forward(surrogate_t *s, const float *q, int64_t n, floa
   if (n > INT32_MAX - kBM) return fail(FK_ERR_CAPACITY, "surrogate_forward: n too large");
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemsetAsync(s->err.p, 0, 64, st));
-  const int64_t n_pad = round_up(n, kBM);
-  int rc = surr_features(s, q, n, n_pad, s->iX, nullptr, st);
+  int rc = surr_forward_fused(s, q, n, out, 0, 0.f, nullptr, nullptr, nullptr, nullptr, st);
   if (rc != FK_OK) return rc;
-  if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_pad, st)) != FK_OK) return rc;
-  CK(cudaMemcpyAsync(out, s->iout.p, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
   return surr_check_err(s, st, "surrogate_forward");
 }
 
@@ -1184,8 +1188,10 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
   // calibrate tau on the held-out rows: the largest |pred| with a wrong sign
   float tau = 0.f, fb = 0.f, wrong_rate = 0.f;
   if (n_hold > 0) {
-    if ((rc = surr_features(s, q + (n - n_hold) * s->chain->D, n_hold, n_hold, s->iX, nullptr, st)) != FK_OK) return rc;
-    if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_hold, st)) != FK_OK) return rc;
+    CK(s->iout.ensure(sizeof(float) * (size_t)n_hold));
+    if ((rc = surr_forward_fused(s, q + (n - n_hold) * s->chain->D, n_hold, s->iout.as<float>(), 0, 0.f, nullptr,
+                                 nullptr, nullptr, nullptr, st)) != FK_OK)
+      return rc;
     CK(launch_scale(s->iout.as<float>(), n_hold, s->scale, st));
     unsigned *tb = reinterpret_cast<unsigned *>(s->scal.as<char>() + 32);
     unsigned long long *wr = reinterpret_cast<unsigned long long *>(s->scal.as<char>() + 40);
@@ -1240,15 +1246,13 @@ extern "C" int surrogate_infer(surrogate_t *s, fastron_model_t *model, const flo
   if (!(t >= 0.f)) return fail(FK_ERR_STATE, "surrogate_infer: no threshold (train with a holdout or pass tau > 0)");
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemsetAsync(s->err.p, 0, 64, st));
-  const int64_t n_pad = round_up(n, kBM);
-  int rc = surr_features(s, q, n, n_pad, s->iX, nullptr, st);
-  if (rc != FK_OK) return rc;
-  if ((rc = surr_forward_infer(s, s->iX.as<bf16>(), n_pad, st)) != FK_OK) return rc;
   CK(s->fb_idx.ensure(sizeof(int32_t) * (size_t)n));
   CK(s->fb_cnt.ensure(sizeof(int32_t) * 2));
   CK(cudaMemsetAsync(s->fb_cnt.p, 0, sizeof(int32_t), st));
-  CK(launch_surr_decide(s->iout.as<float>(), s->scale, n, t, pred, label, s->fb_idx.as<int32_t>(),
-                        s->fb_cnt.as<int32_t>(), st));
+  // features, network and decision in one launch
+  int rc = surr_forward_fused(s, q, n, nullptr, 1, t, pred, label, s->fb_idx.as<int32_t>(), s->fb_cnt.as<int32_t>(),
+                              st);
+  if (rc != FK_OK) return rc;
   int32_t nfb = 0;
   CK(cudaMemcpyAsync(&nfb, s->fb_cnt.p, sizeof nfb, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -3,6 +3,7 @@
 // layers run on tcgen05 tensor cores (BF16 operands, FP32 accumulation),
 // mean-squared-error training with Adam on FP32 master weights, and inference
 // that answers confident queries and sends the rest to the exact score.
+#include "surr_features.cuh"
 #include "tc_gemm.cuh"
 
 namespace fk {
@@ -31,48 +32,14 @@ cudaError_t launch_gemm_f32(const GemmArgs &g0, int splits, cudaStream_t s) {
 namespace fk {
 
 // ------------------------------------------------------------ features ---
-// Per control point m < min(M, D + 1) (frame j = cj[m]): its position, then
-// sin/cos of the joint values q_j and q_{j+1} (q_0 = q_{D+1} = 0): 7 values
-// per point, zero-padded to kSurrIn.  Points beyond the first D + 1 (on the
-// chains here: link midpoints, averages of two frame origins) add no
-// information and are left out.  Rows n..n_pad-1 are zeros.
+// One row of features per query (surr_features.cuh), written row-major and,
+// for training, transposed.  Rows n..n_pad-1 are zeros.
 __global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q, int64_t n, int64_t n_pad,
                                      bf16 *__restrict__ X, bf16 *__restrict__ XT) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n_pad) return;
-  float f[kSurrIn];
-#pragma unroll
-  for (int i = 0; i < kSurrIn; ++i) f[i] = 0.f;
-  if (k < n) {
-    float qv[FK_MAX_DOF + 2];
-    qv[0] = 0.f;
-    for (int i = 0; i < c.D; ++i) qv[i + 1] = q[k * c.D + i];
-    qv[c.D + 1] = 0.f;
-    PoseF P;
-    pose_base(c, P);
-    for (int fr = 0; fr <= c.D; ++fr) {
-      if (fr > 0) pose_step(c, fr - 1, qv[fr], P);
-      for (int m = 0; m < c.M && m <= c.D; ++m)
-        if (c.cj[m] == fr) {
-          float o[3];
-          pose_point(P, c.ct[m], o);
-          float s0, c0, s1, c1;
-          sincosf(qv[fr], &s0, &c0);
-          sincosf(qv[fr + 1], &s1, &c1);
-          const int b = 7 * m;
-          f[b + 0] = o[0];
-          f[b + 1] = o[1];
-          f[b + 2] = o[2];
-          f[b + 3] = s0;
-          f[b + 4] = c0;
-          f[b + 5] = s1;
-          f[b + 6] = c1;
-        }
-    }
-  }
   __align__(16) bf16 h[kSurrIn];
-#pragma unroll
-  for (int i = 0; i < kSurrIn; ++i) h[i] = __float2bfloat16_rn(f[i]);
+  surr_feature_row(c, k < n ? q + k * c.D : nullptr, h);
   uint4 *dst = reinterpret_cast<uint4 *>(X + k * kSurrIn);
 #pragma unroll
   for (int i = 0; i < kSurrIn / 8; ++i) dst[i] = reinterpret_cast<const uint4 *>(h)[i];

@@ -51,6 +51,24 @@ struct GemmArgs {
   uint32_t wait_limit;
 };
 
+// Fused surrogate inference (mlp_fused.cu): features, three hidden layers and
+// the output unit for n queries in one persistent launch.
+struct MlpArgs {
+  const float *q;            // [n][D]
+  int64_t n, ntiles;         // ntiles is set by the launcher
+  const bf16 *w1, *w2, *w3;  // [256][64], [256][256], [256][256], K-major
+  const float *b1, *b2, *b3, *w4, *b4;
+  float *out;                // network outputs [n] or null
+  int decide;                // 1: labels and fallback list below
+  float scale, tau;
+  float *pred;               // [n] or null: out * scale
+  int8_t *label;             // [n]
+  int32_t *fb_idx, *fb_cnt;  // fallback list and its length
+  int32_t *err;
+  uint32_t wait_limit;
+};
+cudaError_t launch_mlp_fused(const ChainF &c, const MlpArgs &a, cudaStream_t s);
+
 constexpr int kSurrIn = 64;   // surrogate input width (56 features, zero-padded)
 constexpr int kSurrW = 256;   // hidden width
 

@@ -173,3 +173,19 @@ def test_forward_twelve_point_arm_matches_oracle(fk):
     finally:
         fk.surrogate_destroy(s)
         fk.fk_chain_destroy(chain)
+
+
+def test_fused_inference_is_tile_independent(fk, setup):
+    # the fused kernel scores 128-query tiles; a query's output must not
+    # depend on the tile it falls in or on the padding of the last tile
+    w, chain, s = setup
+    fk.surrogate_set_params(s, _flat(_params(5)))
+    q = torch.from_numpy(w.query_configs(1500)).cuda()
+    a = torch.empty(1500, dtype=torch.float32, device="cuda")
+    b = torch.empty(1000, dtype=torch.float32, device="cuda")
+    fk.surrogate_forward(s, q, a)
+    fk.surrogate_forward(s, q[437:1437].contiguous(), b)
+    assert torch.equal(a[437:1437], b)
+    one = torch.empty(1, dtype=torch.float32, device="cuda")
+    fk.surrogate_forward(s, q[999:1000].contiguous(), one)
+    assert torch.equal(one, a[999:1000])
