@@ -30,7 +30,8 @@
 // The BF16 rounding points and the MMA order are those of the layer-by-layer
 // path, so both give the same outputs.
 //
-// Every mbarrier wait is bounded.  A thread whose wait gives up sets an abort
+// Every mbarrier wait is bounded (try_wait polls, which suspend the thread in
+// hardware until the phase flips).  A thread whose wait gives up sets an abort
 // flag in shared memory; every loop checks it; before the CTA exits, the MMAs
 // and copies it issued are drained (bounded), tensor memory is freed and an
 // error bit is raised.
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
       int64_t g = 0;
       for (int64_t it = 0, t = blockIdx.x; t < a.ntiles && !aborted(); ++it, t += gridDim.x) {
         const int ab = (int)(it & 1);
-        if (issued_a[ab] > 0 && !mbar_wait_bounded(&sh.empty_a[ab], (issued_a[ab] - 1) & 1, lim)) {
+        if (issued_a[ab] > 0 && !mbar_wait_suspend(&sh.empty_a[ab], (issued_a[ab] - 1) & 1, lim)) {
           give_up();
           break;
         }
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
         bool stop = false;
         for (int j = 0; j < 8; ++j, ++g) {
           const int s = (int)(g % kStages);
-          if (issued_w[s] > 0 && !mbar_wait_bounded(&sh.empty_w[s], (issued_w[s] - 1) & 1, lim)) {
+          if (issued_w[s] > 0 && !mbar_wait_suspend(&sh.empty_w[s], (issued_w[s] - 1) & 1, lim)) {
             give_up();
             stop = true;
             break;
@@ -184,10 +185,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
       if (aborted()) {
         // let every copy this thread issued land before the CTA can exit
         for (int i = 0; i < 2; ++i)
-          if (issued_a[i] > 0) mbar_wait_bounded(&sh.full_a[i], (issued_a[i] - 1) & 1, kGemmDrain);
+          if (issued_a[i] > 0) mbar_wait_suspend(&sh.full_a[i], (issued_a[i] - 1) & 1, kGemmDrain);
         for (int i = 0; i < kStages; ++i)
-          if (issued_w[i] > 0) mbar_wait_bounded(&sh.full_w[i], (issued_w[i] - 1) & 1, kGemmDrain);
-        mbar_wait_bounded(&sh.bar_w1, 0, kGemmDrain);
+          if (issued_w[i] > 0) mbar_wait_suspend(&sh.full_w[i], (issued_w[i] - 1) & 1, kGemmDrain);
+        mbar_wait_suspend(&sh.bar_w1, 0, kGemmDrain);
       }
     }
   } else {
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
     uint32_t n_acc = 0;                                 // commits to bar_acc so far
     bool acc_pending = false;                           // a commit not yet waited for
     int64_t g = 0;
-    bool ok = mbar_wait_bounded(&sh.bar_w1, 0, lim);
+    bool ok = mbar_wait_suspend(&sh.bar_w1, 0, lim);
     if (!ok) give_up();
     ok = compute_sync_and(ok);
 
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
     // compute threads agree on going on (a failed wait anywhere, the
     // producer's included, stops them all at the same point)
     auto wait_acc = [&]() -> bool {
-      const bool got = mbar_wait_bounded(&sh.bar_acc, (n_acc - 1) & 1, lim);
+      const bool got = mbar_wait_suspend(&sh.bar_acc, (n_acc - 1) & 1, lim);
       if (!got) give_up();
       acc_pending = !got;
       if (!compute_sync_and(got && !aborted())) return false;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
         for (int kc = 0; kc < 4; ++kc) {
           const int64_t gg = g + kc;
           const int s = (int)(gg % kStages);
-          if (!mbar_wait_bounded(&sh.full_w[s], (uint32_t)((gg / kStages) & 1), lim)) {
+          if (!mbar_wait_suspend(&sh.full_w[s], (uint32_t)((gg / kStages) & 1), lim)) {
             give_up();
             break;
           }
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
       const int ab = (int)(it & 1);
       // layer 1: features x W1^T -> columns 0..255
       if (tid == 0) {
-        if (!mbar_wait_bounded(&sh.full_a[ab], (uint32_t)((it >> 1) & 1), lim)) {
+        if (!mbar_wait_suspend(&sh.full_a[ab], (uint32_t)((it >> 1) & 1), lim)) {
           give_up();
         } else {
           tc_fence_after();
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_fused_kernel(const MlpArgs
       tc_fence_before();
       compute_sync();
     }
-    if (aborted() && tid == 0 && acc_pending) mbar_wait_bounded(&sh.bar_acc, (n_acc - 1) & 1, kGemmDrain);
+    if (aborted() && tid == 0 && acc_pending) mbar_wait_suspend(&sh.bar_acc, (n_acc - 1) & 1, kGemmDrain);
   }
   tc_fence_before();
   __syncthreads();
