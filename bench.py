@@ -446,10 +446,11 @@ def main():
     total_ms = shard.max_over_ranks(sum(times), dev)  # the slowest rank's time
     ms_per_step = total_ms / args.steps
     value = shard.aggregate_rate(nq, ws, ms_per_step)
-    # kernels of this library per step: label; FK, kernel matrix, Algorithm 1,
-    # compaction, packing; FP32 score, then band FK, double-float summands,
-    # their finish and the FP64 re-score when the band is not empty
-    launches = 7 + (4 if nres > 0 else 0)
+    # kernels of this library per step: label; FK, pair split, kernel
+    # matrix, Algorithm 1, compaction, packing; FP32 score, then band FK,
+    # double-float summands, their finish and the FP64 re-score when the band
+    # is not empty
+    launches = 8 + (4 if nres > 0 else 0)
 
     # roofline of the dominant kernel: the FP32 score, one launch per step.
     # Algorithmic work = |S| * Mv RQ evaluations per query.
