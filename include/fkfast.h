@@ -122,7 +122,9 @@ typedef struct {
                           FK_DF32, stored in FP32 (N^2 floats; 17.2 GB at N = 65,536) */
     int32_t reuse_gram;/* 1: X is the training set of this model's previous call, with the same
                           N and gram: its stored kernel matrix is used again instead of being
-                          rebuilt (a changing environment relabels a fixed training set);
+                          rebuilt (a changing environment relabels a fixed training set).  X
+                          must be the same device buffer as in the call that built the matrix
+                          (else FK_ERR_STATE), with unchanged contents (not checked);
                           0: build it */
 } fastron_params;
 

@@ -260,6 +260,7 @@ struct fastron_model {
   // training state (full training set)
   int64_t N = 0;
   int gram = -1;  // arithmetic/storage of G for the training set of the last call (-1: none)
+  const double *gram_X = nullptr;  // the device buffer G was built from
   DevBuf cpX, cpdf, G, alpha, F, stats, sup_idx, sup_alpha, trace_kind, trace_idx, trace_delta;
   int64_t trace_len = 0;
   // support set packed for scoring
@@ -344,8 +345,9 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     return fail(FK_ERR_STATE, "fastron_train: carrying the support set needs a trained model with |S| <= N");
   if (p->warm_start == 2 && p->reuse_gram)
     return fail(FK_ERR_ARG, "fastron_train: a carried support set means a new training set: reuse_gram must be 0");
-  if (p->reuse_gram && (m->N != N || m->gram != gram))
-    return fail(FK_ERR_STATE, "fastron_train: reuse_gram needs a previous call with the same N and gram");
+  if (p->reuse_gram && (m->N != N || m->gram != gram || m->gram_X != X))
+    return fail(FK_ERR_STATE, "fastron_train: reuse_gram needs a previous call on the same X buffer with the same N "
+                              "and gram");
   cudaStream_t s = (cudaStream_t)stream;
   const fk_chain *c = m->chain;
   const bool keep = p->warm_start == 1;
@@ -384,6 +386,7 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
         CK(launch_gram_df(c->cd, p->gamma, cp, N, cp, N, 1, m->G.as<double>(), w, w, s));
     }
     m->gram = gram;
+    m->gram_X = X;
   }
   if (p->warm_start == 2) {
     // loadPreviousModel on a changed training set: the first ns rows are the

@@ -75,3 +75,46 @@ def test_every_tuned_variant_agrees(fk, batch):
     fk.fk_score_batched(b, q, off, lab)
     torch.cuda.synchronize()
     assert torch.equal(lab, ref)
+
+
+def test_batched_band_reaches_fp64_for_cancelling_scene(fk):
+    # one scene whose two support points coincide with weights +1 and -1
+    # (f = 0 for every query) among ordinary scenes: inside the captured graph
+    # its queries pass the FP32 band and the double-float tier to the FP64
+    # re-score, which returns f = 0 and the label +1; the other scenes keep
+    # their own labels
+    scenes = synth.batch_scenes(11, 3, support=(50, 300), queries=(200, 800))
+    x = scenes[1].support[:1]
+    scenes[1].support = np.concatenate([x, x])
+    scenes[1].alpha = np.array([1.0, -1.0])
+    chains, models = [], []
+    try:
+        for sc in scenes:
+            ch = fk.chain_from_arm(sc.scene.arm)
+            m = fk.fastron_model_create(ch)
+            fk.fastron_model_set(m, sc.support.astype(np.float64), sc.alpha, sc.gamma)
+            chains.append(ch)
+            models.append(m)
+        b = fk.fk_batch_create(models)
+        try:
+            off = np.concatenate([[0], np.cumsum([len(sc.queries) for sc in scenes])]).astype(np.int64)
+            q = torch.from_numpy(np.concatenate([sc.queries for sc in scenes])).cuda()
+            lab = torch.zeros(int(off[-1]), dtype=torch.int8, device="cuda")
+            f = torch.full((int(off[-1]),), 7.0, dtype=torch.float32, device="cuda")
+            fk.fk_score_batched(b, q, off, lab, f)
+            torch.cuda.synchronize()
+            lab, f = lab.cpu().numpy(), f.cpu().numpy()
+            a, z = off[1], off[2]
+            assert np.all(f[a:z] == 0.0) and np.all(lab[a:z] == 1)
+            for i in (0, 2):
+                sc = scenes[i]
+                want = O.score(sc.scene.arm, sc.support.astype(np.float64), sc.alpha,
+                               sc.queries.astype(np.float64), sc.gamma, nthreads=8)
+                assert np.array_equal(lab[off[i]:off[i + 1]], O.labels_from_f(want))
+        finally:
+            fk.fk_batch_destroy(b)
+    finally:
+        for m in models:
+            fk.fastron_model_destroy(m)
+        for ch in chains:
+            fk.fk_chain_destroy(ch)

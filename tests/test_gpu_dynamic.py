@@ -135,6 +135,9 @@ def test_reuse_gram_needs_a_matching_previous_call(fk, arm12, dev):
             fk.fastron_train(m, X, y, w.gamma, gram=fk.FK_DF64, reuse_gram=True)
         with pytest.raises(fk.FkError):
             fk.fastron_train(m, X[:200], y[:200], w.gamma, gram=fk.FK_DF32, reuse_gram=True)
+        with pytest.raises(fk.FkError) as e:  # same size, another buffer: the matrix is not X2's
+            fk.fastron_train(m, X.clone(), y, w.gamma, gram=fk.FK_DF32, reuse_gram=True)
+        assert e.value.code == fk.FK_ERR_STATE
         st = fk.fastron_train(m, X, y, w.gamma, gram=fk.FK_DF32, reuse_gram=True)
         assert st["converged"]
     finally:
