@@ -318,7 +318,8 @@ def surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev):
         fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32)
         torch.cuda.synchronize()
         a = ev()
-        fk.surrogate_train(sur, m, qtr, epochs=6, batch=8192, lr=1e-3, holdout=0.0625, reinit=True)
+        fk.surrogate_train(sur, m, qtr, epochs=96, batch=8192, lr=3e-3, holdout=0.0625, reinit=True,
+                           schedule=fk.FK_LR_COSINE)
         b = ev()
         torch.cuda.synchronize()
         first = a.elapsed_time(b)
@@ -361,7 +362,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=N_QUERY, help="query batch size (profiling runs use a smaller one)")
     ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
-    ap.add_argument("--surrogate-epochs", type=int, default=12)
+    ap.add_argument("--surrogate-epochs", type=int, default=96)
+    ap.add_argument("--surrogate-lr", type=float, default=3e-3, help="peak of the cosine learning-rate schedule")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the multi-scene measurement (0: skip)")
     ap.add_argument("--dynamic-frames", type=int, default=8,
                     help="frames of the changing-environment measurement (0: skip)")
@@ -472,10 +474,15 @@ def main():
         score_times.append(ev[0].elapsed_time(ev[1]))
     score_ms = statistics.median(score_times)
     achieved = evals / (score_ms * 1e-3) / 1e12
-    # peak: 152 SMs x 128 FP32 lanes x max SM clock / 5 FMA-pipe ops per evaluation
+    # peak: the slower of the reciprocal (MUFU: 16 lanes/clk/SM, one per
+    # evaluation) and the FP32 pipe (128 lanes/clk/SM, five operations per
+    # evaluation: three products and two sums); the second, stricter figure
+    # ignores the reciprocal altogether
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(clocks.get("sm_max_mhz") or _peaks().get("sm_max_mhz") or 2070.0)
-    peak = props.multi_processor_count * 128 * sm_max * 1e6 / 5 / 1e12
+    sm_clk = props.multi_processor_count * sm_max * 1e6
+    peak_fp32_floor = sm_clk * 128 / 5 / 1e12
+    peak = min(sm_clk * 16 / 1, sm_clk * 128 / 5) / 1e12
 
     # end to end through the public API with host buffers
     Qh = Q.cpu().pin_memory()
@@ -542,8 +549,8 @@ def main():
         try:
             qtr = torch.from_numpy(synth.uniform_configs(w.seed + 7, args.surrogate_train, arm.D, arm.qlim)).to(dev)
             t0 = time.perf_counter()
-            sst = fk.surrogate_train(sur, model, qtr, epochs=args.surrogate_epochs, batch=8192, lr=1e-3,
-                                     holdout=0.0625)
+            sst = fk.surrogate_train(sur, model, qtr, epochs=args.surrogate_epochs, batch=8192,
+                                     lr=args.surrogate_lr, holdout=0.0625, schedule=fk.FK_LR_COSINE)
             torch.cuda.synchronize()
             train_s = time.perf_counter() - t0
             del qtr
@@ -567,6 +574,7 @@ def main():
                                   "tau": sst["tau"], "holdout_fallback": sst["holdout_fallback"],
                                   "holdout_sign_error": sst["holdout_sign_error"], "train_s": train_s,
                                   "train_rows": sst["n_train"], "epochs": args.surrogate_epochs,
+                                  "lr_schedule": f"cosine from {args.surrogate_lr:g}",
                                   "loss_last": sst["loss_last"], "speedup_vs_fp32_exact": query_ms / sms}
             del slab, ex
         finally:
@@ -660,6 +668,9 @@ def main():
             "obstacle_sweep": sweep,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak,
+                         "peak_basis": "min(MUFU 16/clk/SM x 1 reciprocal, FP32 128/clk/SM / 5 ops) per evaluation "
+                                       "x SMs x max SM clock",
+                         "peak_fp32_floor": peak_fp32_floor, "frac_fp32_floor": achieved / peak_fp32_floor,
                          "traffic": SCORE_TRAFFIC_BYTES if nq == N_QUERY and Mv == 7 else None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},

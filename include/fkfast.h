@@ -49,6 +49,9 @@ extern "C" {
 #define FK_DF32 4 /* as FK_DF64, each result rounded to FP32 once: the kernel matrix stored in
                      single precision (fk_gram: float K; training: half the memory) */
 
+#define FK_LR_STEP 0   /* surrogate_train_params.schedule */
+#define FK_LR_COSINE 1
+
 #define FK_MAX_DOF 16
 #define FK_MAX_CP 32
 
@@ -310,10 +313,11 @@ typedef struct surrogate surrogate_t;
 typedef struct {
     int32_t epochs;   /* passes over the training rows */
     int32_t batch;    /* rows per step, a multiple of 128, <= 65536 */
-    float lr;         /* Adam step size (divided by 3 for the last third of the epochs) */
+    float lr;         /* Adam step size (schedule below) */
     float holdout;    /* fraction of the queries held out to calibrate tau, in [0, 1) */
     int32_t reinit;   /* 1: reinitialise the weights first; 0: continue (fine-tune) */
-    int32_t reserved;
+    int32_t schedule; /* FK_LR_STEP: lr, divided by 3 for the last third of the epochs;
+                         FK_LR_COSINE: lr * (1 + cos(pi k / K)) / 2 at step k of K */
 } surrogate_train_params;
 
 typedef struct {

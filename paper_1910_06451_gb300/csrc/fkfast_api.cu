@@ -1142,6 +1142,8 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
   if (B < kBM || B % kBM || B > (1 << 16)) return fail(FK_ERR_ARG, "surrogate_train: batch must be a multiple of 128 up to 65536");
   if (prm->epochs < 0 || !(prm->lr > 0.f) || !(prm->holdout >= 0.f && prm->holdout < 1.f))
     return fail(FK_ERR_ARG, "surrogate_train: bad epochs, lr or holdout");
+  if (prm->schedule != FK_LR_STEP && prm->schedule != FK_LR_COSINE)
+    return fail(FK_ERR_ARG, "surrogate_train: unknown learning-rate schedule %d", prm->schedule);
   const int64_t n_hold = round_up((int64_t)(prm->holdout * (double)n), kBM) <= n ? round_up((int64_t)(prm->holdout * (double)n), kBM) : 0;
   const int64_t n_tr = (n - n_hold) / B * B;
   if (n_tr < B) return fail(FK_ERR_ARG, "surrogate_train: fewer training rows than one batch");
@@ -1176,8 +1178,11 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
   CK(s->loss_hist.ensure(sizeof(float) * (size_t)(total > 0 ? total : 1)));
   int64_t step = 0;
   for (int ep = 0; ep < prm->epochs; ++ep) {
-    const float lr = ep < (2 * prm->epochs + 2) / 3 ? prm->lr : prm->lr / 3.f;
+    const float lr_ep = ep < (2 * prm->epochs + 2) / 3 ? prm->lr : prm->lr / 3.f;
     for (int64_t b = 0; b < steps_per_epoch; ++b, ++step) {
+      const float lr = prm->schedule == FK_LR_COSINE
+                           ? (float)(0.5 * prm->lr * (1.0 + cos(M_PI * (double)step / (double)total)))
+                           : lr_ep;
       const int64_t b0 = b * B;
       if ((rc = surr_forward_train(s, s->X.as<bf16>() + b0 * kSurrIn, B, st)) != FK_OK) return rc;
       if ((rc = surr_backward(s, s->XT.as<bf16>() + b0, n_tr, s->Y.as<float>() + b0, B,

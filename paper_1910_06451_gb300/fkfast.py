@@ -26,6 +26,8 @@ FK_F64 = 1
 FK_F16 = 2
 FK_DF64 = 3
 FK_DF32 = 4
+FK_LR_STEP = 0
+FK_LR_COSINE = 1
 FK_MAX_DOF = 16
 FK_MAX_CP = 32
 
@@ -62,7 +64,7 @@ class FastronParams(ctypes.Structure):
 
 class SurrogateTrainParams(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("holdout", ctypes.c_float), ("reinit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("holdout", ctypes.c_float), ("reinit", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 class SurrogateStats(ctypes.Structure):
@@ -384,10 +386,13 @@ def surrogate_destroy(s):
     load().surrogate_destroy(s)
 
 
-def surrogate_train(s, model, q, epochs=10, batch=8192, lr=1e-3, holdout=0.1, reinit=True, stream=None) -> dict:
-    """Trains the surrogate on float32 queries q (n, D); targets are the model's FP32 scores."""
+def surrogate_train(s, model, q, epochs=10, batch=8192, lr=1e-3, holdout=0.1, reinit=True, schedule=None,
+                    stream=None) -> dict:
+    """Trains the surrogate on float32 queries q (n, D); targets are the model's FP32 scores.
+    schedule: FK_LR_STEP (default) or FK_LR_COSINE."""
     import torch
-    p = SurrogateTrainParams(int(epochs), int(batch), float(lr), float(holdout), int(bool(reinit)), 0)
+    p = SurrogateTrainParams(int(epochs), int(batch), float(lr), float(holdout), int(bool(reinit)),
+                             FK_LR_STEP if schedule is None else int(schedule))
     st = SurrogateStats()
     _check(load().surrogate_train(s, model, _dev(q, torch.float32, "q"), q.shape[0], ctypes.byref(p),
                                   ctypes.byref(st), _stream(stream)))
