@@ -821,7 +821,7 @@ struct surrogate {
   int B = 0;           // batch of the training buffers
   DevBuf H1, H1T, H2, H2T, H3, dP3, dP3T, dP2, dP2T, dP1, dP1T, out, part, pw4, pb4, ploss, loss_hist;
   DevBuf X, XT, Y, Yh, lab_tmp;
-  DevBuf iout, ixc, iwc, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
+  DevBuf iout, iwc, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
   DevBuf err, scal;
 };
 
@@ -895,7 +895,7 @@ extern "C" void surrogate_destroy(surrogate_t *s) {
   DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w1t, &s->w2b, &s->w2t, &s->w3b, &s->w3t,
                     &s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1,
                     &s->dP1T, &s->out, &s->part, &s->pw4, &s->pb4, &s->ploss, &s->loss_hist, &s->X, &s->XT,
-                    &s->Y, &s->Yh, &s->lab_tmp, &s->iout, &s->ixc, &s->iwc, &s->fb_idx, &s->fb_cnt,
+                    &s->Y, &s->Yh, &s->lab_tmp, &s->iout, &s->iwc, &s->fb_idx, &s->fb_cnt,
                     &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred, &s->err, &s->scal};
   for (DevBuf *b : bufs) b->release();
   delete s;
@@ -1063,9 +1063,8 @@ static int surr_forward_fused(surrogate *s, const float *q, int64_t n, float *ou
   a.fb_cnt = fb_cnt;
   a.err = s->err.as<int32_t>();
   a.wait_limit = g_wait_limit;
-  CK(s->ixc.ensure(mlp_xc_bytes(n)));
   CK(s->iwc.ensure(mlp_wc_bytes()));
-  CK(launch_mlp_fused(s->chain->cf, a, s->ixc.as<uint8_t>(), s->iwc.as<uint8_t>(), st));
+  CK(launch_mlp_fused(s->chain->cf, a, s->iwc.as<uint8_t>(), st));
   return FK_OK;
 }
 

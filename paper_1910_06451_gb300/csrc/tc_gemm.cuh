@@ -66,12 +66,10 @@ struct MlpArgs {
   int32_t *fb_idx, *fb_cnt;  // fallback list and its length
   int32_t *err;
   uint32_t wait_limit;
-  const uint8_t *xc, *wc;    // set by the launcher: tiled features and weights
+  const uint8_t *wc;         // set by the launcher: tiled weights
 };
-// xc: mlp_xc_bytes(n) bytes of scratch for the tiled features, wc:
-// mlp_wc_bytes() for the tiled weights.
-cudaError_t launch_mlp_fused(const ChainF &c, const MlpArgs &a, uint8_t *xc, uint8_t *wc, cudaStream_t s);
-size_t mlp_xc_bytes(int64_t n);
+// wc: mlp_wc_bytes() bytes of scratch for the tiled weights.
+cudaError_t launch_mlp_fused(const ChainF &c, const MlpArgs &a, uint8_t *wc, cudaStream_t s);
 size_t mlp_wc_bytes();
 
 constexpr int kSurrIn = 64;   // surrogate input width (56 features, zero-padded)
