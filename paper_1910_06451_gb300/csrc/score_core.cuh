@@ -160,10 +160,11 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     const float4 *tile = tiles + (size_t)(t & 1) * TP * REC;
     const int64_t p0 = (int64_t)t * TP;
     const int cnt = (int)(npair - p0 < TP ? npair - p0 : TP);
-    // four support pairs per loop trip: fewer loop and address instructions
-    // on a kernel bound by instruction dispatch (5.25 -> 5.11 ms on 4M 7-DOF
-    // queries), still within 128 registers for two CTAs per SM
-#pragma unroll 4
+    // eight support pairs per loop trip: fewer loop and address instructions
+    // on a kernel bound by instruction dispatch (4M 7-DOF queries: 5.25 ms
+    // one pair per trip, 5.11 ms four, 5.06 ms eight), still within 128
+    // registers for two CTAs per SM
+#pragma unroll 8
     for (int j = 0; j < cnt; ++j) {
       const float4 *r = tile + j * REC;
       f2 acc[Q];
