@@ -36,7 +36,7 @@ N_QUERY = 1 << 22
 # workload (4,194,304 queries, 800 support points), from an ncu capture of
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum): the
 # queries in and the labels out, no re-reads
-SCORE_TRAFFIC_BYTES = 117_568_000 + 4_515_072
+SCORE_TRAFFIC_BYTES = 117_803_008 + 4_629_248
 METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -362,7 +362,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=N_QUERY, help="query batch size (profiling runs use a smaller one)")
     ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
-    ap.add_argument("--surrogate-epochs", type=int, default=96)
+    ap.add_argument("--surrogate-epochs", type=int, default=192)
     ap.add_argument("--surrogate-lr", type=float, default=3e-3, help="peak of the cosine learning-rate schedule")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the multi-scene measurement (0: skip)")
     ap.add_argument("--dynamic-frames", type=int, default=8,
