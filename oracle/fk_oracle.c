@@ -108,28 +108,61 @@ double orc_k_rq(int dim, const double *x, const double *xp, double gamma)
     return 1.0 / (t * t);
 }
 
-/* FK kernel, Eq. 4: the mean over the M corresponding control points of the
- * RQ kernel, summed in ascending m.  cpa, cpb: M x 3 each. */
-double orc_k_fk(int M, const double *cpa, const double *cpb, double gamma)
+/* Gaussian summand exp(-gamma/2 * |x - x'|^2) between two dim-vectors.  NOT
+ * the paper's kernel: the paper builds the FK kernel from the RQ kernel of
+ * Eq. 3 only.  It is the library's optional alternative summand (the same
+ * mean over control points as Eq. 4, exp in place of the RQ term). */
+double orc_k_gauss(int dim, const double *x, const double *xp, double gamma)
+{
+    double d2 = 0.0;
+    for (int c = 0; c < dim; ++c) {
+        double dc = x[c] - xp[c];
+        d2 += dc * dc;
+    }
+    return exp(-0.5 * gamma * d2);
+}
+
+/* The summand of kind `kind`: 0 the RQ kernel of Eq. 3 (the paper's), 1 the
+ * Gaussian above. */
+static double summand(int kind, const double *x, const double *xp, double gamma)
+{
+    return kind == 1 ? orc_k_gauss(3, x, xp, gamma) : orc_k_rq(3, x, xp, gamma);
+}
+
+/* FK kernel, Eq. 4, with summand `kind`: the mean over the M corresponding
+ * control points, summed in ascending m.  cpa, cpb: M x 3 each. */
+double orc_k_fk_s(int M, const double *cpa, const double *cpb, double gamma, int kind)
 {
     double s = 0.0;
     for (int m = 0; m < M; ++m)
-        s += orc_k_rq(3, cpa + 3 * m, cpb + 3 * m, gamma);
+        s += summand(kind, cpa + 3 * m, cpb + 3 * m, gamma);
     return s / M;
 }
 
-/* Kernel matrix K[i][j] = K_FK(a_i, b_j) (Sec. II-B), na x nb. */
-void orc_gram(int M, double gamma, int64_t na, const double *cpa, int64_t nb, const double *cpb, double *K)
+/* FK kernel, Eq. 4, with the paper's RQ summand. */
+double orc_k_fk(int M, const double *cpa, const double *cpb, double gamma)
+{
+    return orc_k_fk_s(M, cpa, cpb, gamma, 0);
+}
+
+/* Kernel matrix K[i][j] = K_FK(a_i, b_j) (Sec. II-B), na x nb, summand kind. */
+void orc_gram_s(int M, double gamma, int64_t na, const double *cpa, int64_t nb, const double *cpb, double *K,
+                int kind)
 {
     for (int64_t i = 0; i < na; ++i)
         for (int64_t j = 0; j < nb; ++j)
-            K[i * nb + j] = orc_k_fk(M, cpa + i * M * 3, cpb + j * M * 3, gamma);
+            K[i * nb + j] = orc_k_fk_s(M, cpa + i * M * 3, cpb + j * M * 3, gamma, kind);
+}
+
+void orc_gram(int M, double gamma, int64_t na, const double *cpa, int64_t nb, const double *cpb, double *K)
+{
+    orc_gram_s(M, gamma, na, cpa, nb, cpb, K, 0);
 }
 
 /* ------------------------------------------------------------- score ---- */
 
 typedef struct {
-    int M;
+    int M, kind;
     double gamma;
     int64_t ns;
     const double *cps, *alpha;
@@ -144,7 +177,7 @@ static void *score_range(void *arg)
     for (int64_t k = j->lo; k < j->hi; ++k) {
         double f = 0.0;
         for (int64_t s = 0; s < j->ns; ++s)
-            f += j->alpha[s] * orc_k_fk(j->M, j->cps + s * j->M * 3, j->cpq + k * j->M * 3, j->gamma);
+            f += j->alpha[s] * orc_k_fk_s(j->M, j->cps + s * j->M * 3, j->cpq + k * j->M * 3, j->gamma, j->kind);
         j->f[k] = f;
     }
     return NULL;
@@ -154,8 +187,8 @@ static void *score_range(void *arg)
  * support points taken in ascending order.  Queries are split into nthreads
  * contiguous blocks; each query is summed by one thread, so the result does
  * not depend on nthreads. */
-int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *alpha, int64_t nq,
-              const double *cpq, double *f, int nthreads)
+int orc_score_s(int M, double gamma, int64_t ns, const double *cps, const double *alpha, int64_t nq,
+                const double *cpq, double *f, int nthreads, int kind)
 {
     if (nthreads < 1)
         nthreads = 1;
@@ -166,7 +199,7 @@ int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *
     int64_t per = (nq + nthreads - 1) / nthreads;
     int started = 0;
     for (int t = 0; t < nthreads; ++t) {
-        score_job j = {M, gamma, ns, cps, alpha, cpq, f, t * per, (t + 1) * per};
+        score_job j = {M, kind, gamma, ns, cps, alpha, cpq, f, t * per, (t + 1) * per};
         if (j.hi > nq)
             j.hi = nq;
         if (j.lo >= j.hi)
@@ -188,16 +221,23 @@ int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *
     return 0;
 }
 
+int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *alpha, int64_t nq,
+              const double *cpq, double *f, int nthreads)
+{
+    return orc_score_s(M, gamma, ns, cps, alpha, nq, cpq, f, nthreads, 0);
+}
+
 /* ----------------------------------------------------------- Fastron ---- */
 
 /* Column i of the kernel matrix over the training set (computeKernelMatrixColumn).
  * store32 != 0: every entry is rounded to the nearest FP32 value, the kernel
  * matrix as it is held when it is stored in single precision (65,536
  * training points take 17.2 GB in FP32); the margins and weights stay FP64. */
-static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col, int store32)
+static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col, int store32,
+                          int kind)
 {
     for (int64_t j = 0; j < N; ++j) {
-        double k = orc_k_fk(M, cpX + j * M * 3, cpX + i * M * 3, gamma);
+        double k = orc_k_fk_s(M, cpX + j * M * 3, cpX + i * M * 3, gamma, kind);
         col[j] = store32 ? (double)(float)k : k;
     }
 }
@@ -225,11 +265,12 @@ static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int
  * converged (1 if the loop ended by break), support size}.  If trace_kind is
  * not NULL, pass k records kind (1 add, 2 removal), index and delta (the
  * change of alpha_i) in trace_kind/trace_idx/trace_delta[k].  store32: see
- * kernel_column.
+ * kernel_column.  kind: the summand of the FK kernel, 0 the paper's RQ
+ * kernel (Eq. 3), 1 the Gaussian alternative (orc_k_gauss).
  */
-int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
-                            int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
-                            int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32)
+int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                           int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                           int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32, int kind)
 {
     double *col = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     if (!col)
@@ -251,7 +292,7 @@ int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, c
             }
         }
         if (i >= 0 && mmin <= 0.0) {
-            kernel_column(M, gamma, N, cpX, i, col, store32);
+            kernel_column(M, gamma, N, cpX, i, col, store32, kind);
             if (nnz < s_max || alpha[i] != 0.0) {
                 double b = y[i] > 0 ? beta : 1.0;
                 double delta = b * y[i] - F[i];
@@ -283,7 +324,7 @@ int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, c
             }
         }
         if (r >= 0 && mmax > 0.0) {
-            kernel_column(M, gamma, N, cpX, r, col, store32);
+            kernel_column(M, gamma, N, cpX, r, col, store32, kind);
             double a = alpha[r];
             for (int64_t j = 0; j < N; ++j)
                 F[j] = fma(-a, col[j], F[j]);
@@ -308,6 +349,14 @@ int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, c
     stats[3] = converged;
     stats[4] = nnz;
     return 0;
+}
+
+int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                            int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                            int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32)
+{
+    return orc_fastron_train_kind(M, gamma, N, cpX, y, beta, iter_max, s_max, alpha, F, stats, trace_kind,
+                                  trace_idx, trace_delta, store32, 0);
 }
 
 int orc_fastron_train(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,

@@ -71,6 +71,16 @@ def _load():
         lib.orc_gram.restype = None
         lib.orc_score.argtypes = [I, Dbl, I64, P, P, I64, P, P, I]
         lib.orc_score.restype = I
+        lib.orc_k_gauss.argtypes = [I, P, P, Dbl]
+        lib.orc_k_gauss.restype = Dbl
+        lib.orc_k_fk_s.argtypes = [I, P, P, Dbl, I]
+        lib.orc_k_fk_s.restype = Dbl
+        lib.orc_gram_s.argtypes = [I, Dbl, I64, P, I64, P, P, I]
+        lib.orc_gram_s.restype = None
+        lib.orc_score_s.argtypes = [I, Dbl, I64, P, P, I64, P, P, I, I]
+        lib.orc_score_s.restype = I
+        lib.orc_fastron_train_kind.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I, I]
+        lib.orc_fastron_train_kind.restype = I
         lib.orc_fastron_train.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P]
         lib.orc_fastron_train.restype = I
         lib.orc_fastron_train_store.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I]
@@ -125,36 +135,48 @@ def k_rq(x, xp, gamma: float) -> float:
     return _load().orc_k_rq(x.shape[0], _p(x), _p(xp), float(gamma))
 
 
-def k_fk(cpa, cpb, gamma: float) -> float:
+# Summand of the FK kernel: "rq" is the paper's (Eq. 3); "gauss" is the
+# library's non-paper alternative exp(-gamma/2 |x - x'|^2) in the same mean
+# over control points (Eq. 4 with exp in place of the RQ term).
+SUMMANDS = {"rq": 0, "gauss": 1}
+
+
+def k_gauss(x, xp, gamma: float) -> float:
+    """Gaussian summand exp(-gamma/2 |x - x'|^2) (not in the paper)."""
+    x, xp = _d(x), _d(xp)
+    return _load().orc_k_gauss(x.shape[0], _p(x), _p(xp), float(gamma))
+
+
+def k_fk(cpa, cpb, gamma: float, summand: str = "rq") -> float:
     """FK kernel, Eq. 4, between two (M, 3) control-point sets."""
     cpa, cpb = _d(cpa), _d(cpb)
-    return _load().orc_k_fk(cpa.shape[0], _p(cpa), _p(cpb), float(gamma))
+    return _load().orc_k_fk_s(cpa.shape[0], _p(cpa), _p(cpb), float(gamma), SUMMANDS[summand])
 
 
-def gram(cpa, cpb, gamma: float) -> np.ndarray:
+def gram(cpa, cpb, gamma: float, summand: str = "rq") -> np.ndarray:
     """Kernel matrix K_ij = K_FK(a_i, b_j) (Sec. II-B)."""
     cpa, cpb = _d(cpa), _d(cpb)
     na, M = cpa.shape[0], cpa.shape[1]
     nb = cpb.shape[0]
     K = np.empty((na, nb))
-    _load().orc_gram(M, float(gamma), na, _p(cpa), nb, _p(cpb), _p(K))
+    _load().orc_gram_s(M, float(gamma), na, _p(cpa), nb, _p(cpb), _p(K), SUMMANDS[summand])
     return K
 
 
-def score_points(cps, alpha, cpq, gamma: float, nthreads: int = 1) -> np.ndarray:
+def score_points(cps, alpha, cpq, gamma: float, nthreads: int = 1, summand: str = "rq") -> np.ndarray:
     """Fastron model value f(x) = sum_s alpha_s K_FK(S_s, x) (Sec. III-B) from control points."""
     cps, alpha, cpq = _d(cps), _d(alpha), _d(cpq)
     f = np.empty(cpq.shape[0])
-    rc = _load().orc_score(cps.shape[1] if cps.ndim == 3 else cpq.shape[1], float(gamma), cps.shape[0],
-                           _p(cps), _p(alpha), cpq.shape[0], _p(cpq), _p(f), int(nthreads))
+    rc = _load().orc_score_s(cps.shape[1] if cps.ndim == 3 else cpq.shape[1], float(gamma), cps.shape[0],
+                             _p(cps), _p(alpha), cpq.shape[0], _p(cpq), _p(f), int(nthreads), SUMMANDS[summand])
     if rc != 0:
         raise RuntimeError("orc_score failed")
     return f
 
 
-def score(arm, support_q, alpha, query_q, gamma: float, nthreads: int = 1) -> np.ndarray:
+def score(arm, support_q, alpha, query_q, gamma: float, nthreads: int = 1, summand: str = "rq") -> np.ndarray:
     """f for query configurations against a support set given as configurations."""
-    return score_points(fk_points(arm, support_q), alpha, fk_points(arm, query_q), gamma, nthreads)
+    return score_points(fk_points(arm, support_q), alpha, fk_points(arm, query_q), gamma, nthreads, summand)
 
 
 def labels_from_f(f) -> np.ndarray:
@@ -179,12 +201,14 @@ class TrainResult:
 
 
 def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000, s_max: int | None = None,
-                  alpha0=None, F0=None, trace: bool = False, store32: bool = False) -> TrainResult:
+                  alpha0=None, F0=None, trace: bool = False, store32: bool = False,
+                  summand: str = "rq") -> TrainResult:
     """Algorithm 1 (Sec. III-B) on training control points cpX (N, M, 3) and labels y in {+1, -1}.
 
     alpha0/F0 warm-start the model (loadPreviousModel); zeros otherwise.
     store32: kernel-matrix entries rounded to the nearest FP32 value (the
-    matrix held in single precision); margins and weights stay FP64."""
+    matrix held in single precision); margins and weights stay FP64.
+    summand: "rq" (the paper's kernel) or "gauss" (see SUMMANDS)."""
     cpX = _d(cpX)
     N, M = cpX.shape[0], cpX.shape[1]
     y = np.ascontiguousarray(y, dtype=np.int8)
@@ -199,8 +223,8 @@ def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000,
         tr = (_p(tk), _p(ti), _p(td))
     else:
         tr = (None, None, None)
-    rc = _load().orc_fastron_train_store(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
-                                         _p(alpha), _p(F), _p(stats), *tr, int(bool(store32)))
+    rc = _load().orc_fastron_train_kind(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
+                                        _p(alpha), _p(F), _p(stats), *tr, int(bool(store32)), SUMMANDS[summand])
     if rc != 0:
         raise RuntimeError("orc_fastron_train failed")
     tr_out = None
