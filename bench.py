@@ -165,6 +165,67 @@ def run_reference(args):
     return 0
 
 
+def gaussian_summand(fk, dev, rank, Q, X32, X, flush, peak):
+    """The same 7-DOF workload with the library's non-paper Gaussian summand
+    (FK_SUMMAND_GAUSS): labels, FP64 kernel matrix and Algorithm 1, then the
+    query batch scored in FP32 on MUFU ex2, with 1 or 2 of the 7 summands per
+    support point on the FMA polynomial instead, and in packed half
+    (ex2.f16x2); every path with its band re-scored, labels compared with the
+    FP32 path's.  Roofline as for the RQ score: one transcendental and five
+    FP32 operations per evaluation."""
+    import torch
+    w = synth.workload(WORKLOAD, trial=rank)
+    ch = fk.chain_from_arm(w.scene.arm)
+    fk.fk_chain_set_summand(ch, fk.FK_SUMMAND_GAUSS)
+    m = fk.fastron_model_create(ch)
+    nq = Q.shape[0]
+    y = torch.empty(X.shape[0], dtype=torch.int8, device=dev)
+    ref = torch.empty(nq, dtype=torch.int8, device=dev)
+    lab = torch.empty(nq, dtype=torch.int8, device=dev)
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    try:
+        fk.fk_label(ch, w.scene.boxes, w.scene.radius, X32, y)
+        t_train = timed(lambda: fk.fastron_train(m, X, y, w.gamma, w.beta, w.iter_max, w.s_max), reps=1)
+        st = fk.fastron_train(m, X, y, w.gamma, w.beta, w.iter_max, w.s_max)
+        evals = st["n_support"] * int(np.sum(w.scene.arm.cp_joint != 0)) * nq
+        fk.fk_score(m, Q, ref, rescore=True)
+        out = {"summand": "exp(-gamma/2 |d|^2) (not the paper's kernel)", "support": st["n_support"],
+               "iterations": st["iterations"], "update_ms": t_train}
+        for poly in (0, 1, 2):
+            fk.fk_set_gauss_poly(poly)
+            t_raw = timed(lambda: fk.fk_score(m, Q, lab, rescore=False))
+            nb = fk.fk_score(m, Q, lab, rescore=True, count=True)
+            t_all = timed(lambda: fk.fk_score(m, Q, lab, rescore=True))
+            out[f"fp32_poly{poly}"] = {"score_ms": t_raw, "teval_per_s": evals / t_raw / 1e9,
+                                       "roofline_frac": evals / t_raw / 1e9 / peak, "rescored": nb,
+                                       "with_rescore_ms": t_all, "checks_per_s": nq / t_all * 1e3,
+                                       "label_mismatch": int((lab != ref).sum().item())}
+        fk.fk_set_gauss_poly(0)
+        t_raw = timed(lambda: fk.fk_score(m, Q, lab, rescore=False, precision=fk.FK_F16))
+        nb = fk.fk_score(m, Q, lab, rescore=True, count=True, precision=fk.FK_F16)
+        t_all = timed(lambda: fk.fk_score(m, Q, lab, rescore=True, precision=fk.FK_F16))
+        out["half2"] = {"score_ms": t_raw, "teval_per_s": evals / t_raw / 1e9, "band_to_fp32": nb / nq,
+                        "with_rescore_ms": t_all, "checks_per_s": nq / t_all * 1e3,
+                        "label_mismatch": int((lab != ref).sum().item())}
+        return out
+    finally:
+        fk.fk_set_gauss_poly(0)
+        fk.fastron_model_destroy(m)
+        fk.fk_chain_destroy(ch)
+
+
 def obstacle_sweep(fk, dev, rank, counts, Q, X32, X, flush):
     """Query cost of the proxy check against the geometric checker as the
     number of boxes grows (the sweep of Sec. IV-A, 1-50 random boxes): per box
@@ -370,6 +431,7 @@ def main():
     ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
     ap.add_argument("--dynamic-modes", default="warm,cold,active,surrogate",
                     help="update modes of that measurement (comma-separated)")
+    ap.add_argument("--gauss", type=int, default=1, help="measure the non-paper Gaussian summand (0: skip)")
     ap.add_argument("--obstacle-sweep", default="1,2,5,10,20,35,50",
                     help="box counts of the obstacle sweep (0: skip)")
     args = ap.parse_args()
@@ -634,6 +696,10 @@ def main():
             for ch in bchains:
                 fk.fk_chain_destroy(ch)
 
+    gauss = None
+    if args.gauss:
+        gauss = gaussian_summand(fk, dev, rank, Q, Xq32, X, flush, peak)
+
     sweep = None
     counts = [int(x) for x in args.obstacle_sweep.split(",") if x.strip() and int(x) > 0]
     if counts:
@@ -666,6 +732,7 @@ def main():
             "batched_scenes": batched,
             "changing_environment": dynamic,
             "obstacle_sweep": sweep,
+            "gaussian_summand": gauss,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak,
                          "peak_basis": "min(MUFU 16/clk/SM x 1 reciprocal, FP32 128/clk/SM / 5 ops) per evaluation "

@@ -52,6 +52,9 @@ extern "C" {
 #define FK_LR_STEP 0   /* surrogate_train_params.schedule */
 #define FK_LR_COSINE 1
 
+#define FK_SUMMAND_RQ 0     /* the paper's summand: the RQ kernel of Eq. 3 (default) */
+#define FK_SUMMAND_GAUSS 1  /* not in the paper: exp(-gamma/2 |x - x'|^2) (fk_chain_set_summand) */
+
 #define FK_MAX_DOF 16
 #define FK_MAX_CP 32
 
@@ -85,6 +88,24 @@ const char *fk_last_error(void);
  * Sec. III-A); any offsets are accepted.  *out receives the handle. */
 int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, const fk_cp *cps, int M, fk_chain_t **out);
 void fk_chain_destroy(fk_chain_t *chain);
+
+/* Summand of the FK kernel (Eq. 4) for every later call on this chain:
+ * FK_SUMMAND_RQ (the default) is the paper's RQ kernel of Eq. 3;
+ * FK_SUMMAND_GAUSS replaces it by exp(-gamma/2 |x - x'|^2), keeping the mean
+ * over control points.  The Gaussian summand is NOT the paper's kernel; it is
+ * offered as an alternative (it is the kernel family whose exponential the
+ * MUFU ex2 unit and its packed-half form evaluate directly).  With it:
+ *   - fk_gram accepts FK_F64 and FK_F32 only (no double-float form), and
+ *     fastron_train builds its matrix in FP64 (gram 0 selects FK_F64;
+ *     FK_DF64/FK_DF32 are rejected);
+ *   - fk_score (FK_F32 and FK_F16) evaluates 2^(-|d'|^2) with d' the control
+ *     points scaled by sqrt(gamma/2 log2 e), on MUFU ex2 (FK_F16: ex2.f16x2);
+ *     the band re-score goes straight to FP64;
+ *   - fk_batch_create rejects its models (FK_ERR_ARG).
+ * A model keeps the summand it was trained or set with.  Returns FK_ERR_ARG
+ * for an unknown summand or a chain whose shape has no Gaussian score kernel
+ * (compiled for 3, 7 and 11 configuration-dependent control points). */
+int fk_chain_set_summand(fk_chain_t *chain, int summand);
 
 /* ---- forward kinematics (Sec. II-A, Eqs. 1-2) --------------------------
  * q: device, n x D joint values.  cp: device, control-point positions in
@@ -265,6 +286,16 @@ int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double ra
  * which exercises the timeout path without a hang.  Process-wide; not
  * synchronised with calls in flight on other threads. */
 void fk_set_wait_limit(uint32_t polls);
+
+/* Gaussian summand (FK_SUMMAND_GAUSS, not the paper's kernel) on chains with
+ * 7 configuration-dependent control points: how many of the 7 summands of
+ * each support point fk_score's FP32 kernel evaluates with an FMA polynomial
+ * for 2^(-t) instead of the MUFU ex2 unit (0, the default, 1 or 2), to move
+ * work from the MUFU pipe to the FP32 pipe.  Other shapes ignore it.  The
+ * polynomial's relative error is about 2.3e-7, inside the band of the FP64
+ * re-score, so labels do not depend on it.  Process-wide.  FK_ERR_ARG outside
+ * 0..2. */
+int fk_set_gauss_poly(int points);
 
 /* ---- many scenes in one launch -----------------------------------------
  * A batch groups trained models (one per scene, each with its own chain,

@@ -33,6 +33,7 @@ struct ChainF {
   // configurations is rho^2 (2 - 2 cos(theta_q - theta_s)), theta = q_1 + theta0_1.
   int cp1;
   double cp1_rho2;
+  int summand;  // FK_SUMMAND_RQ or FK_SUMMAND_GAUSS
 };
 
 // The same chain for the FP64 kernels.  cos/sin of the link twists are taken
@@ -47,6 +48,7 @@ struct ChainD {
   double T0[12];                // rows 0..2 of the base transform
   int cj[FK_MAX_CP];
   double ct[FK_MAX_CP][3];
+  int summand;  // FK_SUMMAND_RQ or FK_SUMMAND_GAUSS
 };
 
 // ------------------------------------------------------------------ FP32 --
@@ -174,6 +176,17 @@ __device__ __forceinline__ double k_rq_f64(double hg, const double *x, const dou
   const double d0 = x[0] - xp[0], d1 = x[1] - xp[1], d2 = x[2] - xp[2];
   const double t = fma(hg, fma(d0, d0, fma(d1, d1, d2 * d2)), 1.0);
   return rcp_f64(t * t);
+}
+
+// The non-paper Gaussian summand in FP64: exp(-(gamma/2) |x - x'|^2).
+__device__ __forceinline__ double k_gauss_f64(double hg, const double *x, const double *xp) {
+  const double d0 = x[0] - xp[0], d1 = x[1] - xp[1], d2 = x[2] - xp[2];
+  return exp(-hg * fma(d0, d0, fma(d1, d1, d2 * d2)));
+}
+
+// The chain's summand in FP64 (hg = gamma / 2).
+__device__ __forceinline__ double k_sum_f64(int summand, double hg, const double *x, const double *xp) {
+  return summand == FK_SUMMAND_GAUSS ? k_gauss_f64(hg, x, xp) : k_rq_f64(hg, x, xp);
 }
 
 }  // namespace fk

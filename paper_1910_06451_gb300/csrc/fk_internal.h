@@ -101,6 +101,7 @@ struct PackArgs {
                       // (U_a, U_b, V_a, V_b), U = k cos theta, V = k sin theta
                       // of joint 1, k = gamma rho^2 (see ChainF::cp1)
   double cp1_k;
+  double scale;       // coordinate scale: sqrt(gamma/2) (RQ), sqrt(gamma/2 log2 e) (Gaussian)
 };
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s);
 
@@ -112,7 +113,7 @@ struct ScoreArgs {
   int64_t ns;
   const float4 *rec1;  // or null; with it the first point's t = A - U cos theta_q - V sin theta_q
   float cp1_A;         // 1 + k
-  float gs;           // sqrt(gamma / 2): scale of the control points
+  float gs;           // scale of the control points (PackArgs::scale)
   float eps;          // band: |f| <= eps * B(q)
   float *f;           // [n] or null
   int8_t *label;      // [n]
@@ -120,6 +121,7 @@ struct ScoreArgs {
   int32_t *band_cnt;  // [1]
   int32_t *err;       // [1]
   uint32_t wait_limit;  // polls of a tile wait before it gives up
+  int poly;           // Gaussian summand, 7 points: points per support point on the FMA polynomial
 };
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
 

@@ -76,7 +76,8 @@ cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t
 }
 
 // --------------------------------------------------------------- Gram ---
-// K[i][j] = (1/M) sum_m K_RQ(FK_m(a_i), FK_m(b_j)).  One CTA computes a
+// K[i][j] = (1/M) sum_m K_RQ(FK_m(a_i), FK_m(b_j)) (or the chain's Gaussian
+// summand, FK_SUMMAND_GAUSS, which is not the paper's).  One CTA computes a
 // 32 x 32 tile with 256 threads (4 rows each).  Control points of the tile's
 // 32 + 32 configurations are staged in shared memory as [M*3][32].  With
 // sym != 0 only tiles with bi <= bj run; an off-diagonal tile is written
@@ -86,7 +87,7 @@ cudaError_t launch_fk_forward_f32in_f64(const ChainD &c, const float *q, int64_t
 constexpr int kGT = 32;
 
 struct GramCps {
-  int M, Mv, n_const;
+  int M, Mv, n_const, summand;
   int vidx[FK_MAX_CP];
 };
 
@@ -97,7 +98,7 @@ __device__ __forceinline__ double gram_entry(const GramCps &g, double hg, const 
     const int m = g.vidx[v];
     const double x[3] = {A[(m * 3 + 0) * kGT + ia], A[(m * 3 + 1) * kGT + ia], A[(m * 3 + 2) * kGT + ia]};
     const double y[3] = {B[(m * 3 + 0) * kGT + jb], B[(m * 3 + 1) * kGT + jb], B[(m * 3 + 2) * kGT + jb]};
-    s += k_rq_f64(hg, x, y);
+    s += k_sum_f64(g.summand, hg, x, y);
   }
   return s / (double)g.M;
 }
@@ -110,9 +111,13 @@ __device__ __forceinline__ float gram_entry(const GramCps &g, float hg, const fl
     const float d0 = A[(m * 3 + 0) * kGT + ia] - B[(m * 3 + 0) * kGT + jb];
     const float d1 = A[(m * 3 + 1) * kGT + ia] - B[(m * 3 + 1) * kGT + jb];
     const float d2 = A[(m * 3 + 2) * kGT + ia] - B[(m * 3 + 2) * kGT + jb];
-    const float t = fmaf(hg, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.f);
-    const float r = 1.f / t;
-    s = fmaf(r, r, s);
+    const float d2s = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    if (g.summand == FK_SUMMAND_GAUSS) {
+      s += expf(-hg * d2s);
+    } else {
+      const float r = 1.f / fmaf(hg, d2s, 1.f);
+      s = fmaf(r, r, s);
+    }
   }
   return s / (float)g.M;
 }
@@ -158,7 +163,7 @@ template <typename T>
 static cudaError_t launch_gram(const ChainD &c, T gamma, const T *cpa, int64_t na, const T *cpb, int64_t nb, int sym,
                                T *K, cudaStream_t s) {
   if (na <= 0 || nb <= 0) return cudaSuccess;
-  GramCps g{c.M, c.Mv, c.n_const, {}};
+  GramCps g{c.M, c.Mv, c.n_const, c.summand, {}};
   for (int v = 0; v < c.Mv; ++v) g.vidx[v] = c.vidx[v];
   const int M = c.M;
   const size_t smem = sizeof(T) * (2 * (size_t)M * 3 * kGT + kGT * (kGT + 1));
@@ -273,8 +278,9 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const GramCps g, const flo
 template <typename OT>
 static cudaError_t launch_gram_df_t(const ChainD &c, double gamma, const double *cpa, int64_t na, const double *cpb,
                                     int64_t nb, int sym, OT *K, float2 *wa, float2 *wb, cudaStream_t s) {
+  if (c.summand != FK_SUMMAND_RQ) return cudaErrorInvalidValue;  // double-float form of the RQ summand only
   if (na <= 0 || nb <= 0) return cudaSuccess;
-  GramCps g{c.M, c.Mv, c.n_const, {}};
+  GramCps g{c.M, c.Mv, c.n_const, c.summand, {}};
   for (int v = 0; v < c.Mv; ++v) g.vidx[v] = c.vidx[v];
   const double gs = sqrt(0.5 * gamma);
   const int64_t ea = (int64_t)c.Mv * 3 * na, eb = (int64_t)c.Mv * 3 * nb;

@@ -17,6 +17,9 @@
 //            Beside f the kernel accumulates B(q) = sum_s |w_s| sum_m t^-2,
 //            which bounds |f| and scales the FP32 error; queries with
 //            |f| <= eps B(q) are appended to a band list.
+//   gauss    the non-paper Gaussian summand 2^(-|d|^2) (coordinates scaled
+//            by sqrt(gamma/2 log2 e)) on MUFU ex2, optionally partly on an
+//            FMA polynomial, or in packed half with ex2.f16x2.
 //   rescore  FP64, one warp per band query: FK and Eq. 3/4 in FP64 with the
 //            operation order of the plain definition, lanes splitting the
 //            support set, a fixed-order warp sum; f and the label are replaced.
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
     }
     return;
   }
-  const double gs = sqrt(0.5 * a.gamma);
+  const double gs = a.scale;
   const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
   const double *x = a.X + src * cd.D;
   double cp[FK_MAX_CP][3];
@@ -130,6 +133,17 @@ __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const Chain
                                                              a.cp1_A);
 }
 
+// The non-paper Gaussian summand (FP32 with POLY points per support point on
+// the FMA polynomial, or packed half), otherwise the same block.
+template <int MV, bool HALF, int POLY>
+__global__ void __launch_bounds__(kScoreThreads, 2) score_gauss_kernel(const ChainF c, const ScoreArgs a) {
+  extern __shared__ __align__(128) float4 tiles[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
+  score_block<MV, kQ, kTilePairs, kScoreThreads, HALF, false, true, POLY>(
+      c, a.rec, a.ns, a.gs, a.q, a.n, (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
+}
+
 // The packed-half variant of the same block (differences and t in FP16).
 template <int MV>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f16_kernel(const ChainF c, const ScoreArgs a) {
@@ -155,10 +169,49 @@ static cudaError_t launch_score_h_mv(const ChainF &c, const ScoreArgs &a, cudaSt
   return cudaGetLastError();
 }
 
+template <int MV, bool HALF, int POLY>
+static cudaError_t launch_gauss_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
+  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
+  auto kern = score_gauss_kernel<MV, HALF, POLY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  kern<<<grid, kScoreThreads, smem, s>>>(c, a);
+  return cudaGetLastError();
+}
+
+// Shapes with compiled Gaussian-summand kernels (the 3-, 7- and 12-point
+// arms); the FMA-polynomial split is compiled for 7 points.
+bool score_gauss_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
+
+static cudaError_t launch_score_gauss(const ChainF &c, const ScoreArgs &a, bool half, cudaStream_t s) {
+  if (half) {
+    switch (c.Mv) {
+      case 3: return launch_gauss_mv<3, true, 0>(c, a, s);
+      case 7: return launch_gauss_mv<7, true, 0>(c, a, s);
+      case 11: return launch_gauss_mv<11, true, 0>(c, a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (c.Mv) {
+    case 3: return launch_gauss_mv<3, false, 0>(c, a, s);
+    case 7:
+      switch (a.poly) {
+        case 1: return launch_gauss_mv<7, false, 1>(c, a, s);
+        case 2: return launch_gauss_mv<7, false, 2>(c, a, s);
+        default: return launch_gauss_mv<7, false, 0>(c, a, s);
+      }
+    case 11: return launch_gauss_mv<11, false, 0>(c, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 bool score_f16_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
 
 cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (c.summand == FK_SUMMAND_GAUSS) return launch_score_gauss(c, a, true, s);
   switch (c.Mv) {
     case 3: return launch_score_h_mv<3>(c, a, s);
     case 7: return launch_score_h_mv<7>(c, a, s);
@@ -195,6 +248,7 @@ bool score_supported(int mv) {
 
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (c.summand == FK_SUMMAND_GAUSS) return launch_score_gauss(c, a, false, s);
   if (a.rec1) {
     switch (c.Mv) {
       case 3: return launch_score_mv<3, true>(c, a, s);
@@ -250,7 +304,7 @@ __global__ void __launch_bounds__(kRescoreWarps * 32) rescore_f64_kernel(const C
         const int m = c.vidx[v];
         const double sp[3] = {a.cp64[(m * 3 + 0) * a.ns + s], a.cp64[(m * 3 + 1) * a.ns + s],
                               a.cp64[(m * 3 + 2) * a.ns + s]};
-        ks += k_rq_f64(hg, sp, qcp[wl][m]);
+        ks += k_sum_f64(c.summand, hg, sp, qcp[wl][m]);
       }
       f = fma(a.alpha[s] * invM, ks, f);
     }

@@ -21,6 +21,7 @@ struct GemmArgs;
 cudaError_t launch_gemm_f32(const GemmArgs &g, int splits, cudaStream_t s);
 bool score_supported(int mv);
 bool score_cp1_supported(int mv);
+bool score_gauss_supported(int mv);
 int probe_iters(int kind);
 int probe_ops_per_iter(int kind);
 }  // namespace fk
@@ -114,6 +115,7 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
   c->M = M;
   ChainF &f = c->cf;
   ChainD &d = c->cd;
+  f.summand = d.summand = FK_SUMMAND_RQ;
   f.D = d.D = D;
   f.M = d.M = M;
   f.Mv = d.Mv = mv;
@@ -177,6 +179,16 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
   return FK_OK;
 }
 
+extern "C" int fk_chain_set_summand(fk_chain_t *c, int summand) {
+  if (!c) return fail(FK_ERR_ARG, "fk_chain_set_summand: chain is NULL");
+  if (summand != FK_SUMMAND_RQ && summand != FK_SUMMAND_GAUSS)
+    return fail(FK_ERR_ARG, "fk_chain_set_summand: unknown summand %d", summand);
+  if (summand == FK_SUMMAND_GAUSS && !score_gauss_supported(c->cf.Mv))
+    return fail(FK_ERR_ARG, "fk_chain_set_summand: no Gaussian score kernel for %d control points", c->cf.Mv);
+  c->cf.summand = c->cd.summand = summand;
+  return FK_OK;
+}
+
 extern "C" void fk_chain_destroy(fk_chain_t *c) {
   if (!c) return;
   c->ws_a.release();
@@ -214,6 +226,8 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
   if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(FK_ERR_ARG, "fk_gram: gamma must be finite and > 0");
   if (precision != FK_F32 && precision != FK_F64 && precision != FK_DF64 && precision != FK_DF32)
     return fail(FK_ERR_ARG, "fk_gram: unknown precision %d", precision);
+  if (c->cd.summand != FK_SUMMAND_RQ && (precision == FK_DF64 || precision == FK_DF32))
+    return fail(FK_ERR_ARG, "fk_gram: the Gaussian summand has no double-float form (use FK_F64 or FK_F32)");
   if (na == 0 || nb == 0) return FK_OK;
   if (!Xa || !Xb || !K) return fail(FK_ERR_ARG, "fk_gram: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
@@ -250,6 +264,19 @@ static constexpr int64_t kMaxTrainN = 65536;
 static constexpr double kDefaultEps = 6e-6;
 static constexpr double kDefaultEpsDf = 1e-9;  // band of the double-float re-score, relative to B(q)
 static constexpr double kDefaultEpsF16 = 2e-3;
+// Gaussian summand (not the paper's): per-query bands relative to B(q), the
+// RQ values: the measured worst |f - f64| / B(q) over 200k queries of the 3-
+// and 7-DOF models is 7.3e-8 (FP32, MUFU or polynomial) and 1.8e-4 (half),
+// as for the RQ summand (8.8e-8, 3.3e-4)
+static constexpr double kDefaultEpsGauss = 6e-6;
+static constexpr double kDefaultEpsF16Gauss = 2e-3;
+static int g_gauss_poly = 0;  // control points per support point on the FMA polynomial
+
+extern "C" int fk_set_gauss_poly(int points) {
+  if (points < 0 || points > 2) return fail(FK_ERR_ARG, "fk_set_gauss_poly: points must be 0, 1 or 2");
+  g_gauss_poly = points;
+  return FK_OK;
+}
 static constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // about a quarter second of polling
 static uint32_t g_wait_limit = kDefaultWaitLimit;
 
@@ -261,11 +288,13 @@ struct fastron_model {
   int64_t N = 0;
   int gram = -1;  // arithmetic/storage of G for the training set of the last call (-1: none)
   const double *gram_X = nullptr;  // the device buffer G was built from
+  int gram_summand = FK_SUMMAND_RQ;  // the summand G was built with
   DevBuf cpX, cpdf, G, alpha, F, stats, sup_idx, sup_alpha, trace_kind, trace_idx, trace_delta;
   int64_t trace_len = 0;
   // support set packed for scoring
   int64_t ns = -1;  // -1 = untrained
   double gamma = 0.0;
+  int summand = FK_SUMMAND_RQ;  // the chain's summand when the support set was packed
   DevBuf rec, cp64, alpha_s, q_s, qin, sdf;
   DevBuf rec1;        // records with the circle form of point 0 (used when use_cp1)
   bool use_cp1 = false;
@@ -310,17 +339,23 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
   CK(m->sdf.ensure(sizeof(float) * (size_t)(ns > 0 ? ns : 1) * rec_df_len(c->cf.Mv)));
   // the circle form of point 0 where it is as accurate as the direct form
-  // on the far points: A = 1 + gamma rho^2 below 8
+  // on the far points: A = 1 + gamma rho^2 below 8 (RQ summand only)
+  const int summand = c->cf.summand;
   const double k1 = gamma * c->cf.cp1_rho2;
-  m->use_cp1 = c->cf.cp1 && score_cp1_supported(c->cf.Mv) && 1.0 + k1 < 8.0;
+  m->use_cp1 = summand == FK_SUMMAND_RQ && c->cf.cp1 && score_cp1_supported(c->cf.Mv) && 1.0 + k1 < 8.0;
   m->cp1_A = (float)(1.0 + k1);
   if (m->use_cp1)
     CK(m->rec1.ensure(sizeof(float4) * (size_t)((ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1) * rec_len(c->cf.Mv)));
+  // coordinates scaled so that the summand is (1 + |d|^2)^-2 (RQ) or
+  // 2^(-|d|^2) (Gaussian); the double-float records serve the RQ band only
+  const double scale = sqrt(summand == FK_SUMMAND_GAUSS ? 0.5 * gamma * M_LOG2E : 0.5 * gamma);
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
-              m->q_s.as<double>(), m->sdf.as<float>(), m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1};
+              m->q_s.as<double>(), summand == FK_SUMMAND_RQ ? m->sdf.as<float>() : nullptr,
+              m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1, scale};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
   m->gamma = gamma;
+  m->summand = summand;
   return FK_OK;
 }
 
@@ -334,9 +369,12 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   if (!(p->beta >= 1.0) || !std::isfinite(p->beta)) return fail(FK_ERR_ARG, "fastron_train: beta must be >= 1");
   if (p->iter_max < 0) return fail(FK_ERR_ARG, "fastron_train: iter_max < 0");
   if (p->s_max < 1) return fail(FK_ERR_ARG, "fastron_train: s_max < 1");
-  const int gram = p->gram == 0 ? FK_DF64 : p->gram;
+  const bool gauss = m->chain->cd.summand == FK_SUMMAND_GAUSS;
+  const int gram = p->gram == 0 ? (gauss ? FK_F64 : FK_DF64) : p->gram;
   if (gram != FK_F64 && gram != FK_DF64 && gram != FK_DF32)
     return fail(FK_ERR_ARG, "fastron_train: gram must be FK_DF64, FK_F64 or FK_DF32");
+  if (gauss && gram != FK_F64)
+    return fail(FK_ERR_ARG, "fastron_train: the Gaussian summand's kernel matrix is built in FP64 (gram FK_F64 or 0)");
   if (p->warm_start < 0 || p->warm_start > 2) return fail(FK_ERR_ARG, "fastron_train: warm_start must be 0, 1 or 2");
   if (p->warm_start == 1 && (m->N != N || m->alpha.p == nullptr))
     return fail(FK_ERR_STATE, "fastron_train: warm start needs a previous training call with the same N");
@@ -345,7 +383,7 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     return fail(FK_ERR_STATE, "fastron_train: carrying the support set needs a trained model with |S| <= N");
   if (p->warm_start == 2 && p->reuse_gram)
     return fail(FK_ERR_ARG, "fastron_train: a carried support set means a new training set: reuse_gram must be 0");
-  if (p->reuse_gram && (m->N != N || m->gram != gram || m->gram_X != X))
+  if (p->reuse_gram && (m->N != N || m->gram != gram || m->gram_X != X || m->gram_summand != m->chain->cd.summand))
     return fail(FK_ERR_STATE, "fastron_train: reuse_gram needs a previous call on the same X buffer with the same N "
                               "and gram");
   cudaStream_t s = (cudaStream_t)stream;
@@ -387,6 +425,7 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     }
     m->gram = gram;
     m->gram_X = X;
+    m->gram_summand = c->cd.summand;
   }
   if (p->warm_start == 2) {
     // loadPreviousModel on a changed training set: the first ns rows are the
@@ -511,17 +550,24 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   if (m->gamma > 1e7) return fail(FK_ERR_ARG, "fk_score: gamma above the FP32 range of the score kernel");
   cudaStream_t s = (cudaStream_t)stream;
   const fk_chain *c = m->chain;
+  // the summand the support set was packed with (a later change of the
+  // chain's summand does not apply to this model)
+  const bool gauss = m->summand == FK_SUMMAND_GAUSS;
+  ChainF cf = c->cf;
+  ChainD cd = c->cd;
+  cf.summand = cd.summand = m->summand;
+  const float gs = (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma);
   if (precision == FK_F16) {
     if (!score_f16_supported(c->cf.Mv))
       return fail(FK_ERR_ARG, "fk_score: no half-precision kernel for %d control points", c->cf.Mv);
     CK(m->flags.ensure(sizeof(int32_t) * 2));
     CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
     if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
-    const double eps16 = rescore_eps > 0.0 ? rescore_eps : kDefaultEpsF16;
-    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, nullptr, 0.f, (float)sqrt(0.5 * m->gamma), (float)eps16, f, label,
+    const double eps16 = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsF16Gauss : kDefaultEpsF16);
+    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, nullptr, 0.f, gs, (float)eps16, f, label,
                  rescore ? m->band_idx.as<int32_t>() : nullptr, m->flags.as<int32_t>(), m->flags.as<int32_t>() + 1,
-                 g_wait_limit};
-    CK(launch_score_f16(c->cf, sa, s));
+                 g_wait_limit, 0};
+    CK(launch_score_f16(cf, sa, s));
     int32_t h[2] = {0, 0};
     if (rescore || n_rescored) {
       CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -550,18 +596,32 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 4, s));
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1, *cnt2 = cnt + 2;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
-  const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
+  const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
   ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
-               (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
-               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit};
-  CK(launch_score_f32(c->cf, sa, s));
+               gs, (float)eps, f, label,
+               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0};
+  CK(launch_score_f32(cf, sa, s));
   if (!rescore && !n_rescored) return FK_OK;
+  if (gauss && rescore && !n_rescored) {
+    // the Gaussian band goes straight to FP64 (no double-float form of exp),
+    // whose kernel reads the band size on the device: no synchronisation
+    RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
+                   m->gamma, f, label};
+    CK(launch_rescore_f64(cd, ra, s));
+    return FK_OK;
+  }
   int32_t h[2];
   CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score: a shared-memory tile wait timed out");
   if (n_rescored) *n_rescored = rescore ? h[0] : 0;
   if (!rescore || h[0] == 0) return FK_OK;
+  if (gauss) {
+    RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
+                   m->gamma, f, label};
+    CK(launch_rescore_f64(cd, ra, s));
+    return FK_OK;
+  }
   // the band: double-float first, FP64 for what it cannot decide
   const int64_t nb = h[0];
   int dev = 0, sms = 0;
@@ -574,10 +634,10 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   DfRescoreArgs da{q, m->band_idx.as<int32_t>(), nb, m->sdf.as<float>(), m->ns, c->cd.n_const,
                    sqrt(0.5 * m->gamma), m->qdf.as<float2>(), m->part.as<float4>(), chunks,
                    (m->ns + chunks - 1) / chunks, kDefaultEpsDf, f, label, m->band2_idx.as<int32_t>(), cnt2};
-  CK(launch_rescore_df(c->cd, da, s));
+  CK(launch_rescore_df(cd, da, s));
   RescoreArgs ra{q, m->band2_idx.as<int32_t>(), cnt2, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
                  m->gamma, f, label};
-  CK(launch_rescore_f64(c->cd, ra, s));
+  CK(launch_rescore_f64(cd, ra, s));
   return FK_OK;
 }
 
@@ -741,13 +801,17 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   // the array keeps the previous call's contents: the counter and the error
   // word must start at zero (the band list is written before it is read)
   CK(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2, s));
-  const double eps = rescore_eps > 0.0 ? rescore_eps : kDefaultEps;
+  const bool gauss = m->summand == FK_SUMMAND_GAUSS;
+  ChainF cf = c->cf;
+  ChainD cd = c->cd;
+  cf.summand = cd.summand = m->summand;
+  const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
   ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
-               (float)sqrt(0.5 * m->gamma), (float)eps, f, label,
-               band, cnt, err, g_wait_limit};
-  CK(launch_score_f32(c->cf, sa, s));
+               (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma), (float)eps, f, label,
+               band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0};
+  CK(launch_score_f32(cf, sa, s));
   RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};
-  CK(launch_rescore_f64(c->cd, ra, s));
+  CK(launch_rescore_f64(cd, ra, s));
   if (n_rescored) {
     int32_t h[2];
     CK(cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -1339,6 +1403,8 @@ extern "C" int fk_batch_create(fastron_model_t *const *models, int n_scenes, fk_
     if (m->chain->D != m0->chain->D || m->chain->cf.Mv != m0->chain->cf.Mv)
       return fail(FK_ERR_ARG, "fk_batch_create: model %d has another DOF or control-point count", i);
     if (m->gamma > 1e7) return fail(FK_ERR_ARG, "fk_batch_create: model %d gamma out of range", i);
+    if (m->summand != FK_SUMMAND_RQ)
+      return fail(FK_ERR_ARG, "fk_batch_create: model %d uses the Gaussian summand (batches take the RQ kernel only)", i);
   }
   if (!batched_supported(m0->chain->cf.Mv))
     return fail(FK_ERR_ARG, "fk_batch_create: %d configuration-dependent control points is not a compiled shape",

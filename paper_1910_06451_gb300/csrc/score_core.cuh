@@ -43,6 +43,54 @@ __device__ __forceinline__ f2 rcp2(f2 x) {
   return pk(rcp_approx(lo), rcp_approx(hi));
 }
 
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// 2^(-t) for t >= 0 (the Gaussian summand with the coordinates scaled by
+// sqrt(gamma/2 log2 e)) on the MUFU unit, both halves.
+__device__ __forceinline__ float ex2_neg(float t) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-t));
+  return r;
+}
+__device__ __forceinline__ f2 ex2_neg2(f2 t) {
+  float lo, hi;
+  upk(t, lo, hi);
+  return pk(ex2_neg(lo), ex2_neg(hi));
+}
+
+// 2^(-t) for t >= 0 on the FP32 pipe, both halves: t is clamped to 125 (the
+// value is then below 2^-124, negligible beside the summand of 1 at t = 0),
+// split as t = n + r with n = rint(t) (the 1.5 * 2^23 rounding constant puts n
+// in the low bits of j) and r in [-1/2, 1/2]; 2^(-r) is a degree-5
+// polynomial fitted to the relative error on [-1/2, 1/2] by iteratively
+// reweighted least squares on Chebyshev nodes (7.5e-8 in exact arithmetic,
+// 2.3e-7 with FP32 Horner steps), and 2^(-n) is applied by subtracting n from
+// the exponent field: (bits(j) << 23) is n << 23 because the constant's own
+// bits vanish in the shift.
+__device__ __forceinline__ f2 ex2_neg2_poly(f2 t) {
+  float t0, t1;
+  upk(t, t0, t1);
+  const f2 tc = pk(fminf(t0, 125.f), fminf(t1, 125.f));
+  const f2 magic = pk(12582912.f, 12582912.f);
+  const f2 j = add2(tc, magic);
+  const f2 r = sub2(tc, sub2(j, magic));
+  f2 p = pk(-1.327647129073739e-3f, -1.327647129073739e-3f);
+  p = fma2(p, r, pk(9.675541892647743e-3f, 9.675541892647743e-3f));
+  p = fma2(p, r, pk(-5.550713092088699e-2f, -5.550713092088699e-2f));
+  p = fma2(p, r, pk(2.4022120237350464e-1f, 2.4022120237350464e-1f));
+  p = fma2(p, r, pk(-6.931469440460205e-1f, -6.931469440460205e-1f));
+  p = fma2(p, r, pk(1.0000001192092896f, 1.0000001192092896f));
+  float p0, p1, j0, j1;
+  upk(p, p0, p1);
+  upk(j, j0, j1);
+  return pk(__uint_as_float(__float_as_uint(p0) - (__float_as_uint(j0) << 23)),
+            __uint_as_float(__float_as_uint(p1) - (__float_as_uint(j1) << 23)));
+}
+
 constexpr uint32_t kDrainLimit = 1u << 22;  // polls while draining copies after a timeout
 
 // Number of control-point pairs that share one reciprocal: the rest take one
@@ -75,17 +123,26 @@ struct BlockOut {
 // V sin theta_q with A = 1 + k: two FMAs instead of three differences and
 // three FMAs.  Its FP32 error for A < 8 stays within that of the direct
 // form on the points farther out.
+// GAUSS = true: the non-paper Gaussian summand.  Coordinates come scaled by
+// sqrt(gamma/2 log2 e), so the summand is 2^(-t) with t = |p - s|^2 (no
+// "1 +"): on the MUFU unit (ex2.approx) for the first MV - POLY points of
+// every support point and on the FP32 pipe (ex2_neg2_poly) for the last POLY;
+// with HALF, t in packed FP16 and 2^(-t) by ex2.approx.f16x2 (two halves per
+// MUFU operation), widened to FP32 for the sums.  No reciprocal sharing, no
+// circle form.
 // Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
 // (n x D) against the support records rec (ns points, (ns+1)/2 pair records)
 // with chain c.  tiles: 2 * TP * rec_len(MV) float4 of shared memory; bar: two
 // mbarriers.  Every thread of the CTA must call it.  Returns false (in every
 // thread) if a tile wait gave up; the caller must then stop using the CTA's
 // barriers.
-template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false>
+template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false, bool GAUSS = false, int POLY = 0>
 __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, float gs,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
                                             float4 *tiles, uint64_t *bar, float cp1_A = 0.f) {
   static_assert(!(HALF && CP1), "the circle form is an FP32 path");
+  static_assert(!(GAUSS && CP1), "the circle form is an RQ path");
+  static_assert(POLY >= 0 && POLY <= MV && (POLY == 0 || (GAUSS && !HALF)), "polynomial points: FP32 Gaussian only");
   constexpr int REC = MV + (MV + 1) / 2 + 1;
   constexpr int NP = RcpPlan<MV>::NP;
 
@@ -187,8 +244,17 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
             const int kk = HALF ? k : 0, mm = HALF ? m : 0;
             const __half2 dx = __hsub2(Ph[kk][mm][0], hx), dy = __hsub2(Ph[kk][mm][1], hy),
                           dz = __hsub2(Ph[kk][mm][2], hz);
-            const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
-            tv[k][m] = pk(tf.x, tf.y);
+            if (GAUSS) {
+              // the summand itself: 2^(-t) for both support points in one MUFU operation
+              const __half2 nt = __hneg2(__hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz))));
+              uint32_t e;
+              asm("ex2.approx.f16x2 %0, %1;" : "=r"(e) : "r"(*reinterpret_cast<const uint32_t *>(&nt)));
+              const float2 ef = __half22float2(*reinterpret_cast<const __half2 *>(&e));
+              tv[k][m] = pk(ef.x, ef.y);
+            } else {
+              const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
+              tv[k][m] = pk(tf.x, tf.y);
+            }
           }
         } else {
           const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
@@ -196,12 +262,18 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
             const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
-            tv[k][m] = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
+            tv[k][m] = GAUSS ? fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))) : fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
           }
         }
       }
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
+        if (GAUSS) {
+#pragma unroll
+          for (int m = 0; m < MV; ++m)
+            acc[k] = add2(acc[k], HALF ? tv[k][m] : (m < MV - POLY ? ex2_neg2(tv[k][m]) : ex2_neg2_poly(tv[k][m])));
+          continue;
+        }
         // pairs: 1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2
 #pragma unroll
         for (int pp = 0; pp < NP; ++pp) {

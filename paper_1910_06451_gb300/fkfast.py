@@ -28,6 +28,8 @@ FK_DF64 = 3
 FK_DF32 = 4
 FK_LR_STEP = 0
 FK_LR_COSINE = 1
+FK_SUMMAND_RQ = 0      # the paper's summand (Eq. 3)
+FK_SUMMAND_GAUSS = 1   # not in the paper: exp(-gamma/2 |d|^2)
 FK_MAX_DOF = 16
 FK_MAX_CP = 32
 
@@ -38,6 +40,7 @@ EXPORTS = (
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
     "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune", "fk_active_samples",
+    "fk_chain_set_summand", "fk_set_gauss_poly",
 )
 
 
@@ -121,6 +124,8 @@ def load(build_if_missing: bool = False):
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
             "fk_active_samples": ([P, ctypes.c_int32, D, I64, D, ctypes.c_uint64, P, P, I64, P, P], I),
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
+            "fk_chain_set_summand": ([P, I], I),
+            "fk_set_gauss_poly": ([I], I),
             "fk_probe_pipe": ([I, P, P], I),
             "fk_tc_gemm_bf16": ([P, I64, P, I64, I, I, I, I, P, P], I),
             "fk_batch_create": ([P, I, PP], I),
@@ -204,6 +209,17 @@ def fk_chain_destroy(chain):
     load().fk_chain_destroy(chain)
 
 
+def fk_chain_set_summand(chain, summand: int):
+    """FK_SUMMAND_RQ (the paper's kernel) or FK_SUMMAND_GAUSS (not the paper's)."""
+    _check(load().fk_chain_set_summand(chain, int(summand)))
+
+
+def fk_set_gauss_poly(points: int):
+    """Gaussian summand on 7 points: how many points per support point use the
+    FMA polynomial instead of MUFU ex2 (0, 1 or 2)."""
+    _check(load().fk_set_gauss_poly(int(points)))
+
+
 # ------------------------------------------------------------ kinematics --
 
 def fk_forward(chain, q, cp, stream=None):
@@ -251,10 +267,12 @@ def fastron_model_destroy(model):
 
 
 def fastron_train(model, X, y, gamma, beta=1.0, iter_max=5000, s_max=None, warm_start=False, trace=False,
-                  gram=FK_DF64, reuse_gram=False, stream=None) -> dict:
+                  gram=0, reuse_gram=False, stream=None) -> dict:
     """Algorithm 1 on device training data X (float64, (N, D)) and y (int8, (N,)).
     warm_start: False/0, True/1 (same training set), or 2 (the first |S|
-    rows are the model's support points, carried with their weights)."""
+    rows are the model's support points, carried with their weights).
+    gram: 0 lets the library choose (FK_DF64 for the RQ summand, FK_F64 for
+    the Gaussian one)."""
     import torch
     N = X.shape[0]
     p = FastronParams(float(gamma), float(beta), int(iter_max), int(N if s_max is None else s_max),
