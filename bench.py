@@ -165,6 +165,52 @@ def run_reference(args):
     return 0
 
 
+def small_3dof(fk, dev, rank, flush, steps=20):
+    """The small 3-DOF workload (3-DOF arm, 4 control points, 6 boxes, N = 1000
+    training configurations, 10,000 queries, gamma = 10): the same step
+    (labels, kernel matrix, Algorithm 1, score with the band re-score), timed
+    over `steps` steps.  At this size the step is bound by launch and
+    synchronisation latency, not by the kernels' throughput."""
+    import torch
+    w = synth.workload("arm3-n1000", trial=rank)
+    ch = fk.chain_from_arm(w.scene.arm)
+    m = fk.fastron_model_create(ch)
+    try:
+        X = torch.from_numpy(w.train_configs().astype(np.float64)).to(dev)
+        X32 = X.float()
+        Q = torch.from_numpy(w.query_configs()).to(dev)
+        y = torch.empty(w.n_train, dtype=torch.int8, device=dev)
+        lab = torch.empty(Q.shape[0], dtype=torch.int8, device=dev)
+
+        def step():
+            fk.fk_label(ch, w.scene.boxes, w.scene.radius, X32, y)
+            st = fk.fastron_train(m, X, y, w.gamma, w.beta, w.iter_max, w.s_max)
+            fk.fk_score(m, Q, lab, rescore=True)
+            return st
+
+        for _ in range(3):
+            st = step()
+        torch.cuda.synchronize()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            step()
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        fk.fk_score(m, Q, lab, rescore=True)
+        e[1].record()
+        e[1].synchronize()
+        return {"workload": w.name, "support": st["n_support"], "iterations": st["iterations"], "ms_per_step": ms,
+                "checks_per_s": Q.shape[0] / ms * 1e3, "query_ms": e[0].elapsed_time(e[1])}
+    finally:
+        fk.fastron_model_destroy(m)
+        fk.fk_chain_destroy(ch)
+
+
 def gaussian_summand(fk, dev, rank, Q, X32, X, flush, peak):
     """The same 7-DOF workload with the library's non-paper Gaussian summand
     (FK_SUMMAND_GAUSS): labels, FP64 kernel matrix and Algorithm 1, then the
@@ -696,6 +742,8 @@ def main():
             for ch in bchains:
                 fk.fk_chain_destroy(ch)
 
+    small = small_3dof(fk, dev, rank, flush)
+
     gauss = None
     if args.gauss:
         gauss = gaussian_summand(fk, dev, rank, Q, Xq32, X, flush, peak)
@@ -733,6 +781,7 @@ def main():
             "changing_environment": dynamic,
             "obstacle_sweep": sweep,
             "gaussian_summand": gauss,
+            "small_3dof": small,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Teval/s",
                          "frac": achieved / peak,
                          "peak_basis": "min(MUFU 16/clk/SM x 1 reciprocal, FP32 128/clk/SM / 5 ops) per evaluation "
