@@ -35,8 +35,9 @@ N_QUERY = 1 << 22
 # DRAM bytes read + written by one launch of the FP32 score kernel on this
 # workload (4,194,304 queries, 800 support points), from an ncu capture of
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum): the
-# queries in and the labels out, no re-reads
-SCORE_TRAFFIC_BYTES = 117_803_008 + 4_629_248
+# queries in and the labels out, no re-reads.  None until the kernel as it
+# stands has been captured.
+SCORE_TRAFFIC_BYTES = None
 METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -787,7 +788,7 @@ def main():
                          "peak_basis": "min(MUFU 16/clk/SM x 1 reciprocal, FP32 128/clk/SM / 5 ops) per evaluation "
                                        "x SMs x max SM clock",
                          "peak_fp32_floor": peak_fp32_floor, "frac_fp32_floor": achieved / peak_fp32_floor,
-                         "traffic": SCORE_TRAFFIC_BYTES if nq == N_QUERY and Mv == 7 else None,
+                         "traffic": SCORE_TRAFFIC_BYTES if SCORE_TRAFFIC_BYTES and nq == N_QUERY and Mv == 7 else None,
                          "kernel": "score_f32_kernel", "evals_per_launch": evals, "launch_ms": score_ms},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": shard.aggregate_rate(nq, ws, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,

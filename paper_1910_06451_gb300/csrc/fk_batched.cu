@@ -25,7 +25,8 @@ struct SceneDev {
   const float *sdf;    // double-float records [ns][rec_df_len(Mv)]
   const double *cp64;
   const double *alpha;
-  int64_t ns;
+  int64_t ns;     // support points
+  int64_t nrec;   // record halves, 2 rec_pairs(ns)
   float gs;
   double gamma;
   int64_t q_off;  // first query of the scene in the concatenated batch
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) 
     const int64_t off = sc->q_off;
     const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, a.eps, a.band_idx, a.band_scene, w.scene, off,
                      a.band_cnt, a.err, a.wait_limit};
-    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->ns, sc->gs, a.q + off * sc->cf.D, sc->n,
+    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->nrec, sc->gs, a.q + off * sc->cf.D, sc->n,
                                                  (int64_t)w.block * (NTHR * Q), o, tiles, bar);
     if (!ok) break;   // identical in every thread
     __syncthreads();  // item_sh, cs and the tiles are reused by the next item
@@ -324,6 +325,7 @@ void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *r
   d.cp64 = cp64;
   d.alpha = alpha;
   d.ns = ns;
+  d.nrec = 2 * rec_pairs(ns);
   d.gs = (float)sqrt(0.5 * gamma);
   d.gamma = gamma;
   d.q_off = q_off;

@@ -76,6 +76,11 @@ cudaError_t launch_margins(const void *G, int g32, int64_t N, const double *alph
 // weights (w_a, w_b, |w_a|, |w_b|) with w = alpha / M; coordinates are scaled
 // by sqrt(gamma / 2).
 __host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 1; }
+// Pair records of a support set of ns points: the points with alpha > 0 come
+// first, then those with alpha < 0, each group padded to an even count with a
+// zero-weight point, so every pair has one sign; one pair more than (ns + 1) / 2
+// leaves room for both pads.
+__host__ __device__ constexpr int64_t rec_pairs(int64_t ns) { return (ns + 1) / 2 + 1; }
 
 // floats of one support point's double-float record (the band re-score): for
 // each configuration-dependent control point (x_h, x_l, y_h, y_l, z_h, z_l) of
@@ -92,7 +97,7 @@ struct PackArgs {
   const double *alpha;
   int64_t ns;
   double gamma;
-  float4 *rec;        // [(ns + 1) / 2][rec_len(Mv)]
+  float4 *rec;        // [rec_pairs(ns)][rec_len(Mv)], positive-weight pairs first
   double *cp64;       // SoA [M][3][ns]
   double *alpha_out;  // [ns] (copy of alpha, compacted)
   double *q_out;      // [ns][D] support configurations
@@ -102,6 +107,8 @@ struct PackArgs {
                       // of joint 1, k = gamma rho^2 (see ChainF::cp1)
   double cp1_k;
   double scale;       // coordinate scale: sqrt(gamma/2) (RQ), sqrt(gamma/2 log2 e) (Gaussian)
+  int32_t *slot;      // [ns] scratch: record half of each support point
+  int32_t *npair_pos; // [1] out: number of positive-weight pairs
 };
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s);
 
@@ -110,7 +117,7 @@ struct ScoreArgs {
   const float *q;
   int64_t n;
   const float4 *rec;
-  int64_t ns;
+  int64_t ns;          // record halves: 2 rec_pairs(support points)
   const float4 *rec1;  // or null; with it the first point's t = A - U cos theta_q - V sin theta_q
   float cp1_A;         // 1 + k
   float gs;           // scale of the control points (PackArgs::scale)
@@ -122,6 +129,7 @@ struct ScoreArgs {
   int32_t *err;       // [1]
   uint32_t wait_limit;  // polls of a tile wait before it gives up
   int poly;           // Gaussian summand, 7 points: points per support point on the FMA polynomial
+  const int32_t *npair_pos;  // device: positive-weight pairs, which lead the records
 };
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
 

@@ -31,34 +31,82 @@
 namespace fk {
 
 // ---------------------------------------------------------------- pack ---
-// One thread per support point s, writing its half h = s & 1 of the pair
-// record j = s >> 1 (components h and 2 + h of each float4); an odd count is
-// padded by a thread that writes zeros (weight 0).  The FP64 kinematics run
-// at 1/64 of the FP32 rate, so the CTAs are small (32 threads) and spread
-// over as many SMs as there are support points / 32.
+// Record slot of every support point: the points with alpha > 0 in ascending
+// order from slot 0, those with alpha < 0 in ascending order from the first
+// even slot after them (the odd slot between stays a zero-weight pad).  One
+// CTA ranks the points chunk by chunk with warp ballots; it also writes the
+// number of positive-weight pairs.
+constexpr int kSlotThreads = 1024;
+
+__global__ void __launch_bounds__(kSlotThreads) sign_slots_kernel(const double *__restrict__ alpha, int64_t ns,
+                                                                  int32_t *__restrict__ slot,
+                                                                  int32_t *__restrict__ npair_pos) {
+  __shared__ int wsum[2][kSlotThreads / 32];
+  __shared__ int total;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int cnt = 0;
+  for (int64_t s = tid; s < ns; s += kSlotThreads) cnt += alpha[s] > 0.0;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0) wsum[0][wid] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int w = 0; w < kSlotThreads / 32; ++w) t += wsum[0][w];
+    total = t;
+  }
+  __syncthreads();
+  const int npos = total;
+  const int neg0 = 2 * ((npos + 1) / 2);
+  int run_pos = 0, run_neg = 0;  // points of each sign in earlier chunks
+  for (int64_t c0 = 0; c0 < ns; c0 += kSlotThreads) {
+    __syncthreads();  // wsum of the previous chunk has been read
+    const int64_t s = c0 + tid;
+    const bool in = s < ns;
+    const bool pos = in && alpha[s] > 0.0, neg = in && !pos;
+    const unsigned bp = __ballot_sync(0xffffffffu, pos), bn = __ballot_sync(0xffffffffu, neg);
+    if (lane == 0) {
+      wsum[0][wid] = __popc(bp);
+      wsum[1][wid] = __popc(bn);
+    }
+    __syncthreads();
+    int before_p = 0, before_n = 0, chunk_p = 0, chunk_n = 0;
+    for (int w = 0; w < kSlotThreads / 32; ++w) {
+      if (w < wid) {
+        before_p += wsum[0][w];
+        before_n += wsum[1][w];
+      }
+      chunk_p += wsum[0][w];
+      chunk_n += wsum[1][w];
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (pos) slot[s] = run_pos + before_p + __popc(bp & lt);
+    if (neg) slot[s] = neg0 + run_neg + before_n + __popc(bn & lt);
+    run_pos += chunk_p;
+    run_neg += chunk_n;
+  }
+  if (tid == 0) *npair_pos = (npos + 1) / 2;
+}
+
+// One thread per support point s, writing its half h = slot & 1 of the pair
+// record slot >> 1 (components h and 2 + h of each float4); the records are
+// zero-filled first, so pads carry weight 0.  The FP64 kinematics run at 1/64
+// of the FP32 rate, so the CTAs are small (32 threads) and spread over as many
+// SMs as there are support points / 32.
 constexpr int kPackThreads = 32;
 
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, const ChainD cd, const PackArgs a) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t npair = (a.ns + 1) / 2;
-  if (s >= 2 * npair) return;
+  if (s >= a.ns) return;
   const int MV = cf.Mv;
   const int REC = rec_len(MV);
-  const int64_t j = s >> 1;
-  const int h = (int)(s & 1);
+  const int64_t j = a.slot[s] >> 1;
+  const int h = a.slot[s] & 1;
   float *rec = reinterpret_cast<float *>(a.rec + j * REC);
   float *rec1 = a.rec1 ? reinterpret_cast<float *>(a.rec1 + j * REC) : nullptr;
   auto put = [&](int e, int c, float v) {  // component c (0..3) of record entry e
     rec[4 * e + c] = v;
     if (rec1) rec1[4 * e + c] = v;
   };
-  if (s >= a.ns) {  // padding half of an odd count
-    for (int e = 0; e < REC; ++e) {
-      put(e, h, 0.f);
-      put(e, 2 + h, 0.f);
-    }
-    return;
-  }
   const double gs = a.scale;
   const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
   const double *x = a.X + src * cd.D;
@@ -111,9 +159,12 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
 }
 
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s) {
-  if (a.ns <= 0) return cudaSuccess;
-  const int64_t npair = (a.ns + 1) / 2;
-  pack_kernel<<<(unsigned)((2 * npair + kPackThreads - 1) / kPackThreads), kPackThreads, 0, s>>>(cf, cd, a);
+  const size_t rec_bytes = sizeof(float4) * (size_t)rec_pairs(a.ns) * rec_len(cf.Mv);
+  cudaError_t e = cudaMemsetAsync(a.rec, 0, rec_bytes, s);
+  if (e == cudaSuccess && a.rec1) e = cudaMemsetAsync(a.rec1, 0, rec_bytes, s);
+  if (e != cudaSuccess) return e;
+  sign_slots_kernel<<<1, kSlotThreads, 0, s>>>(a.alpha, a.ns, a.slot, a.npair_pos);
+  if (a.ns > 0) pack_kernel<<<(unsigned)((a.ns + kPackThreads - 1) / kPackThreads), kPackThreads, 0, s>>>(cf, cd, a);
   return cudaGetLastError();
 }
 
@@ -127,8 +178,8 @@ template <int MV, bool CP1>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
-  score_block<MV, kQ, kTilePairs, kScoreThreads, false, CP1>(c, CP1 ? a.rec1 : a.rec, a.ns, a.gs, a.q, a.n,
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, a.npair_pos};
+  score_block<MV, kQ, kTilePairs, kScoreThreads, false, CP1, false, 0, true>(c, CP1 ? a.rec1 : a.rec, a.ns, a.gs, a.q, a.n,
                                                              (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar,
                                                              a.cp1_A);
 }
@@ -139,8 +190,8 @@ template <int MV, bool HALF, int POLY>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_gauss_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
-  score_block<MV, kQ, kTilePairs, kScoreThreads, HALF, false, true, POLY>(
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, a.npair_pos};
+  score_block<MV, kQ, kTilePairs, kScoreThreads, HALF, false, true, POLY, !HALF>(
       c, a.rec, a.ns, a.gs, a.q, a.n, (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
 }
 
@@ -149,7 +200,7 @@ template <int MV>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f16_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit};
+  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, nullptr};
   score_block<MV, kQ, kTilePairs, kScoreThreads, true>(c, a.rec, a.ns, a.gs, a.q, a.n,
                                                        (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
 }

@@ -297,6 +297,7 @@ struct fastron_model {
   int summand = FK_SUMMAND_RQ;  // the chain's summand when the support set was packed
   DevBuf rec, cp64, alpha_s, q_s, qin, sdf;
   DevBuf rec1;        // records with the circle form of point 0 (used when use_cp1)
+  DevBuf slot, npos;  // record slot of each support point; positive-weight pairs (device int)
   bool use_cp1 = false;
   float cp1_A = 0.f;
   std::vector<int64_t> host_idx;  // training indices of the support points (model_set: positions)
@@ -324,7 +325,7 @@ extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
   DevBuf *bufs[] = {&m->cpX, &m->cpdf, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
                     &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf, &m->rec1,
-                    &m->qdf, &m->part, &m->band2_idx,
+                    &m->qdf, &m->part, &m->band2_idx, &m->slot, &m->npos,
                     &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
   for (DevBuf *b : bufs) b->release();
   delete m;
@@ -333,7 +334,9 @@ extern "C" void fastron_model_destroy(fastron_model_t *m) {
 static int pack(fastron_model *m, const double *X, const int32_t *idx, const double *alpha, int64_t ns, double gamma,
                 cudaStream_t s) {
   const fk_chain *c = m->chain;
-  CK(m->rec.ensure(sizeof(float4) * (size_t)((ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1) * rec_len(c->cf.Mv)));
+  CK(m->rec.ensure(sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv)));
+  CK(m->slot.ensure(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1)));
+  CK(m->npos.ensure(sizeof(int32_t)));
   CK(m->cp64.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->M * 3));
   CK(m->alpha_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
@@ -345,13 +348,13 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   m->use_cp1 = summand == FK_SUMMAND_RQ && c->cf.cp1 && score_cp1_supported(c->cf.Mv) && 1.0 + k1 < 8.0;
   m->cp1_A = (float)(1.0 + k1);
   if (m->use_cp1)
-    CK(m->rec1.ensure(sizeof(float4) * (size_t)((ns + 1) / 2 > 0 ? (ns + 1) / 2 : 1) * rec_len(c->cf.Mv)));
+    CK(m->rec1.ensure(sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv)));
   // coordinates scaled so that the summand is (1 + |d|^2)^-2 (RQ) or
   // 2^(-|d|^2) (Gaussian); the double-float records serve the RQ band only
   const double scale = sqrt(summand == FK_SUMMAND_GAUSS ? 0.5 * gamma * M_LOG2E : 0.5 * gamma);
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
               m->q_s.as<double>(), summand == FK_SUMMAND_RQ ? m->sdf.as<float>() : nullptr,
-              m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1, scale};
+              m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1, scale, m->slot.as<int32_t>(), m->npos.as<int32_t>()};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
   m->gamma = gamma;
@@ -564,9 +567,9 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
     CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
     if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
     const double eps16 = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsF16Gauss : kDefaultEpsF16);
-    ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, nullptr, 0.f, gs, (float)eps16, f, label,
+    ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), nullptr, 0.f, gs, (float)eps16, f, label,
                  rescore ? m->band_idx.as<int32_t>() : nullptr, m->flags.as<int32_t>(), m->flags.as<int32_t>() + 1,
-                 g_wait_limit, 0};
+                 g_wait_limit, 0, m->npos.as<int32_t>()};
     CK(launch_score_f16(cf, sa, s));
     int32_t h[2] = {0, 0};
     if (rescore || n_rescored) {
@@ -597,9 +600,10 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1, *cnt2 = cnt + 2;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
   const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
-  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
-               gs, (float)eps, f, label,
-               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0};
+  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), m->use_cp1 ? m->rec1.as<float4>() : nullptr,
+               m->cp1_A, gs, (float)eps, f, label,
+               rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0,
+               m->npos.as<int32_t>()};
   CK(launch_score_f32(cf, sa, s));
   if (!rescore && !n_rescored) return FK_OK;
   if (gauss && rescore && !n_rescored) {
@@ -806,9 +810,9 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   ChainD cd = c->cd;
   cf.summand = cd.summand = m->summand;
   const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
-  ScoreArgs sa{q, n, m->rec.as<float4>(), m->ns, m->use_cp1 ? m->rec1.as<float4>() : nullptr, m->cp1_A,
-               (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma), (float)eps, f, label,
-               band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0};
+  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), m->use_cp1 ? m->rec1.as<float4>() : nullptr,
+               m->cp1_A, (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma), (float)eps, f, label,
+               band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0, m->npos.as<int32_t>()};
   CK(launch_score_f32(cf, sa, s));
   RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};
   CK(launch_rescore_f64(cd, ra, s));

@@ -112,6 +112,7 @@ struct BlockOut {
   int32_t *band_cnt;
   int32_t *err;
   uint32_t wait_limit;
+  const int32_t *npair_pos;  // SPLIT kernels: positive-weight pairs, which lead the records
 };
 
 // HALF = true: the differences and t = 1 + |d|^2 are computed in packed
@@ -136,7 +137,12 @@ struct BlockOut {
 // mbarriers.  Every thread of the CTA must call it.  Returns false (in every
 // thread) if a tile wait gave up; the caller must then stop using the CTA's
 // barriers.
-template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false, bool GAUSS = false, int POLY = 0>
+// SPLIT = true: the records hold the positive-weight pairs first
+// (o.npair_pos of them, see rec_pairs), so each pair adds w * acc into one of
+// two accumulators, the positive part P or the negative part N; f = P + N and
+// B(q) = P - N, one packed FMA per pair and query instead of two.
+template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false, bool GAUSS = false, int POLY = 0,
+          bool SPLIT = false>
 __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, float gs,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
                                             float4 *tiles, uint64_t *bar, float cp1_A = 0.f) {
@@ -149,6 +155,7 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
   const int tid = threadIdx.x;
   const int64_t npair = (ns + 1) / 2;
   const int ntiles = (int)((npair + TP - 1) / TP);
+  const int64_t npp = SPLIT ? (int64_t)*o.npair_pos : 0;  // pairs of the positive part
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -217,83 +224,114 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     const float4 *tile = tiles + (size_t)(t & 1) * TP * REC;
     const int64_t p0 = (int64_t)t * TP;
     const int cnt = (int)(npair - p0 < TP ? npair - p0 : TP);
-    // eight support pairs per loop trip: fewer loop and address instructions
-    // on a kernel bound by instruction dispatch (4M 7-DOF queries: 5.25 ms
-    // one pair per trip, 5.11 ms four, 5.06 ms eight), still within 128
-    // registers for two CTAs per SM
-#pragma unroll 8
-    for (int j = 0; j < cnt; ++j) {
-      const float4 *r = tile + j * REC;
-      f2 acc[Q];
+    // the summands of one support pair for this thread's queries
+    auto pair_sums = [&](const float4 *r, f2 (&acc)[Q]) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) acc[k] = nc2;
-      f2 tv[Q][MV];
+        for (int k = 0; k < Q; ++k) acc[k] = nc2;
+        f2 tv[Q][MV];
 #pragma unroll
-      for (int m = 0; m < MV; ++m) {
-        const float4 xy = r[m];
-        const float4 zz = r[MV + m / 2];
-        if (CP1 && m == 0) {
-          const f2 u = pk(xy.x, xy.y), v = pk(xy.z, xy.w);
+        for (int m = 0; m < MV; ++m) {
+          const float4 xy = r[m];
+          const float4 zz = r[MV + m / 2];
+          if (CP1 && m == 0) {
+            const f2 u = pk(xy.x, xy.y), v = pk(xy.z, xy.w);
 #pragma unroll
-          for (int k = 0; k < Q; ++k) tv[k][0] = fma2(u, ncq[CP1 ? k : 0], fma2(v, nsq[CP1 ? k : 0], A2));
-        } else if (HALF) {
-          const __half2 hx = __floats2half2_rn(xy.x, xy.y), hy = __floats2half2_rn(xy.z, xy.w);
-          const __half2 hz = (m & 1) ? __floats2half2_rn(zz.z, zz.w) : __floats2half2_rn(zz.x, zz.y);
+            for (int k = 0; k < Q; ++k) tv[k][0] = fma2(u, ncq[CP1 ? k : 0], fma2(v, nsq[CP1 ? k : 0], A2));
+          } else if (HALF) {
+            const __half2 hx = __floats2half2_rn(xy.x, xy.y), hy = __floats2half2_rn(xy.z, xy.w);
+            const __half2 hz = (m & 1) ? __floats2half2_rn(zz.z, zz.w) : __floats2half2_rn(zz.x, zz.y);
 #pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            const int kk = HALF ? k : 0, mm = HALF ? m : 0;
-            const __half2 dx = __hsub2(Ph[kk][mm][0], hx), dy = __hsub2(Ph[kk][mm][1], hy),
-                          dz = __hsub2(Ph[kk][mm][2], hz);
-            if (GAUSS) {
-              // the summand itself: 2^(-t) for both support points in one MUFU operation
-              const __half2 nt = __hneg2(__hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz))));
-              uint32_t e;
-              asm("ex2.approx.f16x2 %0, %1;" : "=r"(e) : "r"(*reinterpret_cast<const uint32_t *>(&nt)));
-              const float2 ef = __half22float2(*reinterpret_cast<const __half2 *>(&e));
-              tv[k][m] = pk(ef.x, ef.y);
-            } else {
-              const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
-              tv[k][m] = pk(tf.x, tf.y);
+            for (int k = 0; k < Q; ++k) {
+              const int kk = HALF ? k : 0, mm = HALF ? m : 0;
+              const __half2 dx = __hsub2(Ph[kk][mm][0], hx), dy = __hsub2(Ph[kk][mm][1], hy),
+                            dz = __hsub2(Ph[kk][mm][2], hz);
+              if (GAUSS) {
+                // the summand itself: 2^(-t) for both support points in one MUFU operation
+                const __half2 nt = __hneg2(__hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz))));
+                uint32_t e;
+                asm("ex2.approx.f16x2 %0, %1;" : "=r"(e) : "r"(*reinterpret_cast<const uint32_t *>(&nt)));
+                const float2 ef = __half22float2(*reinterpret_cast<const __half2 *>(&e));
+                tv[k][m] = pk(ef.x, ef.y);
+              } else {
+                const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
+                tv[k][m] = pk(tf.x, tf.y);
+              }
+            }
+          } else {
+            const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
+            const f2 sz = (m & 1) ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+              const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
+              tv[k][m] = GAUSS ? fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))) : fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
             }
           }
-        } else {
-          const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);
-          const f2 sz = (m & 1) ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+        }
 #pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            const f2 dx = sub2(P[k][m][0], sx), dy = sub2(P[k][m][1], sy), dz = sub2(P[k][m][2], sz);
-            tv[k][m] = GAUSS ? fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))) : fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, one2)));
+        for (int k = 0; k < Q; ++k) {
+          if constexpr (GAUSS) {
+#pragma unroll
+            for (int m = 0; m < MV; ++m)
+              acc[k] = add2(acc[k], HALF ? tv[k][m] : (m < MV - POLY ? ex2_neg2(tv[k][m]) : ex2_neg2_poly(tv[k][m])));
+          } else {
+            // pairs: 1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+              const f2 t1 = tv[k][2 * pp], t2 = tv[k][2 * pp + 1];
+              const f2 pr = mul2(t1, t2);
+              const f2 num = fma2(t1, t1, mul2(t2, t2));
+              acc[k] = fma2(num, rcp2(mul2(pr, pr)), acc[k]);
+            }
+#pragma unroll
+            for (int m = 2 * NP; m < MV; ++m) {
+              const f2 rr = rcp2(tv[k][m]);
+              acc[k] = fma2(rr, rr, acc[k]);
+            }
           }
         }
+    };
+    // eight support pairs per loop trip (four for more than 8 points, which
+    // would spill otherwise): fewer loop and address instructions on a kernel
+    // bound by instruction dispatch (4M 7-DOF queries: 5.25 ms one pair per
+    // trip, 5.11 ms four, 5.06 ms eight), within 128 registers for two CTAs
+    // per SM
+    constexpr int UNR = MV > 8 ? 4 : 8;
+    if constexpr (SPLIT) {
+      int64_t js = npp - p0;
+      js = js < 0 ? 0 : (js > cnt ? cnt : js);
+#pragma unroll UNR
+      for (int j = 0; j < (int)js; ++j) {
+        const float4 *r = tile + j * REC;
+        f2 acc[Q];
+        pair_sums(r, acc);
+        const float4 W = r[REC - 1];
+        const f2 w = pk(W.x, W.y);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) F[k] = fma2(w, acc[k], F[k]);
       }
+#pragma unroll UNR
+      for (int j = (int)js; j < cnt; ++j) {
+        const float4 *r = tile + j * REC;
+        f2 acc[Q];
+        pair_sums(r, acc);
+        const float4 W = r[REC - 1];
+        const f2 w = pk(W.x, W.y);
 #pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        if (GAUSS) {
-#pragma unroll
-          for (int m = 0; m < MV; ++m)
-            acc[k] = add2(acc[k], HALF ? tv[k][m] : (m < MV - POLY ? ex2_neg2(tv[k][m]) : ex2_neg2_poly(tv[k][m])));
-          continue;
-        }
-        // pairs: 1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2
-#pragma unroll
-        for (int pp = 0; pp < NP; ++pp) {
-          const f2 t1 = tv[k][2 * pp], t2 = tv[k][2 * pp + 1];
-          const f2 pr = mul2(t1, t2);
-          const f2 num = fma2(t1, t1, mul2(t2, t2));
-          acc[k] = fma2(num, rcp2(mul2(pr, pr)), acc[k]);
-        }
-#pragma unroll
-        for (int m = 2 * NP; m < MV; ++m) {
-          const f2 rr = rcp2(tv[k][m]);
-          acc[k] = fma2(rr, rr, acc[k]);
-        }
+        for (int k = 0; k < Q; ++k) B[k] = fma2(w, acc[k], B[k]);
       }
-      const float4 W = r[REC - 1];
-      const f2 w = pk(W.x, W.y), aw = pk(W.z, W.w);
+    } else {
+#pragma unroll UNR
+      for (int j = 0; j < cnt; ++j) {
+        const float4 *r = tile + j * REC;
+        f2 acc[Q];
+        pair_sums(r, acc);
+        const float4 W = r[REC - 1];
+        const f2 w = pk(W.x, W.y), aw = pk(W.z, W.w);
 #pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        F[k] = fma2(w, acc[k], F[k]);
-        B[k] = fma2(aw, acc[k], B[k]);
+        for (int k = 0; k < Q; ++k) {
+          F[k] = fma2(w, acc[k], F[k]);
+          B[k] = fma2(aw, acc[k], B[k]);
+        }
       }
     }
     __syncthreads();  // every thread is done with this buffer
@@ -319,7 +357,9 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     float f0, f1, b0, b1;
     upk(F[k], f0, f1);
     upk(B[k], b0, b1);
-    const float f = f0 + f1, bq = b0 + b1;
+    // SPLIT: F holds the positive part, B the negative part of f
+    const float f = SPLIT ? (f0 + f1) + (b0 + b1) : f0 + f1;
+    const float bq = SPLIT ? (f0 + f1) - (b0 + b1) : b0 + b1;
     const int64_t qi = qbase + k * NTHR;
     const bool valid = qi < n;
     if (valid) {
