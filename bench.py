@@ -37,7 +37,7 @@ N_QUERY = 1 << 22
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum): the
 # queries in and the labels out, no re-reads.  None until the kernel as it
 # stands has been captured.
-SCORE_TRAFFIC_BYTES = None
+SCORE_TRAFFIC_BYTES = 117_628_928 + 4_305_152
 METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -479,6 +479,7 @@ def main():
     ap.add_argument("--dynamic-modes", default="warm,cold,active,surrogate",
                     help="update modes of that measurement (comma-separated)")
     ap.add_argument("--gauss", type=int, default=1, help="measure the non-paper Gaussian summand (0: skip)")
+    ap.add_argument("--small", type=int, default=1, help="measure the 3-DOF workload's step (0: skip)")
     ap.add_argument("--obstacle-sweep", default="1,2,5,10,20,35,50",
                     help="box counts of the obstacle sweep (0: skip)")
     args = ap.parse_args()
@@ -743,7 +744,7 @@ def main():
             for ch in bchains:
                 fk.fk_chain_destroy(ch)
 
-    small = small_3dof(fk, dev, rank, flush)
+    small = small_3dof(fk, dev, rank, flush) if args.small else None
 
     gauss = None
     if args.gauss:

@@ -27,6 +27,7 @@ struct SceneDev {
   const double *alpha;
   int64_t ns;     // support points
   int64_t nrec;   // record halves, 2 rec_pairs(ns)
+  const int32_t *npair_pos;  // device: positive-weight pairs, which lead the records
   float gs;
   double gamma;
   int64_t q_off;  // first query of the scene in the concatenated batch
@@ -76,9 +77,9 @@ __global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) 
     __syncthreads();
     const int64_t off = sc->q_off;
     const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, a.eps, a.band_idx, a.band_scene, w.scene, off,
-                     a.band_cnt, a.err, a.wait_limit};
-    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->nrec, sc->gs, a.q + off * sc->cf.D, sc->n,
-                                                 (int64_t)w.block * (NTHR * Q), o, tiles, bar);
+                     a.band_cnt, a.err, a.wait_limit, sc->npair_pos};
+    const bool ok = score_block<MV, Q, TP, NTHR, false, false, false, 0, true>(
+        cs, sc->rec, sc->nrec, sc->gs, a.q + off * sc->cf.D, sc->n, (int64_t)w.block * (NTHR * Q), o, tiles, bar);
     if (!ok) break;   // identical in every thread
     __syncthreads();  // item_sh, cs and the tiles are reused by the next item
   }
@@ -315,7 +316,8 @@ size_t work_item_size() { return sizeof(WorkItem); }
 
 // Host-side filling of a SceneDev record (the layout stays private to this file).
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
-                    const double *cp64, const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n) {
+                    const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
+                    int64_t q_off, int64_t n) {
   SceneDev d;
   memset(&d, 0, sizeof d);
   d.cf = cf;
@@ -326,6 +328,7 @@ void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *r
   d.alpha = alpha;
   d.ns = ns;
   d.nrec = 2 * rec_pairs(ns);
+  d.npair_pos = npair_pos;
   d.gs = (float)sqrt(0.5 * gamma);
   d.gamma = gamma;
   d.q_off = q_off;

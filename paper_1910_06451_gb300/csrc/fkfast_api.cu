@@ -1358,7 +1358,8 @@ bool batched_supported(int mv);
 size_t scene_dev_size();
 size_t work_item_size();
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
-                    const double *cp64, const double *alpha, int64_t ns, double gamma, int64_t q_off, int64_t n);
+                    const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
+                    int64_t q_off, int64_t n);
 void fill_work_item(void *dst, int32_t scene, int32_t block);
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
                                       int32_t *counter, const float *q, float *f, int8_t *label, float eps,
@@ -1452,7 +1453,8 @@ static int batch_plan(fk_batch *b, const int64_t *q_off) {
     const fastron_model *m = b->models[i];
     const int64_t n = q_off[i + 1] - q_off[i];
     fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p, m->sdf.as<float>(),
-                   m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, q_off[i], n);
+                   m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->npos.as<int32_t>(), m->gamma, q_off[i],
+                   n);
     for (int64_t blk = 0; blk * bq < n; ++blk) {
       const int64_t qn = n - blk * bq < bq ? n - blk * bq : bq;
       it.push_back({(m->ns + 1) * qn, {i, (int32_t)blk}});

@@ -385,3 +385,20 @@ def test_score_half_precision_path(fk, arm3, arm7, dev, which):
     print(f"half pass: max |df|/B = {err.max():.3e}, band = {nb} of {len(Q)}")
     assert err.max() <= 0.5 * 2e-3
     assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
+
+
+@pytest.mark.parametrize("pattern", ["all_pos", "all_neg", "odd_odd", "even_odd", "one_pos"])
+def test_score_sign_ordered_records(fk, arm7, dev, pattern):
+    # the pair records hold the positive weights first, each sign group
+    # padded to an even count: every mix of group sizes scores as the oracle
+    w, ch = arm7
+    rng = np.random.default_rng(len(pattern))
+    n_pos, n_neg = {"all_pos": (129, 0), "all_neg": (0, 130), "odd_odd": (63, 65), "even_odd": (64, 33),
+                    "one_pos": (1, 200)}[pattern]
+    S = w.train_configs()[:n_pos + n_neg].astype(np.float64)
+    mag = rng.uniform(0.5, 3.0, n_pos + n_neg)
+    sign = np.concatenate([np.ones(n_pos), -np.ones(n_neg)])
+    alpha = mag * sign[rng.permutation(n_pos + n_neg)]  # signs interleaved in support order
+    Q = w.query_configs(3001)
+    out = _score_case(fk, w, ch, dev, S, alpha, Q)
+    _check_score(*out, alpha)
