@@ -100,7 +100,8 @@ void fk_chain_destroy(fk_chain_t *chain);
  *     FK_DF64/FK_DF32 are rejected);
  *   - fk_score (FK_F32 and FK_F16) evaluates 2^(-|d'|^2) with d' the control
  *     points scaled by sqrt(gamma/2 log2 e), on MUFU ex2 (FK_F16: ex2.f16x2);
- *     the band re-score goes straight to FP64;
+ *     the band is re-scored in double-float (a pair-arithmetic 2^(-t)),
+ *     then in FP64;
  *   - fk_batch_create rejects its models (FK_ERR_ARG).
  * A model keeps the summand it was trained or set with.  Returns FK_ERR_ARG
  * for an unknown summand or a chain whose shape has no Gaussian score kernel

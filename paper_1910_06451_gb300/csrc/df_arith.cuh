@@ -94,4 +94,66 @@ __device__ __forceinline__ void df_rq_term(const float qh[3], const float ql[3],
   rl = y * res;
 }
 
+// a + b for pairs of any signs
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return quick_two_sum(s.h, s.l);
+}
+
+// 1/k! for k = 0..12 as pairs, from FP64 (whose 53 bits cover the pair's 48)
+struct InvFact {
+  float h[13], l[13];
+};
+constexpr InvFact make_inv_fact() {
+  InvFact c{};
+  double v = 1.0;
+  for (int k = 0; k <= 12; ++k) {
+    if (k > 0) v /= (double)k;
+    c.h[k] = (float)v;
+    c.l[k] = (float)(v - (double)c.h[k]);
+  }
+  return c;
+}
+__constant__ constexpr InvFact kInvFact = make_inv_fact();
+constexpr double kLn2 = 0.69314718055994530942;
+
+// One Gaussian summand 2^(-t) (the non-paper summand, coordinates scaled by
+// sqrt(gamma/2 log2 e)) in pair arithmetic, t = |q - s|^2 formed as in
+// df_rq_term without the 1.  t = n + r with n = rint(t_h), r = (t_h - n) + t_l
+// (the first difference is exact), 2^(-r) = e^(-r ln 2) by its Taylor series
+// to the 12th power in pair Horner steps (|r ln 2| <= 0.347: the first
+// neglected term is below 2e-16), then scaled by 2^(-n) exactly.  t_h > 125
+// gives 0 (below 2^-125 of the largest summand).  Relative error about 1e-13
+// plus ln 2 t times the relative error of t (2^-46).
+__device__ __forceinline__ void df_gauss_term(const float qh[3], const float ql[3], const float *s, float &rh,
+                                              float &rl) {
+  float p[3], ep[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const dfl d = two_sum(qh[r], -s[2 * r]);
+    const float dl = d.l + (ql[r] - s[2 * r + 1]);
+    p[r] = d.h * d.h;
+    ep[r] = fmaf(dl, fmaf(2.f, d.h, dl), fmaf(d.h, d.h, -p[r]));
+  }
+  const dfl t1 = two_sum(p[0], p[1]);
+  const dfl t2 = two_sum(t1.h, p[2]);
+  const float th = t2.h;
+  const float tl = (t1.l + t2.l) + ((ep[0] + ep[1]) + ep[2]);
+  if (th > 125.f) {
+    rh = rl = 0.f;
+    return;
+  }
+  const float n = rintf(th);
+  const dfl r = two_sum(th - n, tl);
+  const dfl ln2{(float)kLn2, (float)(kLn2 - (double)(float)kLn2)};
+  const dfl mx = df_mul(dfl{-r.h, -r.l}, ln2);  // -r ln 2
+  dfl y{kInvFact.h[12], kInvFact.l[12]};
+#pragma unroll
+  for (int k = 11; k >= 0; --k) y = df_add(df_mul(y, mx), dfl{kInvFact.h[k], kInvFact.l[k]});
+  const float scale = __int_as_float((127 - (int)n) << 23);  // 2^(-n), n in [0, 125]
+  rh = y.h * scale;
+  rl = y.l * scale;
+}
+
 }  // namespace fk

@@ -158,7 +158,7 @@ struct DfRescoreArgs {
   const float *sdf;         // [ns][rec_df_len(Mv)]
   int64_t ns;
   int n_const;              // control points fixed to the base (summand exactly 1)
-  double gs;                // sqrt(gamma / 2)
+  double gs;                // coordinate scale (PackArgs::scale)
   float2 *qdf;              // [Mv * 3][nb] scratch: band control points as pairs
   float4 *part;             // [chunks][nb] scratch: (f_h, f_l, B, 0) per chunk
   int chunks;

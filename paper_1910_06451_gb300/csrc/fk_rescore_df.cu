@@ -4,7 +4,8 @@
 // The FP32 pass hands over every query with |f32| <= eps B(q).  Those are
 // evaluated here with about 46 significant bits on the FP32 pipes:
 //   band_fk     FP64 kinematics of each band query (Eqs. 1-2), control points
-//               scaled by sqrt(gamma/2) in FP64 and split into FP32 pairs;
+//               scaled by sqrt(gamma/2) (Gaussian summand: sqrt(gamma/2 log2 e))
+//               in FP64 and split into FP32 pairs;
 //   df          per (query, support point, control point) the summand
 //               t^-2, t = 1 + |p - s|^2 in scaled coordinates, from pair
 //               arithmetic (df_rq_term), summed per support point, weighted by
@@ -15,7 +16,8 @@
 //               |f| > eps2 B(q) decides the label (the double-float error is
 //               far below eps2 B(q)); the rest go to the FP64 re-score.
 //
-// Summand arithmetic: df_rq_term (df_arith.cuh).
+// Summand arithmetic: df_rq_term, or df_gauss_term for the non-paper
+// Gaussian summand (df_arith.cuh).
 // Error budget per query: coordinates 2^-48 relative (the pair split),
 // summands ~1e-13 relative (the neglected square of the Newton residual is
 // 2^-44), the unnormalised low words of the sums n 2^-48 of B(q) for n
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(32) band_fk_kernel(const ChainD c, const float
 }
 
 // ------------------------------------------------------ df summands ---
-template <int MV>
+template <int MV, bool GAUSS>
 __global__ void __launch_bounds__(kDfThreads) rescore_df_kernel(const DfRescoreArgs a) {
   constexpr int RL = rec_df_len(MV);
   __shared__ __align__(16) float tile[kDfTile * RL];
@@ -85,7 +87,10 @@ __global__ void __launch_bounds__(kDfThreads) rescore_df_kernel(const DfRescoreA
 #pragma unroll
       for (int v = 0; v < MV; ++v) {
         float rh, rl;
-        df_rq_term(qh[v], ql[v], S + v * 6, rh, rl);
+        if (GAUSS)
+          df_gauss_term(qh[v], ql[v], S + v * 6, rh, rl);
+        else
+          df_rq_term(qh[v], ql[v], S + v * 6, rh, rl);
         const dfl ks = two_sum(kh, rh);
         kh = ks.h;
         kl += ks.l + rl;
@@ -126,8 +131,11 @@ __global__ void __launch_bounds__(256) rescore_df_finish_kernel(const DfRescoreA
 }
 
 template <int MV>
-static cudaError_t launch_df_mv(const DfRescoreArgs &a, unsigned qblocks, cudaStream_t s) {
-  rescore_df_kernel<MV><<<dim3(qblocks, (unsigned)a.chunks), kDfThreads, 0, s>>>(a);
+static cudaError_t launch_df_mv(const DfRescoreArgs &a, bool gauss, unsigned qblocks, cudaStream_t s) {
+  if (gauss)
+    rescore_df_kernel<MV, true><<<dim3(qblocks, (unsigned)a.chunks), kDfThreads, 0, s>>>(a);
+  else
+    rescore_df_kernel<MV, false><<<dim3(qblocks, (unsigned)a.chunks), kDfThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -148,18 +156,28 @@ cudaError_t launch_rescore_df(const ChainD &c, const DfRescoreArgs &a, cudaStrea
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned qblocks = (unsigned)((a.nb + kDfThreads - 1) / kDfThreads);
-  switch (c.Mv) {
-    case 1: e = launch_df_mv<1>(a, qblocks, s); break;
-    case 2: e = launch_df_mv<2>(a, qblocks, s); break;
-    case 3: e = launch_df_mv<3>(a, qblocks, s); break;
-    case 4: e = launch_df_mv<4>(a, qblocks, s); break;
-    case 5: e = launch_df_mv<5>(a, qblocks, s); break;
-    case 6: e = launch_df_mv<6>(a, qblocks, s); break;
-    case 7: e = launch_df_mv<7>(a, qblocks, s); break;
-    case 8: e = launch_df_mv<8>(a, qblocks, s); break;
-    case 11: e = launch_df_mv<11>(a, qblocks, s); break;
-    case 12: e = launch_df_mv<12>(a, qblocks, s); break;
-    default: return cudaErrorInvalidValue;
+  const bool gauss = c.summand == FK_SUMMAND_GAUSS;
+  if (gauss) {
+    switch (c.Mv) {  // the shapes with Gaussian score kernels
+      case 3: e = launch_df_mv<3>(a, true, qblocks, s); break;
+      case 7: e = launch_df_mv<7>(a, true, qblocks, s); break;
+      case 11: e = launch_df_mv<11>(a, true, qblocks, s); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (c.Mv) {
+      case 1: e = launch_df_mv<1>(a, false, qblocks, s); break;
+      case 2: e = launch_df_mv<2>(a, false, qblocks, s); break;
+      case 3: e = launch_df_mv<3>(a, false, qblocks, s); break;
+      case 4: e = launch_df_mv<4>(a, false, qblocks, s); break;
+      case 5: e = launch_df_mv<5>(a, false, qblocks, s); break;
+      case 6: e = launch_df_mv<6>(a, false, qblocks, s); break;
+      case 7: e = launch_df_mv<7>(a, false, qblocks, s); break;
+      case 8: e = launch_df_mv<8>(a, false, qblocks, s); break;
+      case 11: e = launch_df_mv<11>(a, false, qblocks, s); break;
+      case 12: e = launch_df_mv<12>(a, false, qblocks, s); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (e != cudaSuccess) return e;
   rescore_df_finish_kernel<<<(unsigned)((a.nb + 255) / 256), 256, 0, s>>>(a);

@@ -350,10 +350,10 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   if (m->use_cp1)
     CK(m->rec1.ensure(sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv)));
   // coordinates scaled so that the summand is (1 + |d|^2)^-2 (RQ) or
-  // 2^(-|d|^2) (Gaussian); the double-float records serve the RQ band only
+  // 2^(-|d|^2) (Gaussian), in the FP32 and the double-float records alike
   const double scale = sqrt(summand == FK_SUMMAND_GAUSS ? 0.5 * gamma * M_LOG2E : 0.5 * gamma);
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
-              m->q_s.as<double>(), summand == FK_SUMMAND_RQ ? m->sdf.as<float>() : nullptr,
+              m->q_s.as<double>(), m->sdf.as<float>(),
               m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1, scale, m->slot.as<int32_t>(), m->npos.as<int32_t>()};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
@@ -606,26 +606,12 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
                m->npos.as<int32_t>()};
   CK(launch_score_f32(cf, sa, s));
   if (!rescore && !n_rescored) return FK_OK;
-  if (gauss && rescore && !n_rescored) {
-    // the Gaussian band goes straight to FP64 (no double-float form of exp),
-    // whose kernel reads the band size on the device: no synchronisation
-    RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
-                   m->gamma, f, label};
-    CK(launch_rescore_f64(cd, ra, s));
-    return FK_OK;
-  }
   int32_t h[2];
   CK(cudaMemcpyAsync(h, m->flags.p, sizeof h, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score: a shared-memory tile wait timed out");
   if (n_rescored) *n_rescored = rescore ? h[0] : 0;
   if (!rescore || h[0] == 0) return FK_OK;
-  if (gauss) {
-    RescoreArgs ra{q, m->band_idx.as<int32_t>(), cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
-                   m->gamma, f, label};
-    CK(launch_rescore_f64(cd, ra, s));
-    return FK_OK;
-  }
   // the band: double-float first, FP64 for what it cannot decide
   const int64_t nb = h[0];
   int dev = 0, sms = 0;
@@ -636,7 +622,8 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   CK(m->part.ensure(sizeof(float4) * (size_t)nb * chunks));
   CK(m->band2_idx.ensure(sizeof(int32_t) * (size_t)nb));
   DfRescoreArgs da{q, m->band_idx.as<int32_t>(), nb, m->sdf.as<float>(), m->ns, c->cd.n_const,
-                   sqrt(0.5 * m->gamma), m->qdf.as<float2>(), m->part.as<float4>(), chunks,
+                   sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma), m->qdf.as<float2>(), m->part.as<float4>(),
+                   chunks,
                    (m->ns + chunks - 1) / chunks, kDefaultEpsDf, f, label, m->band2_idx.as<int32_t>(), cnt2};
   CK(launch_rescore_df(cd, da, s));
   RescoreArgs ra{q, m->band2_idx.as<int32_t>(), cnt2, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,

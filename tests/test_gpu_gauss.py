@@ -6,6 +6,8 @@ FP64 oracle (oracle.SUMMANDS["gauss"]), through the C ABI.  Tolerances:
   score FP32 (MUFU ex2, and  |df| <= eps/2 * B(q), eps = 6e-6 the library's band,
   1 or 2 polynomial points)  B(q) = sum_s |alpha_s| K(S_s, q)
   score packed half          |df| <= eps16/2 * B(q), eps16 = 2e-3
+  double-float tier          every query forced into the band: f = the FP64 value
+                             rounded to FP32, 1 ulp at most on at most 1e-3 of them
   labels after re-score      identical to the oracle's
 """
 import numpy as np
@@ -203,3 +205,36 @@ def test_gauss_model_keeps_its_summand_and_batches_reject_it(fk, dev):
         fk.fastron_model_destroy(m_g)
     finally:
         fk.fk_chain_destroy(ch)
+
+
+def _ulps32(a, b):
+    ia = np.asarray(a, dtype=np.float32).view(np.int32).astype(np.int64)
+    ib = np.asarray(b, dtype=np.float32).view(np.int32).astype(np.int64)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("which", ["arm3", "arm7"])
+def test_gauss_double_float_tier_on_every_query(fk, g3, g7, dev, which):
+    # a band of eps = 1 holds every query, so the double-float tier (the pair
+    # arithmetic 2^(-t)) evaluates all of them: rounded to FP32 its f is the
+    # FP64 value rounded to FP32 (1 ulp where that value sits on a rounding
+    # boundary within the pair error)
+    w, ch = g3 if which == "arm3" else g7
+    S, alpha = _trained(w, None if which == "arm3" else 1500)
+    Q = w.query_configs(6000)
+    cps, cpq = O.fk_points(w.scene.arm, S), O.fk_points(w.scene.arm, Q.astype(np.float64))
+    want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8, summand="gauss")
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, S, alpha, w.gamma)
+        tq = torch.from_numpy(Q).to(dev)
+        f = torch.empty(len(Q), dtype=torch.float32, device=dev)
+        lab = torch.empty(len(Q), dtype=torch.int8, device=dev)
+        nres = fk.fk_score(m, tq, lab, f, rescore=True, eps=1.0, count=True)
+        torch.cuda.synchronize()
+    finally:
+        fk.fastron_model_destroy(m)
+    assert nres == len(Q)
+    u = _ulps32(f.cpu().numpy(), want.astype(np.float32))
+    assert u.max() <= 1 and np.mean(u > 0) <= 1e-3, (u.max(), np.mean(u > 0))
+    assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
