@@ -253,3 +253,24 @@ def test_trained_network_gains_over_the_exact_path(fk):
         fk.surrogate_destroy(s)
         fk.fastron_model_destroy(model)
         fk.fk_chain_destroy(chain)
+
+
+def test_fused_inference_wait_limit_reports_timeout(fk, setup):
+    # every bounded wait of the fused kernel gives up at once: the call
+    # returns FK_ERR_TIMEOUT without a hang, and the next call with the
+    # normal limit succeeds with the same outputs as before
+    w, chain, s = setup
+    fk.surrogate_set_params(s, _flat(_params(7)))
+    q = torch.from_numpy(w.query_configs(4096)).cuda()
+    ref = torch.empty(4096, dtype=torch.float32, device="cuda")
+    fk.surrogate_forward(s, q, ref)
+    out = torch.empty(4096, dtype=torch.float32, device="cuda")
+    fk.fk_set_wait_limit(0)
+    try:
+        with pytest.raises(fk.FkError) as e:
+            fk.surrogate_forward(s, q, out)
+        assert e.value.code == fk.FK_ERR_TIMEOUT
+    finally:
+        fk.fk_set_wait_limit(1 << 22)
+    fk.surrogate_forward(s, q, out)
+    assert torch.equal(out, ref)
