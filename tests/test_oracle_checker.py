@@ -102,9 +102,33 @@ def test_special_cases():
     assert O.check(synth.Scene(arm, touch, 0.03), q[:1])[0] == 1
 
 
+def test_touching_the_first_link_is_a_collision():
+    # one link from the origin to (1, 0, 0) (a = 1, q = 0) and a box whose
+    # lower y face lies 0.25 from it: at radius 0.25 the swept link touches
+    # the box (distance equal to the radius counts), at 0.2499 it does not
+    box = np.array([[0.2, 0.25, -1.0, 0.8, 1.0, 1.0]])
+    one = synth.Arm(np.array([[1.0, 0.0, 0.0, 0.0, 0.0]]), np.eye(4), np.array([1], dtype=np.int32),
+                    np.zeros((1, 3)), math.pi)
+    q1 = np.zeros((1, 1))
+    assert O.check(synth.Scene(one, box, 0.25), q1)[0] == 1
+    assert O.check(synth.Scene(one, box, 0.2499), q1)[0] == -1
+    # a second link turned away (to (1, -1, 0)) stays clear, so the first
+    # link alone decides
+    two = synth.Arm(np.array([[1.0, 0.0, 0.0, 0.0, 0.0]] * 2), np.eye(4), np.array([2], dtype=np.int32),
+                    np.zeros((1, 3)), math.pi)
+    q2 = np.array([[0.0, -math.pi / 2]])
+    assert O.check(synth.Scene(two, box, 0.25), q2)[0] == 1
+    assert O.check(synth.Scene(two, box, 0.2499), q2)[0] == -1
+
+
 def test_metrics_identities():
     yt = np.array([1, 1, 1, -1, -1, -1, -1, 1])
     yp = np.array([1, -1, 1, -1, 1, -1, -1, 1])
     m = O.metrics(yt, yp)
     assert (m["tp"], m["fn"], m["tn"], m["fp"]) == (3, 1, 3, 1)
     assert m["accuracy"] == 6 / 8 and m["tpr"] == 3 / 4 and m["tnr"] == 3 / 4
+    # an unbalanced matrix (tp 1, fn 2, fp 1, tn 3) separates every ratio:
+    # TPR = tp / (tp + fn), TNR = tn / (tn + fp) (Sec. IV)
+    m = O.metrics(np.array([1, 1, 1, -1, -1, -1, -1]), np.array([1, -1, -1, 1, -1, -1, -1]))
+    assert (m["tp"], m["fn"], m["tn"], m["fp"]) == (1, 2, 3, 1)
+    assert m["accuracy"] == 4 / 7 and m["tpr"] == 1 / 3 and m["tnr"] == 3 / 4

@@ -47,6 +47,36 @@ def test_two_points_opposite_labels_closed_form():
     assert r.converged and list(r.support) == [0, 1]
 
 
+def test_adjusting_a_support_point_when_the_set_is_full():
+    # two close points of opposite labels, k > (sqrt 5 - 1) / 2: after both
+    # are added, F_0 = 1 - k - k^2 < 0, so pass 3 adjusts point 0 although the
+    # support set is full (S_max = 2 = N): delta = 1 - F_0 = k + k^2 (Eq. 6)
+    g = 10.0
+    cp = _two_points(0.1)
+    k = O.k_fk(cp[0], cp[1], g)
+    assert k > (5 ** 0.5 - 1) / 2
+    r = O.fastron_train(cp, np.array([1, -1]), g, iter_max=3, s_max=2, trace=True)
+    kind, idx, delta = r.trace
+    assert list(kind) == [1, 1, 1] and list(idx) == [0, 1, 0]
+    assert delta[2] == pytest.approx(k + k * k, rel=1e-14)
+    assert r.alpha[0] == pytest.approx(1 + k + k * k, rel=1e-14)
+
+
+def test_removal_ties_go_to_the_lowest_index():
+    # two pairs of coincident points (K = 1 within a pair, e between pairs),
+    # all labelled +1, warm-started with every alpha = 1 and F = K alpha =
+    # 2 + 2e: every removal margin y (F - alpha) is the same positive value,
+    # and the removal takes the lowest index
+    g = 10.0
+    cp = np.zeros((4, 1, 3))
+    cp[2:, 0, 0] = 0.5
+    e = O.k_fk(cp[0], cp[2], g)
+    r = O.fastron_train(cp, np.ones(4, dtype=np.int8), g, iter_max=1, alpha0=np.ones(4),
+                        F0=np.full(4, 2.0 + 2.0 * e), trace=True)
+    assert list(r.trace[0]) == [2] and list(r.trace[1]) == [0]
+    assert r.alpha[0] == 0.0 and np.all(r.alpha[1:] == 1.0)
+
+
 def test_two_points_same_label_keeps_one():
     cp = _two_points(0.2)
     r = O.fastron_train(cp, np.array([1, 1]), 10.0, iter_max=100, trace=True)

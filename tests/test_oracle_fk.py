@@ -92,6 +92,26 @@ def test_dh_equals_elementary_product(arm_fn):
             np.testing.assert_allclose(T[i + 1], W, atol=1e-13)
 
 
+def test_joint_offsets_add_to_the_joint_values():
+    # theta = q + theta0 (Eq. 1): one link of length 1 with theta0 = pi/2
+    # points along y at q = 0 and along x at q = -pi/2
+    dh = np.array([[1.0, 0.0, 0.0, math.pi / 2, 0.0]])
+    np.testing.assert_allclose(O.frames(dh, np.eye(4), np.array([0.0]))[1, :3, 3], [0, 1, 0], atol=1e-15)
+    np.testing.assert_allclose(O.frames(dh, np.eye(4), np.array([-math.pi / 2]))[1, :3, 3], [1, 0, 0], atol=1e-15)
+    # and every frame of a twisted chain with offsets is the elementary product
+    arm = synth.arm_7dof(5)
+    dh = arm.dh.copy()
+    dh[:, 3] = np.random.default_rng(3).uniform(-math.pi, math.pi, arm.D)
+    q = synth.uniform_configs(12, 10, arm.D, arm.qlim).astype(np.float64)
+    for k in range(q.shape[0]):
+        T = O.frames(dh, np.eye(4), q[k])
+        W = np.eye(4)
+        for i in range(arm.D):
+            a, al, d, th0, _ = dh[i]
+            W = W @ _rz(q[k, i] + th0) @ _tz(d) @ _tx(a) @ _rx(al)
+            np.testing.assert_allclose(T[i + 1], W, atol=1e-13)
+
+
 def test_link_length_invariant():
     arm = synth.arm_7dof(3)
     q = synth.uniform_configs(5, 200, arm.D, arm.qlim).astype(np.float64)
