@@ -333,6 +333,36 @@ def test_score_timeout_path_reports_and_recovers(fk, arm7, dev):
         fk.fastron_model_destroy(m)
 
 
+def test_empty_batches_are_no_ops(fk, arm7, dev):
+    """Zero configurations, zero queries and an empty side of the kernel
+    matrix return FK_OK without a launch, and the next full call still
+    matches the oracle."""
+    w, ch = arm7
+    arm = w.scene.arm
+    e32 = torch.empty((0, arm.D), dtype=torch.float32, device=dev)
+    e64 = torch.empty((0, arm.D), dtype=torch.float64, device=dev)
+    fk.fk_forward(ch, e32, torch.empty((arm.M, 3, 0), dtype=torch.float32, device=dev))
+    fk.fk_forward_f64(ch, e64, torch.empty((arm.M, 3, 0), dtype=torch.float64, device=dev))
+    fk.fk_label(ch, w.scene.boxes, w.scene.radius, e32, torch.empty(0, dtype=torch.int8, device=dev))
+    X = torch.from_numpy(w.train_configs()[:40].astype(np.float64)).to(dev)
+    fk.fk_gram(ch, e64, X, w.gamma, torch.empty((0, 40), dtype=torch.float64, device=dev))
+    fk.fk_gram(ch, X, e64, w.gamma, torch.empty((40, 0), dtype=torch.float64, device=dev))
+    Xn = X.cpu().numpy()
+    y = O.check(w.scene, Xn)
+    r = O.fastron_train(O.fk_points(arm, Xn), y, w.gamma, w.beta, w.iter_max, w.s_max)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, Xn[r.support], r.alpha[r.support], w.gamma)
+        assert fk.fk_score(m, e32, torch.empty(0, dtype=torch.int8, device=dev), count=True) == 0
+        Q = w.query_configs(300)
+        lab = torch.empty(300, dtype=torch.int8, device=dev)
+        fk.fk_score(m, torch.from_numpy(Q).to(dev), lab)
+        want = O.labels_from_f(O.score(arm, Xn[r.support], r.alpha[r.support], Q.astype(np.float64), w.gamma))
+        np.testing.assert_array_equal(lab.cpu().numpy(), want)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
 def test_argument_errors(fk, arm3, dev):
     w, ch = arm3
     m = fk.fastron_model_create(ch)
