@@ -179,7 +179,12 @@ void fastron_model_destroy(fastron_model_t *model);
  * The kernel matrix is stored (N^2 entries of 8 or 4 bytes, see gram) and
  * kept with the model.  Requires N <= 65,536, else FK_ERR_CAPACITY; the
  * matrix must fit in device memory, else FK_ERR_CUDA.  Sizes above 32,768
- * need a 16-CTA thread-block cluster. */
+ * need a 16-CTA thread-block cluster.  The CTAs of the cluster exchange
+ * their candidates through shared-memory barriers polled at most
+ * fk_set_wait_limit times per pass; if one runs out the call returns
+ * FK_ERR_TIMEOUT, the model keeps its previous support set, and the
+ * incomplete weights and margins are discarded (no warm start or matrix
+ * reuse follows from them). */
 int fastron_train(fastron_model_t *model, const double *X, const int8_t *y, int64_t N, const fastron_params *p,
                   fastron_stats *stats, void *stream);
 
@@ -281,8 +286,9 @@ int fk_score_noalloc(fastron_model_t *model, const float *q, int64_t n, double r
 int fk_label(const fk_chain_t *chain, const double *boxes, int64_t nb, double radius, const float *q, int64_t n,
              int8_t *y, void *stream);
 
-/* Sets how many times a kernel polls a shared-memory tile barrier before it
- * gives up, raises FK_ERR_TIMEOUT and exits cleanly (default 4194304 polls,
+/* Sets how many times a kernel polls a shared-memory barrier (a tile, a
+ * tensor-core completion, a cluster exchange) before it gives up, raises
+ * FK_ERR_TIMEOUT and exits cleanly (default 4194304 polls,
  * about a quarter of a second).  0 makes every such wait give up at once,
  * which exercises the timeout path without a hang.  Process-wide; not
  * synchronised with calls in flight on other threads. */

@@ -44,12 +44,13 @@ struct TrainArgs {
   int64_t iter_max, s_max;
   double *alpha;       // [N] in/out
   double *F;           // [N] in/out
-  int64_t *stats;      // [5] out: iterations, adds, removes, converged, n_support
+  int64_t *stats;      // [6] out: iterations, adds, removes, converged, n_support, timeout (zeroed by the caller)
   int32_t *sup_idx;    // [N] out: ascending support indices
   double *sup_alpha;   // [N] out
   int8_t *trace_kind;  // [iter_max] or null
   int32_t *trace_idx;
   double *trace_delta;
+  uint32_t wait_limit;  // polls per exchange wait of the cluster reduction
 };
 cudaError_t launch_fastron_train(const TrainArgs &a, cudaStream_t s);
 

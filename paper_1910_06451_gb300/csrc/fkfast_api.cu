@@ -402,7 +402,7 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
     CK(cudaMemsetAsync(m->alpha.p, 0, sizeof(double) * (size_t)N, s));
     CK(cudaMemsetAsync(m->F.p, 0, sizeof(double) * (size_t)N, s));
   }
-  CK(m->stats.ensure(sizeof(int64_t) * 5));
+  CK(m->stats.ensure(sizeof(int64_t) * 6));
   CK(m->sup_idx.ensure(sizeof(int32_t) * (size_t)N));
   CK(m->sup_alpha.ensure(sizeof(double) * (size_t)N));
   const bool trace = p->trace != 0;
@@ -440,11 +440,18 @@ extern "C" int fastron_train(fastron_model_t *m, const double *X, const int8_t *
   TrainArgs ta{m->G.p, gram == FK_DF32 ? 1 : 0, y, N, p->beta, p->iter_max, p->s_max, m->alpha.as<double>(), m->F.as<double>(),
                m->stats.as<int64_t>(), m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(),
                trace ? m->trace_kind.as<int8_t>() : nullptr, trace ? m->trace_idx.as<int32_t>() : nullptr,
-               trace ? m->trace_delta.as<double>() : nullptr};
+               trace ? m->trace_delta.as<double>() : nullptr, g_wait_limit};
+  CK(cudaMemsetAsync(m->stats.p, 0, sizeof(int64_t) * 6, s));
   CK(launch_fastron_train(ta, s));
-  int64_t hs[5];
+  int64_t hs[6];
   CK(cudaMemcpyAsync(hs, m->stats.p, sizeof hs, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (hs[5] != 0) {  // alpha and F are incomplete: no warm start or matrix reuse from them
+    m->N = 0;
+    m->gram = -1;
+    m->trace_len = 0;
+    return fail(FK_ERR_TIMEOUT, "fastron_train: a cluster exchange wait timed out");
+  }
   m->trace_len = trace ? hs[0] : 0;
   int rc = pack(m, X, m->sup_idx.as<int32_t>(), m->sup_alpha.as<double>(), hs[4], p->gamma, s);
   if (rc != FK_OK) return rc;

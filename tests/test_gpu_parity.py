@@ -333,6 +333,40 @@ def test_score_timeout_path_reports_and_recovers(fk, arm7, dev):
         fk.fastron_model_destroy(m)
 
 
+@pytest.mark.parametrize("n", [333, 1000, 5000])
+def test_training_timeout_path_reports_and_recovers(fk, arm3, arm7, dev, n):
+    # the cluster exchange of Algorithm 1 giving up at once returns
+    # FK_ERR_TIMEOUT (a cluster of 1 CTA at 333 points, 2 at 1000, 16 at
+    # 5000); the context stays usable, warm start and matrix reuse are
+    # refused, and the next cold call with the normal limit reproduces the
+    # oracle's model
+    w, ch = arm3 if n < 5000 else arm7
+    X = w.train_configs()[:n].astype(np.float64)
+    y = O.check(w.scene, X)
+    Xt, yt = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fk_set_wait_limit(0)
+        try:
+            with pytest.raises(fk.FkError) as e:
+                fk.fastron_train(m, Xt, yt, w.gamma, w.beta, w.iter_max, w.s_max)
+            assert e.value.code == fk.FK_ERR_TIMEOUT
+        finally:
+            fk.fk_set_wait_limit(1 << 22)
+        for kw in ({"warm_start": True}, {"reuse_gram": True}):
+            with pytest.raises(fk.FkError) as e:
+                fk.fastron_train(m, Xt, yt, w.gamma, w.beta, w.iter_max, w.s_max, **kw)
+            assert e.value.code == fk.FK_ERR_STATE
+        st = fk.fastron_train(m, Xt, yt, w.gamma, w.beta, w.iter_max, w.s_max)
+        r = O.fastron_train(O.fk_points(w.scene.arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+        assert st["n_support"] == len(r.support) and st["iterations"] == r.iters
+        idx, alpha = fk.fastron_model_get(m)
+        np.testing.assert_array_equal(idx, r.support)
+        np.testing.assert_allclose(alpha, r.alpha[r.support], rtol=1e-12, atol=0)
+    finally:
+        fk.fastron_model_destroy(m)
+
+
 def test_empty_batches_are_no_ops(fk, arm7, dev):
     """Zero configurations, zero queries and an empty side of the kernel
     matrix return FK_OK without a launch, and the next full call still
