@@ -72,6 +72,13 @@ MUTANTS = [
      "for (int64_t s = 1; s < ns; ++s) {"),
     ("carried margins ignore fp32 storage", C, "k = (double)(float)k;", "k = k + 0.0;"),
     ("active samples not clipped", PY, "v = np.clip(S + near[c], -qlim, qlim)", "v = S + near[c]"),
+    ("active samples drawn point-major", PY,
+     "near = st.uniform(k_near * ns * D, -sigma, sigma).reshape(k_near, ns, D)",
+     "near = st.uniform(k_near * ns * D, -sigma, sigma).reshape(ns, k_near, D).transpose(1, 0, 2)"),
+    ("active samples rounded after the clip only for copies", PY,
+     "out.append(v.astype(np.float32).astype(np.float64))", "out.append(v)"),
+    ("uniform samples over half the limits", PY, "uni = st.uniform(n_uniform * D, -qlim, qlim)",
+     "uni = st.uniform(n_uniform * D, 0.0, qlim)"),
     # capsule-box checker and metrics (Sec. IV, Eqs. 10-12)
     ("touching is free", C, "boxes + 6 * b + 3) <= r2)", "boxes + 6 * b + 3) < r2)"),
     ("radius not squared", C, "double r2 = radius * radius;", "double r2 = radius;"),
