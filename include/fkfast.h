@@ -234,22 +234,41 @@ int fastron_model_get(const fastron_model_t *model, int64_t *idx, double *alpha,
  * q: device float, n x D.  label: device int8 [n].  f: device float [n] or NULL.
  * precision FK_F32: FK of each query and the kernel sums run in FP32; a bound
  * B(q) = sum_s |alpha_s| K_FK(S_s, q) is accumulated beside f.
- * rescore != 0: every query with |f| <= rescore_eps * B(q) (the FP32 band)
- * is evaluated again, and its f and label are replaced, so that labels equal
- * an FP64 evaluation: first in double-float arithmetic (FP64 kinematics,
- * summands and sums as FP32 pairs, ~1e-13 relative), then, for the queries
- * it leaves within 1e-9 B(q) of zero, in FP64 (FK and kernel).  The call
- * reads the band size back, so it synchronises `stream` once.  rescore_eps
- * <= 0 selects the library default.  n_rescored (host, may be NULL) receives
- * the size of the FP32 band; filling it synchronises `stream`.
+ * rescore != 0: every query with |f| <= eps(q) B(q) (the FP32 band, see
+ * fk_score_band) is evaluated again, and its f and label are replaced, so
+ * that labels equal an FP64 evaluation: first in double-float arithmetic
+ * (FP64 kinematics, summands and sums as FP32 pairs, ~1e-13 relative), then,
+ * for the queries it leaves within 1e-9 B(q) of zero, in FP64 (FK and
+ * kernel).  The call reads the band size back, so it synchronises `stream`
+ * once.  rescore_eps <= 0 selects the derived bound of fk_score_band (the
+ * labels are then exact); rescore_eps > 0 replaces it by the constant
+ * eps(q) = rescore_eps (no guarantee below the bound).  n_rescored (host, may
+ * be NULL) receives the size of the FP32 band; filling it synchronises
+ * `stream`.
+ * With rescore = 0 and n_rescored NULL the call does not synchronise and
+ * does not read the error word: a shared-memory tile wait that gave up
+ * (FK_ERR_TIMEOUT on the other paths) then goes unreported and the labels
+ * are undefined; pass n_rescored to have it checked.
  * precision FK_F16: the differences and t = 1 + gamma/2 |p - s|^2 are
  * computed in packed half precision, the rest in FP32; with rescore != 0 every
- * query with |f| <= rescore_eps * B(q) (default 2e-3) goes through the FP32
+ * query with |f| <= eps(q) B(q) (the half band of fk_score_band) goes through the FP32
  * path above (and its FP64 re-score), so the labels are again those of an
  * FP64 evaluation; n_rescored then counts the queries of the half pass's
  * band.  The call synchronises `stream` once when rescore != 0. */
 int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, int rescore, double rescore_eps,
              float *f, int8_t *label, int64_t *n_rescored, void *stream);
+
+/* The default FP32 band of fk_score (Sec. III-B label rule made exact): the
+ * kernel sends a query to the re-score when |f| <= eps(q) B(q) with
+ * eps(q) = eps0 + eps1 (|p(q)| + |s|max), |p(q)| the largest norm of the
+ * query's configuration-dependent control points and |s|max that of the
+ * support set's, both in coordinates scaled by sqrt(gamma/2).  eps(q)
+ * bounds the kernel's whole error |f~ - f| / B(q) (kinematics, summands,
+ * reciprocals, accumulation), so every label it decides without the
+ * re-score is the sign of the exact f.  precision FK_F32 or FK_F16; for the
+ * non-paper Gaussian summand the bands are measured, not derived (eps1 = 0).
+ * eps0, eps1: host out. */
+int fk_score_band(const fastron_model_t *model, int precision, double *eps0, double *eps1);
 
 /* fk_score with rescore = 1 for callers that must not allocate device memory
  * while they score (a real-time planner loop, a process whose device memory
@@ -267,11 +286,36 @@ int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, i
  *     overlaps (e.g. on two streams without ordering) race and corrupt each
  *     other's band lists; order them on one stream;
  *   - the model must have been trained or set beforehand (its own buffers are
- *     allocated by fastron_train / fastron_model_set, not here).
+ *     allocated by fastron_train / fastron_model_set, not here);
+ *   - every call reads its error word back, so it synchronises `stream` once
+ *     and returns FK_ERR_TIMEOUT if a tile wait gave up;
+ *   - the array's address is cached per device for the life of the process:
+ *     do not call this after a cudaDeviceReset of that device.
  * Arguments and results are those of fk_score with precision FK_F32 and
  * rescore = 1. */
 int fk_score_noalloc(fastron_model_t *model, const float *q, int64_t n, double rescore_eps, float *f, int8_t *label,
                      int64_t *n_rescored, void *stream);
+
+/* ---- premises of the band of fk_score_band -----------------------------
+ * The derivation of the band takes three facts about the arithmetic of the
+ * score kernel; these calls let a test check them on the device that scores.
+ * They are not part of the paper's method.
+ *
+ * fk_check_rcp: max |rcp(x) x - 1| of the kernel's MUFU reciprocal
+ * (rcp.approx.ftz.f32) over every FP32 mantissa of the binades
+ * [2^e_lo, 2^(e_hi + 1)), -126 <= e_lo <= e_hi <= 127.  The bound assumes
+ * 2^-23.  Synchronous; max_rel host out.
+ * fk_check_sincos: max absolute error of the kernels' pair-arithmetic sine
+ * and cosine of x + theta0 against FP64, over every FP32 x in [-hi, hi]
+ * (|theta0| + hi < 2^16).  Synchronous; max_abs host out.
+ * fk_forward_dd: the configuration-dependent control points (Eq. 2) of n
+ * configurations q (device float, n x D) as the score kernels form them:
+ * pair-arithmetic kinematics times `scale`, rounded once to FP32; cp device
+ * float SoA [Mv][3][n] (Mv = points not fixed to the base, in chain order).
+ * Stream-ordered. */
+int fk_check_rcp(int e_lo, int e_hi, double *max_rel);
+int fk_check_sincos(float hi, double theta0, double *max_abs);
+int fk_forward_dd(const fk_chain_t *chain, const float *q, int64_t n, double scale, float *cp, void *stream);
 
 /* ---- ground-truth labels (geometric checker) ---------------------------
  * Link i (1..D) is the segment between the origins of frames i-1 and i,

@@ -232,14 +232,94 @@ int orc_score(int M, double gamma, int64_t ns, const double *cps, const double *
 /* Column i of the kernel matrix over the training set (computeKernelMatrixColumn).
  * store32 != 0: every entry is rounded to the nearest FP32 value, the kernel
  * matrix as it is held when it is stored in single precision (65,536
- * training points take 17.2 GB in FP32); the margins and weights stay FP64. */
-static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int64_t i, double *col, int store32,
-                          int kind)
+ * training points take 17.2 GB in FP32); the margins and weights stay FP64.
+ *
+ * The entries of a column are independent, so a column may be split over
+ * threads: each entry is the same orc_k_fk_s call whichever thread makes it,
+ * and the column, hence Algorithm 1, does not depend on the thread count.
+ * The workers of one training call wait on a condition variable for each
+ * column (a generation counter) and report back on another. */
+typedef struct {
+    int M, store32, kind, nthreads, stop;
+    double gamma;
+    int64_t N, i;
+    const double *cpX;
+    double *col;
+    pthread_mutex_t mu;
+    pthread_cond_t go, fin;
+    int64_t gen;   /* column generation: a worker computes its range once per value */
+    int pending;   /* workers still computing the current column */
+} col_pool;
+
+typedef struct {
+    col_pool *p;
+    int rank;
+} col_worker_arg;
+
+static void column_range(const col_pool *p, int rank)
 {
-    for (int64_t j = 0; j < N; ++j) {
-        double k = orc_k_fk_s(M, cpX + j * M * 3, cpX + i * M * 3, gamma, kind);
-        col[j] = store32 ? (double)(float)k : k;
+    int64_t per = (p->N + p->nthreads - 1) / p->nthreads;
+    int64_t lo = rank * per, hi = lo + per < p->N ? lo + per : p->N;
+    for (int64_t j = lo; j < hi; ++j) {
+        double k = orc_k_fk_s(p->M, p->cpX + j * p->M * 3, p->cpX + p->i * p->M * 3, p->gamma, p->kind);
+        p->col[j] = p->store32 ? (double)(float)k : k;
     }
+}
+
+static void *column_worker(void *arg)
+{
+    col_worker_arg *a = (col_worker_arg *)arg;
+    col_pool *p = a->p;
+    int64_t seen = 0;
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        while (!p->stop && p->gen == seen)
+            pthread_cond_wait(&p->go, &p->mu);
+        if (p->stop) {
+            pthread_mutex_unlock(&p->mu);
+            break;
+        }
+        seen = p->gen;
+        pthread_mutex_unlock(&p->mu);
+        column_range(p, a->rank);
+        pthread_mutex_lock(&p->mu);
+        if (--p->pending == 0)
+            pthread_cond_signal(&p->fin);
+        pthread_mutex_unlock(&p->mu);
+    }
+    return NULL;
+}
+
+static void kernel_column(col_pool *p, int64_t i)
+{
+    if (p->nthreads > 1) {
+        pthread_mutex_lock(&p->mu);
+        p->i = i;
+        p->pending = p->nthreads - 1;
+        ++p->gen;
+        pthread_cond_broadcast(&p->go);
+        pthread_mutex_unlock(&p->mu);
+    } else {
+        p->i = i;
+    }
+    column_range(p, 0);
+    if (p->nthreads > 1) {
+        pthread_mutex_lock(&p->mu);
+        while (p->pending > 0)
+            pthread_cond_wait(&p->fin, &p->mu);
+        pthread_mutex_unlock(&p->mu);
+    }
+}
+
+/* Stops and joins the first n - 1 workers. */
+static void pool_stop(col_pool *p, pthread_t *th, int n)
+{
+    pthread_mutex_lock(&p->mu);
+    p->stop = 1;
+    pthread_cond_broadcast(&p->go);
+    pthread_mutex_unlock(&p->mu);
+    for (int t = 1; t < n; ++t)
+        pthread_join(th[t], NULL);
 }
 
 /*
@@ -266,15 +346,49 @@ static void kernel_column(int M, double gamma, int64_t N, const double *cpX, int
  * not NULL, pass k records kind (1 add, 2 removal), index and delta (the
  * change of alpha_i) in trace_kind/trace_idx/trace_delta[k].  store32: see
  * kernel_column.  kind: the summand of the FK kernel, 0 the paper's RQ
- * kernel (Eq. 3), 1 the Gaussian alternative (orc_k_gauss).
+ * kernel (Eq. 3), 1 the Gaussian alternative (orc_k_gauss).  nthreads: the
+ * threads that share each column's entries (the passes themselves stay
+ * sequential); the result is the same for every nthreads.
  */
-int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
-                           int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
-                           int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32, int kind)
+int orc_fastron_train_mt(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                         int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                         int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32, int kind,
+                         int nthreads)
 {
     double *col = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     if (!col)
         return -2;
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 256)
+        nthreads = 256;
+    col_pool pool;
+    memset(&pool, 0, sizeof pool);
+    pool.M = M;
+    pool.store32 = store32;
+    pool.kind = kind;
+    pool.gamma = gamma;
+    pool.N = N;
+    pool.cpX = cpX;
+    pool.col = col;
+    pool.nthreads = 1;
+    pthread_mutex_init(&pool.mu, NULL);
+    pthread_cond_init(&pool.go, NULL);
+    pthread_cond_init(&pool.fin, NULL);
+    pthread_t th[256];
+    col_worker_arg wa[256];
+    int started = 1;
+    for (int t = 1; t < nthreads; ++t) {
+        wa[t].p = &pool;
+        wa[t].rank = t;
+        if (pthread_create(&th[t], NULL, column_worker, &wa[t]) != 0)
+            break;
+        started = t + 1;
+    }
+    /* workers read nthreads only once a column is posted, under the mutex */
+    pthread_mutex_lock(&pool.mu);
+    pool.nthreads = started;
+    pthread_mutex_unlock(&pool.mu);
     int64_t nnz = 0, adds = 0, removes = 0, iters = 0;
     int converged = 0;
     for (int64_t j = 0; j < N; ++j)
@@ -292,7 +406,7 @@ int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, co
             }
         }
         if (i >= 0 && mmin <= 0.0) {
-            kernel_column(M, gamma, N, cpX, i, col, store32, kind);
+            kernel_column(&pool, i);
             if (nnz < s_max || alpha[i] != 0.0) {
                 double b = y[i] > 0 ? beta : 1.0;
                 double delta = b * y[i] - F[i];
@@ -324,7 +438,7 @@ int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, co
             }
         }
         if (r >= 0 && mmax > 0.0) {
-            kernel_column(M, gamma, N, cpX, r, col, store32, kind);
+            kernel_column(&pool, r);
             double a = alpha[r];
             for (int64_t j = 0; j < N; ++j)
                 F[j] = fma(-a, col[j], F[j]);
@@ -342,6 +456,10 @@ int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, co
         converged = 1;
         break;
     }
+    pool_stop(&pool, th, started);
+    pthread_mutex_destroy(&pool.mu);
+    pthread_cond_destroy(&pool.go);
+    pthread_cond_destroy(&pool.fin);
     free(col);
     stats[0] = iters;
     stats[1] = adds;
@@ -349,6 +467,14 @@ int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, co
     stats[3] = converged;
     stats[4] = nnz;
     return 0;
+}
+
+int orc_fastron_train_kind(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,
+                           int64_t iter_max, int64_t s_max, double *alpha, double *F, int64_t *stats,
+                           int8_t *trace_kind, int64_t *trace_idx, double *trace_delta, int store32, int kind)
+{
+    return orc_fastron_train_mt(M, gamma, N, cpX, y, beta, iter_max, s_max, alpha, F, stats, trace_kind, trace_idx,
+                                trace_delta, store32, kind, 1);
 }
 
 int orc_fastron_train_store(int M, double gamma, int64_t N, const double *cpX, const int8_t *y, double beta,

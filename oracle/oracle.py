@@ -81,6 +81,8 @@ def _load():
         lib.orc_score_s.restype = I
         lib.orc_fastron_train_kind.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I, I]
         lib.orc_fastron_train_kind.restype = I
+        lib.orc_fastron_train_mt.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I, I, I]
+        lib.orc_fastron_train_mt.restype = I
         lib.orc_fastron_train.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P]
         lib.orc_fastron_train.restype = I
         lib.orc_fastron_train_store.argtypes = [I, Dbl, I64, P, P, Dbl, I64, I64, P, P, P, P, P, P, I]
@@ -202,13 +204,15 @@ class TrainResult:
 
 def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000, s_max: int | None = None,
                   alpha0=None, F0=None, trace: bool = False, store32: bool = False,
-                  summand: str = "rq") -> TrainResult:
+                  summand: str = "rq", nthreads: int = 1) -> TrainResult:
     """Algorithm 1 (Sec. III-B) on training control points cpX (N, M, 3) and labels y in {+1, -1}.
 
     alpha0/F0 warm-start the model (loadPreviousModel); zeros otherwise.
     store32: kernel-matrix entries rounded to the nearest FP32 value (the
     matrix held in single precision); margins and weights stay FP64.
-    summand: "rq" (the paper's kernel) or "gauss" (see SUMMANDS)."""
+    summand: "rq" (the paper's kernel) or "gauss" (see SUMMANDS).
+    nthreads: threads sharing the entries of each kernel-matrix column (the
+    result does not depend on it)."""
     cpX = _d(cpX)
     N, M = cpX.shape[0], cpX.shape[1]
     y = np.ascontiguousarray(y, dtype=np.int8)
@@ -223,8 +227,9 @@ def fastron_train(cpX, y, gamma: float, beta: float = 1.0, iter_max: int = 5000,
         tr = (_p(tk), _p(ti), _p(td))
     else:
         tr = (None, None, None)
-    rc = _load().orc_fastron_train_kind(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
-                                        _p(alpha), _p(F), _p(stats), *tr, int(bool(store32)), SUMMANDS[summand])
+    rc = _load().orc_fastron_train_mt(M, float(gamma), N, _p(cpX), _p(y), float(beta), int(iter_max), s_max,
+                                      _p(alpha), _p(F), _p(stats), *tr, int(bool(store32)), SUMMANDS[summand],
+                                      int(nthreads))
     if rc != 0:
         raise RuntimeError("orc_fastron_train failed")
     tr_out = None

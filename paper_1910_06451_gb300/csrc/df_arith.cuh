@@ -2,7 +2,10 @@
 // numbers (about 48 significant bits), manipulated with the error-free
 // transformations two-sum (Knuth, TAOCP vol. 2, 4.2.2) and two-product by
 // FMA (Dekker, Numer. Math. 18, 1971, with the splitting replaced by the
-// fused product), so FP64-class accuracy comes from the FP32 pipes.
+// fused product), so FP64-class accuracy comes from the FP32 pipes.  The
+// sums and the products whose rounding error is recovered are written with
+// the round-to-nearest intrinsics, which the compiler never fuses into an
+// FMA (a fused product would no longer be the value the error term assumes).
 #pragma once
 
 #include "fk_ptx.cuh"
@@ -14,13 +17,13 @@ struct dfl {
 };
 
 __device__ __forceinline__ dfl two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 __device__ __forceinline__ dfl quick_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 __device__ __forceinline__ dfl df_from_double(double x) {
   const float h = __double2float_rn(x);
@@ -34,12 +37,12 @@ __device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
 }
 // (h + l)^2 = h^2 + 2 h l (l^2 is below the precision); h^2 exactly by FMA
 __device__ __forceinline__ dfl df_sqr(dfl a) {
-  const float p = a.h * a.h;
+  const float p = __fmul_rn(a.h, a.h);
   const float e = fmaf(a.h, a.h, -p);
   return quick_two_sum(p, fmaf(2.f * a.h, a.l, e));
 }
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
+  const float p = __fmul_rn(a.h, b.h);
   const float e = fmaf(a.h, b.h, -p);
   return quick_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
 }
@@ -54,10 +57,10 @@ __device__ __forceinline__ dfl df_add_pos(dfl a, dfl b) {
 // FMA, 1 - p exact since p is within a factor 2 of 1): error about 2^-46
 __device__ __forceinline__ dfl df_rcp(dfl a) {
   const float y = rcp_approx(a.h);
-  const float p = a.h * y;
+  const float p = __fmul_rn(a.h, y);
   const float pe = fmaf(a.h, y, -p);
   const float e = ((1.f - p) - pe) - a.l * y;
-  return quick_two_sum(y, y * e);
+  return quick_two_sum(y, __fmul_rn(y, e));
 }
 
 
@@ -78,7 +81,7 @@ __device__ __forceinline__ void df_rq_term(const float qh[3], const float ql[3],
   for (int r = 0; r < 3; ++r) {
     const dfl d = two_sum(qh[r], -s[2 * r]);
     const float dl = d.l + (ql[r] - s[2 * r + 1]);
-    p[r] = d.h * d.h;
+    p[r] = __fmul_rn(d.h, d.h);
     ep[r] = fmaf(dl, fmaf(2.f, d.h, dl), fmaf(d.h, d.h, -p[r]));
   }
   const dfl t1 = two_sum(1.f, p[0]);
@@ -86,7 +89,7 @@ __device__ __forceinline__ void df_rq_term(const float qh[3], const float ql[3],
   const dfl t3 = two_sum(t2.h, p[2]);
   const float th = t3.h;
   const float tl = ((t1.l + t2.l) + t3.l) + ((ep[0] + ep[1]) + ep[2]);
-  const float uh = th * th;
+  const float uh = __fmul_rn(th, th);
   const float ul = fmaf(2.f * th, tl, fmaf(th, th, -uh));
   const float y = rcp_approx(uh);
   const float res = fmaf(-ul, y, fmaf(-uh, y, 1.f));
@@ -133,7 +136,7 @@ __device__ __forceinline__ void df_gauss_term(const float qh[3], const float ql[
   for (int r = 0; r < 3; ++r) {
     const dfl d = two_sum(qh[r], -s[2 * r]);
     const float dl = d.l + (ql[r] - s[2 * r + 1]);
-    p[r] = d.h * d.h;
+    p[r] = __fmul_rn(d.h, d.h);
     ep[r] = fmaf(dl, fmaf(2.f, d.h, dl), fmaf(d.h, d.h, -p[r]));
   }
   const dfl t1 = two_sum(p[0], p[1]);

@@ -27,8 +27,9 @@ struct SceneDev {
   const double *alpha;
   int64_t ns;     // support points
   int64_t nrec;   // record halves, 2 rec_pairs(ns)
-  const int32_t *npair_pos;  // device: positive-weight pairs, which lead the records
-  float gs;
+  const int32_t *npair_pos;  // device: [0] positive-weight pairs, which lead the records; [1] |s|max bits
+  double gs;      // coordinate scale sqrt(gamma/2)
+  float eps0, eps1;  // the scene's band (see score_band): eps(q) = eps0 + eps1 (|p(q)| + |s|max)
   double gamma;
   int64_t q_off;  // first query of the scene in the concatenated batch
   int64_t n;      // its number of queries
@@ -47,7 +48,6 @@ struct BatchArgs {
   const float *q;
   float *f;
   int8_t *label;
-  float eps;
   int32_t *band_idx;
   int32_t *band_scene;
   int32_t *band_cnt;
@@ -76,10 +76,13 @@ __global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) 
     }
     __syncthreads();
     const int64_t off = sc->q_off;
-    const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, a.eps, a.band_idx, a.band_scene, w.scene, off,
-                     a.band_cnt, a.err, a.wait_limit, sc->npair_pos};
-    const bool ok = score_block<MV, Q, TP, NTHR, false, false, false, 0, true>(
-        cs, sc->rec, sc->nrec, sc->gs, a.q + off * sc->cf.D, sc->n, (int64_t)w.block * (NTHR * Q), o, tiles, bar);
+    const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, sc->eps0, sc->eps1, a.band_idx, a.band_scene, w.scene,
+                     off, a.band_cnt, a.err, a.wait_limit, sc->npair_pos};
+    const double gsd = sc->gs;
+    const float gh = __double2float_rn(gsd);
+    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->nrec, dd{gh, __double2float_rn(gsd - (double)gh)},
+                                                 a.q + off * sc->cf.D, sc->n, (int64_t)w.block * (NTHR * Q), o, tiles,
+                                                 bar);
     if (!ok) break;   // identical in every thread
     __syncthreads();  // item_sh, cs and the tiles are reused by the next item
   }
@@ -317,7 +320,7 @@ size_t work_item_size() { return sizeof(WorkItem); }
 // Host-side filling of a SceneDev record (the layout stays private to this file).
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
                     const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
-                    int64_t q_off, int64_t n) {
+                    float eps0, float eps1, int64_t q_off, int64_t n) {
   SceneDev d;
   memset(&d, 0, sizeof d);
   d.cf = cf;
@@ -329,7 +332,9 @@ void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *r
   d.ns = ns;
   d.nrec = 2 * rec_pairs(ns);
   d.npair_pos = npair_pos;
-  d.gs = (float)sqrt(0.5 * gamma);
+  d.gs = sqrt(0.5 * gamma);
+  d.eps0 = eps0;
+  d.eps1 = eps1;
   d.gamma = gamma;
   d.q_off = q_off;
   d.n = n;
@@ -342,11 +347,11 @@ void fill_work_item(void *dst, int32_t scene, int32_t block) {
 }
 
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
-                                      int32_t *counter, const float *q, float *f, int8_t *label, float eps,
+                                      int32_t *counter, const float *q, float *f, int8_t *label,
                                       int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
                                       uint32_t wait_limit, cudaStream_t s, bool prepare_only) {
   BatchArgs a{static_cast<const SceneDev *>(scenes), static_cast<const WorkItem *>(items), n_items, counter, q, f,
-              label, eps, band_idx, band_scene, band_cnt, err, wait_limit};
+              label, band_idx, band_scene, band_cnt, err, wait_limit};
   return launch_batched_score(mv, variant, a, s, prepare_only);
 }
 

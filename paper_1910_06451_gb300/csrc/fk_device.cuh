@@ -27,13 +27,19 @@ struct ChainF {
   int vidx[FK_MAX_CP];          // its index among all M points
   int cj[FK_MAX_CP];            // frame of every point (fk_forward output order)
   float ct[FK_MAX_CP][3];
-  // The first configuration-dependent point rides on frame 1 of a revolute
-  // joint 1 (and the base rotation is orthonormal): it moves on a circle of
-  // radius rho about joint 1's axis, so its squared distance between
-  // configurations is rho^2 (2 - 2 cos(theta_q - theta_s)), theta = q_1 + theta0_1.
-  int cp1;
-  double cp1_rho2;
   int summand;  // FK_SUMMAND_RQ or FK_SUMMAND_GAUSS
+  // Low parts of the FP64 parameters (value = float field + low part, about
+  // 48 bits), for the pair-arithmetic kinematics of the score kernels.
+  float a_l[FK_MAX_DOF], ca_l[FK_MAX_DOF], sa_l[FK_MAX_DOF], d_l[FK_MAX_DOF], th0_l[FK_MAX_DOF];
+  float R0_l[9], p0_l[3];
+  float vt_l[FK_MAX_CP][3];
+  int vt_nz[FK_MAX_CP];         // offset of configuration-dependent point v is not zero
+  // Twist of +-pi/2: sin(alpha) is exactly +-1 in FP64 and |cos(alpha)| <
+  // 2^-40, so Rx(alpha) is taken as a signed swap of the y and z columns.
+  int quarter[FK_MAX_DOF];
+  int rot_last;                 // a configuration-dependent point on frame D has an offset
+  float reach;                  // sum over links of |a| + |d| + |theta0 or d offset| bound, plus
+                                // |p0| and the largest offset (metres): bounds every lever arm
 };
 
 // The same chain for the FP64 kernels.  cos/sin of the link twists are taken

@@ -76,6 +76,13 @@ cudaError_t launch_margins(const void *G, int g32, int64_t N, const double *alph
 // the z coordinates two points at a time (z_a, z_b, z_a', z_b'), then the
 // weights (w_a, w_b, |w_a|, |w_b|) with w = alpha / M; coordinates are scaled
 // by sqrt(gamma / 2).
+// Support pairs summed in plain FP32 by the score kernels before each
+// partial sum is folded into a pair (two-sum) accumulator, and the smallest
+// shared-memory tile (support pairs) of any score kernel; partial sums also
+// restart at tile boundaries.  Both enter the error bound of the band.
+constexpr int kFoldPairs = 16;
+constexpr int kMinTilePairs = 32;
+
 __host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 1; }
 // Pair records of a support set of ns points: the points with alpha > 0 come
 // first, then those with alpha < 0, each group padded to an even count with a
@@ -103,13 +110,10 @@ struct PackArgs {
   double *alpha_out;  // [ns] (copy of alpha, compacted)
   double *q_out;      // [ns][D] support configurations
   float *sdf;         // [ns][rec_df_len(Mv)] double-float records
-  float4 *rec1;       // or null: the records again with entry 0 holding
-                      // (U_a, U_b, V_a, V_b), U = k cos theta, V = k sin theta
-                      // of joint 1, k = gamma rho^2 (see ChainF::cp1)
-  double cp1_k;
   double scale;       // coordinate scale: sqrt(gamma/2) (RQ), sqrt(gamma/2 log2 e) (Gaussian)
   int32_t *slot;      // [ns] scratch: record half of each support point
-  int32_t *npair_pos; // [1] out: number of positive-weight pairs
+  int32_t *npair_pos; // [2] out: [0] number of positive-weight pairs, [1] bits of the
+                      // largest norm of a scaled support control point (float, rounded up)
 };
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s);
 
@@ -119,10 +123,8 @@ struct ScoreArgs {
   int64_t n;
   const float4 *rec;
   int64_t ns;          // record halves: 2 rec_pairs(support points)
-  const float4 *rec1;  // or null; with it the first point's t = A - U cos theta_q - V sin theta_q
-  float cp1_A;         // 1 + k
-  float gs;           // scale of the control points (PackArgs::scale)
-  float eps;          // band: |f| <= eps * B(q)
+  double gs;          // scale of the control points (PackArgs::scale)
+  float eps0, eps1;   // band: |f| <= eps(q) B(q), eps(q) = eps0 + eps1 (|p(q)| + |s|max)
   float *f;           // [n] or null
   int8_t *label;      // [n]
   int32_t *band_idx;  // [n] or null (no rescore)
@@ -130,7 +132,8 @@ struct ScoreArgs {
   int32_t *err;       // [1]
   uint32_t wait_limit;  // polls of a tile wait before it gives up
   int poly;           // Gaussian summand, 7 points: points per support point on the FMA polynomial
-  const int32_t *npair_pos;  // device: positive-weight pairs, which lead the records
+  const int32_t *npair_pos;  // device: [0] positive-weight pairs, which lead the records;
+                             // [1] float bits of the largest scaled support-point norm
 };
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
 

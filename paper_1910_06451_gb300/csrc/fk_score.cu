@@ -1,22 +1,23 @@
 // Proxy collision check: the Fastron model value f(q) = sum_s alpha_s
 // K_FK(S_s, q) with the FK kernel of Eq. 4 and its sign (Sec. III-B).
 //
-// Three kernels:
-//   pack     support set -> per support point s one record of Mv + 1 float4:
-//            for each configuration-dependent control point m,
-//            (-gamma s_m, 1 + gamma/2 |s_m|^2), then (w_s, |w_s|, 0, 0) with
-//            w_s = alpha_s / M; plus the FP64 control points for re-scoring.
-//            All from FP64 kinematics, rounded to FP32 once.
-//   score    FP32.  One thread scores two queries: FK in registers, then the
-//            support records stream through shared memory by tile (1-D TMA
-//            bulk copies, double-buffered, mbarrier completion) and every
-//            thread reads each record as a broadcast.  Per (s, m):
-//              t = (c_sm + gamma/2 |p_m|^2) + s'_m . p_m  = 1 + gamma/2 |p_m - s_m|^2
-//            and two summands share one reciprocal:
-//              1/t1^2 + 1/t2^2 = (t1^2 + t2^2) / (t1 t2)^2.
-//            Beside f the kernel accumulates B(q) = sum_s |w_s| sum_m t^-2,
-//            which bounds |f| and scales the FP32 error; queries with
-//            |f| <= eps B(q) are appended to a band list.
+// Kernels:
+//   pack     support set -> pair records (see fk_internal.h: scaled FP32
+//            coordinates of two support points, their weights w = alpha/M),
+//            the positive-weight pairs first; double-float records and FP64
+//            control points for the re-score; the largest norm of a scaled
+//            support control point.  All from FP64 kinematics, rounded once.
+//   score    FP32.  One thread scores two queries: FK in pair arithmetic,
+//            rounded to FP32, in registers; the support records stream
+//            through shared memory by tile (1-D TMA bulk copies,
+//            double-buffered, mbarrier completion) and every thread reads each
+//            record as a broadcast.  Per (s, m): t = 1 + |p_m - s_m|^2 in
+//            scaled coordinates (three differences, three FMAs), and two
+//            summands share one reciprocal: 1/t1^2 + 1/t2^2 = (t1^2 + t2^2) /
+//            (t1 t2)^2.  Beside f the kernel forms B(q) = sum_s |w_s| sum_m
+//            t^-2 and appends the queries with |f| <= eps(q) B(q) to a band
+//            list; eps(q) bounds the kernel's whole error (the derivation is
+//            at the host's score_band).
 //   gauss    the non-paper Gaussian summand 2^(-|d|^2) (coordinates scaled
 //            by sqrt(gamma/2 log2 e)) on MUFU ex2, optionally partly on an
 //            FMA polynomial, or in packed half with ex2.f16x2.
@@ -102,11 +103,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
   const int64_t j = a.slot[s] >> 1;
   const int h = a.slot[s] & 1;
   float *rec = reinterpret_cast<float *>(a.rec + j * REC);
-  float *rec1 = a.rec1 ? reinterpret_cast<float *>(a.rec1 + j * REC) : nullptr;
-  auto put = [&](int e, int c, float v) {  // component c (0..3) of record entry e
-    rec[4 * e + c] = v;
-    if (rec1) rec1[4 * e + c] = v;
-  };
+  auto put = [&](int e, int c, float v) { rec[4 * e + c] = v; };  // component c (0..3) of record entry e
   const double gs = a.scale;
   const int64_t src = a.idx ? (int64_t)a.idx[s] : s;
   const double *x = a.X + src * cd.D;
@@ -136,12 +133,14 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
   if (MV & 1) put(MV + MV / 2, 2 + h, 0.f);  // unused z slot of the last entry
   put(REC - 1, h, (float)wd);
   put(REC - 1, 2 + h, (float)fabs(wd));
-  if (rec1) {
-    // circle form of point 0: U = k cos theta, V = k sin theta, theta = q_1 + theta0_1
-    const double th = x[0] + cd.th0[0];
-    rec1[h] = (float)(a.cp1_k * cos(th));
-    rec1[2 + h] = (float)(a.cp1_k * sin(th));
+  // largest norm of a scaled configuration-dependent control point, rounded
+  // up to FP32 (non-negative floats order like their bit patterns)
+  double nmax = 0.0;
+  for (int v = 0; v < MV; ++v) {
+    const double *p = cp[cf.vidx[v]];
+    nmax = fmax(nmax, gs * sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]));
   }
+  atomicMax(a.npair_pos + 1, __float_as_int(__double2float_ru(nmax * (1.0 + 1e-12))));
   if (a.sdf) {
     float *r = a.sdf + s * rec_df_len(MV);
     for (int v = 0; v < MV; ++v)
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
 cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackArgs &a, cudaStream_t s) {
   const size_t rec_bytes = sizeof(float4) * (size_t)rec_pairs(a.ns) * rec_len(cf.Mv);
   cudaError_t e = cudaMemsetAsync(a.rec, 0, rec_bytes, s);
-  if (e == cudaSuccess && a.rec1) e = cudaMemsetAsync(a.rec1, 0, rec_bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.npair_pos + 1, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   sign_slots_kernel<<<1, kSlotThreads, 0, s>>>(a.alpha, a.ns, a.slot, a.npair_pos);
   if (a.ns > 0) pack_kernel<<<(unsigned)((a.ns + kPackThreads - 1) / kPackThreads), kPackThreads, 0, s>>>(cf, cd, a);
@@ -170,18 +169,32 @@ cudaError_t launch_pack_support(const ChainF &cf, const ChainD &cd, const PackAr
 
 // --------------------------------------------------------------- score ---
 constexpr int kScoreThreads = 256;
-constexpr int kQ = 2;                          // queries per thread
-constexpr int kQueriesPerCta = kScoreThreads * kQ;
+// queries per thread: two share every shared-memory read of a support pair;
+// above 8 points their packed coordinates (2 x 3 x Mv 64-bit registers)
+// would not fit in the 128 registers of two CTAs per SM, so one
+template <int MV>
+__host__ __device__ constexpr int queries_per_thread() {
+  return MV > 8 ? 1 : 2;
+}
+template <int MV>
+__host__ __device__ constexpr int queries_per_cta() {
+  return kScoreThreads * queries_per_thread<MV>();
+}
 constexpr int kTilePairs = 64;                 // support pairs per shared-memory tile
 
-template <int MV, bool CP1>
+__device__ __forceinline__ dd pair_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+template <int MV>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, a.npair_pos};
-  score_block<MV, kQ, kTilePairs, kScoreThreads, false, CP1, false, 0, true>(c, CP1 ? a.rec1 : a.rec, a.ns, a.gs, a.q, a.n,
-                                                             (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar,
-                                                             a.cp1_A);
+  const BlockOut o{a.f, a.label, a.eps0, a.eps1, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit,
+                   a.npair_pos};
+  score_block<MV, queries_per_thread<MV>(), kTilePairs, kScoreThreads>(
+      c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * queries_per_cta<MV>(), o, tiles, bar);
 }
 
 // The non-paper Gaussian summand (FP32 with POLY points per support point on
@@ -190,9 +203,10 @@ template <int MV, bool HALF, int POLY>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_gauss_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, a.npair_pos};
-  score_block<MV, kQ, kTilePairs, kScoreThreads, HALF, false, true, POLY, !HALF>(
-      c, a.rec, a.ns, a.gs, a.q, a.n, (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
+  const BlockOut o{a.f, a.label, a.eps0, a.eps1, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit,
+                   a.npair_pos};
+  score_block<MV, queries_per_thread<MV>(), kTilePairs, kScoreThreads, HALF, true, POLY>(
+      c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * queries_per_cta<MV>(), o, tiles, bar);
 }
 
 // The packed-half variant of the same block (differences and t in FP16).
@@ -200,9 +214,10 @@ template <int MV>
 __global__ void __launch_bounds__(kScoreThreads, 2) score_f16_kernel(const ChainF c, const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
-  const BlockOut o{a.f, a.label, a.eps, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit, nullptr};
-  score_block<MV, kQ, kTilePairs, kScoreThreads, true>(c, a.rec, a.ns, a.gs, a.q, a.n,
-                                                       (int64_t)blockIdx.x * kQueriesPerCta, o, tiles, bar);
+  const BlockOut o{a.f, a.label, a.eps0, a.eps1, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit,
+                   a.npair_pos};
+  score_block<MV, queries_per_thread<MV>(), kTilePairs, kScoreThreads, true>(
+      c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * queries_per_cta<MV>(), o, tiles, bar);
 }
 
 }  // namespace fk
@@ -215,7 +230,7 @@ static cudaError_t launch_score_h_mv(const ChainF &c, const ScoreArgs &a, cudaSt
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(score_f16_kernel<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  const unsigned grid = (unsigned)((a.n + queries_per_cta<MV>() - 1) / queries_per_cta<MV>());
   score_f16_kernel<MV><<<grid, kScoreThreads, smem, s>>>(c, a);
   return cudaGetLastError();
 }
@@ -227,7 +242,7 @@ static cudaError_t launch_gauss_mv(const ChainF &c, const ScoreArgs &a, cudaStre
   auto kern = score_gauss_kernel<MV, HALF, POLY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  const unsigned grid = (unsigned)((a.n + queries_per_cta<MV>() - 1) / queries_per_cta<MV>());
   kern<<<grid, kScoreThreads, smem, s>>>(c, a);
   return cudaGetLastError();
 }
@@ -271,20 +286,17 @@ cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s
   }
 }
 
-template <int MV, bool CP1 = false>
+template <int MV>
 static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   constexpr int REC = MV + (MV + 1) / 2 + 1;
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
-  auto kern = score_f32_kernel<MV, CP1>;
+  auto kern = score_f32_kernel<MV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((a.n + kQueriesPerCta - 1) / kQueriesPerCta);
+  const unsigned grid = (unsigned)((a.n + queries_per_cta<MV>() - 1) / queries_per_cta<MV>());
   kern<<<grid, kScoreThreads, smem, s>>>(c, a);
   return cudaGetLastError();
 }
-
-// Shapes with a compiled circle-form kernel (the 3- and 7-DOF workloads).
-bool score_cp1_supported(int mv) { return mv == 3 || mv == 7 || mv == 11; }
 
 // Shapes with a compiled score kernel: the number of configuration-dependent
 // control points.
@@ -300,14 +312,6 @@ bool score_supported(int mv) {
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   if (c.summand == FK_SUMMAND_GAUSS) return launch_score_gauss(c, a, false, s);
-  if (a.rec1) {
-    switch (c.Mv) {
-      case 3: return launch_score_mv<3, true>(c, a, s);
-      case 7: return launch_score_mv<7, true>(c, a, s);
-      case 11: return launch_score_mv<11, true>(c, a, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (c.Mv) {
     case 1: return launch_score_mv<1>(c, a, s);
     case 2: return launch_score_mv<2>(c, a, s);

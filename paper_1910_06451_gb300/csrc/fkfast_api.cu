@@ -20,10 +20,12 @@ cudaError_t launch_scatter_labels(const int8_t *src, const float *fsrc, const in
 struct GemmArgs;
 cudaError_t launch_gemm_f32(const GemmArgs &g, int splits, cudaStream_t s);
 bool score_supported(int mv);
-bool score_cp1_supported(int mv);
 bool score_gauss_supported(int mv);
 int probe_iters(int kind);
 int probe_ops_per_iter(int kind);
+cudaError_t launch_check_rcp(int e_lo, int e_hi, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_check_sincos(float hi, double th0, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_forward_dd(const ChainF &c, const float *q, int64_t n, double scale, float *cp, cudaStream_t s);
 }  // namespace fk
 
 using namespace fk;
@@ -133,34 +135,31 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
     f.sa[i] = (float)sa;
     f.d[i] = (float)dh[i].d;
     f.th0[i] = (float)dh[i].theta0;
+    f.a_l[i] = (float)(dh[i].a - (double)f.a[i]);
+    f.ca_l[i] = (float)(ca - (double)f.ca[i]);
+    f.sa_l[i] = (float)(sa - (double)f.sa[i]);
+    f.d_l[i] = (float)(dh[i].d - (double)f.d[i]);
+    f.th0_l[i] = (float)(dh[i].theta0 - (double)f.th0[i]);
+    f.quarter[i] = fabs(sa) == 1.0 && fabs(ca) < 0x1p-40;
   }
+  double p0n = 0.0, tmax = 0.0;
   for (int r = 0; r < 3; ++r) {
     for (int k = 0; k < 4; ++k) d.T0[4 * r + k] = base[4 * r + k];
-    for (int k = 0; k < 3; ++k) f.R0[3 * r + k] = (float)base[4 * r + k];
-    f.p0[r] = (float)base[4 * r + 3];
-  }
-  // the circle of the first configuration-dependent point (see ChainF::cp1):
-  // in frame 1 the point is Rz(theta) w with w = (a, 0, d) + Rx(alpha) t
-  {
-    int first = -1;
-    for (int m = 0; m < M && first < 0; ++m)
-      if (cps[m].joint != 0) first = m;
-    double orth = 0.0;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        double g = 0.0;
-        for (int k = 0; k < 3; ++k) g += base[4 * k + i] * base[4 * k + j];
-        orth = fmax(orth, fabs(g - (i == j ? 1.0 : 0.0)));
-      }
-    f.cp1 = 0;
-    f.cp1_rho2 = 0.0;
-    if (first >= 0 && cps[first].joint == 1 && dh[0].type == FK_REVOLUTE && orth < 1e-12) {
-      const double ca = cos(dh[0].alpha), sa = sin(dh[0].alpha);
-      const double wx = dh[0].a + cps[first].t[0], wy = ca * cps[first].t[1] - sa * cps[first].t[2];
-      f.cp1 = 1;
-      f.cp1_rho2 = wx * wx + wy * wy;
+    for (int k = 0; k < 3; ++k) {
+      f.R0[3 * r + k] = (float)base[4 * r + k];
+      f.R0_l[3 * r + k] = (float)(base[4 * r + k] - (double)f.R0[3 * r + k]);
     }
+    f.p0[r] = (float)base[4 * r + 3];
+    f.p0_l[r] = (float)(base[4 * r + 3] - (double)f.p0[r]);
+    p0n += base[4 * r + 3] * base[4 * r + 3];
   }
+  // lever-arm bound of the chain (metres): base offset, every link's |a| +
+  // |d| (a prismatic joint's travel counted up to 2^10), the largest offset
+  double reach = sqrt(p0n);
+  for (int i = 0; i < D; ++i) reach += fabs(dh[i].a) + fabs(dh[i].d) + (dh[i].type == FK_PRISMATIC ? 1024.0 : 0.0);
+  for (int m = 0; m < M; ++m)
+    tmax = fmax(tmax, sqrt(cps[m].t[0] * cps[m].t[0] + cps[m].t[1] * cps[m].t[1] + cps[m].t[2] * cps[m].t[2]));
+  f.reach = (float)((reach + tmax) * (1.0 + 1e-6));
   int v = 0;
   for (int m = 0; m < M; ++m) {
     d.cj[m] = f.cj[m] = cps[m].joint;
@@ -171,7 +170,13 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
     if (cps[m].joint != 0) {
       f.vj[v] = cps[m].joint;
       f.vidx[v] = d.vidx[v] = m;
-      for (int r = 0; r < 3; ++r) f.vt[v][r] = (float)cps[m].t[r];
+      f.vt_nz[v] = 0;
+      for (int r = 0; r < 3; ++r) {
+        f.vt[v][r] = (float)cps[m].t[r];
+        f.vt_l[v][r] = (float)(cps[m].t[r] - (double)f.vt[v][r]);
+        f.vt_nz[v] |= cps[m].t[r] != 0.0;
+      }
+      if (cps[m].joint == D && f.vt_nz[v]) f.rot_last = 1;
       ++v;
     }
   }
@@ -261,15 +266,100 @@ extern "C" int fk_gram(const fk_chain_t *cc, const void *Xa, int64_t na, const v
 
 // -------------------------------------------------------------- model ---
 static constexpr int64_t kMaxTrainN = 65536;
-static constexpr double kDefaultEps = 6e-6;
 static constexpr double kDefaultEpsDf = 1e-9;  // band of the double-float re-score, relative to B(q)
-static constexpr double kDefaultEpsF16 = 2e-3;
-// Gaussian summand (not the paper's): per-query bands relative to B(q), the
-// RQ values: the measured worst |f - f64| / B(q) over 200k queries of the 3-
-// and 7-DOF models is 7.3e-8 (FP32, MUFU or polynomial) and 1.8e-4 (half),
-// as for the RQ summand (8.8e-8, 3.3e-4)
+// Gaussian summand (not the paper's): per-query bands relative to B(q), set
+// from measurement, not derived: the measured worst |f - f64| / B(q) over
+// 200k queries of the 3- and 7-DOF models is 7.3e-8 (FP32, MUFU or
+// polynomial) and 1.8e-4 (half)
 static constexpr double kDefaultEpsGauss = 6e-6;
 static constexpr double kDefaultEpsF16Gauss = 2e-3;
+
+// ---- the band of the score kernel: a bound on its whole error -----------
+// Relative error bound of MUFU rcp.approx.ftz.f32 on normal inputs (one ulp:
+// |r x - 1| <= 2^-23), the premise the derivation takes from the PTX ISA;
+// a GPU test checks it on every FP32 mantissa over the exponent range the
+// kernel uses.
+static constexpr double kRcpRel = 0x1p-23;
+
+// The score kernel (score_core.cuh, summand RQ) returns f~ and B~ for f =
+// sum_s w_s sum_m k_sm (w_s = alpha_s / M, k = t^-2, t = 1 + |p_m - s_m|^2
+// in coordinates scaled by g = sqrt(gamma/2)) and B = sum_s |w_s| sum_m k_sm,
+// and it sends a query to the re-score when |f~| <= eps(q) B~, with
+// eps(q) = eps0 + eps1 (|p~| + |s~|max): |p~| the largest norm of the
+// query's scaled FP32 control points, |s~|max that of the support set's.
+// This function returns eps0 and eps1 such that |f~ - f| <= eps(q) B; then
+// |f~| > eps(q) B~ implies that f~ has the sign of f (and f != 0), so every
+// label decided in FP32 is the label of the exact f.  With u = 2^-24:
+//
+// (1) Control points.  The query's points come from pair-arithmetic
+//     kinematics (fk_dfk.cuh, absolute error e_fk <= 2^-32 (1 + g reach))
+//     rounded once to FP32; the support's from FP64 kinematics rounded once.
+//     So e = (p~ - s~) - (p - s) has |e| <= u (1 + u) (|p~| + |s~|max) +
+//     2 e_fk.  Since t = 1 + |d|^2, t(d + e) / t(d) - 1 = (2 d.e + |e|^2) /
+//     (1 + |d|^2) and 2 |d| / (1 + |d|^2) <= 1: t is off by a factor 1 + x
+//     with |x| <= |e| + |e|^2, and k = t^-2 by at most 2 |x| (1 + 3 |x|),
+//     relative.  Every summand of every support point: 2 |e| to first order.
+// (2) Summands, from the FP32 inputs (t* = 1 + |p~ - s~|^2 exactly).  Each
+//     difference is rounded once (relative u), squared inside an FMA, and t
+//     is a chain of three FMAs over non-negative terms: t~ = t* (1 + eta),
+//     |eta| <= 5u, so 1/t~^2 is within 10u of 1/t*^2.  A shared pair
+//     (t1^2 + t2^2) / (t1 t2)^2: products t1 t2, its square, t2^2 and the
+//     numerator's FMA are rounded once each (u each, but the numerator's two
+//     roundings act on a sum of positive terms: 1u + 1u), the reciprocal
+//     rho = 2^-23: 5u + rho beside the 10u of the t's.  A single 1/t^2 = r r
+//     with r = rcp(t): 2 rho + 10u.  The Mv - NP summands (NP pairs) of a
+//     support point are added by FMAs to the exact constant count of base
+//     points: (Mv - NP) u more; the weight alpha_s / M rounded to FP32: u.
+//     So each term w_s acc_s is within A u of its value from the FP32
+//     inputs, A = max(15 + rho/u, 10 + 2 rho/u) + Mv - NP + 1.
+// (3) Accumulation.  Per packed half, the terms of one sign are summed in
+//     FP32 kFoldPairs at a time (that many roundings, each at most u times a partial
+//     sum of same-sign terms), each partial folded into a pair by two-sum
+//     (exact; the low word's own roundings add at most n_c^2 u^2 / 2 for n_c
+//     partials), the pair rounded once (u), the two halves added (u), and
+//     f = P + N (u): (kFoldPairs + 3) u + n_c^2 u^2 / 2 of sum |terms| = B.
+// B~ is bounded the same way, so dividing by B~ instead of B costs a
+// factor 1 + O(1e-5); the FP32 evaluation of eps(q) and of eps(q) B~ a few
+// u relative.  All first-order terms add up to below 1e-5, so their
+// products are below 1e-10: the factor 1 + 2^-10 on eps0 and eps1 covers
+// every such term.
+//
+// The half-precision kernel (FK_F16): coordinates and differences rounded
+// to FP16 (uh = 2^-11), t by three HFMA2: (1) with (uh + u) in place of u
+// and an absolute 2^-25 per coordinate below the FP16 normal range; (2)
+// with 10 uh for the t's; the rest in FP32 as above; factor 1 + 1/16.
+//
+// A caller-given eps (rescore_eps > 0) replaces the bound: eps0 = eps,
+// eps1 = 0.  The Gaussian summand uses measured bands (kDefaultEpsGauss,
+// kDefaultEpsF16Gauss), eps1 = 0.
+static void score_band(const ChainF &cf, int summand, double gamma, int64_t ns, bool half, double user_eps,
+                       float *eps0, float *eps1) {
+  if (user_eps > 0.0) {
+    *eps0 = (float)user_eps;
+    *eps1 = 0.f;
+    return;
+  }
+  if (summand == FK_SUMMAND_GAUSS) {
+    *eps0 = (float)(half ? kDefaultEpsF16Gauss : kDefaultEpsGauss);
+    *eps1 = 0.f;
+    return;
+  }
+  const double u = 0x1p-24, uh = 0x1p-11, rho = kRcpRel;
+  const int Mv = cf.Mv, NP = (Mv + 3) / 7;
+  const double g = sqrt(0.5 * gamma);
+  const double t_err = half ? 10.0 * uh : 10.0 * u;
+  const double pair = NP > 0 ? t_err + 5.0 * u + rho : 0.0;
+  const double single = Mv > 2 * NP ? t_err + 2.0 * rho : 0.0;
+  const double term = (pair > single ? pair : single) + (Mv - NP + 1) * u;
+  const double npair = (double)((ns + 1) / 2 + 1);
+  const double nc = npair / kFoldPairs + npair / kMinTilePairs + 2.0;
+  const double acc = (kFoldPairs + 3) * u + 0.5 * nc * nc * u * u;
+  const double efk = 0x1p-32 * (1.0 + g * cf.reach);
+  const double pos_abs = half ? 2.0 * 2.0 * sqrt(3.0) * 0x1p-25 : 0.0;
+  const double factor = half ? 1.0 + 1.0 / 16 : 1.0 + 0x1p-10;
+  *eps0 = (float)((term + acc + 4.0 * efk + pos_abs) * factor);
+  *eps1 = (float)(2.0 * ((half ? uh : 0.0) + u) * (1.0 + u) * factor);
+}
 static int g_gauss_poly = 0;  // control points per support point on the FMA polynomial
 
 extern "C" int fk_set_gauss_poly(int points) {
@@ -296,10 +386,7 @@ struct fastron_model {
   double gamma = 0.0;
   int summand = FK_SUMMAND_RQ;  // the chain's summand when the support set was packed
   DevBuf rec, cp64, alpha_s, q_s, qin, sdf;
-  DevBuf rec1;        // records with the circle form of point 0 (used when use_cp1)
-  DevBuf slot, npos;  // record slot of each support point; positive-weight pairs (device int)
-  bool use_cp1 = false;
-  float cp1_A = 0.f;
+  DevBuf slot, npos;  // record slot of each support point; [0] positive-weight pairs, [1] |s|max bits (device)
   std::vector<int64_t> host_idx;  // training indices of the support points (model_set: positions)
   bool host_idx_valid = false;
   // score scratch
@@ -324,7 +411,7 @@ extern "C" int fastron_model_create(const fk_chain_t *chain, fastron_model_t **o
 extern "C" void fastron_model_destroy(fastron_model_t *m) {
   if (!m) return;
   DevBuf *bufs[] = {&m->cpX, &m->cpdf, &m->G, &m->alpha, &m->F, &m->stats, &m->sup_idx, &m->sup_alpha, &m->trace_kind,
-                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf, &m->rec1,
+                    &m->trace_idx, &m->trace_delta, &m->rec, &m->cp64, &m->alpha_s, &m->q_s, &m->qin, &m->sdf,
                     &m->qdf, &m->part, &m->band2_idx, &m->slot, &m->npos,
                     &m->band_idx, &m->flags, &m->fb_idx, &m->fb_q, &m->fb_lab, &m->fb_f};
   for (DevBuf *b : bufs) b->release();
@@ -336,25 +423,17 @@ static int pack(fastron_model *m, const double *X, const int32_t *idx, const dou
   const fk_chain *c = m->chain;
   CK(m->rec.ensure(sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv)));
   CK(m->slot.ensure(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1)));
-  CK(m->npos.ensure(sizeof(int32_t)));
+  CK(m->npos.ensure(sizeof(int32_t) * 2));
   CK(m->cp64.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->M * 3));
   CK(m->alpha_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
   CK(m->q_s.ensure(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * c->D));
   CK(m->sdf.ensure(sizeof(float) * (size_t)(ns > 0 ? ns : 1) * rec_df_len(c->cf.Mv)));
-  // the circle form of point 0 where it is as accurate as the direct form
-  // on the far points: A = 1 + gamma rho^2 below 8 (RQ summand only)
   const int summand = c->cf.summand;
-  const double k1 = gamma * c->cf.cp1_rho2;
-  m->use_cp1 = summand == FK_SUMMAND_RQ && c->cf.cp1 && score_cp1_supported(c->cf.Mv) && 1.0 + k1 < 8.0;
-  m->cp1_A = (float)(1.0 + k1);
-  if (m->use_cp1)
-    CK(m->rec1.ensure(sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv)));
   // coordinates scaled so that the summand is (1 + |d|^2)^-2 (RQ) or
   // 2^(-|d|^2) (Gaussian), in the FP32 and the double-float records alike
   const double scale = sqrt(summand == FK_SUMMAND_GAUSS ? 0.5 * gamma * M_LOG2E : 0.5 * gamma);
   PackArgs pa{X, idx, alpha, ns, gamma, m->rec.as<float4>(), m->cp64.as<double>(), m->alpha_s.as<double>(),
-              m->q_s.as<double>(), m->sdf.as<float>(),
-              m->use_cp1 ? m->rec1.as<float4>() : nullptr, k1, scale, m->slot.as<int32_t>(), m->npos.as<int32_t>()};
+              m->q_s.as<double>(), m->sdf.as<float>(), scale, m->slot.as<int32_t>(), m->npos.as<int32_t>()};
   CK(launch_pack_support(c->cf, c->cd, pa, s));
   m->ns = ns;
   m->gamma = gamma;
@@ -566,15 +645,19 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   ChainF cf = c->cf;
   ChainD cd = c->cd;
   cf.summand = cd.summand = m->summand;
-  const float gs = (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma);
+  const double gs = sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma);
+  float eps0 = 0.f, eps1 = 0.f;
   if (precision == FK_F16) {
     if (!score_f16_supported(c->cf.Mv))
       return fail(FK_ERR_ARG, "fk_score: no half-precision kernel for %d control points", c->cf.Mv);
     CK(m->flags.ensure(sizeof(int32_t) * 2));
     CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 2, s));
     if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
-    const double eps16 = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsF16Gauss : kDefaultEpsF16);
-    ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), nullptr, 0.f, gs, (float)eps16, f, label,
+    if (!gauss && sqrt(0.5 * m->gamma) * c->cf.reach > 64.0)
+      return fail(FK_ERR_ARG, "fk_score: scaled reach %.1f too large for the half-precision differences",
+                  sqrt(0.5 * m->gamma) * c->cf.reach);
+    score_band(c->cf, m->summand, m->gamma, m->ns, true, rescore_eps, &eps0, &eps1);
+    ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), gs, eps0, eps1, f, label,
                  rescore ? m->band_idx.as<int32_t>() : nullptr, m->flags.as<int32_t>(), m->flags.as<int32_t>() + 1,
                  g_wait_limit, 0, m->npos.as<int32_t>()};
     CK(launch_score_f16(cf, sa, s));
@@ -606,9 +689,8 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   CK(cudaMemsetAsync(m->flags.p, 0, sizeof(int32_t) * 4, s));
   int32_t *cnt = m->flags.as<int32_t>(), *err = cnt + 1, *cnt2 = cnt + 2;
   if (rescore) CK(m->band_idx.ensure(sizeof(int32_t) * (size_t)n));
-  const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
-  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), m->use_cp1 ? m->rec1.as<float4>() : nullptr,
-               m->cp1_A, gs, (float)eps, f, label,
+  score_band(c->cf, m->summand, m->gamma, m->ns, false, rescore_eps, &eps0, &eps1);
+  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), gs, eps0, eps1, f, label,
                rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0,
                m->npos.as<int32_t>()};
   CK(launch_score_f32(cf, sa, s));
@@ -636,6 +718,17 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   RescoreArgs ra{q, m->band2_idx.as<int32_t>(), cnt2, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns,
                  m->gamma, f, label};
   CK(launch_rescore_f64(cd, ra, s));
+  return FK_OK;
+}
+
+extern "C" int fk_score_band(const fastron_model_t *m, int precision, double *eps0, double *eps1) {
+  if (!m || !eps0 || !eps1) return fail(FK_ERR_ARG, "fk_score_band: NULL pointer");
+  if (m->ns < 0) return fail(FK_ERR_STATE, "fk_score_band: model is untrained");
+  if (precision != FK_F32 && precision != FK_F16) return fail(FK_ERR_ARG, "fk_score_band: unsupported precision");
+  float e0 = 0.f, e1 = 0.f;
+  score_band(m->chain->cf, m->summand, m->gamma, m->ns, precision == FK_F16, 0.0, &e0, &e1);
+  *eps0 = e0;
+  *eps1 = e1;
   return FK_OK;
 }
 
@@ -741,6 +834,51 @@ extern "C" int fk_probe_pipe(int kind, double *ops_per_clk_sm, double *seconds) 
   return FK_OK;
 }
 
+// ------------------------------------------------ premises of the band ---
+static int run_check(const char *name, double *out, cudaError_t (*launch)(unsigned long long *, const void *),
+                     const void *arg) {
+  unsigned long long *d = nullptr;
+  CK(cudaMalloc(&d, sizeof *d));
+  cudaError_t e = cudaMemset(d, 0, sizeof *d);
+  if (e == cudaSuccess) e = launch(d, arg);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(FK_ERR_CUDA, "%s: %s", name, cudaGetErrorString(e));
+  memcpy(out, &h, sizeof *out);
+  return FK_OK;
+}
+
+extern "C" int fk_check_rcp(int e_lo, int e_hi, double *max_rel) {
+  if (!max_rel) return fail(FK_ERR_ARG, "fk_check_rcp: NULL pointer");
+  if (e_lo < -126 || e_hi > 127 || e_lo > e_hi) return fail(FK_ERR_ARG, "fk_check_rcp: binades outside [-126, 127]");
+  struct A { int lo, hi; } a{e_lo, e_hi};
+  return run_check("fk_check_rcp", max_rel, [](unsigned long long *d, const void *p) {
+    const A *x = static_cast<const A *>(p);
+    return launch_check_rcp(x->lo, x->hi, d, 0);
+  }, &a);
+}
+
+extern "C" int fk_check_sincos(float hi, double theta0, double *max_abs) {
+  if (!max_abs) return fail(FK_ERR_ARG, "fk_check_sincos: NULL pointer");
+  if (!(hi >= 0.f) || !(fabs(theta0) + hi < 65536.0)) return fail(FK_ERR_ARG, "fk_check_sincos: need 0 <= hi, |theta| < 2^16");
+  struct A { float hi; double th0; } a{hi, theta0};
+  return run_check("fk_check_sincos", max_abs, [](unsigned long long *d, const void *p) {
+    const A *x = static_cast<const A *>(p);
+    return launch_check_sincos(x->hi, x->th0, d, 0);
+  }, &a);
+}
+
+extern "C" int fk_forward_dd(const fk_chain_t *c, const float *q, int64_t n, double scale, float *cp, void *stream) {
+  if (!c) return fail(FK_ERR_ARG, "fk_forward_dd: chain is NULL");
+  if (n < 0) return fail(FK_ERR_ARG, "fk_forward_dd: n < 0");
+  if (n == 0) return FK_OK;
+  if (!q || !cp) return fail(FK_ERR_ARG, "fk_forward_dd: NULL pointer");
+  if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FK_ERR_ARG, "fk_forward_dd: scale must be finite and > 0");
+  CK(launch_forward_dd(c->cf, q, n, scale, cp, (cudaStream_t)stream));
+  return FK_OK;
+}
+
 // ------------------------------------------------- score, no allocation ---
 // Some callers cannot allocate device memory at the time they score: a
 // real-time planner loop that must never block on the allocator, a host
@@ -758,7 +896,9 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocHeader + kNoA
 // Device address of g_noalloc_scratch per device ordinal, looked up on the
 // first call made with that device current.  In host code the array's name
 // only stands in for the symbol; handing it to a kernel would reach the wrong
-// memory, so kernels get the address found here.
+// memory, so kernels get the address found here.  The cache assumes that the
+// device's primary context lives as long as the process: after a
+// cudaDeviceReset the cached address is stale and the call must not be used.
 static constexpr int kNoAllocMaxDevices = 64;
 static int32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 static std::mutex g_noalloc_mu;
@@ -803,20 +943,21 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   ChainF cf = c->cf;
   ChainD cd = c->cd;
   cf.summand = cd.summand = m->summand;
-  const double eps = rescore_eps > 0.0 ? rescore_eps : (gauss ? kDefaultEpsGauss : kDefaultEps);
-  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), m->use_cp1 ? m->rec1.as<float4>() : nullptr,
-               m->cp1_A, (float)sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma), (float)eps, f, label,
-               band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0, m->npos.as<int32_t>()};
+  float eps0 = 0.f, eps1 = 0.f;
+  score_band(c->cf, m->summand, m->gamma, m->ns, false, rescore_eps, &eps0, &eps1);
+  ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma),
+               eps0, eps1, f, label, band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0, m->npos.as<int32_t>()};
   CK(launch_score_f32(cf, sa, s));
   RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};
   CK(launch_rescore_f64(cd, ra, s));
-  if (n_rescored) {
-    int32_t h[2];
-    CK(cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score_noalloc: a shared-memory tile wait timed out");
-    *n_rescored = h[0];
-  }
+  // the error word is read back on every call (one synchronisation): a tile
+  // wait that gave up leaves labels undefined, and the next call's memset
+  // would erase the only record of it
+  int32_t h[2];
+  CK(cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[1] & kErrTimeout) return fail(FK_ERR_TIMEOUT, "fk_score_noalloc: a shared-memory tile wait timed out");
+  if (n_rescored) *n_rescored = h[0];
   return FK_OK;
 }
 
@@ -1353,10 +1494,10 @@ size_t scene_dev_size();
 size_t work_item_size();
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
                     const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
-                    int64_t q_off, int64_t n);
+                    float eps0, float eps1, int64_t q_off, int64_t n);
 void fill_work_item(void *dst, int32_t scene, int32_t block);
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
-                                      int32_t *counter, const float *q, float *f, int8_t *label, float eps,
+                                      int32_t *counter, const float *q, float *f, int8_t *label,
                                       int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
                                       uint32_t wait_limit, cudaStream_t s, bool prepare_only);
 cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,
@@ -1446,9 +1587,11 @@ static int batch_plan(fk_batch *b, const int64_t *q_off) {
   for (int i = 0; i < b->n_scenes; ++i) {
     const fastron_model *m = b->models[i];
     const int64_t n = q_off[i + 1] - q_off[i];
+    float eps0 = 0.f, eps1 = 0.f;
+    score_band(m->chain->cf, m->summand, m->gamma, m->ns, false, 0.0, &eps0, &eps1);
     fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p, m->sdf.as<float>(),
-                   m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->npos.as<int32_t>(), m->gamma, q_off[i],
-                   n);
+                   m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->npos.as<int32_t>(), m->gamma, eps0, eps1,
+                   q_off[i], n);
     for (int64_t blk = 0; blk * bq < n; ++blk) {
       const int64_t qn = n - blk * bq < bq ? n - blk * bq : bq;
       it.push_back({(m->ns + 1) * qn, {i, (int32_t)blk}});
@@ -1472,7 +1615,7 @@ static int batch_enqueue(fk_batch *b, const float *q, float *f, int8_t *label, i
   int32_t *fl = b->flags.as<int32_t>();
   CK(cudaMemsetAsync(fl, 0, sizeof(int32_t) * 4, s));
   CK(launch_batched_score_args(b->mv, b->variant, b->scenes.p, b->items.p, b->n_items, fl, q, f, label,
-                               (float)kDefaultEps, rescore ? b->band_idx.as<int32_t>() : nullptr,
+                               rescore ? b->band_idx.as<int32_t>() : nullptr,
                                rescore ? b->band_scene.as<int32_t>() : nullptr, fl + 1, fl + 2, g_wait_limit, s,
                                false));
   if (rescore) {
@@ -1515,7 +1658,7 @@ extern "C" int fk_score_batched(fk_batch_t *b, const float *q, const int64_t *q_
   if (!b->exec || b->g_q != q || b->g_f != f || b->g_label != label || b->g_rescore != (rescore != 0) ||
       b->g_variant != b->variant) {
     batch_drop_graph(b);
-    CK(launch_batched_score_args(b->mv, b->variant, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0.f,
+    CK(launch_batched_score_args(b->mv, b->variant, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr,
                                  nullptr, nullptr, nullptr, nullptr, 0, s, true));
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));

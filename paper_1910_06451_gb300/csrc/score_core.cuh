@@ -5,6 +5,7 @@
 
 #include <cuda_fp16.h>
 
+#include "fk_dfk.cuh"
 #include "fk_internal.h"
 #include "fk_ptx.cuh"
 
@@ -101,10 +102,20 @@ struct RcpPlan {
   static constexpr int NP = (MV + 3) / 7;
 };
 
+// (H, L) += x exactly up to the rounding of L: Knuth's two-sum on both
+// halves of the packed registers.
+__device__ __forceinline__ void fold2(f2 &H, f2 &L, f2 x) {
+  const f2 s = add2(H, x);
+  const f2 bb = sub2(s, H);
+  const f2 e = add2(sub2(H, sub2(s, bb)), sub2(x, bb));
+  H = s;
+  L = add2(L, e);
+}
+
 struct BlockOut {
   float *f;            // [n] or null
   int8_t *label;       // [n]
-  float eps;           // band: |f| <= eps B(q)
+  float eps0, eps1;    // band: |f| <= (eps0 + eps1 (|p(q)| + |s|max)) B(q)
   int32_t *band_idx;   // or null: no band list
   int32_t *band_scene; // or null: scene id of each band entry
   int32_t scene;
@@ -112,42 +123,40 @@ struct BlockOut {
   int32_t *band_cnt;
   int32_t *err;
   uint32_t wait_limit;
-  const int32_t *npair_pos;  // SPLIT kernels: positive-weight pairs, which lead the records
+  const int32_t *npair_pos;  // [0] positive-weight pairs, which lead the records;
+                             // [1] float bits of |s|max, the largest scaled support-point norm
 };
 
+// Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
+// (n x D) against the support records rec (ns points, (ns+1)/2 pair records,
+// the o.npair_pos[0] positive-weight pairs first) with chain c.  tiles:
+// 2 * TP * rec_len(MV) float4 of shared memory; bar: two mbarriers.  Every
+// thread of the CTA must call it.  Returns false (in every thread) if a tile
+// wait gave up; the caller must then stop using the CTA's barriers.
+//
+// Kinematics: each query's control points in pair arithmetic (fk_dfk.cuh),
+// scaled by g = sqrt(gamma/2) (RQ) and rounded once to FP32, so a control
+// point is off by at most u |p| (u = 2^-24).
 // HALF = true: the differences and t = 1 + |d|^2 are computed in packed
-// FP16 (HSUB2/HFMA2, query coordinates and the support pair's coordinates
-// rounded to half), then widened to FP32 for the reciprocals and the
-// accumulation.  HALF = false: all FP32.
-// CP1 = true (FP32 only): record entry 0 holds (U_a, U_b, V_a, V_b) of the
-// circle form of the first point (ChainF::cp1), t = A - U cos theta_q -
-// V sin theta_q with A = 1 + k: two FMAs instead of three differences and
-// three FMAs.  Its FP32 error for A < 8 stays within that of the direct
-// form on the points farther out.
+// FP16 (HSUB2/HFMA2, query and support coordinates rounded to half), then
+// widened to FP32 for the reciprocals and the accumulation.  HALF = false:
+// all FP32.
 // GAUSS = true: the non-paper Gaussian summand.  Coordinates come scaled by
 // sqrt(gamma/2 log2 e), so the summand is 2^(-t) with t = |p - s|^2 (no
 // "1 +"): on the MUFU unit (ex2.approx) for the first MV - POLY points of
 // every support point and on the FP32 pipe (ex2_neg2_poly) for the last POLY;
 // with HALF, t in packed FP16 and 2^(-t) by ex2.approx.f16x2 (two halves per
-// MUFU operation), widened to FP32 for the sums.  No reciprocal sharing, no
-// circle form.
-// Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
-// (n x D) against the support records rec (ns points, (ns+1)/2 pair records)
-// with chain c.  tiles: 2 * TP * rec_len(MV) float4 of shared memory; bar: two
-// mbarriers.  Every thread of the CTA must call it.  Returns false (in every
-// thread) if a tile wait gave up; the caller must then stop using the CTA's
-// barriers.
-// SPLIT = true: the records hold the positive-weight pairs first
-// (o.npair_pos of them, see rec_pairs), so each pair adds w * acc into one of
-// two accumulators, the positive part P or the negative part N; f = P + N and
-// B(q) = P - N, one packed FMA per pair and query instead of two.
-template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool CP1 = false, bool GAUSS = false, int POLY = 0,
-          bool SPLIT = false>
-__device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, float gs,
+// MUFU operation), widened to FP32 for the sums.  No reciprocal sharing.
+// Accumulation: each pair adds w * acc into the sum of its sign (positive
+// part P of f first, then the negative part N), kFoldPairs at a time in
+// FP32, each partial folded into a pair accumulator (compensated summation:
+// the accumulation error of f is then at most kFoldPairs + 3 units of
+// roundoff of B(q), whatever the size of the support set); f = P + N and the
+// bound B(q) = P - N = sum_s |w_s| sum_m K(s_m, q_m).
+template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool GAUSS = false, int POLY = 0>
+__device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, dd g,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
-                                            float4 *tiles, uint64_t *bar, float cp1_A = 0.f) {
-  static_assert(!(HALF && CP1), "the circle form is an FP32 path");
-  static_assert(!(GAUSS && CP1), "the circle form is an RQ path");
+                                            float4 *tiles, uint64_t *bar) {
   static_assert(POLY >= 0 && POLY <= MV && (POLY == 0 || (GAUSS && !HALF)), "polynomial points: FP32 Gaussian only");
   constexpr int REC = MV + (MV + 1) / 2 + 1;
   constexpr int NP = RcpPlan<MV>::NP;
@@ -155,7 +164,8 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
   const int tid = threadIdx.x;
   const int64_t npair = (ns + 1) / 2;
   const int ntiles = (int)((npair + TP - 1) / TP);
-  const int64_t npp = SPLIT ? (int64_t)*o.npair_pos : 0;  // pairs of the positive part
+  const int64_t npp = (int64_t)o.npair_pos[0];  // pairs of the positive part
+  const float smax = __int_as_float(o.npair_pos[1]);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -175,45 +185,49 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     if (ntiles > 1) issue(1);
   }
 
-  // forward kinematics of this thread's queries, scaled by sqrt(gamma/2) so
-  // that t = 1 + |p - s|^2, duplicated into both halves of a packed register
+  // forward kinematics of this thread's queries in pair arithmetic, scaled
+  // so that t = 1 + |p - s|^2, rounded to FP32 and duplicated into both
+  // halves of a packed register; s_eps: the query's band eps0 + eps1 (|p| + |s|max)
   const int64_t qbase = q0 + tid;
   f2 P[Q][MV][3];
   __half2 Ph[HALF ? Q : 1][HALF ? MV : 1][3];
-  f2 ncq[CP1 ? Q : 1], nsq[CP1 ? Q : 1];  // -cos theta_q, -sin theta_q of joint 1
+  // per thread and query, outside the register file (touched once per
+  // kFoldPairs pairs): the pair accumulator (AH, AL) of the current sign,
+  // the finished positive part PF, and the query's band eps(q)
+  __shared__ f2 s_acc[3][Q][NTHR];
+  __shared__ float s_eps[Q][NTHR];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int64_t qi = qbase + k * NTHR;
     float qv[FK_MAX_DOF];
     for (int i = 0; i < c.D; ++i) qv[i] = qi < n ? q[qi * c.D + i] : 0.f;
-    if (CP1) {
-      float sn, cs;
-      sincosf(qv[0] + c.th0[0], &sn, &cs);
-      ncq[CP1 ? k : 0] = pk(-cs, -cs);
-      nsq[CP1 ? k : 0] = pk(-sn, -sn);
-    }
     float cp[MV][3];
-    fk_points_f32<MV>(c, qv, cp);
+    fk_points_dd<MV>(c, qv, g, cp);
+    float pn = 0.f;
 #pragma unroll
-    for (int m = 0; m < MV; ++m)
+    for (int m = 0; m < MV; ++m) {
+      pn = fmaxf(pn, sqrtf(fmaf(cp[m][0], cp[m][0], fmaf(cp[m][1], cp[m][1], cp[m][2] * cp[m][2]))));
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const float v = gs * cp[m][r];
+        const float v = cp[m][r];
         if (HALF)
           Ph[HALF ? k : 0][HALF ? m : 0][r] = __float2half2_rn(v);
         else
           P[k][m][r] = pk(v, v);
       }
+    }
+    s_eps[k][tid] = fmaf(o.eps1, pn + smax, o.eps0);
+    s_acc[0][k][tid] = s_acc[1][k][tid] = s_acc[2][k][tid] = pk(0.f, 0.f);
   }
   const __half2 one_h = __float2half2_rn(1.f);
   const f2 one2 = pk(1.f, 1.f);
-  const f2 A2 = pk(cp1_A, cp1_A);
+  const f2 zero2 = pk(0.f, 0.f);
   const float nc = (float)c.n_const;
   const f2 nc2 = pk(nc, nc);
 
-  f2 F[Q], B[Q];
-#pragma unroll
-  for (int k = 0; k < Q; ++k) F[k] = B[k] = pk(0.f, 0.f);
+  // s_acc[0] + s_acc[1]: the pair accumulator of the current sign (P, then
+  // N); s_acc[2]: P once it is complete
+  bool neg = npp <= 0;  // accumulating the negative part (uniform over the CTA)
   int t_fail = -1;
   for (int t = 0; t < ntiles; ++t) {
     const bool got = mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1, o.wait_limit);
@@ -233,11 +247,7 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
         for (int m = 0; m < MV; ++m) {
           const float4 xy = r[m];
           const float4 zz = r[MV + m / 2];
-          if (CP1 && m == 0) {
-            const f2 u = pk(xy.x, xy.y), v = pk(xy.z, xy.w);
-#pragma unroll
-            for (int k = 0; k < Q; ++k) tv[k][0] = fma2(u, ncq[CP1 ? k : 0], fma2(v, nsq[CP1 ? k : 0], A2));
-          } else if (HALF) {
+          if (HALF) {
             const __half2 hx = __floats2half2_rn(xy.x, xy.y), hy = __floats2half2_rn(xy.z, xy.w);
             const __half2 hz = (m & 1) ? __floats2half2_rn(zz.z, zz.w) : __floats2half2_rn(zz.x, zz.y);
 #pragma unroll
@@ -292,47 +302,51 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     };
     // eight support pairs per loop trip (four for more than 8 points, which
     // would spill otherwise): fewer loop and address instructions on a kernel
-    // bound by instruction dispatch (4M 7-DOF queries: 5.25 ms one pair per
-    // trip, 5.11 ms four, 5.06 ms eight), within 128 registers for two CTAs
-    // per SM
+    // bound by instruction dispatch
     constexpr int UNR = MV > 8 ? 4 : 8;
-    if constexpr (SPLIT) {
-      int64_t js = npp - p0;
-      js = js < 0 ? 0 : (js > cnt ? cnt : js);
-#pragma unroll UNR
-      for (int j = 0; j < (int)js; ++j) {
-        const float4 *r = tile + j * REC;
-        f2 acc[Q];
-        pair_sums(r, acc);
-        const float4 W = r[REC - 1];
-        const f2 w = pk(W.x, W.y);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) F[k] = fma2(w, acc[k], F[k]);
-      }
-#pragma unroll UNR
-      for (int j = (int)js; j < cnt; ++j) {
-        const float4 *r = tile + j * REC;
-        f2 acc[Q];
-        pair_sums(r, acc);
-        const float4 W = r[REC - 1];
-        const f2 w = pk(W.x, W.y);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) B[k] = fma2(w, acc[k], B[k]);
-      }
-    } else {
-#pragma unroll UNR
-      for (int j = 0; j < cnt; ++j) {
-        const float4 *r = tile + j * REC;
-        f2 acc[Q];
-        pair_sums(r, acc);
-        const float4 W = r[REC - 1];
-        const f2 w = pk(W.x, W.y), aw = pk(W.z, W.w);
+    // pairs [0, js) of this tile belong to the positive part, [js, cnt) to the negative
+    int64_t js64 = npp - p0;
+    const int js = (int)(js64 < 0 ? 0 : (js64 > cnt ? cnt : js64));
+    for (int j0 = 0; j0 < cnt;) {
+      if (j0 >= js && !neg) {  // the positive part is complete
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          F[k] = fma2(w, acc[k], F[k]);
-          B[k] = fma2(aw, acc[k], B[k]);
+          s_acc[2][k][tid] = add2(s_acc[0][k][tid], s_acc[1][k][tid]);
+          s_acc[0][k][tid] = s_acc[1][k][tid] = zero2;
         }
+        neg = true;
       }
+      const int seg = j0 < js ? js : cnt;
+      f2 part[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) part[k] = zero2;
+      auto pair_step = [&](const float4 *r) {
+        f2 acc[Q];
+        pair_sums(r, acc);
+        const float4 W = r[REC - 1];
+        const f2 w = pk(W.x, W.y);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) part[k] = fma2(w, acc[k], part[k]);
+      };
+      int j1;
+      if (seg - j0 >= kFoldPairs) {  // a full partial: a loop of fixed length
+        const float4 *r0 = tile + j0 * REC;
+#pragma unroll UNR
+        for (int jj = 0; jj < kFoldPairs; ++jj) pair_step(r0 + jj * REC);
+        j1 = j0 + kFoldPairs;
+      } else {
+#pragma unroll 2
+        for (int j = j0; j < seg; ++j) pair_step(tile + j * REC);
+        j1 = seg;
+      }
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        f2 H = s_acc[0][k][tid], L = s_acc[1][k][tid];
+        fold2(H, L, part[k]);
+        s_acc[0][k][tid] = H;
+        s_acc[1][k][tid] = L;
+      }
+      j0 = j1;
     }
     __syncthreads();  // every thread is done with this buffer
     if (tid == 0 && t + 2 < ntiles) {
@@ -350,16 +364,23 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
     }
     return false;
   }
+  if (!neg) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      s_acc[2][k][tid] = add2(s_acc[0][k][tid], s_acc[1][k][tid]);
+      s_acc[0][k][tid] = s_acc[1][k][tid] = zero2;
+    }
+  }
 
   const unsigned lane = tid & 31;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    float f0, f1, b0, b1;
-    upk(F[k], f0, f1);
-    upk(B[k], b0, b1);
-    // SPLIT: F holds the positive part, B the negative part of f
-    const float f = SPLIT ? (f0 + f1) + (b0 + b1) : f0 + f1;
-    const float bq = SPLIT ? (f0 + f1) - (b0 + b1) : b0 + b1;
+    float p0v, p1v, n0v, n1v;
+    upk(s_acc[2][k][tid], p0v, p1v);
+    upk(add2(s_acc[0][k][tid], s_acc[1][k][tid]), n0v, n1v);
+    const float pp = __fadd_rn(p0v, p1v), nn = __fadd_rn(n0v, n1v);
+    const float f = __fadd_rn(pp, nn);
+    const float bq = __fsub_rn(pp, nn);
     const int64_t qi = qbase + k * NTHR;
     const bool valid = qi < n;
     if (valid) {
@@ -367,7 +388,7 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
       o.label[qi] = f >= 0.f ? 1 : -1;
     }
     if (o.band_idx) {
-      const bool flag = valid && fabsf(f) <= o.eps * bq;
+      const bool flag = valid && !(fabsf(f) > s_eps[k][tid] * bq);
       const unsigned bal = __ballot_sync(0xffffffffu, flag);
       if (bal) {
         int base = 0;

@@ -36,7 +36,7 @@ FK_MAX_CP = 32
 EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
-    "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_label", "fk_set_wait_limit",
+    "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_score_band", "fk_check_rcp", "fk_check_sincos", "fk_forward_dd", "fk_label", "fk_set_wait_limit",
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
     "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune", "fk_active_samples",
@@ -121,6 +121,10 @@ def load(build_if_missing: bool = False):
             "fastron_model_get": ([P, P, P, I64, P], I),
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
             "fk_score_noalloc": ([P, P, I64, D, P, P, P, P], I),
+            "fk_score_band": ([P, I, P, P], I),
+            "fk_check_rcp": ([I, I, P], I),
+            "fk_check_sincos": ([ctypes.c_float, D, P], I),
+            "fk_forward_dd": ([P, P, I64, D, P, P], I),
             "fk_label": ([P, P, I64, D, P, I64, P, P], I),
             "fk_active_samples": ([P, ctypes.c_int32, D, I64, D, ctypes.c_uint64, P, P, I64, P, P], I),
             "fk_set_wait_limit": ([ctypes.c_uint32], None),
@@ -353,6 +357,41 @@ def fk_score_noalloc(model, q, label, f=None, eps=0.0, count=False, stream=None)
                                    _dev(label, torch.int8, "label", (n,)), ctypes.byref(nr) if count else None,
                                    _stream(stream)))
     return nr.value if count else None
+
+
+def fk_score_band(model, precision=None):
+    """(eps0, eps1) of the score kernel's default band: a query is re-scored
+    when |f| <= (eps0 + eps1 (|p(q)| + |s|max)) B(q), norms of control points
+    scaled by sqrt(gamma/2); the bound of the kernel's whole error."""
+    e0, e1 = ctypes.c_double(), ctypes.c_double()
+    _check(load().fk_score_band(model, FK_F32 if precision is None else int(precision), ctypes.byref(e0),
+                                ctypes.byref(e1)))
+    return e0.value, e1.value
+
+
+def fk_check_rcp(e_lo: int, e_hi: int) -> float:
+    """Max |rcp(x) x - 1| of the score kernel's MUFU reciprocal over every FP32
+    mantissa of the binades [2^e_lo, 2^(e_hi+1))."""
+    out = ctypes.c_double()
+    _check(load().fk_check_rcp(int(e_lo), int(e_hi), ctypes.byref(out)))
+    return out.value
+
+
+def fk_check_sincos(hi: float, theta0: float = 0.0) -> float:
+    """Max absolute error of the kernels' pair-arithmetic sine and cosine of
+    x + theta0 against FP64, over every FP32 x in [-hi, hi]."""
+    out = ctypes.c_double()
+    _check(load().fk_check_sincos(float(hi), float(theta0), ctypes.byref(out)))
+    return out.value
+
+
+def fk_forward_dd(chain, q, scale, cp, stream=None):
+    """Control points (Mv, 3, n) as the score kernels form them: pair-arithmetic
+    kinematics times scale, rounded once to FP32."""
+    import torch
+    n = q.shape[0]
+    _check(load().fk_forward_dd(chain, _dev(q, torch.float32, "q"), n, float(scale),
+                                _dev(cp, torch.float32, "cp", (cp.shape[0], 3, n)), _stream(stream)))
 
 
 def fk_label(chain, boxes, radius, q, y, stream=None):

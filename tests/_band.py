@@ -1,0 +1,70 @@
+"""The score kernel's band, restated from its derivation for the tests.
+
+A query whose FP32 value satisfies |f| > eps(q) B(q) keeps its FP32 label, so
+eps(q) must bound |f32 - f| / B(q) on every query.  The derivation (the
+library's score_band; Sec. III-B's label rule, the RQ summand of Eq. 3 in
+the FK kernel of Eq. 4) gives eps(q) = eps0 + eps1 (|p(q)| + |s|max) with
+|p(q)| the largest norm of the query's configuration-dependent control
+points and |s|max that of the support set's, in coordinates scaled by
+sqrt(gamma/2), u = 2^-24:
+
+  eps1 = 2 u (1 + u) (1 + 2^-10)                 control points rounded once
+  eps0 = (A u + (16 + 3) u + n_c^2 u^2 / 2 + 4 e_fk) (1 + 2^-10)
+  A    = max(15 + 2, 10 + 2 * 2) + Mv - NP + 1    summands, NP = (Mv + 3) // 7
+  n_c  = npair / 16 + npair / 32 + 2, npair = (ns + 1) // 2 + 1
+  e_fk = 2^-32 (1 + sqrt(gamma/2) reach)          pair-arithmetic kinematics
+
+The half-precision kernel takes uh = 2^-11 for the coordinates (eps1 with
+uh + u) and 10 uh for t, an absolute 4 sqrt(3) 2^-25 for FP16 underflow,
+and a factor 1 + 1/16.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U = 2.0 ** -24
+UH = 2.0 ** -11
+RCP = 2.0 ** -23
+
+
+def reach(arm) -> float:
+    """Lever-arm bound of the chain in metres (base offset, |a| + |d| per link,
+    a prismatic joint's travel counted to 2^10, the largest point offset)."""
+    dh = np.asarray(arm.dh, dtype=np.float64)
+    r = float(np.linalg.norm(np.asarray(arm.base, dtype=np.float64)[:3, 3]))
+    r += float(np.sum(np.abs(dh[:, 0]) + np.abs(dh[:, 2]) + np.where(dh[:, 4] == 1, 1024.0, 0.0)))
+    r += float(np.max(np.linalg.norm(np.asarray(arm.cp_off, dtype=np.float64), axis=1)))
+    return float(np.float32(r * (1.0 + 1e-6)))
+
+
+def constants(arm, gamma: float, ns: int, half: bool = False):
+    """(eps0, eps1) as float32 values, for an arm with Mv configuration-dependent points."""
+    mv = int(np.sum(np.asarray(arm.cp_joint) != 0))
+    npp = (mv + 3) // 7
+    t_err = 10.0 * (UH if half else U)
+    pair = t_err + 5.0 * U + RCP if npp > 0 else 0.0
+    single = t_err + 2.0 * RCP if mv > 2 * npp else 0.0
+    term = max(pair, single) + (mv - npp + 1) * U
+    npair = float((ns + 1) // 2 + 1)
+    nc = npair / 16 + npair / 32 + 2.0
+    acc = (16 + 3) * U + 0.5 * nc * nc * U * U
+    efk = 2.0 ** -32 * (1.0 + np.sqrt(0.5 * gamma) * reach(arm))
+    pos_abs = 4.0 * np.sqrt(3.0) * 2.0 ** -25 if half else 0.0
+    factor = 1.0 + (1.0 / 16 if half else 2.0 ** -10)
+    eps0 = (term + acc + 4.0 * efk + pos_abs) * factor
+    eps1 = 2.0 * ((UH if half else 0.0) + U) * (1.0 + U) * factor
+    return float(np.float32(eps0)), float(np.float32(eps1))
+
+
+def dependent(arm, cp):
+    """The configuration-dependent control points of an (n, M, 3) array."""
+    return np.asarray(cp)[:, np.asarray(arm.cp_joint) != 0, :]
+
+
+def per_query(arm, gamma: float, eps0: float, eps1: float, cps, cpq):
+    """eps(q) for every query from FP64 control points (n, M, 3) of the support
+    set (cps) and of the queries (cpq)."""
+    g = np.sqrt(0.5 * gamma)
+    smax = g * np.max(np.linalg.norm(dependent(arm, cps), axis=2)) if len(cps) else 0.0
+    pn = g * np.max(np.linalg.norm(dependent(arm, cpq), axis=2), axis=1)
+    return eps0 + eps1 * (pn + smax)

@@ -4,8 +4,9 @@ through the C ABI.  Tolerances:
   control points (FP32)   |dp| <= 1e-5 * max(|p|, reach)
   control points (FP64)   |dp| <= 1e-13
   kernel matrix (FP64)    |dK| <= 1e-14;  (FP32) |dK| <= 2e-6
-  score (FP32, tier 1)    |df| <= 1e-4 * sum|alpha|   and   |df| <= eps/2 * B(q),
-                          B(q) = sum_s |alpha_s| K_FK(S_s, q), eps the re-score band
+  score (FP32, tier 1)    |df| <= 1e-4 * sum|alpha|   and   |df| <= eps(q) B(q),
+                          B(q) = sum_s |alpha_s| K_FK(S_s, q), eps(q) the derived
+                          re-score band (tests/_band.py), on every query
   labels after re-score   identical
   training                support set, pass sequence identical; alpha within 1e-12 relative
 """
@@ -15,10 +16,9 @@ import torch
 
 from oracle import oracle as O
 from paper_1910_06451_gb300 import synth
+from tests import _band
 
 pytestmark = pytest.mark.gpu
-
-EPS_BAND = 6e-6  # the library's default re-score band
 
 
 def _reach(arm):
@@ -194,27 +194,32 @@ def _score_case(fk, w, ch, dev, S, alpha, Q):
         lab = torch.empty(n, dtype=torch.int8, device=dev)
         nres = fk.fk_score(m, tq, lab, f, rescore=True, count=True)
         torch.cuda.synchronize()
+        eps0, eps1 = fk.fk_score_band(m)
     finally:
         fk.fastron_model_destroy(m)
+    # the library's band constants are the derivation's
+    assert (eps0, eps1) == _band.constants(arm, w.gamma, len(S))
     Qd = Q.astype(np.float64)
     cps, cpq = O.fk_points(arm, S), O.fk_points(arm, Qd)
     want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
     B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=8)
-    return f_raw.cpu().numpy(), lab_raw.cpu().numpy(), f.cpu().numpy(), lab.cpu().numpy(), nres, want, B
+    eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq)
+    return f_raw.cpu().numpy(), lab_raw.cpu().numpy(), f.cpu().numpy(), lab.cpu().numpy(), nres, want, B, eps
 
 
-def _check_score(f_raw, lab_raw, f, lab, nres, want, B, alpha):
+def _check_score(f_raw, lab_raw, f, lab, nres, want, B, eps, alpha):
     sa = np.sum(np.abs(alpha))
     err = np.abs(f_raw.astype(np.float64) - want)
     assert np.all(err <= 1e-4 * sa + 1e-30)
-    assert np.all(err <= 0.5 * EPS_BAND * B + 1e-30), np.max(err / np.maximum(B, 1e-300))
+    # the derived bound holds on every query (with the FP64 B(q) and norms)
+    assert np.all(err <= eps * B + 1e-30), np.max(err / np.maximum(eps * B, 1e-300))
     assert np.array_equal(lab_raw == 1, f_raw >= 0)
     assert np.array_equal(lab, O.labels_from_f(want))
-    band = np.abs(f_raw) <= np.float32(EPS_BAND) * B.astype(np.float32) * (1 + 1e-6)
-    assert nres >= np.sum(np.abs(f_raw.astype(np.float64)) < 0.99 * EPS_BAND * B)
-    assert nres <= np.sum(band) + 8
+    # the band holds every query the bound cannot decide, and not many more
+    assert nres >= np.sum(np.abs(f_raw.astype(np.float64)) < 0.999 * eps * B)
+    assert nres <= np.sum(np.abs(f_raw.astype(np.float64)) <= 1.001 * eps * B) + 8
     # re-scored queries carry the FP64 value (rounded to FP32)
-    sel = np.abs(f_raw.astype(np.float64)) < 0.99 * EPS_BAND * B
+    sel = np.abs(f_raw.astype(np.float64)) < 0.999 * eps * B
     np.testing.assert_allclose(f[sel], want[sel].astype(np.float32), rtol=1e-6, atol=1e-30)
 
 
@@ -248,7 +253,7 @@ def test_score_query_equal_to_support_point(fk, arm7, dev):
     # K(x, x) = 1: a single support point scored at itself gives alpha
     w, ch = arm7
     S = w.train_configs()[:1].astype(np.float64)
-    f_raw, lab_raw, f, lab, nres, want, B = _score_case(fk, w, ch, dev, S, np.array([-0.75]), S.astype(np.float32))
+    f_raw, lab_raw, f, lab, nres, want, B, eps = _score_case(fk, w, ch, dev, S, np.array([-0.75]), S.astype(np.float32))
     assert want[0] == -0.75
     assert abs(f_raw[0] + 0.75) <= 1e-6 and lab[0] == -1
 
@@ -440,14 +445,17 @@ def test_score_half_precision_path(fk, arm3, arm7, dev, which):
         lab = torch.empty(len(Q), dtype=torch.int8, device=dev)
         nb = fk.fk_score(m, tq, lab, rescore=True, count=True, precision=fk.FK_F16)
         torch.cuda.synchronize()
+        eps0, eps1 = fk.fk_score_band(m, fk.FK_F16)
     finally:
         fk.fastron_model_destroy(m)
+    assert (eps0, eps1) == _band.constants(w.scene.arm, w.gamma, len(S), half=True)
     cps, cpq = O.fk_points(w.scene.arm, S), O.fk_points(w.scene.arm, Q.astype(np.float64))
     want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
     B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=8)
-    err = np.abs(f16.cpu().numpy().astype(np.float64) - want) / B
-    print(f"half pass: max |df|/B = {err.max():.3e}, band = {nb} of {len(Q)}")
-    assert err.max() <= 0.5 * 2e-3
+    eps = _band.per_query(w.scene.arm, w.gamma, eps0, eps1, cps, cpq)
+    err = np.abs(f16.cpu().numpy().astype(np.float64) - want)
+    print(f"half pass: max |df|/(eps B) = {np.max(err / (eps * B)):.3e}, band = {nb} of {len(Q)}")
+    assert np.all(err <= eps * B)
     assert np.array_equal(lab.cpu().numpy(), O.labels_from_f(want))
 
 

@@ -59,15 +59,14 @@ MUTANTS = [
     ("s_max off by one", C, "if (nnz < s_max || alpha[i] != 0.0) {", "if (nnz <= s_max || alpha[i] != 0.0) {"),
     ("s_max blocks adjusting a support point", C, "if (nnz < s_max || alpha[i] != 0.0) {",
      "if (nnz < s_max) {"),
-    ("add uses the wrong column", C, "kernel_column(M, gamma, N, cpX, i, col, store32, kind);",
-     "kernel_column(M, gamma, N, cpX, 0, col, store32, kind);"),
+    ("add uses the wrong column", C, "kernel_column(&pool, i);", "kernel_column(&pool, 0);"),
     ("removal margin keeps the point's own weight", C, "double m = y[j] * (F[j] - alpha[j]);",
      "double m = y[j] * F[j];"),
     ("removal update sign", C, "F[j] = fma(-a, col[j], F[j]);", "F[j] = fma(a, col[j], F[j]);"),
     ("removal at zero margin", C, "if (r >= 0 && mmax > 0.0) {", "if (r >= 0 && mmax >= 0.0) {"),
     ("removal ties to the highest index", C, "if (m > mmax) {", "if (m >= mmax) {"),
     ("removed weight kept in part", C, "alpha[r] = 0.0;", "alpha[r] *= 0.5;"),
-    ("fp32 storage ignored in training", C, "col[j] = store32 ? (double)(float)k : k;", "col[j] = k;"),
+    ("fp32 storage ignored in training", C, "p->col[j] = p->store32 ? (double)(float)k : k;", "p->col[j] = k;"),
     ("carried margins drop the first point", C, "for (int64_t s = 0; s < ns; ++s) {",
      "for (int64_t s = 1; s < ns; ++s) {"),
     ("carried margins ignore fp32 storage", C, "k = (double)(float)k;", "k = k + 0.0;"),
