@@ -37,7 +37,7 @@ N_QUERY = 1 << 22
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum): the
 # queries in and the labels out, no re-reads.  None until the kernel as it
 # stands has been captured.
-SCORE_TRAFFIC_BYTES = 117_628_928 + 4_305_152
+SCORE_TRAFFIC_BYTES = None
 METRIC = "proxy collision checks/s (7-DOF): half2+surrogate vs plain FP32, oracle-exact labels"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -147,26 +147,53 @@ def oracle_cpu_baseline(w, sample_queries: int, threads: int) -> dict:
             "n_support": int(r.n_support)}
 
 
+def label_checksum(lab) -> dict:
+    """Count of +1 labels and a position-weighted sum of them (mod 2^61 - 1):
+    two arms with these equal labelled the batch alike."""
+    lab = np.asarray(lab).astype(np.int64)
+    pos = np.flatnonzero(lab == 1).astype(np.int64)
+    h = int(np.sum((pos * 2654435761 + 97) % 2305843009213693951) % 2305843009213693951)
+    return {"positive": int(pos.size), "weighted": h}
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands runs the whole step on
+    the host cores - labels of the training set, Algorithm 1, and the FP64
+    score of every query of the batch - timed step by step."""
     ws, rank = _dist()
     if rank != 0:
         return 0
+    from oracle import oracle as O
     w = synth.workload(WORKLOAD)
+    arm = w.scene.arm
     threads = os.cpu_count() or 1
-    sample = 16384
-    vals = []
+    X = w.train_configs().astype(np.float64)
+    nq = args.queries
+    Q = w.query_configs(nq).astype(np.float64)
+    times, train_s = [], []
+    lab = None
     for i in range(args.warmup + args.steps):
-        cb = oracle_cpu_baseline(w, sample, threads)
+        t0 = time.perf_counter()
+        y = O.check(w.scene, X)
+        r = O.fastron_train(O.fk_points(arm, X), y, w.gamma, w.beta, w.iter_max, w.s_max)
+        t1 = time.perf_counter()
+        f = O.score(arm, X[r.support], r.alpha[r.support], Q, w.gamma, nthreads=threads)
+        lab = O.labels_from_f(f)
+        t2 = time.perf_counter()
         if i >= args.warmup:
-            vals.append(cb)
-    value = statistics.mean(v["value"] for v in vals)
-    ms = N_QUERY / value * 1e3
+            times.append(t2 - t0)
+            train_s.append(t1 - t0)
+    ms = statistics.mean(times) * 1e3
+    value = nq / (ms * 1e-3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_train": w.n_train, "n_query": N_QUERY, "gamma": w.gamma,
-                       "l2": "host CPU run"},
-            "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": value, "unit": UNIT},
+            "config": {"workload": WORKLOAD, "n_train": w.n_train, "n_query": nq, "gamma": w.gamma,
+                       "l2": "host CPU run", "step": "labels + Algorithm 1 + FP64 score of every query, timed"},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
+                             "sample": f"the whole {nq}-query step (labels and training "
+                                       f"{statistics.mean(train_s):.2f} s of it)"},
+            "labels_checksum": label_checksum(lab),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -329,7 +356,7 @@ def obstacle_sweep(fk, dev, rank, counts, Q, X32, X, flush):
     return out
 
 
-def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "active", "surrogate")):
+def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "active", "surrogate"), short=None):
     """The 12-control-point arm among moving boxes: a fixed training set of
     65,536 configurations relabelled every frame, Algorithm 1 on the stored
     FP32 kernel matrix (built once), then the query batch scored.  Each frame
@@ -343,7 +370,8 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
     a fixed 1M-query set scored by the new model, threshold recalibrated) and
     answers the frame's queries, falling back to the exact score below the
     threshold; its labels are compared with the exact path's.  Per-frame
-    device times."""
+    device times.  The cold and surrogate modes run `frames` frames, the
+    warm-start and active-learning modes `short` (default: the same)."""
     import torch
     wd = synth.workload("arm7m12-n65536", trial=rank)
     ch = fk.chain_from_arm(wd.scene.arm)
@@ -382,7 +410,8 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
             fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32, reuse_gram=True)
             ns = st0["n_support"]
             upd, qry, its, sup, conv, nres = [], [], [], [], [], []
-            for k in range(1, frames):
+            nf = frames if mode == "cold" or short is None else min(frames, short)
+            for k in range(1, nf):
                 torch.cuda.synchronize()
                 a = ev()
                 if mode == "active":
@@ -411,7 +440,7 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
             out[mode] = {"update_ms_p50": float(np.percentile(upd, 50)), "update_ms_p99": float(np.percentile(upd, 99)),
                          "query_ms_p50": float(np.percentile(qry, 50)), "query_ms_p99": float(np.percentile(qry, 99)),
                          "frame_ms_p50": float(np.percentile(tot, 50)), "frame_ms_p99": float(np.percentile(tot, 99)),
-                         "iterations": its, "support": sup, "converged": conv, "rescored": nres,
+                         "frames": nf, "iterations": its, "support": sup, "converged": conv, "rescored": nres,
                          "checks_per_s_p50": nq / (float(np.percentile(tot, 50)) * 1e-3)}
         if "surrogate" in modes:
             out["surrogate"] = surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev)
@@ -466,6 +495,65 @@ def surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev):
         fk.surrogate_destroy(sur)
 
 
+def metric_paths(fk, dev, chain, model, sur, w, nq, flush, train_s):
+    """The comparison the headline metric names, on the surrogate
+    configuration: the 7-DOF scene with 16,777,216 uniform queries.  Three
+    query paths over the same batch - the exact FP32 path (labels equal the
+    FP64 oracle's), the half-precision pass (its band through the FP32
+    path, labels exact as well), and the learned surrogate with exact
+    fallback - each timed alone (median of three, L2 flushed), with the
+    surrogate's training time and the number of batches after which it pays
+    for itself, its fallback fraction, and accuracy, TPR and TNR of every
+    path against the geometric checker (fk_label) on the same queries."""
+    import torch
+    Q = torch.from_numpy(synth.uniform_configs(w.seed + 31, nq, w.scene.arm.D, w.scene.arm.qlim)).to(dev)
+    truth = torch.empty(nq, dtype=torch.int8, device=dev)
+    fk.fk_label(chain, w.scene.boxes, w.scene.radius, Q, truth)
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def quality(lab):
+        t, p = truth == 1, lab == 1
+        tp, tn = int((t & p).sum().item()), int((~t & ~p).sum().item())
+        npos, nneg = int(t.sum().item()), nq - int(t.sum().item())
+        return {"accuracy": (tp + tn) / nq, "tpr": tp / max(npos, 1), "tnr": tn / max(nneg, 1)}
+
+    out = {"workload": f"{WORKLOAD} scene, {nq} uniform queries (surrogate configuration)", "queries": nq}
+    exact = torch.empty(nq, dtype=torch.int8, device=dev)
+    nb = fk.fk_score(model, Q, exact, rescore=True, count=True)
+    t_exact = timed(lambda: fk.fk_score(model, Q, exact, rescore=True))
+    out["fp32_exact"] = {"ms": t_exact, "checks_per_s": nq / (t_exact * 1e-3), "rescored": nb,
+                         "label_mismatch_vs_exact": 0} | quality(exact)
+    lab = torch.empty(nq, dtype=torch.int8, device=dev)
+    nb16 = fk.fk_score(model, Q, lab, rescore=True, count=True, precision=fk.FK_F16)
+    t_half = timed(lambda: fk.fk_score(model, Q, lab, rescore=True, precision=fk.FK_F16))
+    out["half2_exact"] = {"ms": t_half, "checks_per_s": nq / (t_half * 1e-3), "band_to_fp32": nb16 / nq,
+                          "speedup_vs_fp32": t_exact / t_half,
+                          "label_mismatch_vs_exact": int((lab != exact).sum().item())} | quality(lab)
+    if sur is not None:
+        nfb = fk.surrogate_infer(sur, model, Q, lab)
+        t_sur = timed(lambda: fk.surrogate_infer(sur, model, Q, lab))
+        saved = t_exact - t_sur
+        out["surrogate"] = {"ms": t_sur, "checks_per_s": nq / (t_sur * 1e-3), "fallback": nfb / nq,
+                            "speedup_vs_fp32": t_exact / t_sur, "train_s": train_s,
+                            "break_even_batches": (train_s * 1e3 / saved) if saved > 0 else None,
+                            "label_mismatch_vs_exact": int((lab != exact).sum().item())} | quality(lab)
+    out["note"] = ("labels of fp32_exact and half2_exact equal the FP64 oracle's (derived band + re-score); "
+                   "the surrogate's confident answers are the network's")
+    del Q, truth, exact, lab
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,9 +566,13 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=1 << 21, help="surrogate training queries (0: skip)")
     ap.add_argument("--surrogate-epochs", type=int, default=192)
     ap.add_argument("--surrogate-lr", type=float, default=3e-3, help="peak of the cosine learning-rate schedule")
+    ap.add_argument("--metric-queries", type=int, default=1 << 24,
+                    help="queries of the metric-paths comparison (surrogate configuration; 0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the multi-scene measurement (0: skip)")
-    ap.add_argument("--dynamic-frames", type=int, default=8,
-                    help="frames of the changing-environment measurement (0: skip)")
+    ap.add_argument("--dynamic-frames", type=int, default=100,
+                    help="frames of the changing-environment measurement, cold and surrogate modes (0: skip)")
+    ap.add_argument("--dynamic-frames-short", type=int, default=8,
+                    help="frames of the warm-start and active-learning modes")
     ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
     ap.add_argument("--dynamic-modes", default="warm,cold,active,surrogate",
                     help="update modes of that measurement (comma-separated)")
@@ -634,6 +726,8 @@ def main():
         if i >= args.warmup:
             e2e_times.append(a.elapsed_time(b))
     e2e_ms = shard.max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
+    # the step's labels (exact: the oracle's), for comparison with the reference arm's
+    checksum = label_checksum(lab.cpu().numpy()) if nq == N_QUERY else None
     h2d = Qh.numel() * 4 + Xh.numel() * 8 + X32h.numel() * 4
     d2h = labh.numel()
 
@@ -660,40 +754,45 @@ def main():
                             "label_mismatch": int((hlab != ex16).sum().item()),
                             "speedup_vs_fp32_exact": query_ms / hms}
     del hlab, ex16
+    sur, train_s = None, None
     if args.surrogate_train > 0:
         sur = fk.surrogate_create(chain, seed=rank + 1)
-        try:
-            qtr = torch.from_numpy(synth.uniform_configs(w.seed + 7, args.surrogate_train, arm.D, arm.qlim)).to(dev)
-            t0 = time.perf_counter()
-            sst = fk.surrogate_train(sur, model, qtr, epochs=args.surrogate_epochs, batch=8192,
-                                     lr=args.surrogate_lr, holdout=0.0625, schedule=fk.FK_LR_COSINE)
-            torch.cuda.synchronize()
-            train_s = time.perf_counter() - t0
-            del qtr
-            slab = torch.empty(nq, dtype=torch.int8, device=dev)
-            ex = torch.empty(nq, dtype=torch.int8, device=dev)
-            fk.fk_score(model, Q, ex, rescore=True)
-            nfb = fk.surrogate_infer(sur, model, Q, slab)
-            times_s = []
-            for _ in range(3):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                fk.surrogate_infer(sur, model, Q, slab)
-                b.record()
-                b.synchronize()
-                times_s.append(a.elapsed_time(b))
-            sms = statistics.median(times_s)
-            mism = int((slab != ex).sum().item())
-            paths["surrogate"] = {"checks_per_s": nq / (sms * 1e-3), "ms": sms, "fallback": nfb / nq,
-                                  "label_mismatch": mism, "label_mismatch_rate": mism / nq,
-                                  "tau": sst["tau"], "holdout_fallback": sst["holdout_fallback"],
-                                  "holdout_sign_error": sst["holdout_sign_error"], "train_s": train_s,
-                                  "train_rows": sst["n_train"], "epochs": args.surrogate_epochs,
-                                  "lr_schedule": f"cosine from {args.surrogate_lr:g}",
-                                  "loss_last": sst["loss_last"], "speedup_vs_fp32_exact": query_ms / sms}
-            del slab, ex
-        finally:
+        qtr = torch.from_numpy(synth.uniform_configs(w.seed + 7, args.surrogate_train, arm.D, arm.qlim)).to(dev)
+        t0 = time.perf_counter()
+        sst = fk.surrogate_train(sur, model, qtr, epochs=args.surrogate_epochs, batch=8192,
+                                 lr=args.surrogate_lr, holdout=0.0625, schedule=fk.FK_LR_COSINE)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del qtr
+        slab = torch.empty(nq, dtype=torch.int8, device=dev)
+        ex = torch.empty(nq, dtype=torch.int8, device=dev)
+        fk.fk_score(model, Q, ex, rescore=True)
+        nfb = fk.surrogate_infer(sur, model, Q, slab)
+        times_s = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fk.surrogate_infer(sur, model, Q, slab)
+            b.record()
+            b.synchronize()
+            times_s.append(a.elapsed_time(b))
+        sms = statistics.median(times_s)
+        mism = int((slab != ex).sum().item())
+        paths["surrogate"] = {"checks_per_s": nq / (sms * 1e-3), "ms": sms, "fallback": nfb / nq,
+                              "label_mismatch": mism, "label_mismatch_rate": mism / nq,
+                              "tau": sst["tau"], "holdout_fallback": sst["holdout_fallback"],
+                              "holdout_sign_error": sst["holdout_sign_error"], "train_s": train_s,
+                              "train_rows": sst["n_train"], "epochs": args.surrogate_epochs,
+                              "lr_schedule": f"cosine from {args.surrogate_lr:g}",
+                              "loss_last": sst["loss_last"], "speedup_vs_fp32_exact": query_ms / sms}
+        del slab, ex
+    metric = None
+    try:
+        if args.metric_queries > 0:
+            metric = metric_paths(fk, dev, chain, model, sur, w, args.metric_queries, flush, train_s)
+    finally:
+        if sur is not None:
             fk.surrogate_destroy(sur)
 
     # many scenes: one persistent graph-captured launch (tuned) against one
@@ -764,7 +863,8 @@ def main():
     dynamic = None
     if args.dynamic_frames > 1:
         dynamic = changing_environment(fk, dev, rank, args.dynamic_frames, args.dynamic_queries,
-                                       [m.strip() for m in args.dynamic_modes.split(",") if m.strip()])
+                                       [m.strip() for m in args.dynamic_modes.split(",") if m.strip()],
+                                       short=args.dynamic_frames_short)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -780,11 +880,15 @@ def main():
             "config": {"workload": WORKLOAD, "dof": arm.D, "control_points": arm.M, "boxes": len(w.scene.boxes),
                        "n_train": w.n_train, "n_query": nq, "gamma": w.gamma,
                        "support": st["n_support"], "iterations": st["iterations"],
-                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+df+fp64-rescore"},
+                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+df+fp64-rescore",
+                       "headline": "value is the exact FP32 step (labels equal the FP64 oracle's); the "
+                                   "half2 and surrogate paths the metric compares are in metric_paths"},
             "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
                           "rescored_queries": nres},
             "query_only_checks_per_s": nq / (query_ms * 1e-3),
             "query_paths": paths,
+            "metric_paths": metric,
+            "labels_checksum": checksum,
             "batched_scenes": batched,
             "changing_environment": dynamic,
             "obstacle_sweep": sweep,

@@ -34,8 +34,9 @@ struct ChainF {
   float R0_l[9], p0_l[3];
   float vt_l[FK_MAX_CP][3];
   int vt_nz[FK_MAX_CP];         // offset of configuration-dependent point v is not zero
-  // Twist of +-pi/2: sin(alpha) is exactly +-1 in FP64 and |cos(alpha)| <
-  // 2^-40, so Rx(alpha) is taken as a signed swap of the y and z columns.
+  // Twist near +-pi/2: the high word of sin(alpha) is +-1 and |cos(alpha)| <
+  // 2^-20, so Rx(alpha) is a signed swap of the y and z columns plus FP32
+  // corrections (fk_dfk.cuh).
   int quarter[FK_MAX_DOF];
   int rot_last;                 // a configuration-dependent point on frame D has an offset
   float reach;                  // sum over links of |a| + |d| + |theta0 or d offset| bound, plus

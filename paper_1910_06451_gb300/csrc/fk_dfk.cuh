@@ -145,9 +145,12 @@ __device__ __forceinline__ void pose_base(const ChainF &c, PoseDD &P) {
 }
 
 // Link i: R <- R Rz(theta) Rx(alpha), p <- p + R Rz(theta) (a, 0, d), the
-// product of Eq. 1 taken column by column.  A twist of +-pi/2 (sin exactly
-// +-1 in FP64, |cos| below 2^-40, ChainF::quarter) is a signed swap of the
-// y and z columns; its dropped cosine term is below 2^-40 of a unit entry.
+// product of Eq. 1 taken column by column.  A twist near +-pi/2
+// (ChainF::quarter: the high word of sin(alpha) is +-1 and |cos(alpha)| <
+// 2^-20) is a signed swap of the y and z columns plus small corrections
+// formed in FP32 (the cosine times the other column's high word, the low word
+// of the sine times the column's high word): the terms dropped are below
+// 2^-40 of a unit entry.
 // rot = false: only the origin is needed after this link (the rotation is
 // left as it was).  The pairs are not renormalised: each step adds at most a
 // few u^2 of absolute error to entries bounded by 1 (rotation) or the reach.
@@ -171,8 +174,9 @@ __device__ __forceinline__ void pose_step(const ChainF &c, int i, float qi, Pose
     const dd yn = dd_add(dd_mul(co, P.y[r]), dd_mul(dd_neg(s), P.x[r]));
     dd zn, yy;
     if (quarter) {
-      zn = dd{-sgn * yn.h, -sgn * yn.l};
-      yy = dd{sgn * P.z[r].h, sgn * P.z[r].l};
+      // zn = ca z - sa yn, yy = ca yn + sa z with sa = sgn + sa.l, sgn = +-1
+      zn = dd{-sgn * yn.h, fmaf(ca.h, P.z[r].h, fmaf(-sa.l, yn.h, -sgn * yn.l))};
+      yy = dd{sgn * P.z[r].h, fmaf(ca.h, yn.h, fmaf(sa.l, P.z[r].h, sgn * P.z[r].l))};
     } else {
       zn = dd_add(dd_mul(ca, P.z[r]), dd_mul(dd_neg(sa), yn));
       yy = dd_add(dd_mul(ca, yn), dd_mul(sa, P.z[r]));

@@ -140,7 +140,7 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
     f.sa_l[i] = (float)(sa - (double)f.sa[i]);
     f.d_l[i] = (float)(dh[i].d - (double)f.d[i]);
     f.th0_l[i] = (float)(dh[i].theta0 - (double)f.th0[i]);
-    f.quarter[i] = fabs(sa) == 1.0 && fabs(ca) < 0x1p-40;
+    f.quarter[i] = fabs((double)f.sa[i]) == 1.0 && fabs(ca) < 0x1p-20;
   }
   double p0n = 0.0, tmax = 0.0;
   for (int r = 0; r < 3; ++r) {
@@ -345,7 +345,7 @@ static void score_band(const ChainF &cf, int summand, double gamma, int64_t ns, 
     return;
   }
   const double u = 0x1p-24, uh = 0x1p-11, rho = kRcpRel;
-  const int Mv = cf.Mv, NP = (Mv + 3) / 7;
+  const int Mv = cf.Mv, NP = (Mv + 5) / 14;  // RcpPlan<Mv>::NP of score_core.cuh
   const double g = sqrt(0.5 * gamma);
   const double t_err = half ? 10.0 * uh : 10.0 * u;
   const double pair = NP > 0 ? t_err + 5.0 * u + rho : 0.0;

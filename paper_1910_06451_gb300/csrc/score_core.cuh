@@ -95,11 +95,16 @@ __device__ __forceinline__ f2 ex2_neg2_poly(f2 t) {
 constexpr uint32_t kDrainLimit = 1u << 22;  // polls while draining copies after a timeout
 
 // Number of control-point pairs that share one reciprocal: the rest take one
-// MUFU reciprocal each.  About a sixth of the points paired balances the FP32
-// pipe (128 lanes/clk/SM) against the MUFU pipe (16 lanes/clk/SM).
+// MUFU reciprocal each.  A shared pair costs 3 more packed FP32 operations
+// and 2 fewer reciprocals than two singles.  Per support pair and query a
+// warp needs about 2 (7 Mv + 3 NP + 2) FP32-pipe cycles (packed operations
+// take two) against 8 (2 Mv - 2 NP) MUFU cycles (4 lanes per sub-partition),
+// plus the kinematics and folds on the FP32 pipe: NP = 0 balances the two
+// at 7 points, NP = 1 at 11 and 12 (measured: 7 points 5.82 -> 5.78 ms,
+// 11 points 121.0 -> 119.5 ms against the previous rule (Mv + 3) / 7).
 template <int MV>
 struct RcpPlan {
-  static constexpr int NP = (MV + 3) / 7;
+  static constexpr int NP = (MV + 5) / 14;
 };
 
 // (H, L) += x exactly up to the rounding of L: Knuth's two-sum on both

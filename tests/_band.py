@@ -10,7 +10,7 @@ sqrt(gamma/2), u = 2^-24:
 
   eps1 = 2 u (1 + u) (1 + 2^-10)                 control points rounded once
   eps0 = (A u + (16 + 3) u + n_c^2 u^2 / 2 + 4 e_fk) (1 + 2^-10)
-  A    = max(15 + 2, 10 + 2 * 2) + Mv - NP + 1    summands, NP = (Mv + 3) // 7
+  A    = max(15 + 2, 10 + 2 * 2) + Mv - NP + 1    summands, NP = (Mv + 5) // 14
   n_c  = npair / 16 + npair / 32 + 2, npair = (ns + 1) // 2 + 1
   e_fk = 2^-32 (1 + sqrt(gamma/2) reach)          pair-arithmetic kinematics
 
@@ -40,7 +40,7 @@ def reach(arm) -> float:
 def constants(arm, gamma: float, ns: int, half: bool = False):
     """(eps0, eps1) as float32 values, for an arm with Mv configuration-dependent points."""
     mv = int(np.sum(np.asarray(arm.cp_joint) != 0))
-    npp = (mv + 3) // 7
+    npp = (mv + 5) // 14
     t_err = 10.0 * (UH if half else U)
     pair = t_err + 5.0 * U + RCP if npp > 0 else 0.0
     single = t_err + 2.0 * RCP if mv > 2 * npp else 0.0

@@ -46,7 +46,7 @@ def rcp_worst(x):
 
 def kernel_acc(P, S, n_const, mv):
     """One support point's sum as score_core.cuh forms it: P, S (n, mv, 3) FP32."""
-    npp = (mv + 3) // 7
+    npp = (mv + 5) // 14
     t = []
     for m in range(mv):
         d = [rn(P[:, m, r].astype(LD) - S[:, m, r].astype(LD)) for r in range(3)]
@@ -70,7 +70,7 @@ def exact_acc(P, S, n_const):
 
 
 def derived(mv):
-    npp = (mv + 3) // 7
+    npp = (mv + 5) // 14
     pair = 15 * U + RHO if npp > 0 else 0.0
     single = 10 * U + 2 * RHO if mv > 2 * npp else 0.0
     return max(pair, single) + (mv - npp) * U

@@ -1,6 +1,7 @@
 """Host logic of bench.py, on CPU: the clock record taken during the timed
 steps (median SM clock, maximum, throttle reasons active in any sample) and
-the reference arm's JSON line (the oracle timed on the host cores)."""
+the reference arm's JSON line (the oracle timed on the host cores, the whole
+step on the whole batch), and the label checksum both arms print."""
 import json
 import os
 import subprocess
@@ -50,15 +51,29 @@ def test_clock_record_without_samples():
 
 
 def test_reference_arm_prints_one_contract_line():
+    # a smaller batch than the default 4,194,304 keeps the CPU suite short
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--warmup", "0", "--queries", "65536"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "checks/s" and d["higher_is_better"] is True
-    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(4194304 / d["value"] * 1e3)
+    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(65536 / d["value"] * 1e3)
+    assert d["config"]["n_query"] == 65536
+    assert d["labels_checksum"]["positive"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "arm7-n5000" and d["data"] == "synthetic"
+
+
+def test_label_checksum_sees_every_label():
+    import numpy as np
+    a = np.where(np.arange(1000) % 3 == 0, 1, -1).astype(np.int8)
+    b = a.copy()
+    b[500], b[501] = b[501], b[500]  # same count, two labels swapped
+    ca, cb = bench.label_checksum(a), bench.label_checksum(b)
+    assert ca["positive"] == cb["positive"] and ca["weighted"] != cb["weighted"]
+    assert bench.label_checksum(a) == ca

@@ -3,17 +3,28 @@ forward values, gradients of every parameter tensor, Adam steps,
 training plus inference with fallback to the exact score, and what the
 trained network gains over the exact path.
 
-Gradient bounds (relative L2 error per tensor): against the oracle that keeps
-activations and deltas in BF16 between layers (the stated precision of the
-tensor-core path) 5e-3; against plain FP64 5e-2, because three BF16-stored
-deltas precede the first layer's gradient (measured 2.5-3.6% at 512 rows,
-1-3% at 4096, the same with the FP64 emulation of the BF16 storage)."""
+Forward values and gradients are compared element by element with the FP64
+oracle that rounds where the kernels do (features, hidden activations and
+deltas stored in bfloat16; oracle/mlp.py backward_bf16_storage), on the
+BF16 weights both sides use.  Each element has its own tolerance: 8 units of
+BF16 roundoff (2^-9) times the sum of the absolute products that form it
+(|h3| |w4| for an output, |delta| |h| over the batch for a weight gradient,
+|delta| for a bias).  This is a test tolerance, not a proven bound: a
+rigorous worst case through three layers of BF16 storage lets every hidden
+unit straddle a rounding boundary and gives bounds larger than the values.
+The GPU differs from this oracle only by its FP32 accumulation order and the
+one-ulp BF16 differences it causes on stored values that sit on a rounding
+boundary (measured below 10% of the tolerance); a plausible mistake (a sign,
+an index, a transposed operand) moves an element by about its own size, which
+exceeds its tolerance on nearly every element that does not cancel to noise
+(tests/test_oracle_mlp.py plants such mistakes in the oracle)."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import mlp as L
 from paper_1910_06451_gb300 import synth
+from tests._surrogate_ref import elementwise_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -57,12 +68,12 @@ def _params(seed):
 
 
 def _oracle_with_bf16(p, w, q):
-    """The oracle evaluated on the BF16-rounded weights and features the GPU uses."""
+    """The oracle's parameters with the BF16-rounded weights the GPU uses, and
+    the FP64 features (rounded to BF16 inside elementwise_reference)."""
     pb = dict(p)
     for k in ("W1", "W2", "W3"):
         pb[k] = _bf16(p[k])
-    X = _bf16(L.features(w.scene.arm, q.astype(np.float64)))
-    return pb, X
+    return pb, L.features(w.scene.arm, q.astype(np.float64))
 
 
 def test_forward_matches_oracle(fk, setup):
@@ -73,9 +84,9 @@ def test_forward_matches_oracle(fk, setup):
     out = torch.empty(1000, dtype=torch.float32, device="cuda")
     fk.surrogate_forward(s, torch.from_numpy(q).cuda(), out)
     pb, X = _oracle_with_bf16(_unflat(_flat(p)), w, q)
-    want, _ = L.forward(pb, X)
-    got = out.cpu().numpy()
-    assert np.linalg.norm(got - want) <= 1e-2 * np.linalg.norm(want)
+    want, tol = elementwise_reference(pb, X)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want) / tol)
 
 
 def test_gradients_match_oracle(fk, setup):
@@ -87,16 +98,15 @@ def test_gradients_match_oracle(fk, setup):
     target = np.random.default_rng(5).normal(size=n).astype(np.float32)
     g, loss = fk.surrogate_gradients(s, torch.from_numpy(q).cuda(), torch.from_numpy(target).cuda())
     pb, X = _oracle_with_bf16(p, w, q)
-    out, cache = L.forward(pb, X)
-    want = L.backward(pb, cache, out, target.astype(np.float64))
+    out, tol_out, want, tol = elementwise_reference(pb, X, target.astype(np.float64))
     got = _unflat(g)
-    emu = L.backward_bf16_storage(pb, X, target.astype(np.float64))
-    assert loss == pytest.approx(L.loss(out, target), rel=1e-2)
+    # the loss: mean of (out - target)^2 with every output within its tolerance
+    r = np.abs(out - target)
+    assert abs(loss - L.loss(out, target)) <= np.mean(2 * r * tol_out + tol_out ** 2) + 1e-6 * L.loss(out, target)
     for k, _ in ORDER:
-        err = np.linalg.norm(got[k] - want[k]) / max(np.linalg.norm(want[k]), 1e-30)
-        err_b = np.linalg.norm(got[k] - emu[k]) / max(np.linalg.norm(emu[k]), 1e-30)
-        assert err_b <= 5e-3, (k, err_b)
-        assert err <= 5e-2, (k, err)
+        err = np.abs(got[k] - want[k])
+        assert np.all(err <= tol[k]), (k, float(np.max(err / tol[k])))
+        print(f"{k}: max |err| / tolerance {float(np.max(err / np.maximum(tol[k], 1e-300))):.3f}")
 
 
 def test_adam_step_matches_oracle(fk, setup):
@@ -171,8 +181,8 @@ def test_forward_twelve_point_arm_matches_oracle(fk):
         out = torch.empty(1000, dtype=torch.float32, device="cuda")
         fk.surrogate_forward(s, torch.from_numpy(q).cuda(), out)
         pb, X = _oracle_with_bf16(_unflat(_flat(p)), w, q)
-        want, _ = L.forward(pb, X)
-        assert np.linalg.norm(out.cpu().numpy() - want) <= 1e-2 * np.linalg.norm(want)
+        want, tol = elementwise_reference(pb, X)
+        assert np.all(np.abs(out.cpu().numpy().astype(np.float64) - want) <= tol)
     finally:
         fk.surrogate_destroy(s)
         fk.fk_chain_destroy(chain)
