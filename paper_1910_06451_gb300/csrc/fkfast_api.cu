@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fk_internal.h"
+#include "surr_step.h"
 #include "tc_gemm.cuh"
 
 namespace fk {
@@ -966,18 +967,12 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
 // parameter vector: W1 [256][64], b1, W2 [256][256], b2, W3 [256][256], b3,
 // w4 [256], b4.
 namespace fk {
-cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, bf16 *XT,
-                                 cudaStream_t s);
+cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, cudaStream_t s);
 
-cudaError_t launch_gemm(int epi, int nt, const GemmArgs &g, int splits, cudaStream_t s);
-cudaError_t launch_surr_head_bwd(const float *out, const float *y, const bf16 *h3, const float *w4, int B, bf16 *dP3,
-                                 float *pw4, float *pb4, float *ploss, cudaStream_t s);
-cudaError_t launch_transpose_bf16(const bf16 *in, int64_t rows, int64_t cols, bf16 *out, cudaStream_t s);
-cudaError_t launch_sum_partials(const float *src, int nz, int64_t stride, int64_t n, float *dst, cudaStream_t s);
-cudaError_t launch_row_sum_bf16(const bf16 *Mt, int64_t rows, int64_t cols, float *dst, cudaStream_t s);
+cudaError_t launch_gemm(int nt, const GemmArgs &g, int splits, cudaStream_t s);
 cudaError_t launch_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
                         float eps, int64_t t, cudaStream_t s);
-cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, bf16 *WTb, cudaStream_t s);
+cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, cudaStream_t s);
 cudaError_t launch_surr_decide(const float *out, float scale, int64_t n, float tau, float *pred, int8_t *label,
                                int32_t *fb_idx, int32_t *fb_cnt, cudaStream_t s);
 cudaError_t launch_gather_rows(const float *q, int D, const int32_t *idx, int64_t n, float *out, cudaStream_t s);
@@ -1017,13 +1012,19 @@ struct surrogate {
   const fk_chain *chain = nullptr;
   uint64_t seed = 0;
   DevBuf p, m, v, g;
-  DevBuf w1b, w1t, w2b, w2t, w3b, w3t;
+  DevBuf w1b, w2b, w3b, wc;
   float scale = 1.f;   // target scale: the network predicts f / scale
   float tau = -1.f;    // calibrated threshold in units of f (< 0: not calibrated)
   int64_t t = 0;       // Adam steps taken
-  int B = 0;           // batch of the training buffers
-  DevBuf H1, H1T, H2, H2T, H3, dP3, dP3T, dP2, dP2T, dP1, dP1T, out, part, pw4, pb4, ploss, loss_hist;
-  DevBuf X, XT, Y, Yh, lab_tmp;
+  // training step (surr_train.cu): batch B's transposed activations and
+  // deltas, loss gradients, split-K partials, the device step counter, the
+  // fork streams of the weight-gradient products and the captured step
+  int tB = 0;
+  DevBuf tT, tdl, tpart, tstep, loss_hist;
+  cudaStream_t cap = nullptr, f2 = nullptr, f3 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_j2 = nullptr, ev_j3 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DevBuf X, Y, Yh, lab_tmp;
   DevBuf iout, iwc, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
   DevBuf err, scal;
 };
@@ -1049,9 +1050,10 @@ static int surr_init_params(surrogate *s, cudaStream_t st) {
 
 static int surr_sync_weights(surrogate *s, cudaStream_t st) {
   const float *P = s->p.as<float>();
-  CK(launch_weights_bf16(P + kOffW1, kSurrW, kSurrIn, s->w1b.as<bf16>(), s->w1t.as<bf16>(), st));
-  CK(launch_weights_bf16(P + kOffW2, kSurrW, kSurrW, s->w2b.as<bf16>(), s->w2t.as<bf16>(), st));
-  CK(launch_weights_bf16(P + kOffW3, kSurrW, kSurrW, s->w3b.as<bf16>(), s->w3t.as<bf16>(), st));
+  CK(launch_weights_bf16(P + kOffW1, kSurrW, kSurrIn, s->w1b.as<bf16>(), st));
+  CK(launch_weights_bf16(P + kOffW2, kSurrW, kSurrW, s->w2b.as<bf16>(), st));
+  CK(launch_weights_bf16(P + kOffW3, kSurrW, kSurrW, s->w3b.as<bf16>(), st));
+  CK(launch_surr_wc(s->w1b.as<bf16>(), s->w2b.as<bf16>(), s->w3b.as<bf16>(), s->wc.as<uint8_t>(), st));
   return FK_OK;
 }
 
@@ -1075,13 +1077,17 @@ extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogat
   ck(s->v.ensure(sizeof(float) * kSurrParams));
   ck(s->g.ensure(sizeof(float) * kSurrParams));
   ck(s->w1b.ensure(2 * kSurrW * kSurrIn));
-  ck(s->w1t.ensure(2 * kSurrW * kSurrIn));
   ck(s->w2b.ensure(2 * kSurrW * kSurrW));
-  ck(s->w2t.ensure(2 * kSurrW * kSurrW));
   ck(s->w3b.ensure(2 * kSurrW * kSurrW));
-  ck(s->w3t.ensure(2 * kSurrW * kSurrW));
+  ck(s->wc.ensure(kSurrWcBytes));
   ck(s->err.ensure(64));
   ck(s->scal.ensure(64));
+  ck(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+  ck(cudaStreamCreateWithFlags(&s->f2, cudaStreamNonBlocking));
+  ck(cudaStreamCreateWithFlags(&s->f3, cudaStreamNonBlocking));
+  ck(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&s->ev_j2, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&s->ev_j3, cudaEventDisableTiming));
   if (rc == FK_OK) rc = surr_init_params(s, 0);
   if (rc == FK_OK) rc = surr_sync_weights(s, 0);
   if (rc == FK_OK && cudaStreamSynchronize(0) != cudaSuccess) rc = fail(FK_ERR_CUDA, "surrogate_create: sync failed");
@@ -1095,27 +1101,43 @@ extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogat
 
 extern "C" void surrogate_destroy(surrogate_t *s) {
   if (!s) return;
-  DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w1t, &s->w2b, &s->w2t, &s->w3b, &s->w3t,
-                    &s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1,
-                    &s->dP1T, &s->out, &s->part, &s->pw4, &s->pb4, &s->ploss, &s->loss_hist, &s->X, &s->XT,
-                    &s->Y, &s->Yh, &s->lab_tmp, &s->iout, &s->iwc, &s->fb_idx, &s->fb_cnt,
-                    &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred, &s->err, &s->scal};
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  for (cudaStream_t x : {s->cap, s->f2, s->f3})
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t x : {s->ev_fork, s->ev_j2, s->ev_j3})
+    if (x) cudaEventDestroy(x);
+  DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w2b, &s->w3b, &s->wc,
+                    &s->tT, &s->tdl, &s->tpart, &s->tstep, &s->loss_hist, &s->X, &s->Y, &s->Yh, &s->lab_tmp,
+                    &s->iout, &s->iwc, &s->fb_idx, &s->fb_cnt, &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred,
+                    &s->err, &s->scal};
   for (DevBuf *b : bufs) b->release();
   delete s;
 }
 
-static int surr_ensure_batch(surrogate *s, int B) {
-  if (s->B == B) return FK_OK;
-  const size_t act = 2 * (size_t)B * kSurrW;
-  DevBuf *acts[] = {&s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->dP3, &s->dP3T, &s->dP2, &s->dP2T, &s->dP1, &s->dP1T};
-  for (DevBuf *b : acts) CK(b->ensure(act));
-  CK(s->out.ensure(sizeof(float) * (size_t)B));
-  const int splits = B / kBM;
-  CK(s->part.ensure(sizeof(float) * (size_t)splits * kSurrW * kSurrW));
-  CK(s->pw4.ensure(sizeof(float) * (size_t)(B / 32) * kSurrW));
-  CK(s->pb4.ensure(sizeof(float) * (size_t)(B / 32)));
-  CK(s->ploss.ensure(sizeof(float) * (size_t)(B / 32)));
-  s->B = B;
+// Split-K factor of the weight-gradient products for batch B: K = B / splits
+// at least 256 (four 64-wide chunks) where B allows, at most 32 splits.
+static int surr_splits(int B) {
+  const int kc = B / kBK;
+  int sp = kc / 4;
+  sp = sp > 32 ? 32 : (sp < 1 ? 1 : sp);
+  while (kc % sp) --sp;
+  return sp;
+}
+
+static void surr_drop_graph(surrogate *s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  s->exec = nullptr;
+}
+
+// Scratch of the training step for batch B.
+static int surr_step_buffers(surrogate *s, int B) {
+  if (s->tB == B) return FK_OK;
+  surr_drop_graph(s);
+  CK(s->tT.ensure(2 * (size_t)B * (kSurrIn + 6 * kSurrW)));
+  CK(s->tdl.ensure(sizeof(float) * 2 * (size_t)B));
+  CK(s->tpart.ensure(sizeof(float) * (size_t)surr_splits(B) * (kSurrW * kSurrIn + 2 * kSurrW * kSurrW)));
+  CK(s->tstep.ensure(sizeof(int64_t)));
+  s->tB = B;
   return FK_OK;
 }
 
@@ -1133,92 +1155,58 @@ static GemmArgs gemm_args(surrogate *s, const bf16 *A, int64_t lda, const bf16 *
   return g;
 }
 
-// Forward pass of the training batch: X [B][64] (row stride 64), XT its
-// transpose with row stride ldxt.  Leaves H1, H1T, H2, H2T, H3 and out.
-static int surr_forward_train(surrogate *s, const bf16 *X, int B, cudaStream_t st) {
+// Enqueues one training step (surr_train.cu) on st: the tile kernel over the
+// batch (rows (step mod steps_per_epoch) B .. + B of X and Y), the three
+// weight-gradient products on st and the fork streams, the reduction into
+// the flat gradient g; with aa also Adam, the BF16 weights and the step
+// counter.  loss_hist[step] receives the batch loss (if not null).
+static int surr_step_enqueue(surrogate *s, const bf16 *X, const float *Y, int B, int64_t steps_per_epoch,
+                             const SurrAdamArgs *aa, float *loss_hist, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const float *P = s->p.as<float>();
-  GemmArgs g = gemm_args(s, X, kSurrIn, s->w1b.as<bf16>(), kSurrIn, B, kSurrW, kSurrIn);
-  g.bias = P + kOffB1;
-  g.C = s->H1.as<bf16>();
-  g.ldc = kSurrW;
-  g.CT = s->H1T.as<bf16>();
-  g.ldct = B;
-  CK(launch_gemm(EPI_RELU, 128, g, 1, st));
-  g = gemm_args(s, s->H1.as<bf16>(), kSurrW, s->w2b.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
-  g.bias = P + kOffB2;
-  g.C = s->H2.as<bf16>();
-  g.ldc = kSurrW;
-  g.CT = s->H2T.as<bf16>();
-  g.ldct = B;
-  CK(launch_gemm(EPI_RELU, 128, g, 1, st));
-  g = gemm_args(s, s->H2.as<bf16>(), kSurrW, s->w3b.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
-  g.bias = P + kOffB3;
-  g.C = s->H3.as<bf16>();
-  g.ldc = kSurrW;
-  g.w4 = P + kOffW4;
-  g.b4 = P + kOffB4;
-  g.out = s->out.as<float>();
-  CK(launch_gemm(EPI_HEAD, 256, g, 1, st));
-  return FK_OK;
-}
-
-// Backward pass into the flat gradient g; XT is the batch's transposed input
-// with row stride ldxt.  loss_out (device, may be null) receives the batch's
-// mean squared error.
-static int surr_backward(surrogate *s, const bf16 *XT, int64_t ldxt, const float *Y, int B, float *loss_out,
-                         cudaStream_t st) {
-  float *G = s->g.as<float>();
-  const float *P = s->p.as<float>();
-  const int nb = B / 32, splits = B / kBM;
-  CK(launch_surr_head_bwd(s->out.as<float>(), Y, s->H3.as<bf16>(), P + kOffW4, B, s->dP3.as<bf16>(),
-                          s->pw4.as<float>(), s->pb4.as<float>(), s->ploss.as<float>(), st));
-  CK(launch_sum_partials(s->pw4.as<float>(), nb, kSurrW, kSurrW, G + kOffW4, st));
-  CK(launch_sum_partials(s->pb4.as<float>(), nb, 1, 1, G + kOffB4, st));
-  if (loss_out) {
-    CK(launch_sum_partials(s->ploss.as<float>(), nb, 1, 1, loss_out, st));
-    CK(launch_scale(loss_out, 1, 1.f / (float)B, st));
-  }
-  CK(launch_transpose_bf16(s->dP3.as<bf16>(), B, kSurrW, s->dP3T.as<bf16>(), st));
-  // layer 3: dW3 = dP3^T H2, db3 = rows of dP3^T
-  GemmArgs g = gemm_args(s, s->dP3T.as<bf16>(), B, s->H2T.as<bf16>(), B, kSurrW, kSurrW, B / splits);
-  g.Cf = s->part.as<float>();
+  bf16 *xT = s->tT.as<bf16>();
+  bf16 *h1T = xT + (int64_t)kSurrIn * B, *h2T = h1T + (int64_t)kSurrW * B, *h3T = h2T + (int64_t)kSurrW * B;
+  bf16 *d3T = h3T + (int64_t)kSurrW * B, *d2T = d3T + (int64_t)kSurrW * B, *d1T = d2T + (int64_t)kSurrW * B;
+  float *dout = s->tdl.as<float>(), *lrow = dout + B;
+  int64_t *step = s->tstep.as<int64_t>();
+  SurrStepArgs a{X, Y, B, steps_per_epoch, step, s->wc.as<uint8_t>(), P + kOffB1, P + kOffB2, P + kOffB3,
+                 P + kOffW4, P + kOffB4, xT, h1T, h2T, h3T, d3T, d2T, d1T, dout, lrow, s->err.as<int32_t>(),
+                 g_wait_limit};
+  CK(launch_surr_tile(a, sms, st));
+  // dW3 = d3^T h2, dW2 = d2^T h1, dW1 = d1^T x: split-K over the batch rows
+  const int splits = surr_splits(B);
+  float *p3 = s->tpart.as<float>(), *p2 = p3 + (int64_t)splits * kSurrW * kSurrW;
+  float *p1 = p2 + (int64_t)splits * kSurrW * kSurrW;
+  CK(cudaEventRecord(s->ev_fork, st));
+  CK(cudaStreamWaitEvent(s->f2, s->ev_fork, 0));
+  CK(cudaStreamWaitEvent(s->f3, s->ev_fork, 0));
+  GemmArgs g = gemm_args(s, d3T, B, h2T, B, kSurrW, kSurrW, B / splits);
+  g.Cf = p3;
   g.ldcf = kSurrW;
   g.zstride = (int64_t)kSurrW * kSurrW;
-  CK(launch_gemm(EPI_F32, 256, g, splits, st));
-  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrW, (int64_t)kSurrW * kSurrW, G + kOffW3, st));
-  CK(launch_row_sum_bf16(s->dP3T.as<bf16>(), kSurrW, B, G + kOffB3, st));
-  // dP2 = (dP3 W3) [H2 > 0]
-  g = gemm_args(s, s->dP3.as<bf16>(), kSurrW, s->w3t.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
-  g.mask = s->H2.as<bf16>();
-  g.ldm = kSurrW;
-  g.C = s->dP2.as<bf16>();
-  g.ldc = kSurrW;
-  g.CT = s->dP2T.as<bf16>();
-  g.ldct = B;
-  CK(launch_gemm(EPI_MASK, 128, g, 1, st));
-  g = gemm_args(s, s->dP2T.as<bf16>(), B, s->H1T.as<bf16>(), B, kSurrW, kSurrW, B / splits);
-  g.Cf = s->part.as<float>();
+  CK(launch_gemm(256, g, splits, st));
+  g = gemm_args(s, d2T, B, h1T, B, kSurrW, kSurrW, B / splits);
+  g.Cf = p2;
   g.ldcf = kSurrW;
   g.zstride = (int64_t)kSurrW * kSurrW;
-  CK(launch_gemm(EPI_F32, 256, g, splits, st));
-  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrW, (int64_t)kSurrW * kSurrW, G + kOffW2, st));
-  CK(launch_row_sum_bf16(s->dP2T.as<bf16>(), kSurrW, B, G + kOffB2, st));
-  // dP1 = (dP2 W2) [H1 > 0]
-  g = gemm_args(s, s->dP2.as<bf16>(), kSurrW, s->w2t.as<bf16>(), kSurrW, B, kSurrW, kSurrW);
-  g.mask = s->H1.as<bf16>();
-  g.ldm = kSurrW;
-  g.C = s->dP1.as<bf16>();
-  g.ldc = kSurrW;
-  g.CT = s->dP1T.as<bf16>();
-  g.ldct = B;
-  CK(launch_gemm(EPI_MASK, 128, g, 1, st));
-  g = gemm_args(s, s->dP1T.as<bf16>(), B, XT, ldxt, kSurrW, kSurrIn, B / splits);
-  g.Cf = s->part.as<float>();
+  CK(launch_gemm(256, g, splits, s->f2));
+  g = gemm_args(s, d1T, B, xT, B, kSurrW, kSurrIn, B / splits);
+  g.Cf = p1;
   g.ldcf = kSurrIn;
   g.zstride = (int64_t)kSurrW * kSurrIn;
-  CK(launch_gemm(EPI_F32, 64, g, splits, st));
-  CK(launch_sum_partials(s->part.as<float>(), splits, (int64_t)kSurrW * kSurrIn, (int64_t)kSurrW * kSurrIn, G + kOffW1, st));
-  CK(launch_row_sum_bf16(s->dP1T.as<bf16>(), kSurrW, B, G + kOffB1, st));
+  CK(launch_gemm(64, g, splits, s->f3));
+  CK(cudaEventRecord(s->ev_j2, s->f2));
+  CK(cudaEventRecord(s->ev_j3, s->f3));
+  CK(cudaStreamWaitEvent(st, s->ev_j2, 0));
+  CK(cudaStreamWaitEvent(st, s->ev_j3, 0));
+  SurrReduceArgs r{p1, p2, p3, splits, d1T, d2T, d3T, h3T, dout, lrow, B, s->g.as<float>(), loss_hist, step};
+  CK(launch_surr_reduce(r, st));
+  if (aa) {
+    CK(launch_surr_adam(*aa, st));
+    CK(launch_surr_advance(step, st));
+  }
   return FK_OK;
 }
 
@@ -1230,12 +1218,10 @@ static int surr_check_err(surrogate *s, cudaStream_t st, const char *who) {
   return FK_OK;
 }
 
-// Features of n queries into buffer X (and XT if non-null), rows padded to n_pad.
-static int surr_features(surrogate *s, const float *q, int64_t n, int64_t n_pad, DevBuf &X, DevBuf *XT,
-                         cudaStream_t st) {
+// Features of n queries into buffer X ([n_pad][64], rows n.. zero).
+static int surr_features(surrogate *s, const float *q, int64_t n, int64_t n_pad, DevBuf &X, cudaStream_t st) {
   CK(X.ensure(2 * (size_t)n_pad * kSurrIn));
-  if (XT) CK(XT->ensure(2 * (size_t)n_pad * kSurrIn));
-  CK(launch_surr_features(s->chain->cf, q, n, n_pad, X.as<bf16>(), XT ? XT->as<bf16>() : nullptr, st));
+  CK(launch_surr_features(s->chain->cf, q, n, n_pad, X.as<bf16>(), st));
   return FK_OK;
 }
 
@@ -1300,12 +1286,12 @@ extern "C" int surrogate_gradients(surrogate_t *s, const float *q, int64_t n, co
   if (n < kBM || n % kBM || n > (1 << 20)) return fail(FK_ERR_ARG, "surrogate_gradients: n must be a multiple of 128");
   cudaStream_t st = 0;
   CK(cudaMemsetAsync(s->err.p, 0, 64, st));
-  int rc = surr_ensure_batch(s, (int)n);
+  int rc = surr_step_buffers(s, (int)n);
   if (rc != FK_OK) return rc;
-  if ((rc = surr_features(s, q, n, n, s->X, &s->XT, st)) != FK_OK) return rc;
-  if ((rc = surr_forward_train(s, s->X.as<bf16>(), (int)n, st)) != FK_OK) return rc;
-  float *dl = s->scal.as<float>();
-  if ((rc = surr_backward(s, s->XT.as<bf16>(), n, target, (int)n, dl, st)) != FK_OK) return rc;
+  if ((rc = surr_features(s, q, n, n, s->X, st)) != FK_OK) return rc;
+  CK(cudaMemsetAsync(s->tstep.p, 0, sizeof(int64_t), st));
+  float *dl = s->scal.as<float>();  // loss_hist[0]
+  if ((rc = surr_step_enqueue(s, s->X.as<bf16>(), target, (int)n, 1, nullptr, dl, st)) != FK_OK) return rc;
   if ((rc = surr_check_err(s, st, "surrogate_gradients")) != FK_OK) return rc;
   CK(cudaMemcpy(grad, s->g.p, sizeof(float) * kSurrParams, cudaMemcpyDeviceToHost));
   if (loss) CK(cudaMemcpy(loss, dl, sizeof(float), cudaMemcpyDeviceToHost));
@@ -1368,9 +1354,9 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
     CK(cudaMemcpyAsync(s->Yh.p, s->Y.as<float>() + (n - n_hold), sizeof(float) * (size_t)n_hold,
                        cudaMemcpyDeviceToDevice, st));
   CK(launch_scale(s->Y.as<float>(), n_tr, 1.f / s->scale, st));
-  // features of the training rows, both layouts
-  if ((rc = surr_features(s, q, n_tr, n_tr, s->X, &s->XT, st)) != FK_OK) return rc;
-  if ((rc = surr_ensure_batch(s, B)) != FK_OK) return rc;
+  // features of the training rows
+  if ((rc = surr_features(s, q, n_tr, n_tr, s->X, st)) != FK_OK) return rc;
+  if ((rc = surr_step_buffers(s, B)) != FK_OK) return rc;
   if (prm->reinit) {
     if ((rc = surr_init_params(s, st)) != FK_OK) return rc;
     if ((rc = surr_sync_weights(s, st)) != FK_OK) return rc;
@@ -1378,23 +1364,34 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
   const int64_t steps_per_epoch = n_tr / B;
   const int64_t total = steps_per_epoch * prm->epochs;
   CK(s->loss_hist.ensure(sizeof(float) * (size_t)(total > 0 ? total : 1)));
-  int64_t step = 0;
-  for (int ep = 0; ep < prm->epochs; ++ep) {
-    const float lr_ep = ep < (2 * prm->epochs + 2) / 3 ? prm->lr : prm->lr / 3.f;
-    for (int64_t b = 0; b < steps_per_epoch; ++b, ++step) {
-      const float lr = prm->schedule == FK_LR_COSINE
-                           ? (float)(0.5 * prm->lr * (1.0 + cos(M_PI * (double)step / (double)total)))
-                           : lr_ep;
-      const int64_t b0 = b * B;
-      if ((rc = surr_forward_train(s, s->X.as<bf16>() + b0 * kSurrIn, B, st)) != FK_OK) return rc;
-      if ((rc = surr_backward(s, s->XT.as<bf16>() + b0, n_tr, s->Y.as<float>() + b0, B,
-                              s->loss_hist.as<float>() + step, st)) != FK_OK)
-        return rc;
-      ++s->t;
-      CK(launch_adam(s->p.as<float>(), s->m.as<float>(), s->v.as<float>(), s->g.as<float>(), kSurrParams, lr, 0.9f,
-                     0.999f, 1e-8f, s->t, st));
-      if ((rc = surr_sync_weights(s, st)) != FK_OK) return rc;
+  CK(cudaMemsetAsync(s->tstep.p, 0, sizeof(int64_t), st));
+  if (total > 0) {
+    // one step captured into a graph (a library stream, the fork streams
+    // joined back), replayed `total` times on st: the batch, learning rate
+    // and Adam step come from the device step counter
+    SurrAdamArgs aa{s->p.as<float>(), s->m.as<float>(), s->v.as<float>(), s->g.as<float>(),
+                    s->tstep.as<int64_t>(), total, steps_per_epoch, prm->epochs, s->t, prm->lr,
+                    prm->schedule == FK_LR_COSINE ? 1 : 0, s->w1b.as<bf16>(), s->w2b.as<bf16>(), s->w3b.as<bf16>(),
+                    s->wc.as<uint8_t>()};
+    surr_drop_graph(s);
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    rc = surr_step_enqueue(s, s->X.as<bf16>(), s->Y.as<float>(), B, steps_per_epoch, &aa, s->loss_hist.as<float>(),
+                           s->cap);
+    cudaError_t ec = cudaStreamEndCapture(s->cap, &graph);
+    if (rc != FK_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
     }
+    if (ec != cudaSuccess) return fail(FK_ERR_CUDA, "surrogate_train: capture failed: %s", cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&s->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+      s->exec = nullptr;
+      return fail(FK_ERR_CUDA, "surrogate_train: instantiate failed: %s", cudaGetErrorString(ec));
+    }
+    for (int64_t k = 0; k < total; ++k) CK(cudaGraphLaunch(s->exec, st));
+    s->t += total;
   }
   if ((rc = surr_check_err(s, st, "surrogate_train")) != FK_OK) return rc;
   // calibrate tau on the held-out rows: the largest |pred| with a wrong sign

@@ -8,13 +8,13 @@
 
 namespace fk {
 
-template <int NT, int EPI>
+template <int NT>
 static cudaError_t launch_gemm_t(const GemmArgs &g, int splits, cudaStream_t s) {
   constexpr size_t smem = gemm_smem_bytes<NT>();
-  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<NT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(g.M / kBM), (unsigned)(g.N / NT), (unsigned)splits);
-  gemm_tc_kernel<NT, EPI><<<grid, kGemmThreads, smem, s>>>(g);
+  gemm_tc_kernel<NT><<<grid, kGemmThreads, smem, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -22,9 +22,9 @@ static cudaError_t launch_gemm_t(const GemmArgs &g, int splits, cudaStream_t s) 
 // written at Cf + z * M * N.
 cudaError_t launch_gemm_f32(const GemmArgs &g0, int splits, cudaStream_t s) {
   GemmArgs g = g0;
-  if (g.N % 256 == 0) return launch_gemm_t<256, EPI_F32>(g, splits, s);
-  if (g.N % 128 == 0) return launch_gemm_t<128, EPI_F32>(g, splits, s);
-  return launch_gemm_t<64, EPI_F32>(g, splits, s);
+  if (g.N % 256 == 0) return launch_gemm_t<256>(g, splits, s);
+  if (g.N % 128 == 0) return launch_gemm_t<128>(g, splits, s);
+  return launch_gemm_t<64>(g, splits, s);
 }
 
 }  // namespace fk
@@ -32,10 +32,10 @@ cudaError_t launch_gemm_f32(const GemmArgs &g0, int splits, cudaStream_t s) {
 namespace fk {
 
 // ------------------------------------------------------------ features ---
-// One row of features per query (surr_features.cuh), written row-major and,
-// for training, transposed.  Rows n..n_pad-1 are zeros.
+// One row of features per query (surr_features.cuh), written row-major.
+// Rows n..n_pad-1 are zeros.
 __global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q, int64_t n, int64_t n_pad,
-                                     bf16 *__restrict__ X, bf16 *__restrict__ XT) {
+                                     bf16 *__restrict__ X) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n_pad) return;
   __align__(16) bf16 h[kSurrIn];
@@ -43,86 +43,6 @@ __global__ void surr_features_kernel(const ChainF c, const float *__restrict__ q
   uint4 *dst = reinterpret_cast<uint4 *>(X + k * kSurrIn);
 #pragma unroll
   for (int i = 0; i < kSurrIn / 8; ++i) dst[i] = reinterpret_cast<const uint4 *>(h)[i];
-  if (XT) {
-#pragma unroll
-    for (int i = 0; i < kSurrIn; ++i) XT[(int64_t)i * n_pad + k] = h[i];
-  }
-}
-
-// ---------------------------------------------------------------- head ---
-// Loss gradient of the output and the back-propagation through the last
-// layer.  One CTA of 256 threads (one per hidden unit) handles 32 rows:
-//   dout_b = 2 (out_b - y_b) / B
-//   dP3[b][k] = dout_b w4[k] [h3[b][k] > 0]
-//   partial dW4[k] = sum_b dout_b h3[b][k], partial db4 and loss sum.
-constexpr int kHeadRows = 32;
-
-__global__ void __launch_bounds__(kSurrW) surr_head_bwd_kernel(const float *__restrict__ out,
-                                                               const float *__restrict__ y, const bf16 *__restrict__ h3,
-                                                               const float *__restrict__ w4, int B,
-                                                               bf16 *__restrict__ dP3, float *__restrict__ pw4,
-                                                               float *__restrict__ pb4, float *__restrict__ ploss) {
-  __shared__ float dout[kHeadRows];
-  const int k = threadIdx.x;
-  const int b0 = blockIdx.x * kHeadRows;
-  if (k < kHeadRows) {
-    const float e = out[b0 + k] - y[b0 + k];
-    dout[k] = 2.f * e / (float)B;
-    float se = e * e, sd = 2.f * e / (float)B;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      se += __shfl_xor_sync(0xffffffffu, se, o);
-      sd += __shfl_xor_sync(0xffffffffu, sd, o);
-    }
-    if (k == 0) {
-      ploss[blockIdx.x] = se;
-      pb4[blockIdx.x] = sd;
-    }
-  }
-  __syncthreads();
-  const float wk = w4[k];
-  float acc = 0.f;
-  for (int r = 0; r < kHeadRows; ++r) {
-    const int64_t b = b0 + r;
-    const float h = __bfloat162float(h3[b * kSurrW + k]);
-    acc = fmaf(dout[r], h, acc);
-    dP3[b * kSurrW + k] = __float2bfloat16_rn(h > 0.f ? dout[r] * wk : 0.f);
-  }
-  pw4[(int64_t)blockIdx.x * kSurrW + k] = acc;
-}
-
-// ---------------------------------------------------------- transposes ---
-// out[c][r] = in[r][c] for a rows x cols bf16 matrix (both multiples of 32).
-__global__ void transpose_bf16_kernel(const bf16 *__restrict__ in, int64_t rows, int64_t cols,
-                                      bf16 *__restrict__ out) {
-  __shared__ bf16 t[32][33];
-  const int64_t r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) t[i][threadIdx.x] = in[(r0 + i) * cols + c0 + threadIdx.x];
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) out[(c0 + i) * rows + r0 + threadIdx.x] = t[threadIdx.x][i];
-}
-
-// ----------------------------------------------------------- reductions --
-// dst[j] = sum_z src[z * stride + j] for j < n (split-K partials, per-block partials).
-__global__ void sum_partials_kernel(const float *__restrict__ src, int nz, int64_t stride, int64_t n,
-                                    float *__restrict__ dst) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  float s = 0.f;
-  for (int z = 0; z < nz; ++z) s += src[z * stride + j];
-  dst[j] = s;
-}
-
-// dst[r] = sum_c M[r][c] for a rows x cols bf16 matrix: one warp per row.
-__global__ void row_sum_bf16_kernel(const bf16 *__restrict__ Mt, int64_t rows, int64_t cols, float *__restrict__ dst) {
-  const int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
-  float s = 0.f;
-  for (int64_t c = lane; c < cols; c += 32) s += __bfloat162float(Mt[r * cols + c]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) dst[r] = s;
 }
 
 // ---------------------------------------------------------------- Adam ---
@@ -140,14 +60,10 @@ __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float 
 }
 
 // BF16 copies of a weight matrix W [rows][cols] (FP32): row-major and transposed.
-__global__ void weights_bf16_kernel(const float *__restrict__ W, int rows, int cols, bf16 *__restrict__ Wb,
-                                    bf16 *__restrict__ WTb) {
+__global__ void weights_bf16_kernel(const float *__restrict__ W, int rows, int cols, bf16 *__restrict__ Wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * cols) return;
-  const int r = i / cols, c = i % cols;
-  const bf16 h = __float2bfloat16_rn(W[i]);
-  Wb[i] = h;
-  WTb[(int64_t)c * rows + r] = h;
+  Wb[i] = __float2bfloat16_rn(W[i]);
 }
 
 // ----------------------------------------------------------- inference ---
@@ -217,46 +133,19 @@ __global__ void scale_kernel(float *__restrict__ x, int64_t n, float s) {
 // ------------------------------------------------------------ launchers ---
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, bf16 *XT,
-                                 cudaStream_t s) {
-  surr_features_kernel<<<blocks_for(n_pad, 128), 128, 0, s>>>(c, q, n, n_pad, X, XT);
+cudaError_t launch_surr_features(const ChainF &c, const float *q, int64_t n, int64_t n_pad, bf16 *X, cudaStream_t s) {
+  surr_features_kernel<<<blocks_for(n_pad, 128), 128, 0, s>>>(c, q, n, n_pad, X);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm(int epi, int nt, const GemmArgs &g, int splits, cudaStream_t s) {
-  switch (epi * 1000 + nt) {
-    case EPI_RELU * 1000 + 128: return launch_gemm_t<128, EPI_RELU>(g, splits, s);
-    case EPI_RELU * 1000 + 256: return launch_gemm_t<256, EPI_RELU>(g, splits, s);
-    case EPI_HEAD * 1000 + 256: return launch_gemm_t<256, EPI_HEAD>(g, splits, s);
-    case EPI_MASK * 1000 + 128: return launch_gemm_t<128, EPI_MASK>(g, splits, s);
-    case EPI_MASK * 1000 + 256: return launch_gemm_t<256, EPI_MASK>(g, splits, s);
-    case EPI_F32 * 1000 + 64: return launch_gemm_t<64, EPI_F32>(g, splits, s);
-    case EPI_F32 * 1000 + 128: return launch_gemm_t<128, EPI_F32>(g, splits, s);
-    case EPI_F32 * 1000 + 256: return launch_gemm_t<256, EPI_F32>(g, splits, s);
+// D = A B^T with FP32 partial products, N tile 64, 128 or 256.
+cudaError_t launch_gemm(int nt, const GemmArgs &g, int splits, cudaStream_t s) {
+  switch (nt) {
+    case 64: return launch_gemm_t<64>(g, splits, s);
+    case 128: return launch_gemm_t<128>(g, splits, s);
+    case 256: return launch_gemm_t<256>(g, splits, s);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_surr_head_bwd(const float *out, const float *y, const bf16 *h3, const float *w4, int B, bf16 *dP3,
-                                 float *pw4, float *pb4, float *ploss, cudaStream_t s) {
-  surr_head_bwd_kernel<<<B / kHeadRows, kSurrW, 0, s>>>(out, y, h3, w4, B, dP3, pw4, pb4, ploss);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_transpose_bf16(const bf16 *in, int64_t rows, int64_t cols, bf16 *out, cudaStream_t s) {
-  dim3 grid((unsigned)(cols / 32), (unsigned)(rows / 32));
-  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sum_partials(const float *src, int nz, int64_t stride, int64_t n, float *dst, cudaStream_t s) {
-  sum_partials_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, nz, stride, n, dst);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_row_sum_bf16(const bf16 *Mt, int64_t rows, int64_t cols, float *dst, cudaStream_t s) {
-  row_sum_bf16_kernel<<<blocks_for(rows, 8), 256, 0, s>>>(Mt, rows, cols, dst);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float *p, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
@@ -266,8 +155,8 @@ cudaError_t launch_adam(float *p, float *m, float *v, const float *g, int64_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, bf16 *WTb, cudaStream_t s) {
-  weights_bf16_kernel<<<blocks_for((int64_t)rows * cols, 256), 256, 0, s>>>(W, rows, cols, Wb, WTb);
+cudaError_t launch_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, cudaStream_t s) {
+  weights_bf16_kernel<<<blocks_for((int64_t)rows * cols, 256), 256, 0, s>>>(W, rows, cols, Wb);
   return cudaGetLastError();
 }
 

@@ -27,26 +27,14 @@ namespace fk {
 
 typedef __nv_bfloat16 bf16;
 
-enum : int { EPI_RELU = 0, EPI_HEAD = 1, EPI_MASK = 2, EPI_F32 = 3 };
-
 struct GemmArgs {
   const bf16 *A;
   int64_t lda;
   const bf16 *B;
   int64_t ldb;
   int M, N, K;          // K of one split (grid.z splits along K)
-  const float *bias;    // [N] for EPI_RELU / EPI_HEAD
-  bf16 *C;              // row-major bf16 output or null
-  int64_t ldc;
-  bf16 *CT;             // transposed bf16 output ([N][M]) or null
-  int64_t ldct;
-  const bf16 *mask;     // EPI_MASK: keep entries where mask > 0
-  int64_t ldm;
-  float *Cf;            // EPI_F32 output; split z at Cf + z * zstride
+  float *Cf;            // FP32 output; split z at Cf + z * zstride
   int64_t ldcf, zstride;
-  const float *w4;      // EPI_HEAD: out[m] = relu(acc + bias) . w4 + *b4
-  const float *b4;
-  float *out;
   int32_t *err;
   uint32_t wait_limit;
 };
@@ -116,6 +104,47 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 columns of this warp's 32 TMEM lanes (one load, then its wait)
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// A TMEM load of 32 columns without its wait, and the wait alone: the wait
+// takes the destination registers as operands, so no use of them can be
+// scheduled before it.  Lets a warp convert one chunk while the next is in
+// flight.
+__device__ __forceinline__ void tc_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: start address, leading and stride byte
 // offsets (all >> 4), descriptor version 1, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -143,7 +172,7 @@ constexpr size_t gemm_smem_bytes() {
   return 2 * (size_t)(kBM * kBK * 2 + NT * kBK * 2);
 }
 
-template <int NT, int EPI>
+template <int NT>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const GemmArgs g) {
   static_assert(NT % 16 == 0 && NT >= 32 && NT <= 256, "N tile");
   constexpr uint32_t A_BYTES = kBM * kBK * 2;
@@ -239,48 +268,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const GemmArgs
     const int r = warp * 32 + lane;
     const int64_t gm = m0 + r;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    float dot = 0.f;
 #pragma unroll 1
     for (int j0 = 0; j0 < NT; j0 += 16) {
       float v[16];
       tc_ld16(trow + j0, v);
-      const int n = n0 + j0;
-      if (EPI == EPI_F32) {
-        float *dst = g.Cf + (int64_t)z * g.zstride + gm * g.ldcf + n;
+      float *dst = g.Cf + (int64_t)z * g.zstride + gm * g.ldcf + n0 + j0;
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        continue;
-      }
-      if (EPI == EPI_RELU || EPI == EPI_HEAD) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + g.bias[n + i], 0.f);
-      }
-      if (EPI == EPI_MASK) {
-        const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + gm * g.ldm + n);
-        uint4 mw[2] = {mp[0], mp[1]};
-        const bf16 *mb = reinterpret_cast<const bf16 *>(mw);
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (!(__bfloat162float(mb[i]) > 0.f)) v[i] = 0.f;
-      }
-      if (EPI == EPI_HEAD) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) dot = fmaf(v[i], g.w4[n + i], dot);
-      }
-      __align__(16) bf16 hb[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16_rn(v[i]);
-      if (g.C) {
-        uint4 *dst = reinterpret_cast<uint4 *>(g.C + gm * g.ldc + n);
-        dst[0] = reinterpret_cast<const uint4 *>(hb)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(hb)[1];
-      }
-      if (g.CT) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) g.CT[(int64_t)(n + i) * g.ldct + gm] = hb[i];
-      }
+      for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
     }
-    if (EPI == EPI_HEAD) g.out[gm] = dot + *g.b4;
   } else if (tid == 0) {
     atomicOr(g.err, kErrTimeout);
   }
