@@ -110,6 +110,18 @@ __device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32
       : "memory");
 }
 
+// 1-D bulk copy shared -> global (both addresses 16-byte aligned, bytes a
+// multiple of 16) in the calling thread's bulk group; tma_bulk_store_wait
+// returns once the thread's copies have completed.
+__device__ __forceinline__ void tma_bulk_store(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_bulk_store_wait() {
+  asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -1020,10 +1020,9 @@ struct surrogate {
   // deltas, loss gradients, split-K partials, the device step counter, the
   // fork streams of the weight-gradient products and the captured step
   int tB = 0;
-  DevBuf tT, tdl, tpart, tstep, loss_hist;
-  cudaStream_t cap = nullptr, f2 = nullptr, f3 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_j2 = nullptr, ev_j3 = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  DevBuf tT, tstat, tpart, tstep, loss_hist;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr, exec_k = nullptr;  // one step; kSurrGraphSteps steps
   DevBuf X, Y, Yh, lab_tmp;
   DevBuf iout, iwc, fb_idx, fb_cnt, fb_q, fb_lab, fb_f, ipred;
   DevBuf err, scal;
@@ -1083,11 +1082,6 @@ extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogat
   ck(s->err.ensure(64));
   ck(s->scal.ensure(64));
   ck(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
-  ck(cudaStreamCreateWithFlags(&s->f2, cudaStreamNonBlocking));
-  ck(cudaStreamCreateWithFlags(&s->f3, cudaStreamNonBlocking));
-  ck(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
-  ck(cudaEventCreateWithFlags(&s->ev_j2, cudaEventDisableTiming));
-  ck(cudaEventCreateWithFlags(&s->ev_j3, cudaEventDisableTiming));
   if (rc == FK_OK) rc = surr_init_params(s, 0);
   if (rc == FK_OK) rc = surr_sync_weights(s, 0);
   if (rc == FK_OK && cudaStreamSynchronize(0) != cudaSuccess) rc = fail(FK_ERR_CUDA, "surrogate_create: sync failed");
@@ -1102,111 +1096,92 @@ extern "C" int surrogate_create(const fk_chain_t *chain, uint64_t seed, surrogat
 extern "C" void surrogate_destroy(surrogate_t *s) {
   if (!s) return;
   if (s->exec) cudaGraphExecDestroy(s->exec);
-  for (cudaStream_t x : {s->cap, s->f2, s->f3})
-    if (x) cudaStreamDestroy(x);
-  for (cudaEvent_t x : {s->ev_fork, s->ev_j2, s->ev_j3})
-    if (x) cudaEventDestroy(x);
+  if (s->exec_k) cudaGraphExecDestroy(s->exec_k);
+  if (s->cap) cudaStreamDestroy(s->cap);
   DevBuf *bufs[] = {&s->p, &s->m, &s->v, &s->g, &s->w1b, &s->w2b, &s->w3b, &s->wc,
-                    &s->tT, &s->tdl, &s->tpart, &s->tstep, &s->loss_hist, &s->X, &s->Y, &s->Yh, &s->lab_tmp,
+                    &s->tT, &s->tstat, &s->tpart, &s->tstep, &s->loss_hist, &s->X, &s->Y, &s->Yh, &s->lab_tmp,
                     &s->iout, &s->iwc, &s->fb_idx, &s->fb_cnt, &s->fb_q, &s->fb_lab, &s->fb_f, &s->ipred,
                     &s->err, &s->scal};
   for (DevBuf *b : bufs) b->release();
   delete s;
 }
 
-// Split-K factor of the weight-gradient products for batch B: K = B / splits
-// at least 256 (four 64-wide chunks) where B allows, at most 32 splits.
+// Split factor of the weight-gradient products for batch B: six CTAs per
+// split (three products, two M tiles), at most 24 splits (144 CTAs) and at
+// least one 64-row chunk per split.
 static int surr_splits(int B) {
   const int kc = B / kBK;
-  int sp = kc / 4;
-  sp = sp > 32 ? 32 : (sp < 1 ? 1 : sp);
-  while (kc % sp) --sp;
-  return sp;
+  return kc < 24 ? kc : 24;
 }
+
+constexpr int kSurrGraphSteps = 8;
 
 static void surr_drop_graph(surrogate *s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
-  s->exec = nullptr;
+  if (s->exec_k) cudaGraphExecDestroy(s->exec_k);
+  s->exec = s->exec_k = nullptr;
 }
 
 // Scratch of the training step for batch B.
 static int surr_step_buffers(surrogate *s, int B) {
   if (s->tB == B) return FK_OK;
   surr_drop_graph(s);
-  CK(s->tT.ensure(2 * (size_t)B * (kSurrIn + 6 * kSurrW)));
-  CK(s->tdl.ensure(sizeof(float) * 2 * (size_t)B));
-  CK(s->tpart.ensure(sizeof(float) * (size_t)surr_splits(B) * (kSurrW * kSurrIn + 2 * kSurrW * kSurrW)));
-  CK(s->tstep.ensure(sizeof(int64_t)));
+  CK(s->tT.ensure(2 * (size_t)B * (kSurrIn + 5 * kSurrW)));
+  CK(s->tstat.ensure(sizeof(float) * (size_t)(B / kBM) * kTileStats));
+  CK(s->tpart.ensure(sizeof(float) * (size_t)surr_splits(B) * kSurrDwPart));
+  CK(s->tstep.ensure(32));  // int64 step, uint32 block counter, float schedule[3]
   s->tB = B;
   return FK_OK;
 }
 
-static GemmArgs gemm_args(surrogate *s, const bf16 *A, int64_t lda, const bf16 *Bm, int64_t ldb, int M, int N, int K) {
-  GemmArgs g{};
-  g.A = A;
-  g.lda = lda;
-  g.B = Bm;
-  g.ldb = ldb;
-  g.M = M;
-  g.N = N;
-  g.K = K;
-  g.err = s->err.as<int32_t>();
-  g.wait_limit = g_wait_limit;
-  return g;
-}
-
 // Enqueues one training step (surr_train.cu) on st: the tile kernel over the
 // batch (rows (step mod steps_per_epoch) B .. + B of X and Y), the three
-// weight-gradient products on st and the fork streams, the reduction into
-// the flat gradient g; with aa also Adam, the BF16 weights and the step
-// counter.  loss_hist[step] receives the batch loss (if not null).
+// weight-gradient products, then the reduction into the flat gradient g and
+// the loss into loss_hist[step] (if not null); with sch also Adam at that
+// schedule, the BF16 weights and the step counter.
 static int surr_step_enqueue(surrogate *s, const bf16 *X, const float *Y, int B, int64_t steps_per_epoch,
-                             const SurrAdamArgs *aa, float *loss_hist, cudaStream_t st) {
+                             const SurrSched *sch, float *loss_hist, cudaStream_t st) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const float *P = s->p.as<float>();
   bf16 *xT = s->tT.as<bf16>();
-  bf16 *h1T = xT + (int64_t)kSurrIn * B, *h2T = h1T + (int64_t)kSurrW * B, *h3T = h2T + (int64_t)kSurrW * B;
-  bf16 *d3T = h3T + (int64_t)kSurrW * B, *d2T = d3T + (int64_t)kSurrW * B, *d1T = d2T + (int64_t)kSurrW * B;
-  float *dout = s->tdl.as<float>(), *lrow = dout + B;
+  bf16 *h1T = xT + (int64_t)kSurrIn * B, *h2T = h1T + (int64_t)kSurrW * B;
+  bf16 *d3T = h2T + (int64_t)kSurrW * B, *d2T = d3T + (int64_t)kSurrW * B, *d1T = d2T + (int64_t)kSurrW * B;
   int64_t *step = s->tstep.as<int64_t>();
+  float *tstat = s->tstat.as<float>();
   SurrStepArgs a{X, Y, B, steps_per_epoch, step, s->wc.as<uint8_t>(), P + kOffB1, P + kOffB2, P + kOffB3,
-                 P + kOffW4, P + kOffB4, xT, h1T, h2T, h3T, d3T, d2T, d1T, dout, lrow, s->err.as<int32_t>(),
-                 g_wait_limit};
+                 P + kOffW4, P + kOffB4, xT, h1T, h2T, d3T, d2T, d1T, tstat, s->err.as<int32_t>(), g_wait_limit};
   CK(launch_surr_tile(a, sms, st));
-  // dW3 = d3^T h2, dW2 = d2^T h1, dW1 = d1^T x: split-K over the batch rows
   const int splits = surr_splits(B);
-  float *p3 = s->tpart.as<float>(), *p2 = p3 + (int64_t)splits * kSurrW * kSurrW;
-  float *p1 = p2 + (int64_t)splits * kSurrW * kSurrW;
-  CK(cudaEventRecord(s->ev_fork, st));
-  CK(cudaStreamWaitEvent(s->f2, s->ev_fork, 0));
-  CK(cudaStreamWaitEvent(s->f3, s->ev_fork, 0));
-  GemmArgs g = gemm_args(s, d3T, B, h2T, B, kSurrW, kSurrW, B / splits);
-  g.Cf = p3;
-  g.ldcf = kSurrW;
-  g.zstride = (int64_t)kSurrW * kSurrW;
-  CK(launch_gemm(256, g, splits, st));
-  g = gemm_args(s, d2T, B, h1T, B, kSurrW, kSurrW, B / splits);
-  g.Cf = p2;
-  g.ldcf = kSurrW;
-  g.zstride = (int64_t)kSurrW * kSurrW;
-  CK(launch_gemm(256, g, splits, s->f2));
-  g = gemm_args(s, d1T, B, xT, B, kSurrW, kSurrIn, B / splits);
-  g.Cf = p1;
-  g.ldcf = kSurrIn;
-  g.zstride = (int64_t)kSurrW * kSurrIn;
-  CK(launch_gemm(64, g, splits, s->f3));
-  CK(cudaEventRecord(s->ev_j2, s->f2));
-  CK(cudaEventRecord(s->ev_j3, s->f3));
-  CK(cudaStreamWaitEvent(st, s->ev_j2, 0));
-  CK(cudaStreamWaitEvent(st, s->ev_j3, 0));
-  SurrReduceArgs r{p1, p2, p3, splits, d1T, d2T, d3T, h3T, dout, lrow, B, s->g.as<float>(), loss_hist, step};
-  CK(launch_surr_reduce(r, st));
-  if (aa) {
-    CK(launch_surr_adam(*aa, st));
-    CK(launch_surr_advance(step, st));
-  }
+  float *p1 = s->tpart.as<float>(), *p2 = p1 + (int64_t)splits * kSurrW * kSurrIn;
+  float *p3 = p2 + (int64_t)splits * kSurrW * kSurrW;
+  float *sched = reinterpret_cast<float *>(s->tstep.as<char>() + 16);
+  SurrDwArgs d{xT, h1T, h2T, d1T, d2T, d3T, B, splits, p1, p2, p3, step, sch ? *sch : SurrSched{},
+               sch ? sched : nullptr, s->err.as<int32_t>(), g_wait_limit};
+  CK(launch_surr_dw(d, st));
+  SurrAdamArgs u{};
+  u.p = s->p.as<float>();
+  u.m = s->m.as<float>();
+  u.v = s->v.as<float>();
+  u.G = s->g.as<float>();
+  u.p1 = p1;
+  u.p2 = p2;
+  u.p3 = p3;
+  u.splits = splits;
+  u.tstat = tstat;
+  u.ntiles = B / kBM;
+  u.B = B;
+  u.loss_hist = loss_hist;
+  u.step = step;
+  u.done = reinterpret_cast<uint32_t *>(s->tstep.as<char>() + 8);
+  u.update = sch ? 1 : 0;
+  u.sched = sched;
+  u.w1 = s->w1b.as<bf16>();
+  u.w2 = s->w2b.as<bf16>();
+  u.w3 = s->w3b.as<bf16>();
+  u.wc = s->wc.as<uint8_t>();
+  CK(launch_surr_adam(u, st));
   return FK_OK;
 }
 
@@ -1289,7 +1264,7 @@ extern "C" int surrogate_gradients(surrogate_t *s, const float *q, int64_t n, co
   int rc = surr_step_buffers(s, (int)n);
   if (rc != FK_OK) return rc;
   if ((rc = surr_features(s, q, n, n, s->X, st)) != FK_OK) return rc;
-  CK(cudaMemsetAsync(s->tstep.p, 0, sizeof(int64_t), st));
+  CK(cudaMemsetAsync(s->tstep.p, 0, 16, st));  // step and block counter
   float *dl = s->scal.as<float>();  // loss_hist[0]
   if ((rc = surr_step_enqueue(s, s->X.as<bf16>(), target, (int)n, 1, nullptr, dl, st)) != FK_OK) return rc;
   if ((rc = surr_check_err(s, st, "surrogate_gradients")) != FK_OK) return rc;
@@ -1364,33 +1339,41 @@ extern "C" int surrogate_train(surrogate_t *s, fastron_model_t *model, const flo
   const int64_t steps_per_epoch = n_tr / B;
   const int64_t total = steps_per_epoch * prm->epochs;
   CK(s->loss_hist.ensure(sizeof(float) * (size_t)(total > 0 ? total : 1)));
-  CK(cudaMemsetAsync(s->tstep.p, 0, sizeof(int64_t), st));
+  CK(cudaMemsetAsync(s->tstep.p, 0, 16, st));  // step and block counter
   if (total > 0) {
-    // one step captured into a graph (a library stream, the fork streams
-    // joined back), replayed `total` times on st: the batch, learning rate
-    // and Adam step come from the device step counter
-    SurrAdamArgs aa{s->p.as<float>(), s->m.as<float>(), s->v.as<float>(), s->g.as<float>(),
-                    s->tstep.as<int64_t>(), total, steps_per_epoch, prm->epochs, s->t, prm->lr,
-                    prm->schedule == FK_LR_COSINE ? 1 : 0, s->w1b.as<bf16>(), s->w2b.as<bf16>(), s->w3b.as<bf16>(),
-                    s->wc.as<uint8_t>()};
+    // one step captured into a graph (on a library stream), replayed `total`
+    // times on st: the batch, learning rate and Adam step come from the
+    // device step counter
+    SurrSched sch{total, steps_per_epoch, prm->epochs, s->t, prm->lr, prm->schedule == FK_LR_COSINE ? 1 : 0};
     surr_drop_graph(s);
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    rc = surr_step_enqueue(s, s->X.as<bf16>(), s->Y.as<float>(), B, steps_per_epoch, &aa, s->loss_hist.as<float>(),
-                           s->cap);
-    cudaError_t ec = cudaStreamEndCapture(s->cap, &graph);
-    if (rc != FK_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
+    // graphs of one and of kSurrGraphSteps steps (within a graph each kernel
+    // may start while its predecessor drains)
+    for (int g = 0; g < 2; ++g) {
+      const int nsteps = g == 0 ? 1 : kSurrGraphSteps;
+      if (g == 1 && total < nsteps) break;
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+      for (int k = 0; k < nsteps && rc == FK_OK; ++k)
+        rc = surr_step_enqueue(s, s->X.as<bf16>(), s->Y.as<float>(), B, steps_per_epoch, &sch,
+                               s->loss_hist.as<float>(), s->cap);
+      cudaError_t ec = cudaStreamEndCapture(s->cap, &graph);
+      if (rc != FK_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (ec != cudaSuccess) return fail(FK_ERR_CUDA, "surrogate_train: capture failed: %s", cudaGetErrorString(ec));
+      cudaGraphExec_t *ex = g == 0 ? &s->exec : &s->exec_k;
+      ec = cudaGraphInstantiate(ex, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ec != cudaSuccess) {
+        *ex = nullptr;
+        return fail(FK_ERR_CUDA, "surrogate_train: instantiate failed: %s", cudaGetErrorString(ec));
+      }
     }
-    if (ec != cudaSuccess) return fail(FK_ERR_CUDA, "surrogate_train: capture failed: %s", cudaGetErrorString(ec));
-    ec = cudaGraphInstantiate(&s->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ec != cudaSuccess) {
-      s->exec = nullptr;
-      return fail(FK_ERR_CUDA, "surrogate_train: instantiate failed: %s", cudaGetErrorString(ec));
-    }
-    for (int64_t k = 0; k < total; ++k) CK(cudaGraphLaunch(s->exec, st));
+    int64_t k = 0;
+    if (s->exec_k)
+      for (; k + kSurrGraphSteps <= total; k += kSurrGraphSteps) CK(cudaGraphLaunch(s->exec_k, st));
+    for (; k < total; ++k) CK(cudaGraphLaunch(s->exec, st));
     s->t += total;
   }
   if ((rc = surr_check_err(s, st, "surrogate_train")) != FK_OK) return rc;

@@ -74,16 +74,17 @@ __device__ __forceinline__ bool tr_fill(TrRing &r, uint32_t upto, uint32_t limit
   return true;
 }
 
-// The MMAs of one layer: A = nk K chunks of [128][64] at a_base + c 16 KB
-// (shared memory) times the next nk weight chunks of the ring, into tmem
-// (cols 0..255).  Returns once the last commit has landed, or false in every
-// thread if a wait gave up (*abort is then set).
-__device__ __forceinline__ bool tr_layer(TrRing &r, uint32_t a_base, int nk, uint32_t tmem, uint32_t limit,
+// The MMAs of one layer, in two halves so that the CTA can work between
+// them: tr_issue (every thread; after the barrier thread 0 issues) multiplies
+// A = nk K chunks of [128][64] at a_base + c 16 KB (shared memory) by the next
+// nk weight chunks of the ring into tmem (cols 0..255); tr_wait returns once
+// the last commit has landed, or false in every thread if a wait gave up
+// (*abort is then set).  Between the two the A tiles may be read, not written.
+__device__ __forceinline__ void tr_issue(TrRing &r, uint32_t a_base, int nk, uint32_t tmem, uint32_t limit,
                                          int *abort) {
-  const int tid = threadIdx.x;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A written by the generic proxy
   __syncthreads();
-  if (tid == 0 && !*abort) {
+  if (threadIdx.x == 0 && !*abort) {
     tc_fence_after();
     for (int c = 0; c < nk; ++c) {
       const uint32_t gc = r.next_mma + c, s = gc % kTrSlots;
@@ -104,17 +105,91 @@ __device__ __forceinline__ bool tr_layer(TrRing &r, uint32_t a_base, int nk, uin
       }
     }
   }
-  __syncthreads();
+}
+__device__ __forceinline__ bool tr_wait(TrRing &r, int nk, uint32_t limit, int *abort) {
+  __syncthreads();  // thread 0's issue, and *abort, before anyone reads them
   if (*abort) return false;
   r.next_mma += nk;
   const uint32_t gl = r.next_mma - 1;
   const bool got = mbar_wait_bounded(&r.done[gl % kTrSlots], (gl / kTrSlots) & 1, limit);
   if (!__syncthreads_and(got)) {
-    if (tid == 0) *abort = 1;
+    if (threadIdx.x == 0) *abort = 1;
     return false;
   }
   tc_fence_after();
   return true;
+}
+
+// Programmatic dependent launch: the three kernels of a step (and the next
+// step's first) are launched so that a kernel's CTAs may start while its
+// predecessor drains.  Each kernel sets up its shared and tensor memory, then
+// waits for the predecessor's completion (and memory) before it touches
+// global memory, then lets its own dependents launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Four 8x8 BF16 core matrices, transposed: lanes 8i..8i+7 address the eight
+// 16-byte lines of matrix i; lane t receives, of each matrix, lines
+// 2 (t mod 4) and 2 (t mod 4) + 1 at element t / 4 (low and high half).
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// A tile of 128 rows x U units held in shared memory (the A-operand layout
+// of tr_put8) written transposed into the chunk-blocked tensor T (rows
+// tile 128 ..), and/or its column sums (weighted by w[row] if w is given)
+// into sums[u].  A core matrix of the tile (8 rows x 8 units) transposed is
+// a core matrix of T (8 units x 8 rows): one ldmatrix reads four row groups
+// of one unit group, each lane then holds two rows of one unit per matrix
+// and the warp's store of one matrix is 128 contiguous bytes.  Warps 1-7
+// share the unit groups (warp 0 holds the thread that issues the MMAs and
+// keeps the weight ring full); the sums add, per unit, the tile's rows in a
+// fixed order.
+template <int U, bool STORE, bool SUM>
+__device__ __forceinline__ void tr_copy_t(const uint8_t *H, bf16 *T, int tile, float *sums, const float *w) {
+  constexpr int kCopyWarps = kTrThreads / 32 - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) return;
+  const uint32_t hs = smem_u32(H);
+#pragma unroll 1
+  for (int ug = warp - 1; ug < U / 8; ug += kCopyWarps) {
+    float acc = 0.f;
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq) {  // a quarter of the row groups
+      uint32_t v[4];
+      ldsm_x4_trans(hs + (uint32_t)(ug >> 3) * kTrChunk + (uint32_t)(((rq * 4 + (lane >> 3)) * 8 + (ug & 7)) * 128) +
+                        (uint32_t)(lane & 7) * 16,
+                    v);
+      if (STORE) {
+        // row groups rq 4 + i of the tile: chunk 2 tile + rq / 2, core row (rq mod 2) 4 + i
+        uint8_t *dst = reinterpret_cast<uint8_t *>(T) + ((size_t)tile * 2 + (rq >> 1)) * U * 128 +
+                       (size_t)(ug * 8 + (rq & 1) * 4) * 128 + lane * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint32_t *>(dst + i * 128) = v[i];
+      }
+      if (SUM) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float lo = __uint_as_float(v[i] << 16), hi = __uint_as_float(v[i] & 0xffff0000u);
+          if (w) {
+            const int r0 = (rq * 4 + i) * 8 + 2 * (lane & 3);
+            acc = fmaf(lo, w[r0], acc);
+            acc = fmaf(hi, w[r0 + 1], acc);
+          } else {
+            acc += lo;
+            acc += hi;
+          }
+        }
+      }
+    }
+    if (SUM) {  // the unit group's 128 rows: add the four lanes of each unit
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if ((lane & 3) == 0) sums[ug * 8 + (lane >> 2)] = acc;
+    }
+  }
 }
 
 // 16-byte store of 8 BF16 values into a hidden tile at (row, k), k % 8 == 0
@@ -152,6 +227,18 @@ __device__ __forceinline__ void surr_wc_put(uint8_t *wc, int layer, int o, int i
   *reinterpret_cast<bf16 *>(wc + surr_wc_off(firstT + o / kBK, i, o)) = v;
 }
 
+// Entries (o, i .. i + 3) of one layer, i % 4 == 0: the four inputs are
+// adjacent in the forward block (one 8-byte store), four rows apart in the
+// transposed one.
+__device__ __forceinline__ void surr_wc_put4(uint8_t *wc, int layer, int o, int i, const bf16 (&v)[4]) {
+  const int first = layer == 0 ? 0 : (layer == 1 ? 1 : 5);
+  *reinterpret_cast<uint2 *>(wc + surr_wc_off(first + i / kBK, o, i)) = *reinterpret_cast<const uint2 *>(v);
+  if (layer == 0) return;
+  const int firstT = layer == 1 ? 13 : 9;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) *reinterpret_cast<bf16 *>(wc + surr_wc_off(firstT + o / kBK, i + q, o)) = v[q];
+}
+
 // The weight blocks from the BF16 weights ([out][in] row-major).
 __global__ void surr_wc_kernel(const bf16 *__restrict__ w1, const bf16 *__restrict__ w2, const bf16 *__restrict__ w3,
                                uint8_t *__restrict__ wc) {
@@ -171,7 +258,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ float sw4[kSurrW];  // b1, b2, b3 are read as vectors through L1 (shared memory is full)
-  __shared__ float sout[2][kBM];               // the two halves of each row's output dot product
+  __shared__ float sout[2][kBM];  // the two halves of each row's output dot product; then dout, squared error
   uint8_t *HA = sm, *HB = sm + kTrH;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int ntiles = a.B / kBM;
@@ -189,6 +276,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  pdl_wait();
+  pdl_trigger();
   for (int i = tid; i < kSurrW; i += kTrThreads) sw4[i] = a.w4[i];
   tc_fence_before();
   __syncthreads();
@@ -200,41 +289,34 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
   const int lane = tid & 31, quad = warp & 3, half = warp >> 2;
   const int row = quad * 32 + lane, c0 = half * (kSurrW / 2);
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-  const int64_t B = a.B;
-  const int64_t row0 = (*a.step % a.steps_per_epoch) * B;   // the batch's first training row
+  const int64_t row0 = (*a.step % a.steps_per_epoch) * a.B;  // the batch's first training row
   const float b4 = *a.b4;
   const float invB2 = 2.f / (float)a.B;
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t rb = (int64_t)tile * kBM + row;  // this thread's row within the batch
-    // features of the tile into HB (A layout, one K chunk), each thread half
-    // of its row; and transposed to global
+    float *ts = a.tstat + (size_t)tile * kTileStats;
+    // features of the tile into HB (A layout, one K chunk), each thread half of its row
     {
       const uint4 *src = reinterpret_cast<const uint4 *>(a.X + (row0 + rb) * kSurrIn);
 #pragma unroll
-      for (int i = half * 4; i < half * 4 + 4; ++i) {
-        uint4 u = src[i];
-        *reinterpret_cast<uint4 *>(HB + tr_cm(row, 8 * i)) = u;
-        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) a.xT[(int64_t)(8 * i + j) * B + rb] = e[j];
-      }
+      for (int i = half * 4; i < half * 4 + 4; ++i) *reinterpret_cast<uint4 *>(HB + tr_cm(row, 8 * i)) = src[i];
     }
 
     uint32_t m1[4], m2[4], m3[4];  // ReLU masks of h1, h2, h3 on this thread's 128 units, one bit each
-    // ---- layer 1: h1 = relu(x W1^T + b1) -> HA, h1T
-    if (!tr_layer(r, smem_u32(HB), 1, tmem, a.wait_limit, &abort_flag)) break;
-    // a hidden layer's epilogue: each 32-column chunk's biases are loaded as
-    // vectors before its TMEM wait, and the next chunk's TMEM load is in flight
-    // while this one is converted and stored
-    auto hidden = [&](const float *__restrict__ bias, uint8_t *H, bf16 *__restrict__ hT, uint32_t (&m)[4]) {
+    // a hidden layer's epilogue: the biases of the first 32-column chunk (xb)
+    // are loaded before the MMA wait, each next chunk's while this one is
+    // converted, and the next chunk's TMEM load is in flight meanwhile
+    auto hidden = [&](const float *__restrict__ bias, uint8_t *H, uint32_t (&m)[4], float (&xb)[32]) {
       uint32_t v[32];
       tc_ld32_issue(trow + c0, v);
 #pragma unroll 1
       for (int j = 0; j < 4; ++j) {
         const int j0 = c0 + 32 * j;
         float x[32];
-        tr_bias32(bias + j0, x);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = xb[i];
+        if (j < 3) tr_bias32(bias + j0 + 32, xb);
         tc_wait_ld32(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
@@ -245,7 +327,6 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
         for (int i = 0; i < 32; ++i) {
           hb[i] = __float2bfloat16_rn(fmaxf(x[i], 0.f));
           bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
-          hT[(int64_t)(j0 + i) * B + rb] = hb[i];
         }
         m[j] = bits;
 #pragma unroll
@@ -253,15 +334,28 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
       }
       tc_fence_before();
     };
-    hidden(a.b1, HA, a.h1T, m1);
-    // ---- layer 2: h2 = relu(h1 W2^T + b2) -> HB, h2T
-    if (!tr_layer(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag)) break;
-    hidden(a.b2, HB, a.h2T, m2);
+    float xb[32];
+    // ---- layer 1: h1 = relu(x W1^T + b1) -> HA; x^T out while the MMAs run
+    tr_issue(r, smem_u32(HB), 1, tmem, a.wait_limit, &abort_flag);
+    tr_copy_t<kSurrIn, true, false>(HB, a.xT, tile, nullptr, nullptr);
+    tr_bias32(a.b1 + c0, xb);
+    if (!tr_wait(r, 1, a.wait_limit, &abort_flag)) break;
+    hidden(a.b1, HA, m1, xb);
+    // ---- layer 2: h2 = relu(h1 W2^T + b2) -> HB; h1^T out
+    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag);
+    tr_copy_t<kSurrW, true, false>(HA, a.h1T, tile, nullptr, nullptr);
+    tr_bias32(a.b2 + c0, xb);
+    if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
+    hidden(a.b2, HB, m2, xb);
     // ---- layer 3 and the output unit: out = relu(z3) . w4 + b4 (FP32),
-    // dout = 2 (out - y) / B, d3 = bf16(dout w4 [z3 > 0]) -> HA, d3T; h3T
-    if (!tr_layer(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag)) break;
-    float out = 0.f;
+    // dout = 2 (out - y) / B, d3 = bf16(dout w4 [z3 > 0]) -> HA, bf16(h3) -> HB;
+    // h2^T out
+    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag);
+    tr_copy_t<kSurrW, true, false>(HB, a.h2T, tile, nullptr, nullptr);
+    tr_bias32(a.b3 + c0, xb);
     const float y = a.Y[row0 + rb];
+    if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
+    float out = 0.f;
     {
       uint32_t v[32];
       tc_ld32_issue(trow + c0, v);
@@ -269,48 +363,51 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
       for (int j = 0; j < 4; ++j) {
         const int j0 = c0 + 32 * j;
         float x[32];
-        tr_bias32(a.b3 + j0, x);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = xb[i];
+        if (j < 3) tr_bias32(a.b3 + j0 + 32, xb);
         tc_wait_ld32(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
         if (j < 3) tc_ld32_issue(trow + j0 + 32, v);
+        __align__(16) bf16 hb[32];
         uint32_t bits = 0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float h = fmaxf(x[i], 0.f);
           out = fmaf(h, sw4[j0 + i], out);
-          const bf16 hb = __float2bfloat16_rn(h);
-          bits |= (uint32_t)(__bfloat162float(hb) > 0.f) << i;
-          a.h3T[(int64_t)(j0 + i) * B + rb] = hb;
+          hb[i] = __float2bfloat16_rn(h);
+          bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
         }
         m3[j] = bits;
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) tr_put8(HB, row, j0 + i, hb + i);
       }
     }
     tc_fence_before();
-    // the row's two halves of the dot product, added in a fixed order
+    // the row's two halves of the dot product, added in a fixed order; then
+    // the same shared words hold the row's dout and squared error
     sout[half][row] = out;
     __syncthreads();
     out = (sout[0][row] + sout[1][row]) + b4;
     const float e = out - y;
     const float dout = e * invB2;
+    __syncthreads();
     if (half == 0) {
-      a.dout[rb] = dout;
-      a.lrow[rb] = e * e;
+      sout[0][row] = dout;
+      sout[1][row] = e * e;
     }
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       const int j0 = c0 + 32 * j;
       __align__(16) bf16 db[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        db[i] = __float2bfloat16_rn(((m3[j] >> i) & 1u) ? dout * sw4[j0 + i] : 0.f);
-        a.d3T[(int64_t)(j0 + i) * B + rb] = db[i];
-      }
+      for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m3[j] >> i) & 1u) ? dout * sw4[j0 + i] : 0.f);
 #pragma unroll
       for (int i = 0; i < 32; i += 8) tr_put8(HA, row, j0 + i, db + i);
     }
     // ---- back through layer 3 and 2: d = bf16((d W) [h > 0])
-    auto delta = [&](uint8_t *H, bf16 *__restrict__ dT, const uint32_t (&m)[4]) {
+    auto delta = [&](uint8_t *H, const uint32_t (&m)[4]) {
       uint32_t v[32];
       tc_ld32_issue(trow + c0, v);
 #pragma unroll 1
@@ -323,21 +420,43 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
         if (j < 3) tc_ld32_issue(trow + j0 + 32, v);
         __align__(16) bf16 db[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          db[i] = __float2bfloat16_rn(((m[j] >> i) & 1u) ? x[i] : 0.f);
-          dT[(int64_t)(j0 + i) * B + rb] = db[i];
-        }
-        if (H) {
+        for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m[j] >> i) & 1u) ? x[i] : 0.f);
 #pragma unroll
-          for (int i = 0; i < 32; i += 8) tr_put8(H, row, j0 + i, db + i);
-        }
+        for (int i = 0; i < 32; i += 8) tr_put8(H, row, j0 + i, db + i);
       }
       tc_fence_before();
     };
-    if (!tr_layer(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag)) break;
-    delta(HB, a.d2T, m2);
-    if (!tr_layer(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag)) break;
-    delta(nullptr, a.d1T, m1);
+    // d2 = d3 W3: d3^T out with the b3 sums, the w4 sums from h3 and dout,
+    // the tile's dout and squared-error sums
+    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag);
+    tr_copy_t<kSurrW, true, true>(HA, a.d3T, tile, ts + kTileStatB3, nullptr);
+    tr_copy_t<kSurrW, false, true>(HB, nullptr, tile, ts + kTileStatW4, sout[0]);
+    if (warp == kTrThreads / 32 - 1) {
+      float sd = 0.f, se = 0.f;
+#pragma unroll
+      for (int k = 0; k < kBM / 32; ++k) {
+        sd += sout[0][lane + 32 * k];
+        se += sout[1][lane + 32 * k];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+      }
+      if (lane == 0) {
+        ts[kTileStatB4] = sd;
+        ts[kTileStatLoss] = se;
+      }
+    }
+    if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
+    delta(HB, m2);
+    // d1 = d2 W2: d2^T out with the b2 sums
+    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag);
+    tr_copy_t<kSurrW, true, true>(HB, a.d2T, tile, ts + kTileStatB2, nullptr);
+    if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
+    delta(HA, m1);
+    __syncthreads();
+    tr_copy_t<kSurrW, true, true>(HA, a.d1T, tile, ts + kTileStatB1, nullptr);
   }
   __syncthreads();
   if (abort_flag && tid == 0) {
@@ -354,166 +473,329 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
   if (warp == 0) tmem_dealloc(tmem, kSurrW);
 }
 
-// ------------------------------------------------------------ reduction --
-// The step's gradient G (flat parameter order W1, b1, W2, b2, W3, b3, w4, b4)
-// and loss: weight entries as the sum of their split-K partials in split
-// order (one thread each); biases, w4 and b4 as sums over the batch rows of
-// dT[u][.], h3T[u][.] dout[.] and dout[.] (one block each, threads over the
-// rows, a fixed-order reduction); the loss (mean of lrow) into loss_hist[step].
-constexpr int64_t kTrOffW1 = 0, kTrOffB1 = kTrOffW1 + (int64_t)kSurrW * kSurrIn, kTrOffW2 = kTrOffB1 + kSurrW,
-                  kTrOffB2 = kTrOffW2 + (int64_t)kSurrW * kSurrW, kTrOffW3 = kTrOffB2 + kSurrW,
-                  kTrOffB3 = kTrOffW3 + (int64_t)kSurrW * kSurrW, kTrOffW4 = kTrOffB3 + kSurrW,
-                  kTrOffB4 = kTrOffW4 + kSurrW, kTrParams = kTrOffB4 + 1;
-constexpr int kRedThreads = 256;
-constexpr int64_t kRedW = (int64_t)kSurrW * kSurrIn + 2 * (int64_t)kSurrW * kSurrW;  // weight entries
-constexpr int kRedWBlocks = (int)((kRedW + kRedThreads - 1) / kRedThreads);
-constexpr int kRedRows = 4 * kSurrW + 2;  // b1, b2, b3, w4 rows; b4; loss
-constexpr int kRedRowBlocks = kRedRows;
+// --------------------------------------------------- weight gradients --
+// dW3 = d3^T h2, dW2 = d2^T h1, dW1 = d1^T x: CTA (product, 128-row M tile,
+// split z) multiplies the split's 64-row chunks of the chunk-blocked
+// operands (A: 128 units of the delta, 16 KB; B: all N units of the
+// activation, N x 128 bytes; one bulk copy each) through a four-stage ring:
+// lane 0 of warp 0 copies, lane 0 of warp 1 issues the MMAs (M 128, N 256 or
+// 64) and commits each stage back; the four warps then write the FP32
+// accumulator as the split's row-major partial (SurrDwArgs).
+constexpr int kDwThreads = 128;
+constexpr int kDwStages = 4;
+constexpr uint32_t kDwA = kBM * kBK * 2;         // 16 KB
+constexpr uint32_t kDwB = kSurrW * kBK * 2;      // 32 KB (N = 256)
+constexpr uint32_t kDwStage = kDwA + kDwB;
+constexpr uint32_t kDwSmem = kDwStages * kDwStage;  // 192 KB
 
-__global__ void __launch_bounds__(kRedThreads) surr_reduce_kernel(const SurrReduceArgs a) {
-  if (blockIdx.x < kRedWBlocks) {
-    const int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
-    if (i >= kRedW) return;
-    const float *src;
-    int64_t j, n, dst;
-    if (i < (int64_t)kSurrW * kSurrIn) {
-      src = a.p1, j = i, n = (int64_t)kSurrW * kSurrIn, dst = kTrOffW1 + i;
-    } else if (i < (int64_t)kSurrW * kSurrIn + (int64_t)kSurrW * kSurrW) {
-      j = i - (int64_t)kSurrW * kSurrIn, src = a.p2, n = (int64_t)kSurrW * kSurrW, dst = kTrOffW2 + j;
-    } else {
-      j = i - (int64_t)kSurrW * kSurrIn - (int64_t)kSurrW * kSurrW, src = a.p3, n = (int64_t)kSurrW * kSurrW,
-      dst = kTrOffW3 + j;
-    }
-    float s = 0.f;
-    for (int z = 0; z < a.splits; ++z) s += src[(int64_t)z * n + j];
-    a.G[dst] = s;
-    return;
+__global__ void __launch_bounds__(kDwThreads, 1) surr_dw_kernel(const SurrDwArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t full[kDwStages], empty[kDwStages], accum;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, loaded, issued;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = a.splits;
+  const int prod = blockIdx.x / (2 * S), mt = (blockIdx.x % (2 * S)) / S, z = blockIdx.x % S;
+  const uint8_t *A, *Bm;
+  float *P;
+  int N;
+  if (prod == 0) {
+    A = reinterpret_cast<const uint8_t *>(a.d3T), Bm = reinterpret_cast<const uint8_t *>(a.h2T), P = a.p3, N = kSurrW;
+  } else if (prod == 1) {
+    A = reinterpret_cast<const uint8_t *>(a.d2T), Bm = reinterpret_cast<const uint8_t *>(a.h1T), P = a.p2, N = kSurrW;
+  } else {
+    A = reinterpret_cast<const uint8_t *>(a.d1T), Bm = reinterpret_cast<const uint8_t *>(a.xT), P = a.p1, N = kSurrIn;
   }
-  // one block per row sum: lanes over the batch rows, a fixed-order reduction
-  const int row = blockIdx.x - kRedWBlocks;
-  if (row >= kRedRows) return;
-  const int t = threadIdx.x;
-  float s = 0.f;
-  if (row < 3 * kSurrW) {  // b1, b2, b3: sum over the batch of the layer's delta
-    const int layer = row / kSurrW, u = row % kSurrW;
-    const bf16 *dT = layer == 0 ? a.d1T : (layer == 1 ? a.d2T : a.d3T);
-    const uint4 *src = reinterpret_cast<const uint4 *>(dT + (int64_t)u * a.B);
-    for (int c = t; c < a.B / 8; c += kRedThreads) {
-      uint4 v = src[c];
-      const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s += __bfloat162float(e[k]);
-    }
-  } else if (row < 4 * kSurrW) {  // w4: sum over the batch of h3 dout
-    const int u = row - 3 * kSurrW;
-    const uint4 *src = reinterpret_cast<const uint4 *>(a.h3T + (int64_t)u * a.B);
-    for (int c = t; c < a.B / 8; c += kRedThreads) {
-      uint4 v = src[c];
-      const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s = fmaf(__bfloat162float(e[k]), a.dout[8 * c + k], s);
-    }
-  } else {  // b4, loss
-    const float *src = row == 4 * kSurrW ? a.dout : a.lrow;
-    for (int c = t; c < a.B; c += kRedThreads) s += src[c];
+  const int kc = a.B / kBK;
+  const int cbeg = (int)((int64_t)z * kc / S), nk = (int)((int64_t)(z + 1) * kc / S) - cbeg;
+  const uint32_t bbytes = (uint32_t)N * kBK * 2;
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, kSurrW);
+    tmem_relinquish();
   }
-  __shared__ float part[kRedThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((t & 31) == 0) part[t >> 5] = s;
+  if (tid == 0) {
+    for (int i = 0; i < kDwStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&accum, 1);
+    abort_flag = 0;
+    loaded = 0;
+    issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_wait();
+  pdl_trigger();
+  tc_fence_before();
   __syncthreads();
-  if (t != 0) return;
-  s = 0.f;
-  for (int w = 0; w < kRedThreads / 32; ++w) s += part[w];
-  if (row < 3 * kSurrW) {
-    const int layer = row / kSurrW, u = row % kSurrW;
-    a.G[(layer == 0 ? kTrOffB1 : (layer == 1 ? kTrOffB2 : kTrOffB3)) + u] = s;
-  } else if (row < 4 * kSurrW) {
-    a.G[kTrOffW4 + row - 3 * kSurrW] = s;
-  } else if (row == 4 * kSurrW) {
-    a.G[kTrOffB4] = s;
-  } else if (a.loss_hist) {
-    a.loss_hist[*a.step] = s / (float)a.B;
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {  // producer
+    for (int c = 0; c < nk && !*(volatile int *)&abort_flag; ++c) {
+      const int st = c % kDwStages;
+      if (c >= kDwStages && !mbar_wait_bounded(&empty[st], ((c - kDwStages) / kDwStages) & 1, a.wait_limit)) {
+        abort_flag = 1;
+        break;
+      }
+      uint8_t *sa = sm + st * kDwStage;
+      mbar_arrive_expect_tx(&full[st], kDwA + bbytes);
+      tma_bulk_load(sa, A + (size_t)(cbeg + c) * (kSurrW * 128) + (size_t)mt * kDwA, kDwA, &full[st]);
+      tma_bulk_load(sa + kDwA, Bm + (size_t)(cbeg + c) * bbytes, bbytes, &full[st]);
+      loaded = c + 1;
+    }
+  } else if (tid == 64 && blockIdx.x == 0 && a.sched) {
+    // the step's learning rate and Adam's bias corrections (FP64 cosine: its
+    // latency is spent here, beside the MMAs, not in every update block)
+    const int64_t st = *a.step;
+    float lr;
+    if (a.sch.cosine) {
+      lr = (float)(0.5 * (double)a.sch.lr * (1.0 + cos(M_PI * (double)st / (double)a.sch.total)));
+    } else {
+      const int64_t ep = st / a.sch.steps_per_epoch;
+      lr = ep < (2 * a.sch.epochs + 2) / 3 ? a.sch.lr : a.sch.lr / 3.f;
+    }
+    const int64_t t = a.sch.t0 + st + 1;
+    a.sched[0] = lr;
+    a.sched[1] = 1.f - powf(0.9f, (float)t);
+    a.sched[2] = 1.f - powf(0.999f, (float)t);
+  } else if (tid == 32) {  // MMA issuer
+    const uint32_t idesc = idesc_bf16_f32(kBM, N);
+    for (int c = 0; c < nk; ++c) {
+      const int st = c % kDwStages;
+      if (!mbar_wait_bounded(&full[st], (c / kDwStages) & 1, a.wait_limit)) {
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(sm + st * kDwStage), sb = sa + kDwA;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        tc_mma(tmem, smem_desc(sa + kk * 256, 128, 1024), smem_desc(sb + kk * 256, 128, 1024), idesc,
+               (c > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(&empty[st]);
+      issued = c + 1;
+    }
+    if (issued == nk) tc_commit(&accum);
   }
+  __syncthreads();
+  bool ok = !abort_flag && issued == nk;
+  if (ok) ok = __syncthreads_and(mbar_wait_bounded(&accum, 0, a.wait_limit));
+  else __syncthreads();
+  if (ok) {
+    // the accumulator through the (now idle) ring memory, rows padded by
+    // 16 bytes so that the lanes' rows fall in different banks, then one bulk
+    // store per row into the split's row-major partial
+    tc_fence_after();
+    const int rl = warp * 32 + lane;  // this thread's accumulator row (TMEM lane)
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t pitch = (uint32_t)N * 4 + 16;
+    float *srow = reinterpret_cast<float *>(sm + (size_t)rl * pitch);
+    uint32_t v[32];
+    tc_ld32_issue(trow, v);
+#pragma unroll 1
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      tc_wait_ld32(v);
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
+      if (j0 + 32 < N) tc_ld32_issue(trow + j0 + 32, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4 *>(srow + j0 + 4 * q) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    tma_bulk_store(P + (size_t)z * N * kSurrW + (size_t)(mt * kBM + rl) * N, srow, (uint32_t)N * 4);
+    tma_bulk_store_wait();
+  } else if (tid == 0) {
+    // let the copies and MMAs already issued land (bounded) before the
+    // shared and tensor memory are released, and report
+    for (int c = issued; c < loaded; ++c) mbar_wait_bounded(&full[c % kDwStages], (c / kDwStages) & 1, kGemmDrain);
+    if (issued > 0)
+      mbar_wait_bounded(&empty[(issued - 1) % kDwStages], ((issued - 1) / kDwStages) & 1, kGemmDrain);
+    atomicOr(a.err, kErrTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kSurrW);
 }
 
 // -------------------------------------------------------------- update ---
-// Adam (beta1 0.9, beta2 0.999, eps 1e-8) with the step's learning rate and
-// bias correction from the device counter, then the BF16 copies of W1, W2,
-// W3 ([out][in]) and of the transposes of W2 and W3 ([in][out]).
-__global__ void __launch_bounds__(256) surr_adam_kernel(const SurrAdamArgs a) {
-  // the step's learning rate and bias corrections, once per block (the
-  // cosine in FP64 would occupy the narrow FP64 pipe in every thread)
+// Flat parameter order: W1, b1, W2, b2, W3, b3, w4, b4.
+constexpr int64_t kTrOffW1 = 0, kTrOffB1 = kTrOffW1 + (int64_t)kSurrW * kSurrIn, kTrOffW2 = kTrOffB1 + kSurrW,
+                  kTrOffB2 = kTrOffW2 + (int64_t)kSurrW * kSurrW, kTrOffW3 = kTrOffB2 + kSurrW,
+                  kTrOffB3 = kTrOffW3 + (int64_t)kSurrW * kSurrW, kTrOffW4 = kTrOffB3 + kSurrW,
+                  kTrOffB4 = kTrOffW4 + kSurrW;
+constexpr int kAdThreads = 256;
+constexpr int kAdW1 = kSurrW * kSurrIn / 4, kAdW2 = kSurrW * kSurrW / 4;  // threads: four entries each
+constexpr int kAdZ = 4;  // threads per four-entry group, each over every fourth split
+constexpr int kAdWBlocks = (kAdW1 + 2 * kAdW2) / (kAdThreads / kAdZ);
+constexpr int kAdSBlocks = (kTileStats + 31) / 32;
+static_assert((kAdW1 + 2 * kAdW2) % (kAdThreads / kAdZ) == 0 && kAdW1 % (kAdThreads / kAdZ) == 0 &&
+                  kAdW2 % (kAdThreads / kAdZ) == 0,
+              "whole blocks of weight threads, each within one matrix");
+
+__device__ __forceinline__ void adam1(float &p, float &m, float &v, float g, float lr, float c1, float c2) {
+  m = 0.9f * m + 0.1f * g;
+  v = 0.999f * v + 0.001f * g * g;
+  p = p - lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+}
+
+// Four threads per four consecutive entries (u, 4 c4 .. + 3) of one weight
+// matrix (the partials' float4); eight per bias, output weight, the output
+// bias and the loss.  Gradients: weight entries sum their partials in
+// split order, the others their tile sums in tile order.  With `update`,
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8) at the step's learning rate and
+// bias correction from the device counter, the BF16 copies of W1, W2, W3
+// ([out][in] and the training step's weight blocks), and the last block to
+// finish advances the step counter.
+__global__ void __launch_bounds__(kAdThreads) surr_adam_kernel(const SurrAdamArgs a) {
   __shared__ float s_lr, s_c1, s_c2;
+  __shared__ int64_t s_step;
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x == 0) {
-    const int64_t st = *a.step;
-    if (a.cosine) {
-      s_lr = (float)(0.5 * (double)a.lr * (1.0 + cos(M_PI * (double)st / (double)a.total)));
-    } else {
-      const int64_t ep = st / a.steps_per_epoch;
-      s_lr = ep < (2 * a.epochs + 2) / 3 ? a.lr : a.lr / 3.f;
+    s_step = *a.step;
+    if (a.update) {
+      s_lr = a.sched[0];
+      s_c1 = a.sched[1];
+      s_c2 = a.sched[2];
     }
-    const int64_t t = a.t0 + st + 1;
-    s_c1 = 1.f - powf(0.9f, (float)t);
-    s_c2 = 1.f - powf(0.999f, (float)t);
   }
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kTrParams) return;
   const float lr = s_lr, c1 = s_c1, c2 = s_c2;
-  const float gi = a.G[i];
-  const float mi = 0.9f * a.m[i] + 0.1f * gi;
-  const float vi = 0.999f * a.v[i] + 0.001f * gi * gi;
-  a.m[i] = mi;
-  a.v[i] = vi;
-  const float pi = a.p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
-  a.p[i] = pi;
-  const bf16 h = __float2bfloat16_rn(pi);
-  if (i < kTrOffB1) {
-    a.w1[i] = h;
-    surr_wc_put(a.wc, 0, (int)(i / kSurrIn), (int)(i % kSurrIn), h);
-  } else if (i >= kTrOffW2 && i < kTrOffB2) {
-    const int64_t j = i - kTrOffW2;
-    a.w2[j] = h;
-    surr_wc_put(a.wc, 1, (int)(j / kSurrW), (int)(j % kSurrW), h);
-  } else if (i >= kTrOffW3 && i < kTrOffB3) {
-    const int64_t j = i - kTrOffW3;
-    a.w3[j] = h;
-    surr_wc_put(a.wc, 2, (int)(j / kSurrW), (int)(j % kSurrW), h);
+  if (blockIdx.x < kAdWBlocks) {
+    // 64 four-entry groups per block; thread group zg (of 4) sums splits
+    // zg, zg + 4, ...; group 0 adds the four sums in group order
+    __shared__ float4 zpart[kAdZ][kAdThreads / kAdZ];
+    const int el = threadIdx.x % (kAdThreads / kAdZ), zg = threadIdx.x / (kAdThreads / kAdZ);
+    int t = blockIdx.x * (kAdThreads / kAdZ) + el, layer, N;
+    const float *part;
+    int64_t off;
+    bf16 *wb;
+    if (t < kAdW1) {
+      layer = 0, N = kSurrIn, part = a.p1, off = kTrOffW1, wb = a.w1;
+    } else if (t < kAdW1 + kAdW2) {
+      t -= kAdW1, layer = 1, N = kSurrW, part = a.p2, off = kTrOffW2, wb = a.w2;
+    } else {
+      t -= kAdW1 + kAdW2, layer = 2, N = kSurrW, part = a.p3, off = kTrOffW3, wb = a.w3;
+    }
+    const int u = t / (N / 4), c4 = t % (N / 4);  // entries (u, 4 c4 .. + 3), flat index 4 t
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *src = reinterpret_cast<const float4 *>(part) + t;
+#pragma unroll 2
+    for (int z = zg; z < a.splits; z += kAdZ) {
+      const float4 q = src[(size_t)z * N * kSurrW / 4];
+      g.x += q.x, g.y += q.y, g.z += q.z, g.w += q.w;
+    }
+    zpart[zg][el] = g;
+    __syncthreads();
+    if (zg == 0) {
+#pragma unroll
+      for (int k = 1; k < kAdZ; ++k) {
+        const float4 q = zpart[k][el];
+        g.x += q.x, g.y += q.y, g.z += q.z, g.w += q.w;
+      }
+      const int64_t i = off + (int64_t)u * N + 4 * c4;
+      *reinterpret_cast<float4 *>(a.G + i) = g;
+      if (a.update) {
+        float4 p = *reinterpret_cast<const float4 *>(a.p + i), m = *reinterpret_cast<const float4 *>(a.m + i),
+               v = *reinterpret_cast<const float4 *>(a.v + i);
+        adam1(p.x, m.x, v.x, g.x, lr, c1, c2);
+        adam1(p.y, m.y, v.y, g.y, lr, c1, c2);
+        adam1(p.z, m.z, v.z, g.z, lr, c1, c2);
+        adam1(p.w, m.w, v.w, g.w, lr, c1, c2);
+        *reinterpret_cast<float4 *>(a.p + i) = p;
+        *reinterpret_cast<float4 *>(a.m + i) = m;
+        *reinterpret_cast<float4 *>(a.v + i) = v;
+        __align__(8) bf16 h[4] = {__float2bfloat16_rn(p.x), __float2bfloat16_rn(p.y), __float2bfloat16_rn(p.z),
+                                  __float2bfloat16_rn(p.w)};
+        *reinterpret_cast<uint2 *>(wb + (int64_t)u * N + 4 * c4) = *reinterpret_cast<const uint2 *>(h);
+        surr_wc_put4(a.wc, layer, u, 4 * c4, h);
+      }
+    }
+  } else {
+    // 32 entries per block: thread group k (of 8) sums tiles k, k + 8, ...;
+    // then the eight group sums are added in group order
+    __shared__ float part[kAdThreads / 32][32];
+    const int el = threadIdx.x & 31, k = threadIdx.x >> 5;
+    const int e = (blockIdx.x - kAdWBlocks) * 32 + el;
+    float g = 0.f;
+    if (e < kTileStats)
+      for (int t = k; t < a.ntiles; t += kAdThreads / 32) g += a.tstat[(size_t)t * kTileStats + e];
+    part[k][el] = g;
+    __syncthreads();
+    if (k == 0 && e < kTileStats) {
+      g = 0.f;
+#pragma unroll
+      for (int j = 0; j < kAdThreads / 32; ++j) g += part[j][el];
+      if (e == kTileStatLoss) {
+        if (a.loss_hist) a.loss_hist[s_step] = g / (float)a.B;
+      } else {
+        const int64_t i = e < kTileStatW4 ? (e < kTileStatB2 ? kTrOffB1 + e
+                                                             : (e < kTileStatB3 ? kTrOffB2 + (e - kTileStatB2)
+                                                                                : kTrOffB3 + (e - kTileStatB3)))
+                                          : (e < kTileStatB4 ? kTrOffW4 + (e - kTileStatW4) : kTrOffB4);
+        a.G[i] = g;
+        if (a.update) adam1(a.p[i], a.m[i], a.v[i], g, lr, c1, c2);
+      }
+    }
+  }
+  if (!a.update) return;
+  // every thread of the block is past its reads of the step counter
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *a.done = 0;
+      *a.step += 1;
+    }
   }
 }
 
-__global__ void surr_advance_kernel(int64_t *step) { *step += 1; }
-
 // ------------------------------------------------------------ launchers --
 static_assert(kTrSmem + kSurrW * sizeof(float) + 2 * kBM * sizeof(float) + 128 <= 232448, "tile kernel above 227 KB of shared memory");
+
+// a launch that may begin while the stream's previous kernel drains (each
+// kernel waits for it with pdl_wait before touching global memory)
+template <typename Arg>
+static cudaError_t launch_pdl(void (*kernel)(Arg), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              const Arg &arg) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, arg);
+}
 
 cudaError_t launch_surr_tile(const SurrStepArgs &a, int sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(surr_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem);
   if (e != cudaSuccess) return e;
   const int ntiles = a.B / kBM;
-  surr_tile_kernel<<<(unsigned)(ntiles < sms ? ntiles : sms), kTrThreads, kTrSmem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(surr_tile_kernel, (unsigned)(ntiles < sms ? ntiles : sms), kTrThreads, kTrSmem, s, a);
 }
 
-cudaError_t launch_surr_reduce(const SurrReduceArgs &a, cudaStream_t s) {
-  surr_reduce_kernel<<<kRedWBlocks + kRedRowBlocks, kRedThreads, 0, s>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_surr_dw(const SurrDwArgs &a, cudaStream_t s) {
+  if (a.B % kBK || a.splits < 1 || a.splits > a.B / kBK) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(surr_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(surr_dw_kernel, (unsigned)(6 * a.splits), kDwThreads, kDwSmem, s, a);
 }
 
 cudaError_t launch_surr_adam(const SurrAdamArgs &a, cudaStream_t s) {
-  surr_adam_kernel<<<(unsigned)((kTrParams + 255) / 256), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(surr_adam_kernel, kAdWBlocks + kAdSBlocks, kAdThreads, 0, s, a);
 }
 
 cudaError_t launch_surr_wc(const bf16 *w1, const bf16 *w2, const bf16 *w3, uint8_t *wc, cudaStream_t s) {
   constexpr int n = kSurrW * kSurrIn + 2 * kSurrW * kSurrW;
   surr_wc_kernel<<<(n + 255) / 256, 256, 0, s>>>(w1, w2, w3, wc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_surr_advance(int64_t *step, cudaStream_t s) {
-  surr_advance_kernel<<<1, 1, 0, s>>>(step);
   return cudaGetLastError();
 }
 
