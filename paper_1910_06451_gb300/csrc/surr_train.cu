@@ -1,23 +1,23 @@
-// One training step of the learned surrogate (not part of the paper) in a few
+// One training step of the learned surrogate (not part of the paper) in three
 // launches, replayed from a CUDA graph:
 //
-//   surr_tile_kernel  persistent, one CTA of 256 threads per SM, over tiles of
-//                     128 batch rows: the three forward layers and the two
-//                     backward-delta products of every row run back to back
-//                     on the tensor cores, the hidden tiles held in shared
-//                     memory (BF16, the A-operand layout), the weights streamed
-//                     through a three-slot ring; each epilogue also writes its
-//                     tile transposed ([unit][batch row]) for the weight
-//                     gradients, whose sums run over the batch;
-//   gemm_tc_kernel    dW3 = d3^T h2, dW2 = d2^T h1, dW1 = d1^T x as split-K
-//                     products with FP32 partials (three independent launches);
-//   surr_reduce       the partials summed in split order, the bias gradients
-//                     and the output unit's gradient as row sums over the
-//                     batch, the batch loss;
-//   surr_adam         Adam on the FP32 master weights, then their BF16 copies
-//                     (row-major, and the weight blocks the tile kernel
-//                     streams) for the next step;
-//   surr_advance      the step counter.
+//   surr_tile_kernel  persistent, clusters of two CTAs (256 threads each), one
+//                     cluster per tile of 128 batch rows: the three forward
+//                     layers and the two backward-delta products run back to
+//                     back on the tensor cores, each CTA computing half of every
+//                     layer's 256 output units (its half of the weights streamed
+//                     through a six-slot ring) and sending its half of each
+//                     hidden or delta tile into its peer's shared memory (the
+//                     A operand of the next layer needs all 256 units).  While
+//                     a layer's MMAs run, the CTA writes its half of the
+//                     layer's input tile transposed for the weight gradients
+//                     and sums it over the tile's rows for the bias gradients;
+//   surr_dw_kernel    dW3 = d3^T h2, dW2 = d2^T h1, dW1 = d1^T x as split-K
+//                     products with FP32 partials, all three in one launch;
+//   surr_adam_kernel  the partials summed in split order and the tile sums in
+//                     tile order, Adam on the FP32 master weights, their BF16
+//                     copies (row-major, and the weight blocks the tile kernel
+//                     streams) for the next step, the step counter.
 //
 // The batch, the learning rate and Adam's step count come from a step counter
 // in device memory, so every step launches the same graph.  The rounding
@@ -30,13 +30,15 @@
 
 namespace fk {
 
-constexpr int kTrThreads = 256;  // two warps per TMEM lane quadrant, each half the columns
+constexpr int kTrThreads = 256;  // two warps per TMEM lane quadrant, each half the CTA's columns
+constexpr int kTrN = kSurrW / 2;   // output units of one CTA (one half of each layer)
 constexpr uint32_t kTrH = kBM * kSurrW * 2;      // 64 KB: a hidden tile (4 K chunks)
 constexpr uint32_t kTrChunk = kBM * kBK * 2;     // 16 KB: one K chunk of a hidden tile
-constexpr uint32_t kTrW = kSurrW * kBK * 2;      // 32 KB: 256 weight rows x 64 K
-constexpr int kTrSlots = 3;                      // weight ring
-constexpr uint32_t kTrSmem = 2 * kTrH + kTrSlots * kTrW;  // 224 KB
-constexpr uint32_t kTrIdesc = idesc_bf16_f32(kBM, kSurrW);
+constexpr uint32_t kTrW = kSurrW * kBK * 2;      // 32 KB: a weight block, 256 rows x 64 K
+constexpr uint32_t kTrHalfW = kTrN * kBK * 2;    // 16 KB: the CTA's 128 rows of a block
+constexpr int kTrSlots = 6;                      // weight ring: more than one layer's chunks
+constexpr uint32_t kTrSmem = 2 * kTrH + kTrSlots * kTrHalfW;  // 224 KB
+constexpr uint32_t kTrIdesc = idesc_bf16_f32(kBM, kTrN);
 // Weight blocks of one tile, in the order the tile's MMAs read them: W1, the
 // four K chunks of W2, of W3, of W3^T (B operand of d3 W3) and of W2^T.
 constexpr int kTrBlocks = 17;
@@ -46,16 +48,16 @@ __device__ __forceinline__ uint32_t tr_cm(int row, int k) {
   return (uint32_t)(((row >> 3) * 8 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Weight ring, fed by 1-D TMA bulk copies of the pre-laid-out 32 KB blocks
-// (surr_wc_off): chunk g of the CTA's sequence (block g mod 17) goes to slot
-// g mod 3, announced on full[slot]; its MMAs commit to done[slot].  Both
-// barriers complete their (g / 3)-th phase for chunk g.  Thread 0 keeps the
-// copies two chunks ahead of the MMAs, refilling a slot once the MMAs of its
-// previous chunk have committed.
+// Weight ring, fed by 1-D TMA bulk copies of the CTA's half (rows 128 rank ..
+// + 127, 16 KB contiguous) of the pre-laid-out 32 KB blocks (surr_wc_off):
+// chunk g of the CTA's sequence (block g mod 17) goes to slot g mod 6,
+// announced on full[slot]; its MMAs commit to done[slot].  Both barriers
+// complete their (g / 6)-th phase for chunk g.  Thread 0 refills a slot once
+// the MMAs of its previous chunk have committed.
 struct TrRing {
   uint8_t *base;
   uint64_t *full, *done;
-  const uint8_t *wc;
+  const uint8_t *wc;   // the blocks, offset to this CTA's half
   uint32_t next_load;  // thread 0: next chunk to copy
   uint32_t next_mma;   // next chunk to multiply (every thread)
   uint32_t end;        // chunks of this CTA (tiles x 17)
@@ -68,42 +70,87 @@ __device__ __forceinline__ bool tr_fill(TrRing &r, uint32_t upto, uint32_t limit
   for (; r.next_load <= upto && r.next_load < r.end; ++r.next_load) {
     const uint32_t gl = r.next_load, s = gl % kTrSlots;
     if (gl >= kTrSlots && !mbar_wait_bounded(&r.done[s], ((gl - kTrSlots) / kTrSlots) & 1, limit)) return false;
-    mbar_arrive_expect_tx(&r.full[s], kTrW);
-    tma_bulk_load(r.base + s * kTrW, r.wc + (size_t)(gl % kTrBlocks) * kTrW, kTrW, &r.full[s]);
+    mbar_arrive_expect_tx(&r.full[s], kTrHalfW);
+    tma_bulk_load(r.base + s * kTrHalfW, r.wc + (size_t)(gl % kTrBlocks) * kTrW, kTrHalfW, &r.full[s]);
   }
   return true;
+}
+
+// Bounded wait with acquire semantics at cluster scope (a phase completed by
+// the peer CTA's arrivals).
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (mbar_test_wait_cluster(bar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// The exchange between the two CTAs of a tile.  Exchange k of a CTA's
+// sequence (five per tile: h1, h2, the output unit's partial sums, d3, d2)
+// completes phase k / 2 of the peer's barrier xin[k mod 2]: every warp of the
+// sender, once its lanes' stores into the peer's shared memory are done,
+// makes them visible to the peer's tensor-core reads (proxy fence) and
+// arrives with release semantics; the receiver waits with acquire semantics.
+// A CTA sends exchange k + 1 only after it has received exchange k, so a
+// barrier is never more than one phase ahead of its waiter.
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void tr_xsend(uint32_t peer_bar) {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0)
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(peer_bar) : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // The MMAs of one layer, in two halves so that the CTA can work between
 // them: tr_issue (every thread; after the barrier thread 0 issues) multiplies
 // A = nk K chunks of [128][64] at a_base + c 16 KB (shared memory) by the next
-// nk weight chunks of the ring into tmem (cols 0..255); tr_wait returns once
-// the last commit has landed, or false in every thread if a wait gave up
-// (*abort is then set).  Between the two the A tiles may be read, not written.
+// nk weight chunks of the ring into tmem (cols 0..127), waiting first (if xbar
+// is given) for the exchange that completes A, then refills the ring up to a
+// full slot count past the layer; tr_wait returns once the last commit has
+// landed, or false in every thread if a wait gave up (*abort is then set).
+// Between the two the A tiles may be read, not written.
 __device__ __forceinline__ void tr_issue(TrRing &r, uint32_t a_base, int nk, uint32_t tmem, uint32_t limit,
-                                         int *abort) {
+                                         int *abort, uint64_t *xbar, uint32_t xpar) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A written by the generic proxy
   __syncthreads();
   if (threadIdx.x == 0 && !*abort) {
+    if (xbar && !mbar_wait_cluster_bounded(xbar, xpar, limit)) {
+      *abort = 1;
+      return;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_after();
     for (int c = 0; c < nk; ++c) {
       const uint32_t gc = r.next_mma + c, s = gc % kTrSlots;
       if (!mbar_wait_bounded(&r.full[s], (gc / kTrSlots) & 1, limit)) {
         *abort = 1;
-        break;
+        return;
       }
-      const uint32_t b_base = smem_u32(r.base + s * kTrW), a_c = a_base + c * kTrChunk;
+      const uint32_t b_base = smem_u32(r.base + s * kTrHalfW), a_c = a_base + c * kTrChunk;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk)
         tc_mma(tmem, smem_desc(a_c + kk * 256, 128, 1024), smem_desc(b_base + kk * 256, 128, 1024), kTrIdesc,
                (c > 0 || kk > 0) ? 1u : 0u);
       tc_commit(&r.done[s]);
       r.issued = gc + 1;
-      if (!tr_fill(r, gc + 2, limit)) {
-        *abort = 1;
-        break;
-      }
     }
+    if (!tr_fill(r, r.next_mma + nk - 1 + kTrSlots, limit)) *abort = 1;
   }
 }
 __device__ __forceinline__ bool tr_wait(TrRing &r, int nk, uint32_t limit, int *abort) {
@@ -137,24 +184,25 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
                : "r"(addr));
 }
 
-// A tile of 128 rows x U units held in shared memory (the A-operand layout
-// of tr_put8) written transposed into the chunk-blocked tensor T (rows
-// tile 128 ..), and/or its column sums (weighted by w[row] if w is given)
-// into sums[u].  A core matrix of the tile (8 rows x 8 units) transposed is
-// a core matrix of T (8 units x 8 rows): one ldmatrix reads four row groups
-// of one unit group, each lane then holds two rows of one unit per matrix
-// and the warp's store of one matrix is 128 contiguous bytes.  Warps 1-7
-// share the unit groups (warp 0 holds the thread that issues the MMAs and
-// keeps the weight ring full); the sums add, per unit, the tile's rows in a
-// fixed order.
+// Unit groups ug0 .. ug0 + nug - 1 (8 units each) of a tile of 128 rows x U
+// units held in shared memory (the A-operand layout of tr_put8) written
+// transposed into the chunk-blocked tensor T (rows tile 128 ..), and/or their
+// column sums (weighted by w[row] if w is given) into sums[u].  A core matrix
+// of the tile (8 rows x 8 units) transposed is a core matrix of T (8 units x
+// 8 rows): one ldmatrix reads four row groups of one unit group, each lane
+// then holds two rows of one unit per matrix and the warp's store of one
+// matrix is 128 contiguous bytes.  Warps 1-7 share the unit groups (warp 0
+// holds the thread that issues the MMAs and keeps the weight ring full); the
+// sums add, per unit, the tile's rows in a fixed order.
 template <int U, bool STORE, bool SUM>
-__device__ __forceinline__ void tr_copy_t(const uint8_t *H, bf16 *T, int tile, float *sums, const float *w) {
+__device__ __forceinline__ void tr_copy_t(const uint8_t *H, bf16 *T, int tile, float *sums, const float *w,
+                                          int ug0, int nug) {
   constexpr int kCopyWarps = kTrThreads / 32 - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) return;
   const uint32_t hs = smem_u32(H);
 #pragma unroll 1
-  for (int ug = warp - 1; ug < U / 8; ug += kCopyWarps) {
+  for (int ug = ug0 + warp - 1; ug < ug0 + nug; ug += kCopyWarps) {
     float acc = 0.f;
 #pragma unroll
     for (int rq = 0; rq < 4; ++rq) {  // a quarter of the row groups
@@ -192,17 +240,19 @@ __device__ __forceinline__ void tr_copy_t(const uint8_t *H, bf16 *T, int tile, f
   }
 }
 
-// 16-byte store of 8 BF16 values into a hidden tile at (row, k), k % 8 == 0
+// 16-byte store of 8 BF16 values into a hidden tile at (row, k), k % 8 == 0,
+// and (with peer, the tile's address in the peer CTA) the same store there
+__device__ __forceinline__ uint32_t tr_off(int row, int k) { return (k >> 6) * kTrChunk + tr_cm(row, k & 63); }
 __device__ __forceinline__ void tr_put8(uint8_t *H, int row, int k, const bf16 *v) {
-  *reinterpret_cast<uint4 *>(H + (k >> 6) * kTrChunk + tr_cm(row, k & 63)) = *reinterpret_cast<const uint4 *>(v);
+  *reinterpret_cast<uint4 *>(H + tr_off(row, k)) = *reinterpret_cast<const uint4 *>(v);
+}
+__device__ __forceinline__ void tr_put8x(uint8_t *H, uint32_t peer, int row, int k, const bf16 *v) {
+  const uint32_t o = tr_off(row, k);
+  const uint4 q = *reinterpret_cast<const uint4 *>(v);
+  *reinterpret_cast<uint4 *>(H + o) = q;
+  st_cluster_v4(peer + o, q);
 }
 
-// Byte offset in the weight blocks of entry (o, i) of W1 (layer 0), W2 (1)
-// or W3 (2) (o the output unit, i the input): the B operand of layer L + 1
-// has row n = o and K index k = i; W2 and W3 appear a second time
-// transposed (B operands of the deltas: d3 W3 and d2 W2), row n = i, k = o.
-// Within a 32 KB block (256 rows x 64 K) the no-swizzle core-matrix layout
-// of the ring.
 // 32 consecutive FP32 biases (16-byte aligned) as eight vector loads
 __device__ __forceinline__ void tr_bias32(const float *__restrict__ b, float (&o)[32]) {
 #pragma unroll
@@ -214,6 +264,13 @@ __device__ __forceinline__ void tr_bias32(const float *__restrict__ b, float (&o
     o[4 * k + 3] = t.w;
   }
 }
+
+// Byte offset in the weight blocks of entry (o, i) of W1 (layer 0), W2 (1)
+// or W3 (2) (o the output unit, i the input): the B operand of layer L + 1
+// has row n = o and K index k = i; W2 and W3 appear a second time
+// transposed (B operands of the deltas: d3 W3 and d2 W2), row n = i, k = o.
+// Within a 32 KB block (256 rows x 64 K) the no-swizzle core-matrix layout
+// of the ring.
 __device__ __forceinline__ uint32_t surr_wc_off(int block, int n, int k) {
   return (uint32_t)block * kTrW + (uint32_t)(((n >> 3) * 8 + ((k & 63) >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2);
 }
@@ -254,18 +311,20 @@ __global__ void surr_wc_kernel(const bf16 *__restrict__ w1, const bf16 *__restri
 
 __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStepArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t full[kTrSlots], done[kTrSlots];
+  __shared__ __align__(8) uint64_t full[kTrSlots], done[kTrSlots], xin[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ float sw4[kSurrW];  // b1, b2, b3 are read as vectors through L1 (shared memory is full)
-  __shared__ float sout[2][kBM];  // the two halves of each row's output dot product; then dout, squared error
+  __shared__ float sw4[kTrN];     // w4 of this CTA's units; b1, b2, b3 are read as vectors through L1
+  __shared__ float sout[2][kBM];  // the two column halves of this CTA's part of each row's output; then dout, e^2
+  __shared__ float sx[2][kBM];    // the two CTAs' parts of each row's output dot product
   uint8_t *HA = sm, *HB = sm + kTrH;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int ntiles = a.B / kBM;
-  const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // tiles of this CTA
-  TrRing r{sm + 2 * kTrH, full, done, a.wc, 0, 0, (uint32_t)mine * kTrBlocks, 0};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
+  const int ntiles = a.B / kBM, cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int mine = cl < ntiles ? (ntiles - 1 - cl) / ncl + 1 : 0;  // tiles of this cluster
+  TrRing r{sm + 2 * kTrH, full, done, a.wc + rank * kTrHalfW, 0, 0, (uint32_t)mine * kTrBlocks, 0};
   if (warp == 0) {
-    tmem_alloc(&tmem_slot, kSurrW);
+    tmem_alloc(&tmem_slot, kTrN);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -273,27 +332,95 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
       mbar_init(&full[i], 1);
       mbar_init(&done[i], 1);
     }
+    mbar_init(&xin[0], kTrThreads / 32);
+    mbar_init(&xin[1], kTrThreads / 32);
     abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_fence_init_cluster();
   }
+  tc_fence_before();
+  cluster_sync_all();  // both CTAs' barriers initialised before any exchange
+  tc_fence_after();
   pdl_wait();
   pdl_trigger();
-  for (int i = tid; i < kSurrW; i += kTrThreads) sw4[i] = a.w4[i];
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid == 0 && !tr_fill(r, 2, a.wait_limit)) abort_flag = 1;  // the first three chunks
+  for (int i = tid; i < kTrN; i += kTrThreads) sw4[i] = a.w4[rank * kTrN + i];
+  if (tid == 0 && !tr_fill(r, kTrSlots - 1, a.wait_limit)) abort_flag = 1;  // the ring's first chunks
   const uint32_t tmem = tmem_slot;
-  // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows) and the columns
-  // of half w / 4 (128 each)
-  const int lane = tid & 31, quad = warp & 3, half = warp >> 2;
-  const int row = quad * 32 + lane, c0 = half * (kSurrW / 2);
+  // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows) and the 64
+  // columns of half w / 4; column c of this CTA is unit 128 rank + c
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane, cc = half * (kTrN / 2), u0 = (int)rank * kTrN + cc;
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+  const uint32_t pHA = cluster_addr(HA, peer), pHB = cluster_addr(HB, peer);
+  const uint32_t pxin[2] = {cluster_addr(&xin[0], peer), cluster_addr(&xin[1], peer)};
+  const uint32_t psx = cluster_addr(&sx[rank][0], peer);
+  const int ug0 = (int)rank * (kTrN / 8);  // this CTA's unit groups: ug0 .. + 15
+  uint32_t xk = 0;                         // exchanges of this CTA so far
   const int64_t row0 = (*a.step % a.steps_per_epoch) * a.B;  // the batch's first training row
   const float b4 = *a.b4;
   const float invB2 = 2.f / (float)a.B;
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // a hidden layer's epilogue on this thread's 64 units, into H here and in
+  // the peer: the biases of the first 32-column chunk (xb) are loaded before
+  // the MMA wait, the second chunk's while the first is converted, and the
+  // second chunk's TMEM load is in flight meanwhile
+  auto hidden = [&](const float *__restrict__ bias, uint8_t *H, uint32_t pH, uint32_t (&m)[2], float (&xb)[32]) {
+    uint32_t v[32];
+    tc_ld32_issue(trow + cc, v);
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const int u = u0 + 32 * j;
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = xb[i];
+      if (j < 1) tr_bias32(bias + u + 32, xb);
+      tc_wait_ld32(v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
+      if (j < 1) tc_ld32_issue(trow + cc + 32, v);
+      __align__(16) bf16 hb[32];
+      uint32_t bits = 0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        hb[i] = __float2bfloat16_rn(fmaxf(x[i], 0.f));
+        bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
+      }
+      m[j] = bits;
+#pragma unroll
+      for (int i = 0; i < 32; i += 8) tr_put8x(H, pH, row, u + i, hb + i);
+    }
+    tc_fence_before();
+  };
+  // back through a layer: d = bf16((d W) [h > 0]) on this thread's units,
+  // into H (and with pH != 0 into the peer's H)
+  auto delta = [&](uint8_t *H, uint32_t pH, const uint32_t (&m)[2]) {
+    uint32_t v[32];
+    tc_ld32_issue(trow + cc, v);
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const int u = u0 + 32 * j;
+      tc_wait_ld32(v);
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
+      if (j < 1) tc_ld32_issue(trow + cc + 32, v);
+      __align__(16) bf16 db[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m[j] >> i) & 1u) ? x[i] : 0.f);
+      if (pH) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) tr_put8x(H, pH, row, u + i, db + i);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) tr_put8(H, row, u + i, db + i);
+      }
+    }
+    tc_fence_before();
+  };
+  auto xsend = [&]() { tr_xsend(pxin[xk & 1]); };
+  auto xbar = [&]() { return &xin[xk & 1]; };
+  auto xpar = [&]() { return (xk >> 1) & 1u; };
+
+  for (int tile = cl; tile < ntiles; tile += ncl) {
     const int64_t rb = (int64_t)tile * kBM + row;  // this thread's row within the batch
     float *ts = a.tstat + (size_t)tile * kTileStats;
     // features of the tile into HB (A layout, one K chunk), each thread half of its row
@@ -302,136 +429,105 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
 #pragma unroll
       for (int i = half * 4; i < half * 4 + 4; ++i) *reinterpret_cast<uint4 *>(HB + tr_cm(row, 8 * i)) = src[i];
     }
-
-    uint32_t m1[4], m2[4], m3[4];  // ReLU masks of h1, h2, h3 on this thread's 128 units, one bit each
-    // a hidden layer's epilogue: the biases of the first 32-column chunk (xb)
-    // are loaded before the MMA wait, each next chunk's while this one is
-    // converted, and the next chunk's TMEM load is in flight meanwhile
-    auto hidden = [&](const float *__restrict__ bias, uint8_t *H, uint32_t (&m)[4], float (&xb)[32]) {
-      uint32_t v[32];
-      tc_ld32_issue(trow + c0, v);
-#pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
-        const int j0 = c0 + 32 * j;
-        float x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = xb[i];
-        if (j < 3) tr_bias32(bias + j0 + 32, xb);
-        tc_wait_ld32(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
-        if (j < 3) tc_ld32_issue(trow + j0 + 32, v);
-        __align__(16) bf16 hb[32];
-        uint32_t bits = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          hb[i] = __float2bfloat16_rn(fmaxf(x[i], 0.f));
-          bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
-        }
-        m[j] = bits;
-#pragma unroll
-        for (int i = 0; i < 32; i += 8) tr_put8(H, row, j0 + i, hb + i);
-      }
-      tc_fence_before();
-    };
+    uint32_t m1[2], m2[2], m3[2];  // ReLU masks of h1, h2, h3 on this thread's 64 units, one bit each
     float xb[32];
-    // ---- layer 1: h1 = relu(x W1^T + b1) -> HA; x^T out while the MMAs run
-    tr_issue(r, smem_u32(HB), 1, tmem, a.wait_limit, &abort_flag);
-    tr_copy_t<kSurrIn, true, false>(HB, a.xT, tile, nullptr, nullptr);
-    tr_bias32(a.b1 + c0, xb);
+    // ---- layer 1: h1 = relu(x W1^T + b1) -> HA (both CTAs); this CTA's half of x^T out
+    tr_issue(r, smem_u32(HB), 1, tmem, a.wait_limit, &abort_flag, nullptr, 0);
+    tr_copy_t<kSurrIn, true, false>(HB, a.xT, tile, nullptr, nullptr, (int)rank * (kSurrIn / 16), kSurrIn / 16);
+    tr_bias32(a.b1 + u0, xb);
     if (!tr_wait(r, 1, a.wait_limit, &abort_flag)) break;
-    hidden(a.b1, HA, m1, xb);
+    hidden(a.b1, HA, pHA, m1, xb);
+    xsend();
     // ---- layer 2: h2 = relu(h1 W2^T + b2) -> HB; h1^T out
-    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag);
-    tr_copy_t<kSurrW, true, false>(HA, a.h1T, tile, nullptr, nullptr);
-    tr_bias32(a.b2 + c0, xb);
+    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag, xbar(), xpar());
+    ++xk;
+    tr_copy_t<kSurrW, true, false>(HA, a.h1T, tile, nullptr, nullptr, ug0, kTrN / 8);
+    tr_bias32(a.b2 + u0, xb);
     if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
-    hidden(a.b2, HB, m2, xb);
+    hidden(a.b2, HB, pHB, m2, xb);
+    xsend();
     // ---- layer 3 and the output unit: out = relu(z3) . w4 + b4 (FP32),
-    // dout = 2 (out - y) / B, d3 = bf16(dout w4 [z3 > 0]) -> HA, bf16(h3) -> HB;
-    // h2^T out
-    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag);
-    tr_copy_t<kSurrW, true, false>(HB, a.h2T, tile, nullptr, nullptr);
-    tr_bias32(a.b3 + c0, xb);
+    // dout = 2 (out - y) / B, d3 = bf16(dout w4 [z3 > 0]) -> HA (both CTAs),
+    // bf16(h3) -> HB (this CTA's units); h2^T out
+    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag, xbar(), xpar());
+    ++xk;
+    tr_copy_t<kSurrW, true, false>(HB, a.h2T, tile, nullptr, nullptr, ug0, kTrN / 8);
+    tr_bias32(a.b3 + u0, xb);
     const float y = a.Y[row0 + rb];
     if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
     float out = 0.f;
     {
       uint32_t v[32];
-      tc_ld32_issue(trow + c0, v);
+      tc_ld32_issue(trow + cc, v);
 #pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
-        const int j0 = c0 + 32 * j;
+      for (int j = 0; j < 2; ++j) {
+        const int u = u0 + 32 * j;
         float x[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] = xb[i];
-        if (j < 3) tr_bias32(a.b3 + j0 + 32, xb);
+        if (j < 1) tr_bias32(a.b3 + u + 32, xb);
         tc_wait_ld32(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
-        if (j < 3) tc_ld32_issue(trow + j0 + 32, v);
+        if (j < 1) tc_ld32_issue(trow + cc + 32, v);
         __align__(16) bf16 hb[32];
         uint32_t bits = 0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float h = fmaxf(x[i], 0.f);
-          out = fmaf(h, sw4[j0 + i], out);
+          out = fmaf(h, sw4[cc + 32 * j + i], out);
           hb[i] = __float2bfloat16_rn(h);
           bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
         }
         m3[j] = bits;
 #pragma unroll
-        for (int i = 0; i < 32; i += 8) tr_put8(HB, row, j0 + i, hb + i);
+        for (int i = 0; i < 32; i += 8) tr_put8(HB, row, u + i, hb + i);
       }
     }
     tc_fence_before();
-    // the row's two halves of the dot product, added in a fixed order; then
-    // the same shared words hold the row's dout and squared error
+    // the row's dot product: this CTA's two column halves, then the two CTAs'
+    // parts, added in a fixed order (unit 0 upwards) in both CTAs
     sout[half][row] = out;
     __syncthreads();
-    out = (sout[0][row] + sout[1][row]) + b4;
+    if (half == 0) {
+      const float part = sout[0][row] + sout[1][row];
+      sx[rank][row] = part;
+      st_cluster_f32(psx + row * 4, part);
+    }
+    xsend();
+    {
+      const bool got = mbar_wait_cluster_bounded(xbar(), xpar(), a.wait_limit);
+      ++xk;
+      if (!__syncthreads_and(got)) {
+        if (tid == 0) abort_flag = 1;
+        break;
+      }
+    }
+    out = (sx[0][row] + sx[1][row]) + b4;
     const float e = out - y;
     const float dout = e * invB2;
-    __syncthreads();
-    if (half == 0) {
+    if (half == 0) {  // sout's reads are behind the barrier above
       sout[0][row] = dout;
       sout[1][row] = e * e;
     }
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      const int j0 = c0 + 32 * j;
+    for (int j = 0; j < 2; ++j) {
+      const int u = u0 + 32 * j;
       __align__(16) bf16 db[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m3[j] >> i) & 1u) ? dout * sw4[j0 + i] : 0.f);
+      for (int i = 0; i < 32; ++i)
+        db[i] = __float2bfloat16_rn(((m3[j] >> i) & 1u) ? dout * sw4[cc + 32 * j + i] : 0.f);
 #pragma unroll
-      for (int i = 0; i < 32; i += 8) tr_put8(HA, row, j0 + i, db + i);
+      for (int i = 0; i < 32; i += 8) tr_put8x(HA, pHA, row, u + i, db + i);
     }
-    // ---- back through layer 3 and 2: d = bf16((d W) [h > 0])
-    auto delta = [&](uint8_t *H, const uint32_t (&m)[4]) {
-      uint32_t v[32];
-      tc_ld32_issue(trow + c0, v);
-#pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
-        const int j0 = c0 + 32 * j;
-        tc_wait_ld32(v);
-        float x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
-        if (j < 3) tc_ld32_issue(trow + j0 + 32, v);
-        __align__(16) bf16 db[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m[j] >> i) & 1u) ? x[i] : 0.f);
-#pragma unroll
-        for (int i = 0; i < 32; i += 8) tr_put8(H, row, j0 + i, db + i);
-      }
-      tc_fence_before();
-    };
-    // d2 = d3 W3: d3^T out with the b3 sums, the w4 sums from h3 and dout,
-    // the tile's dout and squared-error sums
-    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag);
-    tr_copy_t<kSurrW, true, true>(HA, a.d3T, tile, ts + kTileStatB3, nullptr);
-    tr_copy_t<kSurrW, false, true>(HB, nullptr, tile, ts + kTileStatW4, sout[0]);
-    if (warp == kTrThreads / 32 - 1) {
+    xsend();
+    // ---- d2 = d3 W3 -> HB (both CTAs): d3^T out with the b3 sums, the w4 sums
+    // from h3 and dout, the tile's dout and squared-error sums
+    tr_issue(r, smem_u32(HA), 4, tmem, a.wait_limit, &abort_flag, xbar(), xpar());
+    ++xk;
+    tr_copy_t<kSurrW, true, true>(HA, a.d3T, tile, ts + kTileStatB3, nullptr, ug0, kTrN / 8);
+    tr_copy_t<kSurrW, false, true>(HB, nullptr, tile, ts + kTileStatW4, sout[0], ug0, kTrN / 8);
+    if (rank == 0 && warp == kTrThreads / 32 - 1) {
       float sd = 0.f, se = 0.f;
 #pragma unroll
       for (int k = 0; k < kBM / 32; ++k) {
@@ -449,14 +545,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
       }
     }
     if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
-    delta(HB, m2);
-    // d1 = d2 W2: d2^T out with the b2 sums
-    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag);
-    tr_copy_t<kSurrW, true, true>(HB, a.d2T, tile, ts + kTileStatB2, nullptr);
+    delta(HB, pHB, m2);
+    xsend();
+    // ---- d1 = d2 W2 -> HA (this CTA's units): d2^T out with the b2 sums
+    tr_issue(r, smem_u32(HB), 4, tmem, a.wait_limit, &abort_flag, xbar(), xpar());
+    ++xk;
+    tr_copy_t<kSurrW, true, true>(HB, a.d2T, tile, ts + kTileStatB2, nullptr, ug0, kTrN / 8);
     if (!tr_wait(r, 4, a.wait_limit, &abort_flag)) break;
-    delta(HA, m1);
+    delta(HA, 0u, m1);
     __syncthreads();
-    tr_copy_t<kSurrW, true, true>(HA, a.d1T, tile, ts + kTileStatB1, nullptr);
+    tr_copy_t<kSurrW, true, true>(HA, a.d1T, tile, ts + kTileStatB1, nullptr, ug0, kTrN / 8);
   }
   __syncthreads();
   if (abort_flag && tid == 0) {
@@ -469,8 +567,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
     atomicOr(a.err, kErrTimeout);
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kSurrW);
+  cluster_sync_all();  // the peer's stores into this CTA are done before either exits
+  if (warp == 0) tmem_dealloc(tmem, kTrN);
 }
 
 // --------------------------------------------------- weight gradients --
@@ -755,7 +853,8 @@ __global__ void __launch_bounds__(kAdThreads) surr_adam_kernel(const SurrAdamArg
 }
 
 // ------------------------------------------------------------ launchers --
-static_assert(kTrSmem + kSurrW * sizeof(float) + 2 * kBM * sizeof(float) + 128 <= 232448, "tile kernel above 227 KB of shared memory");
+static_assert(kTrSmem + kTrN * sizeof(float) + 4 * kBM * sizeof(float) + 256 <= 232448,
+              "tile kernel above 227 KB of shared memory");
 
 // a launch that may begin while the stream's previous kernel drains (each
 // kernel waits for it with pdl_wait before touching global memory)
@@ -778,8 +877,22 @@ static cudaError_t launch_pdl(void (*kernel)(Arg), unsigned grid, unsigned block
 cudaError_t launch_surr_tile(const SurrStepArgs &a, int sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(surr_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem);
   if (e != cudaSuccess) return e;
-  const int ntiles = a.B / kBM;
-  return launch_pdl(surr_tile_kernel, (unsigned)(ntiles < sms ? ntiles : sms), kTrThreads, kTrSmem, s, a);
+  const int ntiles = a.B / kBM, clusters = ntiles < sms / 2 ? ntiles : sms / 2;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(2 * clusters));
+  cfg.blockDim = dim3(kTrThreads);
+  cfg.dynamicSmemBytes = kTrSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, surr_tile_kernel, a);
 }
 
 cudaError_t launch_surr_dw(const SurrDwArgs &a, cudaStream_t s) {
