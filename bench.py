@@ -356,7 +356,8 @@ def obstacle_sweep(fk, dev, rank, counts, Q, X32, X, flush):
     return out
 
 
-def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "active", "surrogate"), short=None):
+def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "active", "pipelined", "surrogate"),
+                         short=None):
     """The 12-control-point arm among moving boxes: a fixed training set of
     65,536 configurations relabelled every frame, Algorithm 1 on the stored
     FP32 kernel matrix (built once), then the query batch scored.  Each frame
@@ -369,8 +370,10 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
     learned surrogate: after each cold update it is fine-tuned (one epoch on
     a fixed 1M-query set scored by the new model, threshold recalibrated) and
     answers the frame's queries, falling back to the exact score below the
-    threshold; its labels are compared with the exact path's.  Per-frame
-    device times.  The cold and surrogate modes run `frames` frames, the
+    threshold; its labels are compared with the exact path's.  A fifth pass
+    repeats the cold mode with each frame's update overlapped with the
+    previous frame's query pass (pipelined_frames).  Per-frame device times.
+    The cold, pipelined and surrogate modes run `frames` frames, the
     warm-start and active-learning modes `short` (default: the same)."""
     import torch
     wd = synth.workload("arm7m12-n65536", trial=rank)
@@ -401,6 +404,7 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
                "frame0_cold_with_matrix_ms": setup_ms, "frame0_support": st0["n_support"],
                "frame0_iterations": st0["iterations"]}
         n_max = X.shape[0]
+        cold_sums = []
         Xa = torch.empty_like(X)
         Xa32 = torch.empty_like(X32)
         for mode in [m for m in ("warm", "cold", "active") if m in modes]:
@@ -432,6 +436,8 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
                 torch.cuda.synchronize()
                 upd.append(a.elapsed_time(b))
                 qry.append(b.elapsed_time(c))
+                if mode == "cold":
+                    cold_sums.append(label_checksum(lab.cpu().numpy()))
                 its.append(st["iterations"])
                 sup.append(st["n_support"])
                 conv.append(bool(st["converged"]))
@@ -442,12 +448,83 @@ def changing_environment(fk, dev, rank, frames, nq, modes=("warm", "cold", "acti
                          "frame_ms_p50": float(np.percentile(tot, 50)), "frame_ms_p99": float(np.percentile(tot, 99)),
                          "frames": nf, "iterations": its, "support": sup, "converged": conv, "rescored": nres,
                          "checks_per_s_p50": nq / (float(np.percentile(tot, 50)) * 1e-3)}
+        if "pipelined" in modes:
+            out["pipelined"] = pipelined_frames(fk, dev, wd, ch, m, X, X32, y, Q, boxes, frames, cold_sums)
         if "surrogate" in modes:
             out["surrogate"] = surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev)
         return out
     finally:
         fk.fastron_model_destroy(m)
         fk.fk_chain_destroy(ch)
+
+
+def pipelined_frames(fk, dev, wd, ch, m, X, X32, y, Q, boxes, frames, cold_sums):
+    """The cold mode's frames with the update and the query pass overlapped:
+    while Algorithm 1 runs for frame k (one 16-CTA cluster, on a
+    higher-priority stream, from one host thread), frame k-1's queries are
+    scored with a snapshot of frame k-1's model (fastron_model_copy) on the
+    other SMs (another stream and thread).  A frame's labels come out one
+    update later; the frame period is the wall time of one such step.  Each
+    frame's label checksum is compared with the sequential cold mode's."""
+    import threading
+    import torch
+    nq = Q.shape[0]
+    snaps = [fk.fastron_model_create(ch), fk.fastron_model_create(ch)]
+    U = torch.cuda.Stream(priority=-1)
+    S = torch.cuda.Stream(priority=0)
+    lab = torch.empty(nq, dtype=torch.int8, device=dev)
+    sums, period, errors = [None] * frames, [], []
+    try:
+        def update(k):
+            try:
+                with torch.cuda.stream(U):
+                    fk.fk_label(ch, boxes[k], wd.scene.radius, X32, y, stream=U)
+                    fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32,
+                                     reuse_gram=True, stream=U)
+                    fk.fastron_model_copy(snaps[k % 2], m, stream=U)
+                    U.synchronize()
+            except Exception as e:  # re-raised by the main thread
+                errors.append(e)
+
+        def query(k):
+            try:
+                with torch.cuda.stream(S):
+                    fk.fk_score(snaps[k % 2], Q, lab, rescore=True, stream=S)
+                    S.synchronize()
+                    sums[k] = label_checksum(lab.cpu().numpy())
+            except Exception as e:
+                errors.append(e)
+
+        # the stored matrix is X's again (the active mode replaced it)
+        fk.fk_label(ch, boxes[0], wd.scene.radius, X32, y)
+        fk.fastron_train(m, X, y, wd.gamma, wd.beta, wd.iter_max, wd.s_max, gram=fk.FK_DF32)
+        torch.cuda.synchronize()
+        fk.fastron_model_copy(snaps[0], m)
+        for k in range(1, frames):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ta = threading.Thread(target=update, args=(k,))
+            tb = threading.Thread(target=query, args=(k - 1,))
+            ta.start()
+            tb.start()
+            ta.join()
+            tb.join()
+            period.append((time.perf_counter() - t0) * 1e3)
+            if errors:
+                raise errors[0]
+        query(frames - 1)
+        if errors:
+            raise errors[0]
+        # frames 1.. of the cold mode are the same updates in the same order
+        same = [sums[k] == cold_sums[k - 1] for k in range(1, frames) if k - 1 < len(cold_sums)]
+        return {"frames": frames, "frame_period_ms_p50": float(np.percentile(period, 50)),
+                "frame_period_ms_p99": float(np.percentile(period, 99)),
+                "checks_per_s_p50": nq / (float(np.percentile(period, 50)) * 1e-3),
+                "labels_equal_cold": bool(same) and all(same), "frames_compared": len(same),
+                "overlap": "update k (cluster kernel, priority stream) beside the query pass of k-1"}
+    finally:
+        for x in snaps:
+            fk.fastron_model_destroy(x)
 
 
 def surrogate_frames(fk, dev, wd, ch, m, X, X32, y, Q, lab, boxes, ev):
@@ -574,7 +651,7 @@ def main():
     ap.add_argument("--dynamic-frames-short", type=int, default=8,
                     help="frames of the warm-start and active-learning modes")
     ap.add_argument("--dynamic-queries", type=int, default=1 << 24, help="queries per frame of that measurement")
-    ap.add_argument("--dynamic-modes", default="warm,cold,active,surrogate",
+    ap.add_argument("--dynamic-modes", default="warm,cold,active,pipelined,surrogate",
                     help="update modes of that measurement (comma-separated)")
     ap.add_argument("--gauss", type=int, default=1, help="measure the non-paper Gaussian summand (0: skip)")
     ap.add_argument("--small", type=int, default=1, help="measure the 3-DOF workload's step (0: skip)")

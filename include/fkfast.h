@@ -224,6 +224,17 @@ int fastron_model_trace(const fastron_model_t *model, int8_t *kind, int64_t *idx
  * score a model trained elsewhere.  Synchronous. */
 int fastron_model_set(fastron_model_t *model, const double *q, const double *alpha, int64_t ns, double gamma);
 
+/* Copies src's support set, as packed for scoring (configurations, weights,
+ * gamma, training indices), into dst, which must use the same chain: dst can
+ * then be scored while src trains again (for example on another stream), the
+ * double buffer of a pipelined update/query loop.  dst's own training state
+ * (kernel matrix, margins) is dropped; it cannot be warm-started.  The device
+ * copies are enqueued on `stream` after whatever is queued there (src's
+ * training, if it ran on that stream); dst must not be in use by another
+ * stream meanwhile.  Returns FK_ERR_STATE if src is untrained.  Not part of
+ * the paper: a device-side form of its model handover between updates. */
+int fastron_model_copy(fastron_model_t *dst, const fastron_model_t *src, void *stream);
+
 /* Copies the support set out: idx (host int64, training indices; NULL
  * allowed) and alpha (host double) for up to cap entries; *ns receives |S|.
  * Synchronous. */

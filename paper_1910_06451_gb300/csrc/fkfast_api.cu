@@ -584,6 +584,39 @@ extern "C" int fastron_model_set(fastron_model_t *m, const double *q, const doub
   return FK_OK;
 }
 
+extern "C" int fastron_model_copy(fastron_model_t *dst, const fastron_model_t *cs, void *stream) {
+  fastron_model *src = const_cast<fastron_model *>(cs);
+  if (!dst || !src) return fail(FK_ERR_ARG, "fastron_model_copy: model is NULL");
+  if (dst == src) return fail(FK_ERR_ARG, "fastron_model_copy: dst and src are the same model");
+  if (dst->chain != src->chain) return fail(FK_ERR_ARG, "fastron_model_copy: the models have different chains");
+  if (src->ns < 0) return fail(FK_ERR_STATE, "fastron_model_copy: src is untrained");
+  const fk_chain *c = src->chain;
+  const int64_t ns = src->ns, n1 = ns > 0 ? ns : 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the buffers pack() fills, at the sizes it gives them
+  const size_t bytes[] = {sizeof(float4) * (size_t)rec_pairs(ns) * rec_len(c->cf.Mv), sizeof(int32_t) * (size_t)n1,
+                          sizeof(int32_t) * 2, sizeof(double) * (size_t)n1 * c->M * 3, sizeof(double) * (size_t)n1,
+                          sizeof(double) * (size_t)n1 * c->D, sizeof(float) * (size_t)n1 * rec_df_len(c->cf.Mv),
+                          sizeof(int32_t) * (size_t)n1};
+  DevBuf *from[] = {&src->rec, &src->slot, &src->npos, &src->cp64, &src->alpha_s, &src->q_s, &src->sdf, &src->sup_idx};
+  DevBuf *to[] = {&dst->rec, &dst->slot, &dst->npos, &dst->cp64, &dst->alpha_s, &dst->q_s, &dst->sdf, &dst->sup_idx};
+  const int nbuf = src->host_idx_valid ? 7 : 8;  // the training indices live on the device after fastron_train
+  for (int i = 0; i < nbuf; ++i) {
+    CK(to[i]->ensure(bytes[i]));
+    CK(cudaMemcpyAsync(to[i]->p, from[i]->p, bytes[i], cudaMemcpyDeviceToDevice, s));
+  }
+  dst->ns = ns;
+  dst->gamma = src->gamma;
+  dst->summand = src->summand;
+  dst->host_idx = src->host_idx;
+  dst->host_idx_valid = src->host_idx_valid;
+  // dst holds no training state of its own
+  dst->N = 0;
+  dst->gram = -1;
+  dst->trace_len = 0;
+  return FK_OK;
+}
+
 extern "C" int fastron_model_get(const fastron_model_t *cm, int64_t *idx, double *alpha, int64_t cap, int64_t *ns) {
   fastron_model *m = const_cast<fastron_model *>(cm);
   if (!m || !ns) return fail(FK_ERR_ARG, "fastron_model_get: NULL pointer");

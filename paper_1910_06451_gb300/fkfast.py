@@ -36,7 +36,7 @@ FK_MAX_CP = 32
 EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
-    "fastron_model_set", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_score_band", "fk_check_rcp", "fk_check_sincos", "fk_forward_dd", "fk_label", "fk_set_wait_limit",
+    "fastron_model_set", "fastron_model_copy", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_score_band", "fk_check_rcp", "fk_check_sincos", "fk_forward_dd", "fk_label", "fk_set_wait_limit",
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
     "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune", "fk_active_samples",
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = False):
             "fastron_model_trace": ([P, P, P, P, I64, P], I),
             "fastron_model_set": ([P, P, P, I64, D], I),
             "fastron_model_get": ([P, P, P, I64, P], I),
+            "fastron_model_copy": ([P, P, P], I),
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
             "fk_score_noalloc": ([P, P, I64, D, P, P, P, P], I),
             "fk_score_band": ([P, I, P, P], I),
@@ -317,6 +318,11 @@ def fastron_model_set(model, q, alpha, gamma):
     qa, qp = _host(q, np.float64)
     aa, ap = _host(alpha, np.float64)
     _check(load().fastron_model_set(model, qp, ap, aa.shape[0], float(gamma)))
+
+
+def fastron_model_copy(dst, src, stream=None):
+    """Copies src's packed support set into dst (same chain) on `stream`."""
+    _check(load().fastron_model_copy(dst, src, _stream(stream)))
 
 
 def fastron_model_get(model):
