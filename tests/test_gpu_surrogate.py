@@ -109,6 +109,32 @@ def test_gradients_match_oracle(fk, setup):
         print(f"{k}: max |err| / tolerance {float(np.max(err / np.maximum(tol[k], 1e-300))):.3f}")
 
 
+def test_gradients_twelve_point_arm_match_oracle(fk):
+    # the 12-point arm's features, an odd number of 128-row tiles (three
+    # two-CTA clusters), every gradient entry within its tolerance
+    w = synth.workload("arm7m12-n65536")
+    chain = fk.chain_from_arm(w.scene.arm)
+    s = fk.surrogate_create(chain, seed=3)
+    try:
+        p = _unflat(_flat(_params(8)))
+        fk.surrogate_set_params(s, _flat(p))
+        n = 384
+        q = w.query_configs(n)
+        target = np.random.default_rng(9).normal(size=n).astype(np.float32)
+        g, loss = fk.surrogate_gradients(s, torch.from_numpy(q).cuda(), torch.from_numpy(target).cuda())
+        pb, X = _oracle_with_bf16(p, w, q)
+        out, tol_out, want, tol = elementwise_reference(pb, X, target.astype(np.float64))
+        got = _unflat(g)
+        r = np.abs(out - target)
+        assert abs(loss - L.loss(out, target)) <= np.mean(2 * r * tol_out + tol_out ** 2) + 1e-6 * L.loss(out, target)
+        for k, _ in ORDER:
+            err = np.abs(got[k] - want[k])
+            assert np.all(err <= tol[k]), (k, float(np.max(err / tol[k])))
+    finally:
+        fk.surrogate_destroy(s)
+        fk.fk_chain_destroy(chain)
+
+
 def test_adam_step_matches_oracle(fk, setup):
     w, chain, s = setup
     s2 = fk.surrogate_create(chain, seed=2)
