@@ -253,6 +253,22 @@ __device__ __forceinline__ void tr_put8x(uint8_t *H, uint32_t peer, int row, int
   st_cluster_v4(peer + o, q);
 }
 
+// 32 FP32 values to BF16 (two per conversion) and their mask: bit i set iff
+// the rounded value i is non-zero (the values are >= 0 or exactly +0, so this
+// is bf16(v) > 0, the ReLU mask of the stored activation)
+__device__ __forceinline__ uint32_t tr_bf16x32(const float (&v)[32], bf16 (&o)[32]) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int i = 0; i < 32; i += 2) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[i], v[i + 1]);
+    const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
+    *reinterpret_cast<uint32_t *>(&o[i]) = u;
+    bits |= (uint32_t)((u & 0xffffu) != 0u) << i;
+    bits |= (uint32_t)((u >> 16) != 0u) << (i + 1);
+  }
+  return bits;
+}
+
 // 32 consecutive FP32 biases (16-byte aligned) as eight vector loads
 __device__ __forceinline__ void tr_bias32(const float *__restrict__ b, float (&o)[32]) {
 #pragma unroll
@@ -377,14 +393,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
       if (j < 1) tc_ld32_issue(trow + cc + 32, v);
-      __align__(16) bf16 hb[32];
-      uint32_t bits = 0;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        hb[i] = __float2bfloat16_rn(fmaxf(x[i], 0.f));
-        bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
-      }
-      m[j] = bits;
+      for (int i = 0; i < 32; ++i) x[i] = fmaxf(x[i], 0.f);
+      __align__(16) bf16 hb[32];
+      m[j] = tr_bf16x32(x, hb);
 #pragma unroll
       for (int i = 0; i < 32; i += 8) tr_put8x(H, pH, row, u + i, hb + i);
     }
@@ -403,9 +415,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
       if (j < 1) tc_ld32_issue(trow + cc + 32, v);
-      __align__(16) bf16 db[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) db[i] = __float2bfloat16_rn(((m[j] >> i) & 1u) ? x[i] : 0.f);
+      for (int i = 0; i < 32; ++i) x[i] = ((m[j] >> i) & 1u) ? x[i] : 0.f;
+      __align__(16) bf16 db[32];
+      tr_bf16x32(x, db);
       if (pH) {
 #pragma unroll
         for (int i = 0; i < 32; i += 8) tr_put8x(H, pH, row, u + i, db + i);
@@ -470,16 +483,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] += __uint_as_float(v[i]);
         if (j < 1) tc_ld32_issue(trow + cc + 32, v);
-        __align__(16) bf16 hb[32];
-        uint32_t bits = 0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float h = fmaxf(x[i], 0.f);
-          out = fmaf(h, sw4[cc + 32 * j + i], out);
-          hb[i] = __float2bfloat16_rn(h);
-          bits |= (uint32_t)(__bfloat162float(hb[i]) > 0.f) << i;
+          x[i] = fmaxf(x[i], 0.f);
+          out = fmaf(x[i], sw4[cc + 32 * j + i], out);
         }
-        m3[j] = bits;
+        __align__(16) bf16 hb[32];
+        m3[j] = tr_bf16x32(x, hb);
 #pragma unroll
         for (int i = 0; i < 32; i += 8) tr_put8(HB, row, u + i, hb + i);
       }
@@ -513,10 +523,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) surr_tile_kernel(const SurrStep
 #pragma unroll 1
     for (int j = 0; j < 2; ++j) {
       const int u = u0 + 32 * j;
-      __align__(16) bf16 db[32];
+      float x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i)
-        db[i] = __float2bfloat16_rn(((m3[j] >> i) & 1u) ? dout * sw4[cc + 32 * j + i] : 0.f);
+      for (int i = 0; i < 32; ++i) x[i] = ((m3[j] >> i) & 1u) ? dout * sw4[cc + 32 * j + i] : 0.f;
+      __align__(16) bf16 db[32];
+      tr_bf16x32(x, db);
 #pragma unroll
       for (int i = 0; i < 32; i += 8) tr_put8x(HA, pHA, row, u + i, db + i);
     }
