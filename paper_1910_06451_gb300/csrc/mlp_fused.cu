@@ -28,7 +28,8 @@
 //   warps 0-7  epilogues: read the accumulators back (tcgen05.ld, 32 columns
 //              per wait; warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
 //              + 31 and take the two 32-column halves of each 64-column
-//              chunk), add the bias, apply ReLU and write the BF16 hidden tile
+//              chunk), add the bias (b1, b2 staged in shared memory), apply
+//              ReLU and write the BF16 hidden tile
 //              into shared memory as the next layer's A operand; then the
 //              output unit (bias + ReLU of layer 3, dot with w4 in FP32: each
 //              thread sums its 128 columns in four interleaved partial sums,
@@ -47,6 +48,8 @@
 // thread whose wait gives up sets an abort flag in shared memory; every loop
 // checks it; before the CTA exits, the MMAs and copies it issued are drained
 // (bounded), tensor memory is freed and an error bit is raised.
+#include <cstddef>
+
 #include "surr_features.cuh"
 #include "tc_gemm.cuh"
 
@@ -122,7 +125,10 @@ struct MlpShared {
   uint32_t tmem_slot;
   int abort;
   float half_dot[kBM];  // output unit: the second half of each row's dot
+  __align__(16) float bias12[2][kSurrW];  // b1 and b2, read by the epilogues as float4
 };
+static_assert(offsetof(MlpShared, bias12) % 16 == 0, "float4 reads of the staged biases");
+static_assert(kMlpSmem + sizeof(MlpShared) <= 232448, "above 227 KB of shared memory per CTA");
 
 __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a, const ChainF c) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -151,6 +157,9 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // b1 and b2 staged once per CTA: the epilogue reads them from shared memory
+  // instead of through L1 (measured: 1.667 -> 1.558 ms for 4M queries)
+  for (int i = tid; i < 2 * kSurrW; i += kMlpThreads) sh.bias12[i / kSurrW][i % kSurrW] = (i < kSurrW ? a.b1 : a.b2)[i % kSurrW];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -319,9 +328,9 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
       const int j0 = 64 * c + 32 * half;
       uint32_t hb[16];
 #pragma unroll
-      for (int g8 = 0; g8 < 4; ++g8) {  // the bias is 16-byte aligned (offsets of 4-float multiples)
-        const float4 b0 = __ldg(reinterpret_cast<const float4 *>(bias + j0 + 8 * g8));
-        const float4 b1 = __ldg(reinterpret_cast<const float4 *>(bias + j0 + 8 * g8 + 4));
+      for (int g8 = 0; g8 < 4; ++g8) {  // 16-byte aligned: bias12 and offsets of 4-float multiples
+        const float4 b0 = *reinterpret_cast<const float4 *>(bias + j0 + 8 * g8);
+        const float4 b1 = *reinterpret_cast<const float4 *>(bias + j0 + 8 * g8 + 4);
         const int e = 8 * g8;
         hb[4 * g8 + 0] = relu_bf16x2(add2(v[e + 0], v[e + 1], b0.x, b0.y));
         hb[4 * g8 + 1] = relu_bf16x2(add2(v[e + 2], v[e + 3], b0.z, b0.w));
@@ -358,9 +367,9 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
     for (int64_t it = 0, t = blockIdx.x; t < a.ntiles; ++it, t += gridDim.x) {
       const int R = (int)(it & 1);
       if (!wait_acc(R)) break;
-      hidden_out(R, a.b1);  // layer 1 out, layer 2 in
+      hidden_out(R, sh.bias12[0]);  // layer 1 out, layer 2 in
       if (!wait_acc(1 - R)) break;
-      hidden_out(1 - R, a.b2);  // layer 2 out, layer 3 in
+      hidden_out(1 - R, sh.bias12[1]);  // layer 2 out, layer 3 in
       if (!wait_acc(R)) break;
       // output unit: this thread's 128 columns of layer 3, in four
       // interleaved partial sums (column j into sum j mod 4)
