@@ -16,7 +16,7 @@
 //              two tiles ahead of their use; a buffer is refilled once the
 //              layer-1 MMAs that read it have committed;
 //   warp 8     producer: one thread issues the bulk copies of W1 (once) and
-//              of the eight weight chunks of each tile (a ring of three 32 KB
+//              of the eight weight chunks of each tile (a ring of two 32 KB
 //              stages), each after the MMAs that read the previous occupant
 //              have committed;
 //   warp 9     MMA issuer: one thread issues the MMAs (M = 128, N = 256,
@@ -28,7 +28,7 @@
 //   warps 0-7  epilogues: read the accumulators back (tcgen05.ld, 32 columns
 //              per wait; warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
 //              + 31 and take the two 32-column halves of each 64-column
-//              chunk), add the bias (b1, b2 staged in shared memory), apply
+//              chunk), add the bias (b1, b2, b3, w4 staged in shared memory), apply
 //              ReLU and write the BF16 hidden tile
 //              into shared memory as the next layer's A operand; then the
 //              output unit (bias + ReLU of layer 3, dot with w4 in FP32: each
@@ -62,8 +62,8 @@ constexpr uint32_t kTileA = kBM * kSurrIn * 2;          // 16 KB of features per
 constexpr uint32_t kWBlock = kSurrW * kBK * 2;          // 32 KB: 256 rows x 64 K
 constexpr uint32_t kHChunk = kBM * kBK * 2;             // 16 KB: 128 rows x 64 K
 constexpr uint32_t kOffA = kWBlock, kOffH = kOffA + 2 * kTileA, kOffWS = kOffH + 4 * kHChunk;
-constexpr int kStages = 3;
-constexpr uint32_t kMlpSmem = kOffWS + kStages * kWBlock;  // 224 KB
+constexpr int kStages = 2;  // measured against 3: 1.531 against 1.559 ms for 4M queries
+constexpr uint32_t kMlpSmem = kOffWS + kStages * kWBlock;  // 192 KB
 constexpr uint32_t kMlpIdesc = idesc_bf16_f32(kBM, kSurrW);
 
 // core-matrix offset of element (row, k) in a [rows][64] K-major tile
@@ -126,8 +126,10 @@ struct MlpShared {
   int abort;
   float half_dot[kBM];  // output unit: the second half of each row's dot
   __align__(16) float bias12[2][kSurrW];  // b1 and b2, read by the epilogues as float4
+  __align__(16) float b3w4[2][kSurrW];    // b3 and w4, read by the output unit as float4
 };
-static_assert(offsetof(MlpShared, bias12) % 16 == 0, "float4 reads of the staged biases");
+static_assert(offsetof(MlpShared, bias12) % 16 == 0 && offsetof(MlpShared, b3w4) % 16 == 0,
+              "float4 reads of the staged biases");
 static_assert(kMlpSmem + sizeof(MlpShared) <= 232448, "above 227 KB of shared memory per CTA");
 
 __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a, const ChainF c) {
@@ -157,9 +159,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // b1 and b2 staged once per CTA: the epilogue reads them from shared memory
-  // instead of through L1 (measured: 1.667 -> 1.558 ms for 4M queries)
-  for (int i = tid; i < 2 * kSurrW; i += kMlpThreads) sh.bias12[i / kSurrW][i % kSurrW] = (i < kSurrW ? a.b1 : a.b2)[i % kSurrW];
+  // b1, b2, b3 and w4 staged once per CTA: the epilogues read them from
+  // shared memory instead of through L1 (measured for 4M queries: b1, b2
+  // 1.667 -> 1.558 ms; b3, w4 with the two-stage ring 1.531 -> 1.518 ms)
+  for (int i = tid; i < 2 * kSurrW; i += kMlpThreads) {
+    sh.bias12[i / kSurrW][i % kSurrW] = (i < kSurrW ? a.b1 : a.b2)[i % kSurrW];
+    sh.b3w4[i / kSurrW][i % kSurrW] = (i < kSurrW ? a.b3 : a.w4)[i % kSurrW];
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
   if (warp == 8) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t issued_w[kStages] = {0, 0, 0};
+      uint32_t issued_w[kStages] = {};
       mbar_arrive_expect_tx(&sh.bar_w1, kWBlock);
       tma_bulk_load(W1s, a.wc, kWBlock, &sh.bar_w1);
       const int64_t nt = a.ntiles > (int64_t)blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -377,10 +383,10 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fused_kernel(const MlpArgs a,
       auto dot_part = [&](const uint32_t (&v)[32], int j0) {
 #pragma unroll
         for (int g8 = 0; g8 < 4; ++g8) {  // 8 columns at a time: b3 and w4 are 16-byte aligned like the biases
-          const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.b3 + j0 + 8 * g8));
-          const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.b3 + j0 + 8 * g8 + 4));
-          const float4 w0 = __ldg(reinterpret_cast<const float4 *>(a.w4 + j0 + 8 * g8));
-          const float4 w1 = __ldg(reinterpret_cast<const float4 *>(a.w4 + j0 + 8 * g8 + 4));
+          const float4 b0 = *reinterpret_cast<const float4 *>(sh.b3w4[0] + j0 + 8 * g8);
+          const float4 b1 = *reinterpret_cast<const float4 *>(sh.b3w4[0] + j0 + 8 * g8 + 4);
+          const float4 w0 = *reinterpret_cast<const float4 *>(sh.b3w4[1] + j0 + 8 * g8);
+          const float4 w1 = *reinterpret_cast<const float4 *>(sh.b3w4[1] + j0 + 8 * g8 + 4);
           const float bf[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
           const float wf[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
