@@ -429,6 +429,10 @@ void surrogate_destroy(surrogate_t *s);
 /* Trains on n query configurations q (device float n x D): the targets are
  * the model's FP32 scores of the same queries, computed here; the last
  * `holdout` fraction (rounded to 128 rows) is held out to calibrate tau.
+ * The steps run on tcgen05 tensor cores as CUDA graphs of three launches per
+ * step (a two-CTA-cluster tile kernel: forward, output unit and both delta
+ * products; the weight-gradient products; the reduction and Adam), replayed
+ * with the batch, learning rate and Adam count taken from a device counter.
  * stats: host, may be NULL.  Synchronous. */
 int surrogate_train(surrogate_t *s, fastron_model_t *model, const float *q, int64_t n,
                     const surrogate_train_params *p, surrogate_stats *stats, void *stream);
@@ -465,8 +469,9 @@ int surrogate_adam_step(surrogate_t *s, const float *grad, float lr);
  * cores: A device bf16 M x K (row stride lda elements), B device bf16 N x K
  * (row stride ldb), C device float splits x M x N.  M % 128 == 0, N % 64 ==
  * 0, K % (64 splits) == 0, lda, ldb >= K and multiples of 8, pointers 16-byte
- * aligned.  The building block of the surrogate's layers, exposed for
- * testing.  Synchronous (checks the kernel's timeout flag). */
+ * aligned.  A plain library GEMM on the tensor cores, exposed for testing
+ * (the surrogate's training step and inference run fused kernels of their
+ * own).  Synchronous (checks the kernel's timeout flag). */
 int fk_tc_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int M, int N, int K, int splits,
                     float *C, void *stream);
 

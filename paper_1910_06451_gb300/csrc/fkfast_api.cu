@@ -1050,8 +1050,9 @@ struct surrogate {
   float tau = -1.f;    // calibrated threshold in units of f (< 0: not calibrated)
   int64_t t = 0;       // Adam steps taken
   // training step (surr_train.cu): batch B's transposed activations and
-  // deltas, loss gradients, split-K partials, the device step counter, the
-  // fork streams of the weight-gradient products and the captured step
+  // deltas (chunk-blocked), per-tile sums, split-K partials, the device step
+  // counter with its block counter and schedule, the capture stream and the
+  // captured graphs
   int tB = 0;
   DevBuf tT, tstat, tpart, tstep, loss_hist;
   cudaStream_t cap = nullptr;
