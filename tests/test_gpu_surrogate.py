@@ -310,3 +310,27 @@ def test_fused_inference_wait_limit_reports_timeout(fk, setup):
         fk.fk_set_wait_limit(1 << 22)
     fk.surrogate_forward(s, q, out)
     assert torch.equal(out, ref)
+
+
+def test_training_step_wait_limit_reports_timeout(fk, setup):
+    # the training step's kernels (the two-CTA tile kernel, the weight-gradient
+    # products, the reduction) with every bounded wait giving up at once: the
+    # call returns FK_ERR_TIMEOUT without a hang; with the normal limit the
+    # next call gives the same gradient as before, bit for bit
+    w, chain, s = setup
+    p = _flat(_params(11))
+    fk.surrogate_set_params(s, p)
+    n = 384
+    q = torch.from_numpy(w.query_configs(n)).cuda()
+    target = torch.from_numpy(np.random.default_rng(12).normal(size=n).astype(np.float32)).cuda()
+    g0, l0 = fk.surrogate_gradients(s, q, target)
+    fk.fk_set_wait_limit(0)
+    try:
+        with pytest.raises(fk.FkError) as e:
+            fk.surrogate_gradients(s, q, target)
+        assert e.value.code == fk.FK_ERR_TIMEOUT
+    finally:
+        fk.fk_set_wait_limit(1 << 22)
+    fk.surrogate_set_params(s, p)
+    g1, l1 = fk.surrogate_gradients(s, q, target)
+    assert np.array_equal(g0, g1) and l0 == l1
