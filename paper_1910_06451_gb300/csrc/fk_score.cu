@@ -180,6 +180,23 @@ template <int MV>
 __host__ __device__ constexpr int queries_per_cta() {
   return kScoreThreads * queries_per_thread<MV>();
 }
+// The FP32 score kernel's own shape: from 7 points up one query per thread,
+// with more resident CTAs to hide the MUFU and FMA latencies (4 per SM at 7
+// and 8 points, 3 above); below, two queries per thread at 2 CTAs (4 would
+// spill).  Measured on 4M queries: 7 points 5.77 -> 5.48 ms (two queries per
+// thread at 2 CTAs against one at 4), 11 points 119.3 -> 118.1 ms (3 CTAs).
+template <int MV>
+__host__ __device__ constexpr int f32_queries_per_thread() {
+  return MV > 6 ? 1 : 2;
+}
+template <int MV>
+__host__ __device__ constexpr int f32_ctas_per_sm() {
+  return MV > 8 ? 3 : (MV > 6 ? 4 : 2);
+}
+template <int MV>
+__host__ __device__ constexpr int f32_queries_per_cta() {
+  return kScoreThreads * f32_queries_per_thread<MV>();
+}
 constexpr int kTilePairs = 64;                 // support pairs per shared-memory tile
 
 __device__ __forceinline__ dd pair_of(double x) {
@@ -188,13 +205,14 @@ __device__ __forceinline__ dd pair_of(double x) {
 }
 
 template <int MV>
-__global__ void __launch_bounds__(kScoreThreads, 2) score_f32_kernel(const ChainF c, const ScoreArgs a) {
+__global__ void __launch_bounds__(kScoreThreads, f32_ctas_per_sm<MV>()) score_f32_kernel(const ChainF c,
+                                                                                          const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
   const BlockOut o{a.f, a.label, a.eps0, a.eps1, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit,
                    a.npair_pos};
-  score_block<MV, queries_per_thread<MV>(), kTilePairs, kScoreThreads>(
-      c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * queries_per_cta<MV>(), o, tiles, bar);
+  score_block<MV, f32_queries_per_thread<MV>(), kTilePairs, kScoreThreads>(
+      c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * f32_queries_per_cta<MV>(), o, tiles, bar);
 }
 
 // The non-paper Gaussian summand (FP32 with POLY points per support point on
@@ -293,7 +311,7 @@ static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStre
   auto kern = score_f32_kernel<MV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((a.n + queries_per_cta<MV>() - 1) / queries_per_cta<MV>());
+  const unsigned grid = (unsigned)((a.n + f32_queries_per_cta<MV>() - 1) / f32_queries_per_cta<MV>());
   kern<<<grid, kScoreThreads, smem, s>>>(c, a);
   return cudaGetLastError();
 }
