@@ -917,7 +917,7 @@ def main():
                        "support_max": max(len(sc.support) for sc in scenes), "ms_persistent_graph": t_batch,
                        "ms_per_scene_launches": t_per, "speedup": t_per / t_batch,
                        "checks_per_s": btot / (t_batch * 1e-3), "teval_per_s": evals_b / (t_batch * 1e-3) / 1e12,
-                       "tuned_variant": best, "variant_ms": [float(x) for x in tms[:5]], "labels_identical": same}
+                       "tuned_variant": best, "variant_ms": [float(x) for x in tms[:6]], "labels_identical": same}
         finally:
             fk.fk_batch_destroy(bb)
             for m in bmodels:

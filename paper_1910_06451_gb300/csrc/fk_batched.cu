@@ -55,8 +55,10 @@ struct BatchArgs {
   uint32_t wait_limit;
 };
 
-template <int MV, int Q, int TP, int NTHR>
-__global__ void __launch_bounds__(NTHR) batched_score_kernel(const BatchArgs a) {
+// MINB: resident CTAs the shape is compiled for (its register budget; 1
+// leaves the choice to the compiler)
+template <int MV, int Q, int TP, int NTHR, int MINB>
+__global__ void __launch_bounds__(NTHR, MINB) batched_score_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ __align__(16) ChainF cs;
@@ -240,19 +242,21 @@ __global__ void __launch_bounds__(kBRescoreWarps * 32) batched_rescore_kernel(co
 
 // ------------------------------------------------------------- variants ---
 // Tile shapes the autotuner chooses among: queries per thread, support pairs
-// per shared-memory tile, threads per CTA.
+// per shared-memory tile, threads per CTA, CTAs per SM compiled for (the last
+// shape: one query per thread with the register budget of 3 CTAs per SM).
 struct Variant {
-  int Q, TP, NTHR;
+  int Q, TP, NTHR, MINB;
 };
-constexpr Variant kVariants[] = {{2, 64, 256}, {1, 64, 256}, {2, 32, 256}, {2, 128, 256}, {1, 32, 128}};
+constexpr Variant kVariants[] = {{2, 64, 256, 1}, {1, 64, 256, 1}, {2, 32, 256, 1},
+                                 {2, 128, 256, 1}, {1, 32, 128, 1}, {1, 64, 256, 3}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int batched_num_variants() { return kNumVariants; }
 int batched_block_queries(int v) { return kVariants[v].Q * kVariants[v].NTHR; }
 
-template <int MV, int Q, int TP, int NTHR>
+template <int MV, int Q, int TP, int NTHR, int MINB>
 static cudaError_t launch_bv(const BatchArgs &a, cudaStream_t s, bool prepare_only) {
-  auto kern = batched_score_kernel<MV, Q, TP, NTHR>;
+  auto kern = batched_score_kernel<MV, Q, TP, NTHR, MINB>;
   const size_t smem = 2 * (size_t)TP * rec_len(MV) * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess || prepare_only) return e;
@@ -271,11 +275,12 @@ static cudaError_t launch_bv(const BatchArgs &a, cudaStream_t s, bool prepare_on
 template <int MV>
 static cudaError_t launch_bmv(int v, const BatchArgs &a, cudaStream_t s, bool prep) {
   switch (v) {
-    case 0: return launch_bv<MV, 2, 64, 256>(a, s, prep);
-    case 1: return launch_bv<MV, 1, 64, 256>(a, s, prep);
-    case 2: return launch_bv<MV, 2, 32, 256>(a, s, prep);
-    case 3: return launch_bv<MV, 2, 128, 256>(a, s, prep);
-    case 4: return launch_bv<MV, 1, 32, 128>(a, s, prep);
+    case 0: return launch_bv<MV, 2, 64, 256, 1>(a, s, prep);
+    case 1: return launch_bv<MV, 1, 64, 256, 1>(a, s, prep);
+    case 2: return launch_bv<MV, 2, 32, 256, 1>(a, s, prep);
+    case 3: return launch_bv<MV, 2, 128, 256, 1>(a, s, prep);
+    case 4: return launch_bv<MV, 1, 32, 128, 1>(a, s, prep);
+    case 5: return launch_bv<MV, 1, 64, 256, 3>(a, s, prep);
     default: return cudaErrorInvalidValue;
   }
 }
