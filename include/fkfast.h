@@ -281,6 +281,27 @@ int fk_score(fastron_model_t *model, const float *q, int64_t n, int precision, i
  * eps0, eps1: host out. */
 int fk_score_band(const fastron_model_t *model, int precision, double *eps0, double *eps1);
 
+/* The circle term of the FP32 band (Sec. II-A, Eqs. 1-2 for link 1; the RQ
+ * summand of Eq. 3).  When the first configuration-dependent control point
+ * sits on frame 1 and joint 1 is revolute, the point moves on a circle of
+ * radius rho about that joint's axis, and |p - s| = 2 rho |sin((theta -
+ * theta_s) / 2)|.  fk_score with precision FK_F32 then computes that point's
+ * summand in this form, which takes three FP32 operations in place of six,
+ * and uses eps(q) = eps0 + eps1 max(|p(q)| + |s|max, cnorm) with
+ * cnorm = 6 rho sqrt(gamma/2).  The derivation is in the source beside
+ * score_circle.  *cnorm = 0 means every point is in the direct form.
+ * The circle form is used when the chain qualifies, the summand is RQ,
+ * 0 < rho sqrt(gamma/2) <= 4, and fk_set_circle_form has not switched it
+ * off.  cnorm: host out.  Errors: FK_ERR_ARG for NULL pointers,
+ * FK_ERR_STATE for an untrained model. */
+int fk_score_circle(const fastron_model_t *model, double *cnorm);
+
+/* Switches the circle form of fk_score_circle on (on != 0, the default) or
+ * off for all later FP32 score calls in this process.  With it off, every
+ * point takes the direct form and eps(q) = eps0 + eps1 (|p(q)| + |s|max).
+ * The labels are exact either way.  Always returns FK_OK. */
+int fk_set_circle_form(int on);
+
 /* fk_score with rescore = 1 for callers that must not allocate device memory
  * while they score (a real-time planner loop, a process whose device memory
  * is handed to a fixed pool, code under a budget fixed at start-up).  The

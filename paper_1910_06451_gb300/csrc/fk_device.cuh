@@ -41,6 +41,8 @@ struct ChainF {
   int rot_last;                 // a configuration-dependent point on frame D has an offset
   float reach;                  // sum over links of |a| + |d| + |theta0 or d offset| bound, plus
                                 // |p0| and the largest offset (metres): bounds every lever arm
+  int circ;                     // configuration-dependent point 0 sits on frame 1 of a revolute
+                                // joint 1, so it moves on a circle about that joint's axis
 };
 
 // The same chain for the FP64 kernels.  cos/sin of the link twists are taken
@@ -56,6 +58,9 @@ struct ChainD {
   int cj[FK_MAX_CP];
   double ct[FK_MAX_CP][3];
   int summand;  // FK_SUMMAND_RQ or FK_SUMMAND_GAUSS
+  int circ;           // as ChainF::circ
+  double circ_rho;    // radius of that circle (metres): the distance of point 0
+                      // from joint 1's axis
 };
 
 // ------------------------------------------------------------------ FP32 --

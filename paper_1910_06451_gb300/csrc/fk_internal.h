@@ -74,8 +74,10 @@ cudaError_t launch_margins(const void *G, int g32, int64_t N, const double *alph
 // float4 entries of one support-pair record of the FP32 score: for each of
 // the Mv configuration-dependent control points (x_a, x_b, y_a, y_b), then
 // the z coordinates two points at a time (z_a, z_b, z_a', z_b'), then the
-// weights (w_a, w_b, |w_a|, |w_b|) with w = alpha / M; coordinates are scaled
-// by sqrt(gamma / 2).
+// circle form of point 0 (C_a, C_b, S_a, S_b) = 2 rho g (cos, sin) of half the
+// joint-1 angle (ChainD::circ; zero otherwise), then the weights (w_a, w_b,
+// |w_a|, |w_b|) with w = alpha / M; coordinates are scaled by
+// g = sqrt(gamma / 2).
 // Support pairs summed in plain FP32 by the score kernels before each
 // partial sum is folded into a pair (two-sum) accumulator, and the smallest
 // shared-memory tile (support pairs) of any score kernel; partial sums also
@@ -83,7 +85,7 @@ cudaError_t launch_margins(const void *G, int g32, int64_t N, const double *alph
 constexpr int kFoldPairs = 16;
 constexpr int kMinTilePairs = 32;
 
-__host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 1; }
+__host__ __device__ constexpr int rec_len(int mv) { return mv + (mv + 1) / 2 + 2; }
 // Pair records of a support set of ns points: the points with alpha > 0 come
 // first, then those with alpha < 0, each group padded to an even count with a
 // zero-weight point, so every pair has one sign; one pair more than (ns + 1) / 2
@@ -134,6 +136,8 @@ struct ScoreArgs {
   int poly;           // Gaussian summand, 7 points: points per support point on the FMA polynomial
   const int32_t *npair_pos;  // device: [0] positive-weight pairs, which lead the records;
                              // [1] float bits of the largest scaled support-point norm
+  float cnorm;        // > 0: point 0 in the circle form (FP32 RQ kernel), and the band
+                      // takes max(|p(q)| + |s|max, cnorm) in place of |p(q)| + |s|max
 };
 cudaError_t launch_score_f32(const ChainF &c, const ScoreArgs &a, cudaStream_t s);
 

@@ -131,6 +131,16 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const ChainF cf, con
     put(MV + v / 2, 2 * (v & 1) + h, (float)(gs * cp[m][2]));
   }
   if (MV & 1) put(MV + MV / 2, 2 + h, 0.f);  // unused z slot of the last entry
+  if (cd.circ) {
+    // point 0 on its circle: with C = 2 rho g cos(theta_s / 2), S = 2 rho g
+    // sin(theta_s / 2), the kernel's sin(theta / 2) C - cos(theta / 2) S is
+    // 2 rho g sin((theta - theta_s) / 2), the scaled distance |p - s| up to sign
+    double sh, ch;
+    sincos(0.5 * (cd.th0[0] + x[0]), &sh, &ch);
+    const double r2 = 2.0 * cd.circ_rho * gs;
+    put(REC - 2, h, (float)(r2 * ch));
+    put(REC - 2, 2 + h, (float)(r2 * sh));
+  }
   put(REC - 1, h, (float)wd);
   put(REC - 1, 2 + h, (float)fabs(wd));
   // largest norm of a scaled configuration-dependent control point, rounded
@@ -204,14 +214,15 @@ __device__ __forceinline__ dd pair_of(double x) {
   return {h, __double2float_rn(x - (double)h)};
 }
 
-template <int MV>
+// CIRC: point 0 in the circle form (ScoreArgs::cnorm > 0).
+template <int MV, bool CIRC>
 __global__ void __launch_bounds__(kScoreThreads, f32_ctas_per_sm<MV>()) score_f32_kernel(const ChainF c,
                                                                                           const ScoreArgs a) {
   extern __shared__ __align__(128) float4 tiles[];  // [2][kTilePairs][rec_len(MV)]
   __shared__ __align__(8) uint64_t bar[2];
   const BlockOut o{a.f, a.label, a.eps0, a.eps1, a.band_idx, nullptr, 0, 0, a.band_cnt, a.err, a.wait_limit,
-                   a.npair_pos};
-  score_block<MV, f32_queries_per_thread<MV>(), kTilePairs, kScoreThreads>(
+                   a.npair_pos, a.cnorm};
+  score_block<MV, f32_queries_per_thread<MV>(), kTilePairs, kScoreThreads, false, false, 0, CIRC>(
       c, a.rec, a.ns, pair_of(a.gs), a.q, a.n, (int64_t)blockIdx.x * f32_queries_per_cta<MV>(), o, tiles, bar);
 }
 
@@ -244,7 +255,7 @@ namespace fk {
 
 template <int MV>
 static cudaError_t launch_score_h_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
-  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  constexpr int REC = rec_len(MV);
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(score_f16_kernel<MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -255,7 +266,7 @@ static cudaError_t launch_score_h_mv(const ChainF &c, const ScoreArgs &a, cudaSt
 
 template <int MV, bool HALF, int POLY>
 static cudaError_t launch_gauss_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
-  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  constexpr int REC = rec_len(MV);
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
   auto kern = score_gauss_kernel<MV, HALF, POLY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -306,9 +317,9 @@ cudaError_t launch_score_f16(const ChainF &c, const ScoreArgs &a, cudaStream_t s
 
 template <int MV>
 static cudaError_t launch_score_mv(const ChainF &c, const ScoreArgs &a, cudaStream_t s) {
-  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  constexpr int REC = rec_len(MV);
   const size_t smem = 2 * (size_t)kTilePairs * REC * sizeof(float4);
-  auto kern = score_f32_kernel<MV>;
+  auto kern = a.cnorm > 0.f ? score_f32_kernel<MV, true> : score_f32_kernel<MV, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.n + f32_queries_per_cta<MV>() - 1) / f32_queries_per_cta<MV>());

@@ -181,6 +181,18 @@ extern "C" int fk_chain_create(const fk_dh *dh, int D, const double *base4x4, co
       ++v;
     }
   }
+  // Point 0 on frame 1 of a revolute joint 1: its position is
+  // p0 + R0 Rz(theta) u with the constant u = (a, 0, d) + Rx(alpha) t (Eq. 1
+  // for link 1, then Eq. 2), so it lies on a circle of radius
+  // rho = |(u_x, u_y)| about the joint's axis and |p - s| = 2 rho
+  // |sin((theta - theta_s) / 2)| for two configurations.
+  f.circ = d.circ = 0;
+  d.circ_rho = 0.0;
+  if (mv > 0 && dh[0].type == FK_REVOLUTE && f.vj[0] == 1) {
+    const double *t = cps[f.vidx[0]].t;
+    f.circ = d.circ = 1;
+    d.circ_rho = hypot(dh[0].a + t[0], d.ca[0] * t[1] - d.sa[0] * t[2]);
+  }
   *out = c;
   return FK_OK;
 }
@@ -361,6 +373,37 @@ static void score_band(const ChainF &cf, int summand, double gamma, int64_t ns, 
   *eps0 = (float)((term + acc + 4.0 * efk + pos_abs) * factor);
   *eps1 = (float)(2.0 * ((half ? uh : 0.0) + u) * (1.0 + u) * factor);
 }
+// The circle form of point 0 in the FP32 RQ score (score_core.cuh, CIRC).
+// Its summand t = 1 + D^2, D = fl(sg C + fl(-cg S)): sg, cg the query's sine
+// and cosine of theta / 2 (pair arithmetic, error e_sc ~ 2^-44, rounded once),
+// C, S the support's 2 rho g (cos, sin)(theta_s / 2) from FP64, rounded once.
+// (1) Inputs.  |sin a cos b| + |cos a sin b| <= 1, so the exact products
+//     from the rounded inputs move D by at most (2u + u^2) 2 rho g + 4 rho g
+//     e_sc; as in (1) above, t moves by a factor 1 + x with |x| <= |e| + e^2
+//     and k = t^-2 by 2|e| to first order: 8 u (1 + u) rho g, plus 8 rho g
+//     e_sc, which is far below the 4 e_fk of eps0.
+// (2) Arithmetic.  fl(cg S) and the FMA for D round once each, t's FMA once:
+//     t~ / t* - 1 <= u |cg S| 2|D| / (1 + D^2) + 2u D^2 / (1 + D^2) + u
+//     <= 2 u (1 + u) rho g + 3u, so k is within 4 u (1 + u) rho g + 6u; the
+//     reciprocal and the sums as for the other points.
+// Together 12 u (1 + u) rho g + 6u + 2 rho_rcp: within 10u + 2 rho_rcp (A u)
+// plus eps1 times cnorm = 6 rho g.  So the kernel takes max(|p~| + |s~|max,
+// cnorm) in eps(q), and every summand of every point stays within eps(q).  The
+// form is used for rho g <= 4 (first-order terms below 1e-5, as above).
+static bool g_circle = true;
+
+static float score_circle(const fk_chain *c, int summand, double gamma) {
+  if (!g_circle || !c->cd.circ || summand != FK_SUMMAND_RQ) return 0.f;
+  const double rg = c->cd.circ_rho * sqrt(0.5 * gamma);
+  if (!(rg > 0.0) || rg > 4.0) return 0.f;
+  return nextafterf((float)(6.0 * rg * (1.0 + 0x1p-20)), INFINITY);
+}
+
+extern "C" int fk_set_circle_form(int on) {
+  g_circle = on != 0;
+  return FK_OK;
+}
+
 static int g_gauss_poly = 0;  // control points per support point on the FMA polynomial
 
 extern "C" int fk_set_gauss_poly(int points) {
@@ -726,7 +769,7 @@ extern "C" int fk_score(fastron_model_t *m, const float *q, int64_t n, int preci
   score_band(c->cf, m->summand, m->gamma, m->ns, false, rescore_eps, &eps0, &eps1);
   ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), gs, eps0, eps1, f, label,
                rescore ? m->band_idx.as<int32_t>() : nullptr, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0,
-               m->npos.as<int32_t>()};
+               m->npos.as<int32_t>(), score_circle(c, m->summand, m->gamma)};
   CK(launch_score_f32(cf, sa, s));
   if (!rescore && !n_rescored) return FK_OK;
   int32_t h[2];
@@ -763,6 +806,13 @@ extern "C" int fk_score_band(const fastron_model_t *m, int precision, double *ep
   score_band(m->chain->cf, m->summand, m->gamma, m->ns, precision == FK_F16, 0.0, &e0, &e1);
   *eps0 = e0;
   *eps1 = e1;
+  return FK_OK;
+}
+
+extern "C" int fk_score_circle(const fastron_model_t *m, double *cnorm) {
+  if (!m || !cnorm) return fail(FK_ERR_ARG, "fk_score_circle: NULL pointer");
+  if (m->ns < 0) return fail(FK_ERR_STATE, "fk_score_circle: model is untrained");
+  *cnorm = score_circle(m->chain, m->summand, m->gamma);
   return FK_OK;
 }
 
@@ -980,7 +1030,8 @@ extern "C" int fk_score_noalloc(fastron_model_t *m, const float *q, int64_t n, d
   float eps0 = 0.f, eps1 = 0.f;
   score_band(c->cf, m->summand, m->gamma, m->ns, false, rescore_eps, &eps0, &eps1);
   ScoreArgs sa{q, n, m->rec.as<float4>(), 2 * rec_pairs(m->ns), sqrt(gauss ? 0.5 * m->gamma * M_LOG2E : 0.5 * m->gamma),
-               eps0, eps1, f, label, band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0, m->npos.as<int32_t>()};
+               eps0, eps1, f, label, band, cnt, err, g_wait_limit, gauss ? g_gauss_poly : 0, m->npos.as<int32_t>(),
+               score_circle(c, m->summand, m->gamma)};
   CK(launch_score_f32(cf, sa, s));
   RescoreArgs ra{q, band, cnt, n, m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->gamma, f, label};
   CK(launch_rescore_f64(cd, ra, s));

@@ -130,6 +130,7 @@ struct BlockOut {
   uint32_t wait_limit;
   const int32_t *npair_pos;  // [0] positive-weight pairs, which lead the records;
                              // [1] float bits of |s|max, the largest scaled support-point norm
+  float cnorm;               // CIRC: the band takes max(|p(q)| + |s|max, cnorm)
 };
 
 // Scores queries q0 .. q0 + NTHR*Q - 1 (those below n) of the query array q
@@ -152,18 +153,27 @@ struct BlockOut {
 // every support point and on the FP32 pipe (ex2_neg2_poly) for the last POLY;
 // with HALF, t in packed FP16 and 2^(-t) by ex2.approx.f16x2 (two halves per
 // MUFU operation), widened to FP32 for the sums.  No reciprocal sharing.
+// CIRC = true (RQ in FP32 only): point 0, on the circle of a revolute
+// joint 1 (ChainF::circ), takes t = 1 + D^2 with D = sin(theta/2) C -
+// cos(theta/2) S from the record's circle entry (C, S) = 2 rho g (cos, sin)
+// (theta_s / 2): one product and two FMAs in place of three differences and
+// three FMAs.  D is 2 rho g sin((theta - theta_s) / 2), the scaled distance of
+// the two points up to sign; sin and cos of theta / 2 come from pair
+// arithmetic rounded once.  Its error is covered by the band term
+// eps1 cnorm, cnorm = 6 rho g (section on the band in fkfast_api.cu).
 // Accumulation: each pair adds w * acc into the sum of its sign (positive
 // part P of f first, then the negative part N), kFoldPairs at a time in
 // FP32, each partial folded into a pair accumulator (compensated summation:
 // the accumulation error of f is then at most kFoldPairs + 3 units of
 // roundoff of B(q), whatever the size of the support set); f = P + N and the
 // bound B(q) = P - N = sum_s |w_s| sum_m K(s_m, q_m).
-template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool GAUSS = false, int POLY = 0>
+template <int MV, int Q, int TP, int NTHR, bool HALF = false, bool GAUSS = false, int POLY = 0, bool CIRC = false>
 __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__restrict__ rec, int64_t ns, dd g,
                                             const float *__restrict__ q, int64_t n, int64_t q0, const BlockOut &o,
                                             float4 *tiles, uint64_t *bar) {
   static_assert(POLY >= 0 && POLY <= MV && (POLY == 0 || (GAUSS && !HALF)), "polynomial points: FP32 Gaussian only");
-  constexpr int REC = MV + (MV + 1) / 2 + 1;
+  static_assert(!CIRC || (!HALF && !GAUSS), "circle form: FP32 RQ only");
+  constexpr int REC = rec_len(MV);
   constexpr int NP = RcpPlan<MV>::NP;
 
   const int tid = threadIdx.x;
@@ -221,7 +231,19 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
           P[k][m][r] = pk(v, v);
       }
     }
-    s_eps[k][tid] = fmaf(o.eps1, pn + smax, o.eps0);
+    if (CIRC) {
+      // point 0: sin and cos of half the joint-1 angle (pair arithmetic,
+      // rounded once), the cosine negated for the kernel's product
+      dd th = dd_add(dd{c.th0[0], c.th0_l[0]}, dd_of(qv[0]));
+      th.h *= 0.5f;
+      th.l *= 0.5f;
+      dd sh, ch;
+      dd_sincos(th, sh, ch);
+      const float sg = dd_round(sh), cg = dd_round(ch);
+      P[k][0][0] = pk(sg, sg);
+      P[k][0][1] = pk(-cg, -cg);
+    }
+    s_eps[k][tid] = fmaf(o.eps1, CIRC ? fmaxf(pn + smax, o.cnorm) : pn + smax, o.eps0);
     s_acc[0][k][tid] = s_acc[1][k][tid] = s_acc[2][k][tid] = pk(0.f, 0.f);
   }
   const __half2 one_h = __float2half2_rn(1.f);
@@ -271,6 +293,14 @@ __device__ __forceinline__ bool score_block(const ChainF &c, const float4 *__res
                 const float2 tf = __half22float2(__hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, one_h))));
                 tv[k][m] = pk(tf.x, tf.y);
               }
+            }
+          } else if (CIRC && m == 0) {
+            const float4 cs = r[REC - 2];
+            const f2 C = pk(cs.x, cs.y), S = pk(cs.z, cs.w);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+              const f2 D = fma2(P[k][0][0], C, mul2(P[k][0][1], S));
+              tv[k][0] = fma2(D, D, one2);
             }
           } else {
             const f2 sx = pk(xy.x, xy.y), sy = pk(xy.z, xy.w);

@@ -36,7 +36,7 @@ FK_MAX_CP = 32
 EXPORTS = (
     "fk_last_error", "fk_chain_create", "fk_chain_destroy", "fk_forward", "fk_forward_f64", "fk_gram",
     "fastron_model_create", "fastron_model_destroy", "fastron_train", "fastron_model_trace",
-    "fastron_model_set", "fastron_model_copy", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_score_band", "fk_check_rcp", "fk_check_sincos", "fk_forward_dd", "fk_label", "fk_set_wait_limit",
+    "fastron_model_set", "fastron_model_copy", "fastron_model_get", "fk_score", "fk_score_noalloc", "fk_score_band", "fk_score_circle", "fk_set_circle_form", "fk_check_rcp", "fk_check_sincos", "fk_forward_dd", "fk_label", "fk_set_wait_limit",
     "fk_probe_pipe", "fk_tc_gemm_bf16", "surrogate_create", "surrogate_destroy", "surrogate_train", "surrogate_infer",
     "surrogate_forward", "surrogate_set_params", "surrogate_get_params", "surrogate_gradients", "surrogate_adam_step",
     "fk_batch_create", "fk_batch_destroy", "fk_score_batched", "fk_batch_tune", "fk_active_samples",
@@ -123,6 +123,8 @@ def load(build_if_missing: bool = False):
             "fk_score": ([P, P, I64, I, I, D, P, P, P, P], I),
             "fk_score_noalloc": ([P, P, I64, D, P, P, P, P], I),
             "fk_score_band": ([P, I, P, P], I),
+            "fk_score_circle": ([P, P], I),
+            "fk_set_circle_form": ([I], I),
             "fk_check_rcp": ([I, I, P], I),
             "fk_check_sincos": ([ctypes.c_float, D, P], I),
             "fk_forward_dd": ([P, P, I64, D, P, P], I),
@@ -373,6 +375,19 @@ def fk_score_band(model, precision=None):
     _check(load().fk_score_band(model, FK_F32 if precision is None else int(precision), ctypes.byref(e0),
                                 ctypes.byref(e1)))
     return e0.value, e1.value
+
+
+def fk_score_circle(model) -> float:
+    """cnorm of the FP32 band's circle term (0: every point in the direct form):
+    eps(q) = eps0 + eps1 max(|p(q)| + |s|max, cnorm)."""
+    c = ctypes.c_double()
+    _check(load().fk_score_circle(model, ctypes.byref(c)))
+    return c.value
+
+
+def fk_set_circle_form(on: bool):
+    """Circle form of the first control point in the FP32 score on (default) or off."""
+    _check(load().fk_set_circle_form(1 if on else 0))
 
 
 def fk_check_rcp(e_lo: int, e_hi: int) -> float:

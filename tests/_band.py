@@ -17,8 +17,20 @@ sqrt(gamma/2), u = 2^-24:
 The half-precision kernel takes uh = 2^-11 for the coordinates (eps1 with
 uh + u) and 10 uh for t, an absolute 4 sqrt(3) 2^-25 for FP16 underflow,
 and a factor 1 + 1/16.
+
+Circle form (FP32 kernel): when the first configuration-dependent point sits
+on frame 1 of a revolute joint 1, it moves on a circle of radius rho about
+that joint's axis (Eq. 1 for link 1, then Eq. 2), and the kernel computes its
+summand from sin and cos of half the joint angle.  That summand's error is
+at most 12 u (1 + u) rho g + 6u + 2 rho_rcp, which eps(q) covers when it
+takes max(|p(q)| + |s|max, cnorm) with cnorm = 6 rho g (rounded up):
+
+  cnorm = 6 rho g (1 + 2^-20), if 0 < rho g <= 4, else 0
+  rho   = |(a_1 + t_x, cos(alpha_1) t_y - sin(alpha_1) t_z)|
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -56,15 +68,39 @@ def constants(arm, gamma: float, ns: int, half: bool = False):
     return float(np.float32(eps0)), float(np.float32(eps1))
 
 
+def circle_radius(arm):
+    """rho of the first configuration-dependent point when it moves on the
+    circle of a revolute joint 1 (metres), else None."""
+    cj = np.asarray(arm.cp_joint)
+    dep = np.flatnonzero(cj != 0)
+    dh = np.asarray(arm.dh, dtype=np.float64)
+    if len(dep) == 0 or cj[dep[0]] != 1 or dh[0, 4] != 0:
+        return None
+    t = np.asarray(arm.cp_off, dtype=np.float64)[dep[0]]
+    a, al = float(dh[0, 0]), float(dh[0, 1])
+    return math.hypot(a + t[0], math.cos(al) * t[1] - math.sin(al) * t[2])
+
+
+def circle_norm(arm, gamma: float, on: bool = True) -> float:
+    """cnorm of the FP32 band (0.0: every point in the direct form)."""
+    rho = circle_radius(arm) if on else None
+    if rho is None:
+        return 0.0
+    rg = rho * math.sqrt(0.5 * gamma)
+    if not (0.0 < rg <= 4.0):
+        return 0.0
+    return float(np.nextafter(np.float32(6.0 * rg * (1.0 + 2.0 ** -20)), np.float32(np.inf)))
+
+
 def dependent(arm, cp):
     """The configuration-dependent control points of an (n, M, 3) array."""
     return np.asarray(cp)[:, np.asarray(arm.cp_joint) != 0, :]
 
 
-def per_query(arm, gamma: float, eps0: float, eps1: float, cps, cpq):
+def per_query(arm, gamma: float, eps0: float, eps1: float, cps, cpq, cnorm: float = 0.0):
     """eps(q) for every query from FP64 control points (n, M, 3) of the support
-    set (cps) and of the queries (cpq)."""
+    set (cps) and of the queries (cpq); cnorm: the circle term."""
     g = np.sqrt(0.5 * gamma)
     smax = g * np.max(np.linalg.norm(dependent(arm, cps), axis=2)) if len(cps) else 0.0
     pn = g * np.max(np.linalg.norm(dependent(arm, cpq), axis=2), axis=1)
-    return eps0 + eps1 * (pn + smax)
+    return eps0 + eps1 * np.maximum(pn + smax, cnorm)

@@ -68,13 +68,15 @@ def test_seven_dof_step_at_full_size(fk, dev):
         lab, f_raw, nres = _raw_and_labels(fk, m, torch.from_numpy(Q).to(dev), nq, dev)
         eps0, eps1 = fk.fk_score_band(m)
         assert (eps0, eps1) == _band.constants(arm, w.gamma, r.n_support)
+        cnorm = fk.fk_score_circle(m)
+        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma), rel=1e-6, abs=0.0)
         assert 0 < nres < nq // 100
         # the oracle's own model on every query
         S, alpha = Xd[r.support], r.alpha[r.support]
         cps, cpq = O.fk_points(arm, S), O.fk_points(arm, Q.astype(np.float64))
         want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=NT)
         B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=NT)
-        eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq)
+        eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq, cnorm)
         assert np.array_equal(lab, O.labels_from_f(want))
         err = np.abs(f_raw - want)
         assert np.all(err <= eps * B), np.max(err / (eps * B))
@@ -109,6 +111,8 @@ def test_twelve_point_scoring_at_full_size(fk, dev):
         _, b_raw, _ = _raw_and_labels(fk, mb, tq, nq, dev)
         eps0, eps1 = fk.fk_score_band(m)
         assert (eps0, eps1) == _band.constants(arm, w.gamma, len(S))
+        cnorm = fk.fk_score_circle(m)
+        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma), rel=1e-6, abs=0.0)
     finally:
         fk.fastron_model_destroy(m)
         fk.fastron_model_destroy(mb)
@@ -117,7 +121,7 @@ def test_twelve_point_scoring_at_full_size(fk, dev):
     g = np.sqrt(0.5 * w.gamma)
     smax = g * np.max(np.linalg.norm(_band.dependent(arm, cps), axis=2))
     # eps(q) upper bound for every query without the oracle: |p(q)| <= reach
-    eps_hi = eps0 + eps1 * (g * _band.reach(arm) + smax)
+    eps_hi = eps0 + eps1 * max(g * _band.reach(arm) + smax, cnorm)
     band = np.flatnonzero(np.abs(f_raw) <= 1.01 * eps_hi * b_raw)
     assert nres <= len(band)
     rng = np.random.default_rng(12)
@@ -127,7 +131,7 @@ def test_twelve_point_scoring_at_full_size(fk, dev):
     want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=NT)
     assert np.array_equal(lab[pick], O.labels_from_f(want))
     # the bound, where it decides: the band and the sample's near-zero queries
-    eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq)
+    eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq, cnorm)
     near = np.isin(pick, band) | (np.abs(want) < 10.0 * eps * b_raw[pick] * 1.01)
     Bn = O.score_points(cps, np.abs(alpha), cpq[near], w.gamma, nthreads=NT)
     err = np.abs(f_raw[pick][near] - want[near])

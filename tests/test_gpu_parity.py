@@ -180,7 +180,7 @@ def test_fastron_train_limits_and_warm_start(fk, arm3, dev):
         fk.fastron_model_destroy(m)
 
 
-def _score_case(fk, w, ch, dev, S, alpha, Q):
+def _score_case(fk, w, ch, dev, S, alpha, Q, circle=True):
     arm = w.scene.arm
     m = fk.fastron_model_create(ch)
     try:
@@ -195,15 +195,17 @@ def _score_case(fk, w, ch, dev, S, alpha, Q):
         nres = fk.fk_score(m, tq, lab, f, rescore=True, count=True)
         torch.cuda.synchronize()
         eps0, eps1 = fk.fk_score_band(m)
+        cnorm = fk.fk_score_circle(m)
     finally:
         fk.fastron_model_destroy(m)
     # the library's band constants are the derivation's
     assert (eps0, eps1) == _band.constants(arm, w.gamma, len(S))
+    assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma, on=circle), rel=1e-6, abs=0.0)
     Qd = Q.astype(np.float64)
     cps, cpq = O.fk_points(arm, S), O.fk_points(arm, Qd)
     want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
     B = O.score_points(cps, np.abs(alpha), cpq, w.gamma, nthreads=8)
-    eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq)
+    eps = _band.per_query(arm, w.gamma, eps0, eps1, cps, cpq, cnorm)
     return f_raw.cpu().numpy(), lab_raw.cpu().numpy(), f.cpu().numpy(), lab.cpu().numpy(), nres, want, B, eps
 
 
@@ -233,6 +235,52 @@ def test_score_trained_model(fk, arm3, arm7, dev, which):
     Q = w.query_configs(10000 if which == "arm3" else 20000)
     out = _score_case(fk, w, ch, dev, S, alpha, Q)
     _check_score(*out, alpha)
+
+
+def test_score_circle_form_on_and_off(fk, arm7, dev):
+    # the first control point of the 7-DOF arm sits on frame 1 of a revolute
+    # joint: the FP32 kernel takes its summand in the circle form unless it is
+    # switched off; both forms give the oracle's labels, and their FP32 values
+    # differ by no more than the two bounds
+    w, ch = arm7
+    rng = np.random.default_rng(41)
+    S = w.train_configs()[:801].astype(np.float64)
+    alpha = rng.normal(size=len(S)) * 2
+    Q = w.query_configs(30001)
+    # queries whose joint-1 angle nearly equals a support point's (the circle
+    # form's worst case: t close to 1 by cancellation)
+    Q[:5000, 0] = (S[rng.integers(0, len(S), 5000), 0] + rng.normal(size=5000) * 1e-5).astype(np.float32)
+    fk.fk_set_circle_form(False)
+    try:
+        off = _score_case(fk, w, ch, dev, S, alpha, Q, circle=False)
+    finally:
+        fk.fk_set_circle_form(True)
+    on = _score_case(fk, w, ch, dev, S, alpha, Q)
+    assert _band.circle_norm(w.scene.arm, w.gamma) > 0
+    _check_score(*off, alpha)
+    _check_score(*on, alpha)
+    B = on[6]
+    assert np.all(np.abs(on[0].astype(np.float64) - off[0]) <= (on[7] + off[7]) * B)
+    assert not np.array_equal(on[0], off[0])  # the two forms do differ in rounding
+    assert np.array_equal(on[3], off[3])
+
+
+def test_score_circle_norm_zero_without_a_circle(fk, arm7, dev):
+    # joint 1 prismatic: no circle; the direct form throughout
+    w, _ = arm7
+    arm = w.scene.arm
+    dh = arm.dh.copy()
+    dh[0, 4] = synth.PRISMATIC
+    arm_p = synth.Arm(dh=dh, base=arm.base, cp_joint=arm.cp_joint, cp_off=arm.cp_off, qlim=arm.qlim)
+    assert _band.circle_norm(arm_p, w.gamma) == 0.0
+    ch = fk.chain_from_arm(arm_p)
+    m = fk.fastron_model_create(ch)
+    try:
+        fk.fastron_model_set(m, w.train_configs()[:10].astype(np.float64), np.ones(10), w.gamma)
+        assert fk.fk_score_circle(m) == 0.0
+    finally:
+        fk.fastron_model_destroy(m)
+        fk.fk_chain_destroy(ch)
 
 
 @pytest.mark.parametrize("ns,n", [(0, 100), (1, 1), (1, 513), (127, 700), (128, 512), (129, 1025), (300, 3)])
