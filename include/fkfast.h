@@ -291,8 +291,9 @@ int fk_score_band(const fastron_model_t *model, int precision, double *eps0, dou
  * cnorm = 6 rho sqrt(gamma/2).  The derivation is in the source beside
  * score_circle.  *cnorm = 0 means every point is in the direct form.
  * The circle form is used when the chain qualifies, the summand is RQ,
- * 0 < rho sqrt(gamma/2) <= 4, and fk_set_circle_form has not switched it
- * off.  cnorm: host out.  Errors: FK_ERR_ARG for NULL pointers,
+ * 0 < rho sqrt(gamma/2) <= 4, the support set has at least 128 points (below
+ * that the per-query sine and cosine cost more than the form saves), and
+ * fk_set_circle_form has not switched it off.  cnorm: host out.  Errors: FK_ERR_ARG for NULL pointers,
  * FK_ERR_STATE for an untrained model. */
 int fk_score_circle(const fastron_model_t *model, double *cnorm);
 

@@ -25,7 +25,7 @@ summand from sin and cos of half the joint angle.  That summand's error is
 at most 12 u (1 + u) rho g + 6u + 2 rho_rcp, which eps(q) covers when it
 takes max(|p(q)| + |s|max, cnorm) with cnorm = 6 rho g (rounded up):
 
-  cnorm = 6 rho g (1 + 2^-20), if 0 < rho g <= 4, else 0
+  cnorm = 6 rho g (1 + 2^-20), if 0 < rho g <= 4 and |S| >= 128, else 0
   rho   = |(a_1 + t_x, cos(alpha_1) t_y - sin(alpha_1) t_z)|
 """
 from __future__ import annotations
@@ -81,10 +81,14 @@ def circle_radius(arm):
     return math.hypot(a + t[0], math.cos(al) * t[1] - math.sin(al) * t[2])
 
 
-def circle_norm(arm, gamma: float, on: bool = True) -> float:
-    """cnorm of the FP32 band (0.0: every point in the direct form)."""
+CIRCLE_MIN_SUPPORT = 128
+
+
+def circle_norm(arm, gamma: float, ns: int, on: bool = True) -> float:
+    """cnorm of the FP32 band for a support set of ns points (0.0: every point
+    in the direct form)."""
     rho = circle_radius(arm) if on else None
-    if rho is None:
+    if rho is None or ns < CIRCLE_MIN_SUPPORT:
         return 0.0
     rg = rho * math.sqrt(0.5 * gamma)
     if not (0.0 < rg <= 4.0):

@@ -142,6 +142,8 @@ def test_circle_form_qualifying_chains():
                                          qlim=arm.qlim)) is None
     # rho g above 4: direct form
     rho = _band.circle_radius(arm)
-    assert _band.circle_norm(arm, 2.0 * (4.0 / rho) ** 2 * 1.01) == 0.0
-    assert _band.circle_norm(arm, 40.0) > 6.0 * rho * math.sqrt(20.0)
-    assert _band.circle_norm(arm, 40.0, on=False) == 0.0
+    assert _band.circle_norm(arm, 2.0 * (4.0 / rho) ** 2 * 1.01, 800) == 0.0
+    assert _band.circle_norm(arm, 40.0, 800) > 6.0 * rho * math.sqrt(20.0)
+    assert _band.circle_norm(arm, 40.0, 800, on=False) == 0.0
+    # small support sets: the per-query sine and cosine would cost more than the form saves
+    assert _band.circle_norm(arm, 40.0, 127) == 0.0 and _band.circle_norm(arm, 40.0, 128) > 0.0

@@ -79,8 +79,8 @@ def test_band_constants_match_the_derivation(fk):
                 fk.fastron_model_set(m, S, np.ones(ns), w.gamma)
                 assert fk.fk_score_band(m) == _band.constants(w.scene.arm, w.gamma, ns)
                 assert fk.fk_score_band(m, fk.FK_F16) == _band.constants(w.scene.arm, w.gamma, ns, half=True)
-                cn = _band.circle_norm(w.scene.arm, w.gamma)
-                assert cn > 0 and fk.fk_score_circle(m) == pytest.approx(cn, rel=1e-6, abs=0.0)
+                cn = _band.circle_norm(w.scene.arm, w.gamma, ns)
+                assert (cn > 0) == (ns >= 128) and fk.fk_score_circle(m) == pytest.approx(cn, rel=1e-6, abs=0.0)
         finally:
             fk.fastron_model_destroy(m)
             fk.fk_chain_destroy(ch)

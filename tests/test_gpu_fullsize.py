@@ -69,7 +69,7 @@ def test_seven_dof_step_at_full_size(fk, dev):
         eps0, eps1 = fk.fk_score_band(m)
         assert (eps0, eps1) == _band.constants(arm, w.gamma, r.n_support)
         cnorm = fk.fk_score_circle(m)
-        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma), rel=1e-6, abs=0.0)
+        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma, r.n_support), rel=1e-6, abs=0.0)
         assert 0 < nres < nq // 100
         # the oracle's own model on every query
         S, alpha = Xd[r.support], r.alpha[r.support]
@@ -112,7 +112,7 @@ def test_twelve_point_scoring_at_full_size(fk, dev):
         eps0, eps1 = fk.fk_score_band(m)
         assert (eps0, eps1) == _band.constants(arm, w.gamma, len(S))
         cnorm = fk.fk_score_circle(m)
-        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma), rel=1e-6, abs=0.0)
+        assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma, len(S)), rel=1e-6, abs=0.0)
     finally:
         fk.fastron_model_destroy(m)
         fk.fastron_model_destroy(mb)

@@ -200,7 +200,7 @@ def _score_case(fk, w, ch, dev, S, alpha, Q, circle=True):
         fk.fastron_model_destroy(m)
     # the library's band constants are the derivation's
     assert (eps0, eps1) == _band.constants(arm, w.gamma, len(S))
-    assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma, on=circle), rel=1e-6, abs=0.0)
+    assert cnorm == pytest.approx(_band.circle_norm(arm, w.gamma, len(S), on=circle), rel=1e-6, abs=0.0)
     Qd = Q.astype(np.float64)
     cps, cpq = O.fk_points(arm, S), O.fk_points(arm, Qd)
     want = O.score_points(cps, alpha, cpq, w.gamma, nthreads=8)
@@ -256,7 +256,7 @@ def test_score_circle_form_on_and_off(fk, arm7, dev):
     finally:
         fk.fk_set_circle_form(True)
     on = _score_case(fk, w, ch, dev, S, alpha, Q)
-    assert _band.circle_norm(w.scene.arm, w.gamma) > 0
+    assert _band.circle_norm(w.scene.arm, w.gamma, len(S)) > 0
     _check_score(*off, alpha)
     _check_score(*on, alpha)
     B = on[6]
@@ -272,11 +272,11 @@ def test_score_circle_norm_zero_without_a_circle(fk, arm7, dev):
     dh = arm.dh.copy()
     dh[0, 4] = synth.PRISMATIC
     arm_p = synth.Arm(dh=dh, base=arm.base, cp_joint=arm.cp_joint, cp_off=arm.cp_off, qlim=arm.qlim)
-    assert _band.circle_norm(arm_p, w.gamma) == 0.0
+    assert _band.circle_norm(arm_p, w.gamma, 800) == 0.0
     ch = fk.chain_from_arm(arm_p)
     m = fk.fastron_model_create(ch)
     try:
-        fk.fastron_model_set(m, w.train_configs()[:10].astype(np.float64), np.ones(10), w.gamma)
+        fk.fastron_model_set(m, w.train_configs()[:800].astype(np.float64), np.ones(800), w.gamma)
         assert fk.fk_score_circle(m) == 0.0
     finally:
         fk.fastron_model_destroy(m)
