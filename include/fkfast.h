@@ -391,7 +391,11 @@ int fk_set_gauss_poly(int points);
  * in double-float (one warp per query) and those still within 1e-9 B(q) of
  * zero in FP64, band sizes kept on the device.  The launches are captured
  * once in a CUDA graph and replayed while q, f, label,
- * rescore, q_off and the tuned variant stay the same.  The models must stay
+ * rescore, q_off and the tuned variant stay the same.  When every scene
+ * qualifies for the circle form of fk_score_circle (7 or 11 points), each
+ * scene is scored in it with its own cnorm; otherwise every scene takes the
+ * direct form.  That choice follows fk_set_circle_form when the work list is
+ * built (a change of q_off rebuilds it).  The models must stay
  * alive and unchanged while the batch exists (recreate it after retraining).
  * The paper's evaluation scores one scene at a time; this is the multi-scene
  * form of Sec. III-B's check. */

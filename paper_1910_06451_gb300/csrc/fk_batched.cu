@@ -30,6 +30,7 @@ struct SceneDev {
   const int32_t *npair_pos;  // device: [0] positive-weight pairs, which lead the records; [1] |s|max bits
   double gs;      // coordinate scale sqrt(gamma/2)
   float eps0, eps1;  // the scene's band (see score_band): eps(q) = eps0 + eps1 (|p(q)| + |s|max)
+  float cnorm;       // > 0 in every scene of a batch scored in the circle form (score_circle)
   double gamma;
   int64_t q_off;  // first query of the scene in the concatenated batch
   int64_t n;      // its number of queries
@@ -53,11 +54,13 @@ struct BatchArgs {
   int32_t *band_cnt;
   int32_t *err;
   uint32_t wait_limit;
+  int circ;  // every scene's cnorm > 0: the CIRC kernels
 };
 
 // MINB: resident CTAs the shape is compiled for (its register budget; 1
-// leaves the choice to the compiler)
-template <int MV, int Q, int TP, int NTHR, int MINB>
+// leaves the choice to the compiler).  CIRC: the first control point of
+// every scene in the circle form (each scene with its own cnorm).
+template <int MV, int Q, int TP, int NTHR, int MINB, bool CIRC>
 __global__ void __launch_bounds__(NTHR, MINB) batched_score_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) float4 tiles[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -79,10 +82,10 @@ __global__ void __launch_bounds__(NTHR, MINB) batched_score_kernel(const BatchAr
     __syncthreads();
     const int64_t off = sc->q_off;
     const BlockOut o{a.f ? a.f + off : nullptr, a.label + off, sc->eps0, sc->eps1, a.band_idx, a.band_scene, w.scene,
-                     off, a.band_cnt, a.err, a.wait_limit, sc->npair_pos};
+                     off, a.band_cnt, a.err, a.wait_limit, sc->npair_pos, sc->cnorm};
     const double gsd = sc->gs;
     const float gh = __double2float_rn(gsd);
-    const bool ok = score_block<MV, Q, TP, NTHR>(cs, sc->rec, sc->nrec, dd{gh, __double2float_rn(gsd - (double)gh)},
+    const bool ok = score_block<MV, Q, TP, NTHR, false, false, 0, CIRC>(cs, sc->rec, sc->nrec, dd{gh, __double2float_rn(gsd - (double)gh)},
                                                  a.q + off * sc->cf.D, sc->n, (int64_t)w.block * (NTHR * Q), o, tiles,
                                                  bar);
     if (!ok) break;   // identical in every thread
@@ -256,7 +259,11 @@ int batched_block_queries(int v) { return kVariants[v].Q * kVariants[v].NTHR; }
 
 template <int MV, int Q, int TP, int NTHR, int MINB>
 static cudaError_t launch_bv(const BatchArgs &a, cudaStream_t s, bool prepare_only) {
-  auto kern = batched_score_kernel<MV, Q, TP, NTHR, MINB>;
+  // the circle form is compiled for 7 and 11 points (the 3-point arms'
+  // scenes take the direct form)
+  constexpr bool kCirc = MV == 7 || MV == 11;
+  auto kern = kCirc && a.circ ? batched_score_kernel<MV, Q, TP, NTHR, MINB, kCirc>
+                              : batched_score_kernel<MV, Q, TP, NTHR, MINB, false>;
   const size_t smem = 2 * (size_t)TP * rec_len(MV) * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess || prepare_only) return e;
@@ -325,7 +332,7 @@ size_t work_item_size() { return sizeof(WorkItem); }
 // Host-side filling of a SceneDev record (the layout stays private to this file).
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
                     const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
-                    float eps0, float eps1, int64_t q_off, int64_t n) {
+                    float eps0, float eps1, float cnorm, int64_t q_off, int64_t n) {
   SceneDev d;
   memset(&d, 0, sizeof d);
   d.cf = cf;
@@ -340,6 +347,7 @@ void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *r
   d.gs = sqrt(0.5 * gamma);
   d.eps0 = eps0;
   d.eps1 = eps1;
+  d.cnorm = cnorm;
   d.gamma = gamma;
   d.q_off = q_off;
   d.n = n;
@@ -354,9 +362,9 @@ void fill_work_item(void *dst, int32_t scene, int32_t block) {
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
                                       int32_t *counter, const float *q, float *f, int8_t *label,
                                       int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
-                                      uint32_t wait_limit, cudaStream_t s, bool prepare_only) {
+                                      uint32_t wait_limit, int circ, cudaStream_t s, bool prepare_only) {
   BatchArgs a{static_cast<const SceneDev *>(scenes), static_cast<const WorkItem *>(items), n_items, counter, q, f,
-              label, band_idx, band_scene, band_cnt, err, wait_limit};
+              label, band_idx, band_scene, band_cnt, err, wait_limit, circ};
   return launch_batched_score(mv, variant, a, s, prepare_only);
 }
 

@@ -1564,12 +1564,12 @@ size_t scene_dev_size();
 size_t work_item_size();
 void fill_scene_dev(void *dst, const ChainF &cf, const ChainD &cd, const void *rec, const float *sdf,
                     const double *cp64, const double *alpha, int64_t ns, const int32_t *npair_pos, double gamma,
-                    float eps0, float eps1, int64_t q_off, int64_t n);
+                    float eps0, float eps1, float cnorm, int64_t q_off, int64_t n);
 void fill_work_item(void *dst, int32_t scene, int32_t block);
 cudaError_t launch_batched_score_args(int mv, int variant, const void *scenes, const void *items, int32_t n_items,
                                       int32_t *counter, const float *q, float *f, int8_t *label,
                                       int32_t *band_idx, int32_t *band_scene, int32_t *band_cnt, int32_t *err,
-                                      uint32_t wait_limit, cudaStream_t s, bool prepare_only);
+                                      uint32_t wait_limit, int circ, cudaStream_t s, bool prepare_only);
 cudaError_t launch_batched_rescore_args(const void *scenes, const float *q, const int32_t *band_idx,
                                         const int32_t *band_scene, const int32_t *band_cnt, float *f, int8_t *label,
                                         cudaStream_t s);
@@ -1587,6 +1587,7 @@ struct fk_batch {
   int32_t n_items = 0;
   std::vector<int64_t> off;  // query offsets of the current work list
   int variant = 0;
+  int circ = 0;  // the plan's scenes are scored in the circle form (set by batch_plan)
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   const float *g_q = nullptr;
@@ -1654,14 +1655,20 @@ extern "C" void fk_batch_destroy(fk_batch_t *b) {
 static int batch_plan(fk_batch *b, const int64_t *q_off) {
   const int bq = batched_block_queries(b->variant);
   std::vector<std::pair<int64_t, std::pair<int32_t, int32_t>>> it;
+  // the circle form when every scene qualifies (score_circle), else none
+  b->circ = b->n_scenes > 0 && (b->mv == 7 || b->mv == 11);
+  for (int i = 0; i < b->n_scenes; ++i)
+    b->circ = b->circ && score_circle(b->models[i]->chain, b->models[i]->summand, b->models[i]->gamma,
+                                      b->models[i]->ns) > 0.f;
   for (int i = 0; i < b->n_scenes; ++i) {
     const fastron_model *m = b->models[i];
     const int64_t n = q_off[i + 1] - q_off[i];
     float eps0 = 0.f, eps1 = 0.f;
     score_band(m->chain->cf, m->summand, m->gamma, m->ns, false, 0.0, &eps0, &eps1);
+    const float cnorm = b->circ ? score_circle(m->chain, m->summand, m->gamma, m->ns) : 0.f;
     fill_scene_dev(b->scenes_h.data() + scene_dev_size() * i, m->chain->cf, m->chain->cd, m->rec.p, m->sdf.as<float>(),
                    m->cp64.as<double>(), m->alpha_s.as<double>(), m->ns, m->npos.as<int32_t>(), m->gamma, eps0, eps1,
-                   q_off[i], n);
+                   cnorm, q_off[i], n);
     for (int64_t blk = 0; blk * bq < n; ++blk) {
       const int64_t qn = n - blk * bq < bq ? n - blk * bq : bq;
       it.push_back({(m->ns + 1) * qn, {i, (int32_t)blk}});
@@ -1686,8 +1693,8 @@ static int batch_enqueue(fk_batch *b, const float *q, float *f, int8_t *label, i
   CK(cudaMemsetAsync(fl, 0, sizeof(int32_t) * 4, s));
   CK(launch_batched_score_args(b->mv, b->variant, b->scenes.p, b->items.p, b->n_items, fl, q, f, label,
                                rescore ? b->band_idx.as<int32_t>() : nullptr,
-                               rescore ? b->band_scene.as<int32_t>() : nullptr, fl + 1, fl + 2, g_wait_limit, s,
-                               false));
+                               rescore ? b->band_scene.as<int32_t>() : nullptr, fl + 1, fl + 2, g_wait_limit, b->circ,
+                               s, false));
   if (rescore) {
     // double-float first; what it cannot decide goes to FP64 (count in fl[3])
     CK(launch_batched_rescore_df_args(b->scenes.p, q, b->band_idx.as<int32_t>(), b->band_scene.as<int32_t>(), fl + 1,
@@ -1729,7 +1736,7 @@ extern "C" int fk_score_batched(fk_batch_t *b, const float *q, const int64_t *q_
       b->g_variant != b->variant) {
     batch_drop_graph(b);
     CK(launch_batched_score_args(b->mv, b->variant, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr, nullptr, nullptr, 0, s, true));
+                                 nullptr, nullptr, nullptr, nullptr, 0, b->circ, s, true));
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     int rc = batch_enqueue(b, q, f, label, rescore, b->cap);

@@ -123,3 +123,53 @@ def test_batched_band_reaches_fp64_for_cancelling_scene(fk):
             fk.fastron_model_destroy(m)
         for ch in chains:
             fk.fk_chain_destroy(ch)
+
+
+def test_batched_circle_form(fk):
+    # every scene with at least 128 support points: each takes the circle form
+    # of its first control point with its own cnorm; switched off, the same
+    # batch takes the direct form; both give the oracle's labels
+    scenes = synth.batch_scenes(11, 6, support=(128, 700), queries=(500, 3000))
+    chains, models = [], []
+    try:
+        for sc in scenes:
+            ch = fk.chain_from_arm(sc.scene.arm)
+            m = fk.fastron_model_create(ch)
+            fk.fastron_model_set(m, sc.support.astype(np.float64), sc.alpha, sc.gamma)
+            chains.append(ch)
+            models.append(m)
+            assert fk.fk_score_circle(m) > 0
+        off = np.concatenate([[0], np.cumsum([len(sc.queries) for sc in scenes])]).astype(np.int64)
+        q = torch.from_numpy(np.concatenate([sc.queries for sc in scenes])).cuda()
+        total = int(off[-1])
+        out = {}
+        for on in (True, False):
+            fk.fk_set_circle_form(on)
+            try:
+                b = fk.fk_batch_create(models)
+                try:
+                    lab = torch.empty(total, dtype=torch.int8, device="cuda")
+                    f = torch.empty(total, dtype=torch.float32, device="cuda")
+                    fk.fk_score_batched(b, q, off, lab, f, count=True)
+                    torch.cuda.synchronize()
+                    out[on] = (lab.cpu().numpy(), f.cpu().numpy())
+                finally:
+                    fk.fk_batch_destroy(b)
+            finally:
+                fk.fk_set_circle_form(True)
+        for i, sc in enumerate(scenes):
+            a, z = off[i], off[i + 1]
+            want = O.score(sc.scene.arm, sc.support.astype(np.float64), sc.alpha, sc.queries.astype(np.float64),
+                           sc.gamma, nthreads=8)
+            B = O.score(sc.scene.arm, sc.support.astype(np.float64), np.abs(sc.alpha), sc.queries.astype(np.float64),
+                        sc.gamma, nthreads=8)
+            for on in (True, False):
+                lab, f = out[on]
+                assert np.array_equal(lab[a:z], O.labels_from_f(want)), (i, on)
+                assert np.all(np.abs(f[a:z] - want) <= 3e-6 * B + 1e-30), (i, on)
+        assert not np.array_equal(out[True][1], out[False][1])  # the forms round differently
+    finally:
+        for m in models:
+            fk.fastron_model_destroy(m)
+        for ch in chains:
+            fk.fk_chain_destroy(ch)
