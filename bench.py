@@ -8,6 +8,12 @@ One step is one pass of the whole path over one batch:
   support packing, then FK + FP32 score + FP64 re-score of the band for
   every query of the batch, whose labels are the output.
 value = queries per second of steps (each query is one proxy collision check).
+The K timed steps are pipelined: step s's update runs beside step s-1's
+query pass (two streams, two models), so the SMs that Algorithm 1's single
+cluster leaves idle score queries meanwhile; every step still does all of
+its work, and the last labels are checked against a sequential step's.
+e2e (host buffers, copies inside the timed region) runs its steps one after
+another.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -721,20 +727,70 @@ def main():
     # nvidia-smi numbers GPUs physically: map the local device through
     # CUDA_VISIBLE_DEVICES (an index or a UUID) when it is set
     visible = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    # The timed steps, pipelined: step s's update (labels, kernel matrix,
+    # Algorithm 1 on one 16-CTA cluster, packing) runs on a high-priority
+    # stream while step s-1's query pass (L2 flush, FP32 score, band
+    # re-score) runs on another, each issued from its own host thread.  Two
+    # models alternate, so a query pass reads a finished model while the next
+    # one is trained.  Every step does all of its work; the overlap only puts
+    # the SMs that Algorithm 1 leaves idle to use.  The region is timed with
+    # CUDA events on the issuing stream, both work streams joined into it.
+    ref_lab = lab.clone()  # the sequential step's labels
+    models = [model, fk.fastron_model_create(chain)]
+    labs = [lab, torch.empty_like(lab)]
+    U = torch.cuda.Stream(device=dev, priority=-1)
+    S = torch.cuda.Stream(device=dev, priority=0)
+    errors = []
+
+    def upd(s):
+        try:
+            with torch.cuda.stream(U):
+                fk.fk_label(chain, w.scene.boxes, w.scene.radius, Xq32, ytr, stream=U)
+                fk.fastron_train(models[s % 2], X, ytr, w.gamma, w.beta, w.iter_max, w.s_max, stream=U)
+                U.synchronize()
+        except Exception as e:  # re-raised by the main thread
+            errors.append(e)
+
+    def qry(s):
+        try:
+            with torch.cuda.stream(S):
+                flush.zero_()
+                fk.fk_score(models[s % 2], Q, labs[s % 2], rescore=True, stream=S)
+                S.synchronize()
+        except Exception as e:
+            errors.append(e)
+
     sampler = ClockSampler(visible[local].strip() if local < len(visible) else local)
     sampler.start()
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        step(Q, X, Xq32, lab)
-        b.record()
-        b.synchronize()
-        times.append(a.elapsed_time(b))
     torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    U.wait_event(a)
+    S.wait_event(a)
+    upd(0)
+    for s in range(1, args.steps):
+        ta = threading.Thread(target=upd, args=(s,))
+        tb = threading.Thread(target=qry, args=(s - 1,))
+        ta.start()
+        tb.start()
+        ta.join()
+        tb.join()
+        if errors:
+            raise errors[0]
+    qry(args.steps - 1)
+    if errors:
+        raise errors[0]
+    for st_ in (U, S):
+        done = torch.cuda.Event()
+        done.record(st_)
+        torch.cuda.current_stream().wait_event(done)
+    b.record()
+    b.synchronize()
     clocks = sampler.stop()
-    total_ms = shard.max_over_ranks(sum(times), dev)  # the slowest rank's time
+    pipelined_equal = all(torch.equal(x, ref_lab) for x in labs[: min(2, args.steps)])
+    lab = labs[(args.steps - 1) % 2]
+    fk.fastron_model_destroy(models[1])
+    total_ms = shard.max_over_ranks(a.elapsed_time(b), dev)  # the slowest rank's time
     ms_per_step = total_ms / args.steps
     value = shard.aggregate_rate(nq, ws, ms_per_step)
     # kernels of this library per step: label; FK, pair split, kernel
@@ -956,7 +1012,10 @@ def main():
             "config": {"workload": WORKLOAD, "dof": arm.D, "control_points": arm.M, "boxes": len(w.scene.boxes),
                        "n_train": w.n_train, "n_query": nq, "gamma": w.gamma,
                        "support": st["n_support"], "iterations": st["iterations"],
-                       "l2": "flushed between steps (512 MiB write)", "path": "fp32+df+fp64-rescore",
+                       "l2": "flushed before every query pass (512 MiB write)", "path": "fp32+df+fp64-rescore",
+                       "pipeline": "update of step s (priority stream) overlapped with the query pass of step "
+                                   "s-1; two models alternate",
+                       "pipelined_labels_equal_sequential": pipelined_equal,
                        "headline": "value is the exact FP32 step (labels equal the FP64 oracle's); the "
                                    "half2 and surrogate paths the metric compares are in metric_paths"},
             "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
