@@ -152,6 +152,36 @@ def oracle_cpu_baseline(w, sample_queries: int, threads: int) -> dict:
             "n_support": int(r.n_support)}
 
 
+def run_pipelined(update, query, steps: int) -> None:
+    """Runs update(0); then, for s = 1 .. steps - 1, update(s) beside
+    query(s - 1), one host thread each, both finished before the next pair
+    starts; then query(steps - 1).  So step s's query pass always follows its
+    own update, and update(s + 1) never starts before query(s - 1) has ended
+    (two models can alternate).  An exception raised by either call is
+    re-raised once both threads of its pair have finished."""
+    errors = []
+
+    def guarded(fn, s):
+        try:
+            fn(s)
+        except BaseException as e:  # re-raised by the calling thread
+            errors.append(e)
+
+    if steps <= 0:
+        return
+    update(0)
+    for s in range(1, steps):
+        ta = threading.Thread(target=guarded, args=(update, s))
+        tb = threading.Thread(target=guarded, args=(query, s - 1))
+        ta.start()
+        tb.start()
+        ta.join()
+        tb.join()
+        if errors:
+            raise errors[0]
+    query(steps - 1)
+
+
 def label_checksum(lab) -> dict:
     """Count of +1 labels and a position-weighted sum of them (mod 2^61 - 1):
     two arms with these equal labelled the batch alike."""
@@ -740,25 +770,18 @@ def main():
     labs = [lab, torch.empty_like(lab)]
     U = torch.cuda.Stream(device=dev, priority=-1)
     S = torch.cuda.Stream(device=dev, priority=0)
-    errors = []
 
     def upd(s):
-        try:
-            with torch.cuda.stream(U):
-                fk.fk_label(chain, w.scene.boxes, w.scene.radius, Xq32, ytr, stream=U)
-                fk.fastron_train(models[s % 2], X, ytr, w.gamma, w.beta, w.iter_max, w.s_max, stream=U)
-                U.synchronize()
-        except Exception as e:  # re-raised by the main thread
-            errors.append(e)
+        with torch.cuda.stream(U):
+            fk.fk_label(chain, w.scene.boxes, w.scene.radius, Xq32, ytr, stream=U)
+            fk.fastron_train(models[s % 2], X, ytr, w.gamma, w.beta, w.iter_max, w.s_max, stream=U)
+            U.synchronize()
 
     def qry(s):
-        try:
-            with torch.cuda.stream(S):
-                flush.zero_()
-                fk.fk_score(models[s % 2], Q, labs[s % 2], rescore=True, stream=S)
-                S.synchronize()
-        except Exception as e:
-            errors.append(e)
+        with torch.cuda.stream(S):
+            flush.zero_()
+            fk.fk_score(models[s % 2], Q, labs[s % 2], rescore=True, stream=S)
+            S.synchronize()
 
     sampler = ClockSampler(visible[local].strip() if local < len(visible) else local)
     sampler.start()
@@ -767,19 +790,7 @@ def main():
     a.record()
     U.wait_event(a)
     S.wait_event(a)
-    upd(0)
-    for s in range(1, args.steps):
-        ta = threading.Thread(target=upd, args=(s,))
-        tb = threading.Thread(target=qry, args=(s - 1,))
-        ta.start()
-        tb.start()
-        ta.join()
-        tb.join()
-        if errors:
-            raise errors[0]
-    qry(args.steps - 1)
-    if errors:
-        raise errors[0]
+    run_pipelined(upd, qry, args.steps)
     for st_ in (U, S):
         done = torch.cuda.Event()
         done.record(st_)

@@ -1,11 +1,14 @@
 """Host logic of bench.py, on CPU: the clock record taken during the timed
-steps (median SM clock, maximum, throttle reasons active in any sample) and
-the reference arm's JSON line (the oracle timed on the host cores, the whole
-step on the whole batch), and the label checksum both arms print."""
+steps (median SM clock, maximum, throttle reasons active in any sample), the
+reference arm's JSON line (the oracle timed on the host cores, the whole
+step on the whole batch), the label checksum both arms print, and the order
+in which the pipelined timed steps run."""
 import json
 import os
 import subprocess
 import sys
+import threading
+import time
 
 import pytest
 
@@ -77,3 +80,60 @@ def test_label_checksum_sees_every_label():
     ca, cb = bench.label_checksum(a), bench.label_checksum(b)
     assert ca["positive"] == cb["positive"] and ca["weighted"] != cb["weighted"]
     assert bench.label_checksum(a) == ca
+
+
+def _record_pipeline(steps, fail_update_at=None):
+    log, lock = [], threading.Lock()
+
+    def call(kind, s):
+        with lock:
+            log.append((kind, s, "start", time.perf_counter()))
+        time.sleep(0.02)
+        if kind == "update" and s == fail_update_at:
+            raise RuntimeError(f"update {s} failed")
+        with lock:
+            log.append((kind, s, "end", time.perf_counter()))
+
+    err = None
+    try:
+        bench.run_pipelined(lambda s: call("update", s), lambda s: call("query", s), steps)
+    except RuntimeError as e:
+        err = e
+    return log, err
+
+
+def _t(log, kind, s, edge):
+    return next(t for k, i, e, t in log if (k, i, e) == (kind, s, edge))
+
+
+def test_pipelined_steps_order_and_overlap():
+    steps = 5
+    log, err = _record_pipeline(steps)
+    assert err is None
+    assert sorted((k, i) for k, i, e, _ in log if e == "end") == sorted(
+        [("update", s) for s in range(steps)] + [("query", s) for s in range(steps)])
+    for s in range(steps):
+        # a step's query pass reads its own finished model
+        assert _t(log, "query", s, "start") >= _t(log, "update", s, "end")
+    for s in range(1, steps):
+        # update s runs beside query s - 1 ...
+        assert _t(log, "update", s, "start") < _t(log, "query", s - 1, "end")
+        assert _t(log, "query", s - 1, "start") < _t(log, "update", s, "end")
+    for s in range(2, steps):
+        # ... and never overwrites the model query s - 2 was reading
+        assert _t(log, "update", s, "start") >= _t(log, "query", s - 2, "end")
+
+
+@pytest.mark.parametrize("steps,calls", [(0, []), (1, [("update", 0), ("query", 0)])])
+def test_pipelined_steps_short_runs(steps, calls):
+    log, err = _record_pipeline(steps)
+    assert err is None and [(k, i) for k, i, e, _ in log if e == "start"] == calls
+
+
+def test_pipelined_steps_reraise_after_the_pair():
+    log, err = _record_pipeline(5, fail_update_at=2)
+    assert isinstance(err, RuntimeError) and "update 2" in str(err)
+    # the failing update's partner, query 1, ran to its end; nothing later started
+    assert ("query", 1, "end") in [(k, i, e) for k, i, e, _ in log]
+    assert not [1 for k, i, e, _ in log if e == "start" and i >= 3]
+    assert ("query", 2, "start") not in [(k, i, e) for k, i, e, _ in log]
