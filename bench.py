@@ -12,8 +12,9 @@ The K timed steps are pipelined: step s's update runs beside step s-1's
 query pass (two streams, two models), so the SMs that Algorithm 1's single
 cluster leaves idle score queries meanwhile; every step still does all of
 its work, and the last labels are checked against a sequential step's.
-e2e (host buffers, copies inside the timed region) runs its steps one after
-another.
+e2e (host buffers, copies inside the timed region) runs the same pipeline:
+each update copies the training set in, each query pass copies the batch in
+and its labels out.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -800,7 +801,6 @@ def main():
     clocks = sampler.stop()
     pipelined_equal = all(torch.equal(x, ref_lab) for x in labs[: min(2, args.steps)])
     lab = labs[(args.steps - 1) % 2]
-    fk.fastron_model_destroy(models[1])
     total_ms = shard.max_over_ranks(a.elapsed_time(b), dev)  # the slowest rank's time
     ms_per_step = total_ms / args.steps
     value = shard.aggregate_rate(nq, ws, ms_per_step)
@@ -843,34 +843,47 @@ def main():
     qd = torch.empty_like(Q)
     xd = torch.empty_like(X)
     x32d = torch.empty_like(Xq32)
-    # the query batch's copy does not depend on the model update, so it runs
-    # on a copy stream while labels, kernel matrix and Algorithm 1 run; the
-    # score waits for it
-    copy_stream = torch.cuda.Stream(device=dev)
-    e2e_times = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        copy_stream.wait_event(a)
-        with torch.cuda.stream(copy_stream):
+    # pipelined like the timed steps: update(s) copies the training set in,
+    # labels it and trains; query(s) copies the query batch in, scores it and
+    # copies the labels out (the caller's host buffer), while the next update
+    # runs.  L2 is flushed before every query pass.
+
+    def upd_e(s):
+        with torch.cuda.stream(U):
+            xd.copy_(Xh, non_blocking=True)
+            x32d.copy_(X32h, non_blocking=True)
+            fk.fk_label(chain, w.scene.boxes, w.scene.radius, x32d, ytr, stream=U)
+            fk.fastron_train(models[s % 2], xd, ytr, w.gamma, w.beta, w.iter_max, w.s_max, stream=U)
+            U.synchronize()
+
+    def qry_e(s):
+        with torch.cuda.stream(S):
             qd.copy_(Qh, non_blocking=True)
-            q_ready = torch.cuda.Event()
-            q_ready.record(copy_stream)
-        xd.copy_(Xh, non_blocking=True)
-        x32d.copy_(X32h, non_blocking=True)
-        fk.fk_label(chain, w.scene.boxes, w.scene.radius, x32d, ytr)
-        fk.fastron_train(model, xd, ytr, w.gamma, w.beta, w.iter_max, w.s_max)
-        torch.cuda.current_stream().wait_event(q_ready)
-        fk.fk_score(model, qd, lab, rescore=True)
-        labh.copy_(lab, non_blocking=True)
-        b.record()
-        b.synchronize()
-        if i >= args.warmup:
-            e2e_times.append(a.elapsed_time(b))
-    e2e_ms = shard.max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
-    # the step's labels (exact: the oracle's), for comparison with the reference arm's
-    checksum = label_checksum(lab.cpu().numpy()) if nq == N_QUERY else None
+            flush.zero_()
+            fk.fk_score(models[s % 2], qd, labs[s % 2], rescore=True, stream=S)
+            labh.copy_(labs[s % 2], non_blocking=True)
+            S.synchronize()
+
+    run_pipelined(upd_e, qry_e, args.warmup)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    U.wait_event(a)
+    S.wait_event(a)
+    run_pipelined(upd_e, qry_e, args.steps)
+    for st_ in (U, S):
+        done = torch.cuda.Event()
+        done.record(st_)
+        torch.cuda.current_stream().wait_event(done)
+    b.record()
+    b.synchronize()
+    e2e_ms = shard.max_over_ranks(a.elapsed_time(b) / max(args.steps, 1), dev)
+    e2e_equal = torch.equal(labh, ref_lab.cpu())
+    fk.fastron_model_destroy(models[1])
+    lab = labs[(args.steps - 1) % 2]
+    # the step's labels as the caller receives them (exact: the oracle's),
+    # for comparison with the reference arm's
+    checksum = label_checksum(labh.numpy()) if nq == N_QUERY else None
     h2d = Qh.numel() * 4 + Xh.numel() * 8 + X32h.numel() * 4
     d2h = labh.numel()
 
@@ -1027,6 +1040,7 @@ def main():
                        "pipeline": "update of step s (priority stream) overlapped with the query pass of step "
                                    "s-1; two models alternate",
                        "pipelined_labels_equal_sequential": pipelined_equal,
+                       "e2e_labels_equal_sequential": e2e_equal,
                        "headline": "value is the exact FP32 step (labels equal the FP64 oracle's); the "
                                    "half2 and surrogate paths the metric compares are in metric_paths"},
             "phases_ms": {"update": update_ms, "query": query_ms, "score_fp32": score_only_ms,
